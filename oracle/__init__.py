@@ -1,0 +1,27 @@
+"""Oracle: a plain, slow FP64 CPU restatement of the method of Chen, Cao and Serra-Capizzano,
+"Fast algebraic multigrid for block-structured dense and Toeplitz-like-plus-Cross systems
+arising from nonlocal diffusion problems" (arXiv:2202.11288).
+
+THIS PACKAGE IS TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / reference leg of ``bench.py`` may import or call it. The solver library
+(``paper_2202_11288_gb300``) never imports it and shares no code with it.
+
+Contents
+--------
+``model``  -- the collocation matrices of section 2.2 assembled densely from the printed
+             coefficients (section 2.2.1 nonsymmetric system, section 2.2.2 eq. (system1)),
+             and independently from exact quadrature of the piecewise-quadratic basis
+             (section 2); the manufactured right-hand side for u = x^2 (1 - x)^2.
+``amg``    -- section 3.1: restriction / prolongation, Galerkin coarse operators (dense
+             R A P, eq. (block Galerkin)), damped Jacobi (eq. 7), the block V-cycle of
+             Algorithm 2 with a dense LU at the coarsest level, the outer iteration and the
+             stopping rule of section 5; the Cross splitting of eq. (split01) read off a
+             dense level matrix; the two-grid factor of Theorem 4.1.
+``large``  -- the same finest-level operator for sizes where a dense matrix does not fit:
+             selected dense rows, and the product computed with numpy's FFT as the
+             convolution step (section 3.2, eq. ccs3.4).
+
+Parity status: every function here is pinned by ``tests/test_oracle_*.py`` (printed
+coefficients vs quadrature, Example 3.1, Toeplitz closure, SPD and the two-grid bound of
+Theorem 4.1, LU agreement, order of accuracy). No function is "parity unpinned".
+"""
