@@ -1,0 +1,299 @@
+"""Benchmark: solves/s to relative residual 1e-10 on the 1-D SPD peridynamic system.
+
+Workload (one step = one whole solve, every row of the hot path): N = 2^22 intervals
+(8,388,607 unknowns), horizon delta = 0.05 (r = 209,715), constant kernel, shifted-symmetric
+system, V(1,1) damped Jacobi (omega = 2/3) down to 15 unknowns, seeded uniform[-1,1) right-hand
+sides, tol 1e-10, FP64. Right-hand sides are resident in HBM before the timed region; the
+per-solve working set (spectra, twiddles, level vectors: > 1 GB) is far larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--K 22]
+
+With N > 1 (torchrun, one process per GPU) every rank solves its own independent problems
+(replicas, no collective on the data path); the value is the total over ranks.
+--impl reference times the oracle (dense FP64 CPU code) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from synth import uniform_pm1  # noqa: E402
+
+METRIC = "solves/s to rel-res 1e-10 (1D SPD peridynamic system, FP64 GPU V-cycle)"
+UNIT = "solves/s"
+FP64_FLOP_PER_CLK_PER_SM = 4      # 2 DFMA per clock per SM (FMA-loop probe: 1.19 TFLOP/s at 1995 MHz)
+N_SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--K", type=int, default=22)
+    ap.add_argument("--delta", type=float, default=0.05)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(K, delta):
+    N = 1 << K
+    r = int(np.floor(delta * N)) if delta > 1.0 / N else 1
+    return {"workload": f"1D SPD peridynamic, N=2^{K}, delta={delta}, constant kernel, "
+                        f"uniform[-1,1) RHS, V(1,1) omega=2/3, kc=3, tol 1e-10",
+            "K": K, "N": N, "unknowns": 2 * N - 1, "delta": delta, "r": r, "variant": "spd",
+            "precision": "fp64", "l2": "working set > L2 (spectra + vectors > 1 GB); no flush"}
+
+
+# --------------------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline object)
+# --------------------------------------------------------------------------------------
+
+def oracle_hierarchy(K_sample, delta):
+    from oracle import amg, model
+    N = 1 << K_sample
+    return amg.Hierarchy(model.assemble(model.SPD, N, model.horizon_ratio(delta, 1.0 / N)), kc=3)
+
+
+def oracle_sample(K_sample, delta, tol, reps, budget_s=20.0, H=None):
+    """Time the dense oracle's solve at N = 2^K_sample; returns (solves/s measured, detail)."""
+    from oracle import amg
+    N = 1 << K_sample
+    if H is None:
+        H = oracle_hierarchy(K_sample, delta)
+    times, its = [], []
+    t_start = time.perf_counter()
+    for i in range(reps):
+        b = uniform_pm1(2 * N - 1, i)
+        t0 = time.perf_counter()
+        _, it, rel, _ = amg.solve(H, b, tol=tol)
+        times.append(time.perf_counter() - t0)
+        its.append(it)
+        if time.perf_counter() - t_start > budget_s:
+            break
+    return len(times) / sum(times), {"solves": len(times), "seconds": sum(times), "iters": its}
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def extrapolate(value_sample, K_sample, K):
+    """Dense oracle cost per solve grows as n^2 (dense matrix-vector products, same count)."""
+    ratio = ((2 ** (K + 1) - 1) / (2 ** (K_sample + 1) - 1)) ** 2
+    return value_sample / ratio
+
+
+def cpu_baseline(args, K_sample=11):
+    v, det = oracle_sample(K_sample, args.delta, args.tol, reps=8)
+    return {"value": extrapolate(v, K_sample, args.K), "unit": UNIT, "cores": cpu_cores(),
+            "kind": "oracle",
+            "sample": f"dense FP64 oracle solve at N=2^{K_sample} ({2 ** (K_sample + 1) - 1} "
+                      f"unknowns): {det['solves']} solves in {det['seconds']:.2f} s "
+                      f"({v:.3f} solves/s, iters {det['iters'][0]}); value extrapolated to "
+                      f"N=2^{args.K} by the n^2 cost of its dense products"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    K_sample = 11
+    H = oracle_hierarchy(K_sample, args.delta)
+    per = []
+    for s in range(args.warmup + args.steps):
+        v, det = oracle_sample(K_sample, args.delta, args.tol, reps=1, H=H)
+        if s >= args.warmup:
+            per.append(1.0 / v)
+    sec = float(np.mean(per))
+    value = extrapolate(1.0 / sec, K_sample, args.K)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload(args.K, args.delta),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": f"each step one dense oracle solve at N=2^{K_sample} "
+                                       f"({sec:.3f} s); extrapolated to N=2^{args.K} by n^2"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------------------
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_2202_11288_gb300 as tpc
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    cfg = workload(args.K, args.delta)
+    n = cfg["unknowns"]
+    stream = torch.cuda.Stream()
+    S = tpc.Solver(args.delta, 2.0 ** -args.K, stream=stream)
+    nrhs = 4
+    with torch.cuda.stream(stream):
+        rhs = [torch.tensor(uniform_pm1(n, 1000 * rank + i), device="cuda") for i in range(nrhs)]
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    stream.synchronize()
+    iters = []
+    for s in range(args.warmup):
+        rc, it, rel = S.solve(rhs[s % nrhs], x, tol=args.tol)
+        assert rc == tpc.TPC_OK and rel < args.tol, (rc, rel)
+    clocks = Clocks(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = tpc.tpc_kernel_launches(S.handle)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for s in range(args.steps):
+        rc, it, rel = S.solve(rhs[s % nrhs], x, tol=args.tol)
+        assert rc == tpc.TPC_OK and rel < args.tol, (rc, rel)
+        iters.append(it)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = tpc.tpc_kernel_launches(S.handle) - l0
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * args.steps / (ms_max / 1000.0)
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    b_host = torch.tensor(uniform_pm1(n, 77 + rank), dtype=torch.float64).pin_memory()
+    x_host = torch.zeros(n, dtype=torch.float64).pin_memory()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        rc, it, rel = tpc.tpc_solve_host(S.handle, b_host.numpy(), x_host.numpy(), args.tol)
+        assert rc == tpc.TPC_OK
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * args.steps / float(te.item())
+
+    # dominant kernel: the contiguous-block kernel of the finest level (forward transform
+    # stages, spectral product, inverse transform stages), timed with CUDA events
+    y = torch.empty(n, dtype=torch.float64, device="cuda")
+    ms3 = tpc.tpc_time_level_kernels(S.handle, args.K, 5, x, rhs[0], y)
+    m = 2 ** (args.K + 1)
+    logL = min(12, (args.K + 2) // 2)
+    flops_mid = m * (2 * 5 * logL + 14)       # DIF + DIT radix-2 stages, spectral product
+    achieved = flops_mid / (ms3[1] * 1e-3) / 1e12
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak = N_SMS * FP64_FLOP_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_mid<double,MID_PAIR> (finest level)",
+                "peak_source": "FP64: 152 SMs x 4 flop/clk x max SM clock (unit counts and "
+                               "clocks; FMA-loop probe 1.19 TFLOP/s)",
+                "ms_per_launch": {"fwd_strided": ms3[0], "mid": ms3[1], "inv_strided": ms3[2]}}
+    S.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": cfg,
+                "dof_per_s": value * n, "iters_per_solve": iters,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+                        "d2h_bytes_per_step": 8 * n},
+                "roofline": roofline, "clocks": clk,
+                "gpu_launches": int(launches)}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

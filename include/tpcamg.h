@@ -1,0 +1,154 @@
+/*
+ * tpcamg.h -- C ABI of the GB300 block V-cycle AMG for Toeplitz-like-plus-Cross systems.
+ *
+ * Method: Chen, Cao, Serra-Capizzano, "Fast algebraic multigrid for block-structured dense
+ * and Toeplitz-like-plus-Cross systems arising from nonlocal diffusion problems"
+ * (arXiv:2202.11288).
+ *
+ * The system (section 2.2): the 1-D peridynamic / nonlocal volume-constrained diffusion
+ * problem -L_delta u = f on (0,1), u = g on [-delta,0] U [1,1+delta], constant kernel,
+ * piecewise-quadratic collocation with N = 1/h = 2^K intervals and horizon ratio
+ * r = floor(delta/h) (r = 1 when delta <= h). Its matrix is the 2x2 block matrix
+ * [A B; C D] of eq. (nonsym system) (variant 1) or the shifted-symmetric [A B; B^T A_hat]
+ * of eq. (system1) (variant 0), of order n_K = 2N - 1.
+ *
+ * Vector layout everywhere (section 2.2.1, the grid function U_h): n = 2 N_k + 1 doubles,
+ * first the N_k node values v, then the N_k + 1 midpoint values w. In the Cross splitting
+ * of eq. (split01), w = [w_o; w_bar]: element N_k (0-based) is w_o.
+ *
+ * Levels (section 3.1): level k has N_k = 2^k - 1 and n_k = 2^(k+1) - 1 unknowns; the finest
+ * level is K = log2(1/h); the coarsest level kc (default 3, 15 unknowns) is solved with a
+ * dense factorisation (Algorithm 2: B_1 = A_1^{-1}).
+ *
+ * Threading: a handle is used by one host thread at a time. All device work is ordered on
+ * the stream given to tpc_setup (NULL = the legacy default stream).
+ *
+ * Errors: every int-returning call returns TPC_OK (0) on success, a positive status for a
+ * completed call whose result is not what was asked (TPC_ENOTCONV), or a negative error.
+ * tpc_last_error() returns a message for the last error of a handle (or of a failed
+ * tpc_setup / host call when given NULL).
+ */
+#ifndef TPCAMG_H
+#define TPCAMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  TPC_OK = 0,
+  TPC_ENOTCONV = 1,   /* solve ended at max_iters above tol; x holds the last iterate */
+  TPC_EINVAL = -1,    /* bad argument: h not 2^-K, r < 1, level out of range, NULL ptr */
+  TPC_ENOMEM = -2,    /* host or device allocation failed */
+  TPC_ECUDA = -3,     /* a CUDA call failed; message in tpc_last_error */
+  TPC_ESINGULAR = -4, /* the coarsest matrix has a zero pivot */
+  TPC_ENOTSUP = -5,   /* a parameter combination this build does not implement */
+  TPC_EDIVERGED = -6  /* the residual became non-finite */
+};
+
+enum { TPC_SPD = 0, TPC_NONSYM = 1 };          /* eq. (system1) / eq. (nonsym system) */
+enum { TPC_FP64 = 0, TPC_MIXED = 1 };          /* precision of the inner V-cycle */
+
+typedef struct tpc_params {
+  int variant;        /* TPC_SPD or TPC_NONSYM                                            */
+  int kernel;         /* 0 = constant kernel gamma_delta (section 2.2); others: ENOTSUP    */
+  double kernel_a;    /* reserved for fractional kernels (not implemented)                 */
+  double gamma0;      /* kernel constant; only scales the right-hand side, not the matrix  */
+  double shift;       /* sigma added to the diagonal of the finest matrix (sigma I + A)    */
+  int m1, m2;         /* pre / post smoothing sweeps of Algorithm 2 (default 1, 1)         */
+  double omega_pre;   /* damped Jacobi weights, eq. (7) (default 2/3, 2/3)                 */
+  double omega_post;
+  int coarsest_level; /* kc, 1 <= kc <= K (default 3)                                      */
+  int precision;      /* TPC_FP64, or TPC_MIXED: FP32 V-cycles inside FP64 refinement      */
+  int max_iters;      /* outer iterations of tpc_solve (default 100)                       */
+  int inner_cycles;   /* TPC_MIXED: FP32 V-cycles per FP64 residual (default 4)            */
+} tpc_params;
+
+typedef struct tpc_handle tpc_handle;
+
+/* Fill *p with the defaults: SPD, constant kernel, V(1,1), omega 2/3, kc 3, FP64, 100
+ * iterations. */
+void tpc_default_params(tpc_params* p);
+
+/* Build the level hierarchy for the system with horizon delta and mesh size h.
+ * h must be 2^-K with K >= coarsest_level; levels = number of levels K - kc + 1 to use,
+ * or 0 for all of them (the coarsest level is then kc). The finest generators come from
+ * the printed coefficients of section 2.2; coarse levels from the Galerkin product
+ * A_{k-1} = R A_k P (eq. block Galerkin) evaluated in generator-plus-Cross form
+ * (Lemma 3.1, eq. split 02); the Toeplitz blocks' circulant-embedding spectra (eq. ccs3.4)
+ * are computed on the device. cuda_stream is a cudaStream_t (NULL = default stream).
+ * On success *out owns all device memory of the hierarchy until tpc_destroy; on failure
+ * *out is NULL and tpc_last_error(NULL) describes the error. */
+int tpc_setup(const tpc_params* p, double delta, double h, int levels, void* cuda_stream,
+              tpc_handle** out);
+
+/* Solve A_K x = b to ||b - A x||_2 / ||b - A x0||_2 < tol (section 5 stopping rule) with
+ * repeated V-cycles (Algorithm 2). b_dev, x_dev: device pointers to n_K doubles (caller
+ * owned; they may not alias). use_x0 != 0 starts from the values in x_dev, else from 0.
+ * iters_out / relres_out (host pointers, may be NULL) receive the number of outer
+ * iterations and the final relative residual. Blocks the host until the result is in
+ * x_dev. Returns TPC_OK, TPC_ENOTCONV, TPC_EDIVERGED or a negative error. The solve path
+ * allocates nothing. */
+int tpc_solve(tpc_handle* H, const double* b_dev, double* x_dev, double tol, int use_x0,
+              int* iters_out, double* relres_out);
+
+/* Same as tpc_solve with host buffers b_host / x_host (n_K doubles each): the call copies
+ * b to the device, solves and copies x back before returning. */
+int tpc_solve_host(tpc_handle* H, const double* b_host, double* x_host, double tol,
+                   int use_x0, int* iters_out, double* relres_out);
+
+/* y = A_level x in FP64 through the Toeplitz-plus-Cross product (eq. split01 and the
+ * matrix-vector formula after it). level in [kc, K]; x_dev, y_dev: device pointers to
+ * n_level doubles, not aliasing. Stream ordered, does not block. */
+int tpc_apply(tpc_handle* H, int level, const double* x_dev, double* y_dev);
+
+/* e = B_K r: one FP64 V-cycle of Algorithm 2 with zero initial guess on the finest level.
+ * r_dev, e_dev: device pointers to n_K doubles, not aliasing. Stream ordered. */
+int tpc_vcycle(tpc_handle* H, const double* r_dev, double* e_dev);
+
+/* Number of unknowns n_k of a level (0 if out of range), and the finest / coarsest level. */
+long long tpc_level_size(const tpc_handle* H, int level);
+int tpc_finest_level(const tpc_handle* H);
+int tpc_coarsest_level(const tpc_handle* H);
+
+/* Copy the generator-plus-Cross form of one level to host memory, as doubles:
+ * [N_k, o, tA, tB, tC, tD, p, q, xi, zeta] where each t* has 2 N_k - 1 entries t[d],
+ * d = i - j = -(N_k-1)..N_k-1 (T(i,j) = t_{i-j}), for the blocks A, B_bar, C_bar, D_bar of
+ * eq. (split01), and p, q, xi, zeta have N_k entries. *need receives the count
+ * 2 + 4(2 N_k - 1) + 4 N_k; nothing is written if cap < *need (returns TPC_EINVAL). */
+int tpc_export_level(const tpc_handle* H, int level, double* host_buf, size_t cap,
+                     size_t* need);
+
+/* Host-only (no GPU used): compute the same hierarchy as tpc_setup and write every level
+ * from K down to kc, each in the tpc_export_level layout, one after another into host_buf.
+ * *need receives the total count; nothing is written if cap < *need. */
+int tpc_host_hierarchy(const tpc_params* p, double delta, double h, int levels,
+                       double* host_buf, size_t cap, size_t* need);
+
+/* Timing of the kernels of one level's product y = f - A_level x on the handle's stream:
+ * each kernel of the pipeline is launched reps times (reps >= 1) between two CUDA events,
+ * after one warm-up launch. ms_out[0..2] receive the average milliseconds per launch of the
+ * forward strided pass, the contiguous-block kernel (transform, spectral product, inverse
+ * transform) and the inverse strided pass with its epilogue; levels small enough to use a
+ * single kernel report 0 for the strided passes. x_dev, f_dev, y_dev: n_level doubles on the
+ * device. Blocks the host. */
+int tpc_time_level_kernels(tpc_handle* H, int level, int reps, const double* x_dev,
+                           const double* f_dev, double* y_dev, double* ms_out);
+
+/* Number of kernels this handle has launched so far (graph launches count every kernel node
+ * of the graph). */
+long long tpc_kernel_launches(const tpc_handle* H);
+
+/* Release everything a handle owns. NULL-safe. */
+void tpc_destroy(tpc_handle* H);
+
+/* Message for the last error on H, or for the last failed handle-less call if H is NULL. */
+const char* tpc_last_error(const tpc_handle* H);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TPCAMG_H */

@@ -1,0 +1,264 @@
+"""Python binding of the C ABI in include/tpcamg.h (argument marshalling only).
+
+Every step of the solver runs inside libtpcamg.so (host setup in C++, every solve step in
+CUDA kernels for sm_103a). This module only loads the library, converts arguments and
+passes device pointers (``torch.Tensor.data_ptr()``) and CUDA streams through. There is no
+CPU fallback: if the library is missing, loading fails with an error.
+
+Functions carry the C names (``tpc_setup``, ``tpc_solve``, ...); ``Solver`` is a small
+convenience wrapper around a handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtpcamg.so")
+
+TPC_OK, TPC_ENOTCONV = 0, 1
+TPC_EINVAL, TPC_ENOMEM, TPC_ECUDA, TPC_ESINGULAR, TPC_ENOTSUP, TPC_EDIVERGED = -1, -2, -3, -4, -5, -6
+TPC_SPD, TPC_NONSYM = 0, 1
+TPC_FP64, TPC_MIXED = 0, 1
+
+EXPORTED = ["tpc_default_params", "tpc_setup", "tpc_solve", "tpc_solve_host", "tpc_apply",
+            "tpc_vcycle", "tpc_level_size", "tpc_finest_level", "tpc_coarsest_level",
+            "tpc_export_level", "tpc_host_hierarchy", "tpc_time_level_kernels",
+            "tpc_kernel_launches", "tpc_destroy", "tpc_last_error"]
+
+
+class TpcParams(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("kernel_a", ctypes.c_double), ("gamma0", ctypes.c_double),
+                ("shift", ctypes.c_double), ("m1", ctypes.c_int), ("m2", ctypes.c_int),
+                ("omega_pre", ctypes.c_double), ("omega_post", ctypes.c_double),
+                ("coarsest_level", ctypes.c_int), ("precision", ctypes.c_int),
+                ("max_iters", ctypes.c_int), ("inner_cycles", ctypes.c_int)]
+
+
+class TpcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"tpcamg error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load the in-tree library (built by ``__graft_entry__.build()``); raise if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2202_11288_gb300._build")
+    L = ctypes.CDLL(LIB_PATH)
+    P, D, I, LL, SZ = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_longlong, ctypes.c_size_t
+    pp = ctypes.POINTER(TpcParams)
+    L.tpc_default_params.argtypes = [pp]
+    L.tpc_default_params.restype = None
+    L.tpc_setup.argtypes = [pp, D, D, I, P, ctypes.POINTER(P)]
+    L.tpc_setup.restype = I
+    L.tpc_solve.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]
+    L.tpc_solve.restype = I
+    L.tpc_solve_host.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]
+    L.tpc_solve_host.restype = I
+    L.tpc_apply.argtypes = [P, I, P, P]
+    L.tpc_apply.restype = I
+    L.tpc_vcycle.argtypes = [P, P, P]
+    L.tpc_vcycle.restype = I
+    L.tpc_level_size.argtypes = [P, I]
+    L.tpc_level_size.restype = LL
+    L.tpc_finest_level.argtypes = [P]
+    L.tpc_finest_level.restype = I
+    L.tpc_coarsest_level.argtypes = [P]
+    L.tpc_coarsest_level.restype = I
+    L.tpc_export_level.argtypes = [P, I, P, SZ, ctypes.POINTER(SZ)]
+    L.tpc_export_level.restype = I
+    L.tpc_host_hierarchy.argtypes = [pp, D, D, I, P, SZ, ctypes.POINTER(SZ)]
+    L.tpc_host_hierarchy.restype = I
+    L.tpc_time_level_kernels.argtypes = [P, I, I, P, P, P, ctypes.POINTER(D)]
+    L.tpc_time_level_kernels.restype = I
+    L.tpc_kernel_launches.argtypes = [P]
+    L.tpc_kernel_launches.restype = LL
+    L.tpc_destroy.argtypes = [P]
+    L.tpc_destroy.restype = None
+    L.tpc_last_error.argtypes = [P]
+    L.tpc_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def tpc_default_params(**overrides) -> TpcParams:
+    p = TpcParams()
+    lib().tpc_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def tpc_last_error(handle=None) -> str:
+    msg = lib().tpc_last_error(handle)
+    return msg.decode() if msg else ""
+
+
+def _check(rc: int, handle=None, allow=(TPC_OK,)) -> int:
+    if rc not in allow:
+        raise TpcError(rc, tpc_last_error(handle))
+    return rc
+
+
+def _split_levels(buf: np.ndarray) -> list:
+    levels, o = [], 0
+    while o < buf.size:
+        N = int(buf[o])
+        G = 2 * N - 1
+        d = {"N": N, "o": float(buf[o + 1])}
+        o += 2
+        for key in ("A", "B", "C", "D"):
+            d[key] = buf[o:o + G].copy()
+            o += G
+        for key in ("p", "q", "xi", "zeta"):
+            d[key] = buf[o:o + N].copy()
+            o += N
+        levels.append(d)
+    return levels
+
+
+def tpc_host_hierarchy(delta: float, h: float, levels: int = 0, params: TpcParams | None = None):
+    """Host-only hierarchy (no GPU): list of levels, finest first, in the export layout."""
+    p = params if params is not None else tpc_default_params()
+    need = ctypes.c_size_t(0)
+    _check(lib().tpc_host_hierarchy(ctypes.byref(p), delta, h, levels, None, 0, ctypes.byref(need)))
+    buf = np.empty(need.value, dtype=np.float64)
+    _check(lib().tpc_host_hierarchy(ctypes.byref(p), delta, h, levels,
+                                    buf.ctypes.data_as(ctypes.c_void_p), need.value,
+                                    ctypes.byref(need)))
+    return _split_levels(buf)
+
+
+def _ptr(t) -> int:
+    return t.data_ptr() if hasattr(t, "data_ptr") else int(t)
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def tpc_setup(delta: float, h: float, levels: int = 0, params: TpcParams | None = None,
+              stream=None) -> ctypes.c_void_p:
+    p = params if params is not None else tpc_default_params()
+    H = ctypes.c_void_p()
+    _check(lib().tpc_setup(ctypes.byref(p), delta, h, levels, _stream_handle(stream),
+                           ctypes.byref(H)))
+    return H
+
+
+def tpc_solve(H, b, x, tol: float = 1e-10, use_x0: bool = False):
+    it, rel = ctypes.c_int(0), ctypes.c_double(0.0)
+    rc = _check(lib().tpc_solve(H, _ptr(b), _ptr(x), tol, int(use_x0), ctypes.byref(it),
+                                ctypes.byref(rel)), H, allow=(TPC_OK, TPC_ENOTCONV))
+    return rc, it.value, rel.value
+
+
+def tpc_solve_host(H, b: np.ndarray, x: np.ndarray, tol: float = 1e-10, use_x0: bool = False):
+    assert b.dtype == np.float64 and x.dtype == np.float64
+    assert b.flags.c_contiguous and x.flags.c_contiguous
+    it, rel = ctypes.c_int(0), ctypes.c_double(0.0)
+    rc = _check(lib().tpc_solve_host(H, b.ctypes.data_as(ctypes.c_void_p),
+                                     x.ctypes.data_as(ctypes.c_void_p), tol, int(use_x0),
+                                     ctypes.byref(it), ctypes.byref(rel)), H,
+                allow=(TPC_OK, TPC_ENOTCONV))
+    return rc, it.value, rel.value
+
+
+def tpc_apply(H, level: int, x, y) -> None:
+    _check(lib().tpc_apply(H, level, _ptr(x), _ptr(y)), H)
+
+
+def tpc_vcycle(H, r, e) -> None:
+    _check(lib().tpc_vcycle(H, _ptr(r), _ptr(e)), H)
+
+
+def tpc_level_size(H, level: int) -> int:
+    return int(lib().tpc_level_size(H, level))
+
+
+def tpc_finest_level(H) -> int:
+    return int(lib().tpc_finest_level(H))
+
+
+def tpc_coarsest_level(H) -> int:
+    return int(lib().tpc_coarsest_level(H))
+
+
+def tpc_export_level(H, level: int) -> dict:
+    need = ctypes.c_size_t(0)
+    _check(lib().tpc_export_level(H, level, None, 0, ctypes.byref(need)), H)
+    buf = np.empty(need.value, dtype=np.float64)
+    _check(lib().tpc_export_level(H, level, buf.ctypes.data_as(ctypes.c_void_p), need.value,
+                                  ctypes.byref(need)), H)
+    return _split_levels(buf)[0]
+
+
+def tpc_time_level_kernels(H, level: int, reps: int, x, f, y):
+    """Average ms per launch of [forward strided, contiguous-block, inverse strided] kernels."""
+    out = (ctypes.c_double * 3)()
+    _check(lib().tpc_time_level_kernels(H, level, reps, _ptr(x), _ptr(f), _ptr(y), out), H)
+    return [out[0], out[1], out[2]]
+
+
+def tpc_kernel_launches(H) -> int:
+    return int(lib().tpc_kernel_launches(H))
+
+
+def tpc_destroy(H) -> None:
+    if H:
+        lib().tpc_destroy(H)
+
+
+class Solver:
+    """Owns one handle: ``Solver(delta, h, variant=TPC_SPD, ...)`` then ``solve(b, x)``."""
+
+    def __init__(self, delta: float, h: float, levels: int = 0, stream=None, **params):
+        self.params = tpc_default_params(**params)
+        self.handle = tpc_setup(delta, h, levels, self.params, stream)
+        self.K = tpc_finest_level(self.handle)
+        self.kc = tpc_coarsest_level(self.handle)
+        self.n = tpc_level_size(self.handle, self.K)
+
+    def solve(self, b, x, tol: float = 1e-10, use_x0: bool = False):
+        return tpc_solve(self.handle, b, x, tol, use_x0)
+
+    def solve_host(self, b: np.ndarray, x: np.ndarray, tol: float = 1e-10, use_x0: bool = False):
+        return tpc_solve_host(self.handle, b, x, tol, use_x0)
+
+    def apply(self, level: int, x, y) -> None:
+        tpc_apply(self.handle, level, x, y)
+
+    def vcycle(self, r, e) -> None:
+        tpc_vcycle(self.handle, r, e)
+
+    def level_size(self, level: int) -> int:
+        return tpc_level_size(self.handle, level)
+
+    def export_level(self, level: int) -> dict:
+        return tpc_export_level(self.handle, level)
+
+    def close(self) -> None:
+        if self.handle:
+            tpc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,682 @@
+// C ABI (include/tpcamg.h): device hierarchy, launch plans, V-cycle and solve loop.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tpc_internal.h"
+#include "tpc_kernels.cuh"
+
+namespace tpc {
+void set_host_error(const std::string& s);
+const char* host_error();
+
+constexpr int LOG_WHOLE = 9;      // m <= 2^9: one CTA per product
+constexpr int LOG_R1_MAX = 11;    // strided pass: at most 2048 rows
+constexpr int LOG_TILE_MAX = 13;  // strided tile: at most 8192 complex entries (128 KB FP64)
+constexpr int NORM_BLOCKS = 304;  // 2 x 152 SMs
+
+template <typename T> struct DevLevel {
+  int k = 0;
+  long long N = 0, n = 0, m = 0;
+  int logm = 0, logR1 = 0, logL = 0, logC = 0;
+  int fwd_blocks = 0, mid_blocks = 0;
+  size_t smem_strided = 0, smem_mid = 0;
+  T* sA = nullptr;
+  T* sD = nullptr;
+  c2<T>* sB = nullptr;
+  c2<T>* sC = nullptr;
+  T* p = nullptr;
+  T* q = nullptr;
+  T* xi = nullptr;
+  T* zeta = nullptr;
+  T o = 0, wA_pre = 0, wO_pre = 0, wD_pre = 0, wA_post = 0, wO_post = 0, wD_post = 0;
+  c2<T>* twm = nullptr;
+};
+
+}  // namespace tpc
+
+using namespace tpc;
+
+struct tpc_handle {
+  tpc_params prm{};
+  int K = 0, kc = 0, r = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;            // created here when the caller passed NULL
+  HostHierarchy host;
+  std::vector<DevLevel<double>> lev;  // lev[i] = level K - i
+  std::vector<double*> f, e, t;       // per level vectors (n_k)
+  double* u = nullptr;                // finest solution
+  double* b = nullptr;                // finest right-hand side (copy)
+  double* r0 = nullptr;               // finest residual
+  c2<double>* z = nullptr;            // complex work array (m_K)
+  double* partials = nullptr;
+  double* sumsq_part = nullptr;
+  double* sumsq = nullptr;            // device scalar
+  double* sumsq_host = nullptr;       // pinned
+  c2<double>* twL = nullptr;
+  double* coarse_inv = nullptr;
+  double* hb = nullptr;               // device staging for tpc_solve_host (b, x)
+  double* hx = nullptr;
+  cudaGraphExec_t iter_exec = nullptr;
+  long long iter_nodes = 0;           // kernel nodes of iter_exec
+  long long launches = 0;             // kernels launched so far (see tpc_kernel_launches)
+  std::string err;
+  std::vector<void*> dev_allocs;
+};
+
+namespace {
+
+thread_local std::string g_setup_err;
+
+int cuda_fail(tpc_handle* H, cudaError_t e, const char* what) {
+  std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+  if (H) H->err = msg;
+  set_host_error(msg);
+  return TPC_ECUDA;
+}
+
+#define TPC_CUDA(H, call)                                   \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(H, e_, #call);  \
+  } while (0)
+
+template <typename P>
+int dalloc(tpc_handle* H, P** ptr, size_t count) {
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, count * sizeof(P) + 16);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    H->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    set_host_error(H->err);
+    return (e == cudaErrorMemoryAllocation) ? TPC_ENOMEM : TPC_ECUDA;
+  }
+  H->dev_allocs.push_back(v);
+  *ptr = reinterpret_cast<P*>(v);
+  return TPC_OK;
+}
+
+#define TPC_TRY(x)                   \
+  do {                               \
+    int rc_ = (x);                   \
+    if (rc_ != TPC_OK) return rc_;   \
+  } while (0)
+
+int grid_for(long long n) {
+  long long g = (n + NTHREADS - 1) / NTHREADS;
+  if (g > 4 * 152) g = 4 * 152;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+template <typename T>
+void plan_level(DevLevel<T>& L) {
+  L.logm = L.k + 1;
+  if (L.logm <= LOG_WHOLE) {
+    L.logR1 = 0;
+    L.logL = L.logm;
+    L.logC = 0;
+    L.fwd_blocks = 0;
+    L.mid_blocks = 1;
+  } else {
+    int logL = (L.logm + 1) / 2;
+    if (logL > LOG_LMAX) logL = LOG_LMAX;
+    L.logL = logL;
+    L.logR1 = L.logm - logL;
+    int logC = 4;
+    if (logC > LOG_TILE_MAX - L.logR1) logC = LOG_TILE_MAX - L.logR1;
+    int want = logL - 9;  // keep >= 512 column blocks when the level is large enough
+    if (want < 0) want = 0;
+    if (logC > want) logC = want;
+    if (logC < 0) logC = 0;
+    L.logC = logC;
+    L.fwd_blocks = 1 << (logL - logC);
+    L.mid_blocks = (1 << (L.logm - logL - 1)) + 1;
+  }
+  L.smem_strided = L.logR1 ? ((size_t)sizeof(c2<T>) << (L.logR1 + L.logC)) : 0;
+  L.smem_mid = (size_t)sizeof(c2<T>) << (L.logL + (L.logR1 ? 1 : 0));
+}
+
+template <typename T>
+LevelArgs<T> level_args(const tpc_handle* H, const DevLevel<T>& L, const c2<T>* twL, c2<T>* z,
+                        T* partials) {
+  LevelArgs<T> a{};
+  a.N = L.N;
+  a.logm = L.logm;
+  a.logR1 = L.logR1;
+  a.logL = L.logL;
+  a.logC = L.logC;
+  a.sA = L.sA;
+  a.sD = L.sD;
+  a.sB = L.sB;
+  a.sC = L.sC;
+  a.p = L.p;
+  a.q = L.q;
+  a.xi = L.xi;
+  a.zeta = L.zeta;
+  a.o = L.o;
+  a.twm = L.twm;
+  a.twL = twL;
+  a.z = z;
+  a.partials = partials;
+  a.nparts = L.fwd_blocks;
+  (void)H;
+  return a;
+}
+
+// y = epilogue(A_k x) for one level on the handle's stream.
+template <bool NS>
+void launch_matvec(tpc_handle* H, const DevLevel<double>& L, const double* x, const double* f,
+                   double* y, int epi, bool post) {
+  LevelArgs<double> a = level_args<double>(H, L, H->twL, H->z, H->partials);
+  a.x = x;
+  a.f = f;
+  a.y = y;
+  a.epi = epi;
+  a.wA = post ? L.wA_post : L.wA_pre;
+  a.wO = post ? L.wO_post : L.wO_pre;
+  a.wD = post ? L.wD_post : L.wD_pre;
+  cudaStream_t s = H->stream;
+  if (L.logR1 == 0) {
+    k_mid<double, MID_WHOLE, NS><<<1, NTHREADS, L.smem_mid, s>>>(a);
+    H->launches += 1;
+    return;
+  }
+  H->launches += 3;
+  k_fwd_strided<double, IN_PACK><<<L.fwd_blocks, NTHREADS, L.smem_strided, s>>>(a);
+  k_mid<double, MID_PAIR, NS><<<L.mid_blocks, NTHREADS, L.smem_mid, s>>>(a);
+  k_inv_strided<double><<<L.fwd_blocks, NTHREADS, L.smem_strided, s>>>(a);
+}
+
+void matvec(tpc_handle* H, int li, const double* x, const double* f, double* y, int epi,
+            bool post) {
+  if (H->prm.variant == TPC_NONSYM)
+    launch_matvec<true>(H, H->lev[li], x, f, y, epi, post);
+  else
+    launch_matvec<false>(H, H->lev[li], x, f, y, epi, post);
+}
+
+// Algorithm 2 on level index li (level K - li) with right-hand side f (not modified).
+// Returns the buffer that holds B_k f: e[li] or t[li].
+double* enqueue_vcycle(tpc_handle* H, int li, const double* f) {
+  const DevLevel<double>& L = H->lev[li];
+  cudaStream_t s = H->stream;
+  double* e = H->e[li];
+  double* t = H->t[li];
+  if (L.k == H->kc) {
+    k_coarse_solve<double><<<1, 256, 0, s>>>(H->coarse_inv, f, e, (int)L.n);
+    H->launches += 1;
+    return e;
+  }
+  H->launches += 3;  // smooth_init, restrict, prolong_add
+  const int g = grid_for(L.n);
+  k_smooth_init<double><<<g, NTHREADS, 0, s>>>(f, e, L.N, L.wA_pre, L.wO_pre, L.wD_pre);
+  for (int l = 1; l < H->prm.m1; ++l) {
+    matvec(H, li, e, f, t, EPI_JACOBI, false);
+    std::swap(e, t);
+  }
+  matvec(H, li, e, f, t, EPI_RESID, false);
+  const DevLevel<double>& Lc = H->lev[li + 1];
+  k_restrict<double><<<grid_for(Lc.n), NTHREADS, 0, s>>>(t, H->f[li + 1], Lc.n);
+  const double* ec = enqueue_vcycle(H, li + 1, H->f[li + 1]);
+  k_prolong_add<double><<<g, NTHREADS, 0, s>>>(e, ec, L.n);
+  for (int l = 0; l < H->prm.m2; ++l) {
+    matvec(H, li, e, f, t, EPI_JACOBI, true);
+    std::swap(e, t);
+  }
+  return e;
+}
+
+void enqueue_sumsq(tpc_handle* H, const double* r, long long n) {
+  H->launches += 2;
+  k_sumsq_partial<double><<<NORM_BLOCKS, NTHREADS, 0, H->stream>>>(r, n, H->sumsq_part);
+  k_sumsq_final<<<1, 32, 0, H->stream>>>(H->sumsq_part, NORM_BLOCKS, H->sumsq);
+}
+
+// One outer iteration: u += B_K r; r = b - A u; ||r||^2.
+void enqueue_iteration(tpc_handle* H) {
+  const DevLevel<double>& L = H->lev[0];
+  double* e = enqueue_vcycle(H, 0, H->r0);
+  H->launches += 1;
+  k_axpy<double><<<grid_for(L.n), NTHREADS, 0, H->stream>>>(H->u, e, L.n);
+  matvec(H, 0, H->u, H->b, H->r0, EPI_RESID, false);
+  enqueue_sumsq(H, H->r0, L.n);
+}
+
+template <typename T, bool NS>
+int set_smem_attrs() {
+  const int big = 1 << 17;  // 128 KB (largest tile)
+  cudaError_t e;
+  e = cudaFuncSetAttribute(k_fwd_strided<T, IN_PACK>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e != cudaSuccess) return (int)e;
+  e = cudaFuncSetAttribute(k_fwd_strided<T, IN_REAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e != cudaSuccess) return (int)e;
+  e = cudaFuncSetAttribute(k_mid<T, MID_PAIR, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e != cudaSuccess) return (int)e;
+  e = cudaFuncSetAttribute(k_mid<T, MID_WHOLE, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e != cudaSuccess) return (int)e;
+  e = cudaFuncSetAttribute(k_mid<T, MID_FWD, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e != cudaSuccess) return (int)e;
+  e = cudaFuncSetAttribute(k_mid<T, MID_FWD_REAL, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e != cudaSuccess) return (int)e;
+  e = cudaFuncSetAttribute(k_inv_strided<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  return (int)e;
+}
+
+// Circulant first column of an N x N Toeplitz generator, embedded in length m (eq. ccs3.4):
+// c[d] = t_d, c[m - d] = t_{-d} for 1 <= d <= N - 1, zero elsewhere.
+void circulant_column(const std::vector<double>& t, long long N, long long m,
+                      std::vector<double>& c) {
+  c.assign((size_t)m, 0.0);
+  c[0] = t[N - 1];
+  for (long long d = 1; d <= N - 1; ++d) {
+    c[d] = t[d + N - 1];
+    c[m - d] = t[-d + N - 1];
+  }
+}
+
+// Forward transform of a real length-m column into H->z (bit-reversed order).
+int forward_real(tpc_handle* H, const DevLevel<double>& L, const double* real_dev) {
+  LevelArgs<double> a = level_args<double>(H, L, H->twL, H->z, H->partials);
+  a.real_in = real_dev;
+  cudaStream_t s = H->stream;
+  H->launches += L.logR1 ? 2 : 1;
+  if (L.logR1 == 0) {
+    k_mid<double, MID_FWD_REAL, false><<<1, NTHREADS, L.smem_mid, s>>>(a);
+  } else {
+    k_fwd_strided<double, IN_REAL><<<L.fwd_blocks, NTHREADS, L.smem_strided, s>>>(a);
+    k_mid<double, MID_FWD, false><<<1 << L.logR1, NTHREADS, (size_t)sizeof(double2) << L.logL, s>>>(a);
+  }
+  TPC_CUDA(H, cudaGetLastError());
+  return TPC_OK;
+}
+
+int setup_device(tpc_handle* H) {
+  const HostHierarchy& HH = H->host;
+  const int nlev = (int)HH.lev.size();
+  H->lev.resize(nlev);
+  if (int rc = set_smem_attrs<double, false>()) return cuda_fail(H, (cudaError_t)rc, "cudaFuncSetAttribute");
+  if (int rc = set_smem_attrs<double, true>()) return cuda_fail(H, (cudaError_t)rc, "cudaFuncSetAttribute");
+  // twiddles for in-shared-memory sub-transforms
+  std::vector<double> tw;
+  twiddles(1LL << LOG_LMAX, 1LL << (LOG_LMAX - 1), tw);
+  TPC_TRY(dalloc(H, &H->twL, (size_t)1 << (LOG_LMAX - 1)));
+  TPC_CUDA(H, cudaMemcpyAsync(H->twL, tw.data(), tw.size() * sizeof(double),
+                              cudaMemcpyHostToDevice, H->stream));
+  long long max_m = 0;
+  int max_parts = 1;
+  for (int i = 0; i < nlev; ++i) {
+    const LevelForm& F = HH.lev[i];
+    DevLevel<double>& L = H->lev[i];
+    L.k = F.k;
+    L.N = F.N;
+    L.n = 2 * F.N + 1;
+    L.m = 2 * F.N + 2;
+    plan_level(L);
+    if (L.logR1 > LOG_R1_MAX) {
+      H->err = "level too large for this build (m > 2^23)";
+      return TPC_ENOTSUP;
+    }
+    if (L.m > max_m) max_m = L.m;
+    if (L.fwd_blocks > max_parts) max_parts = L.fwd_blocks;
+    const double dA = F.tA[F.N - 1], dO = F.o, dD = F.tD[F.N - 1];
+    const double wpre = H->prm.omega_pre, wpost = H->prm.omega_post;
+    L.o = F.o;
+    L.wA_pre = wpre / dA;
+    L.wO_pre = wpre / dO;
+    L.wD_pre = wpre / dD;
+    L.wA_post = wpost / dA;
+    L.wO_post = wpost / dO;
+    L.wD_post = wpost / dD;
+    // the coarsest level only needs its inverse, unless it is also the finest (its product
+    // then gives the outer residual)
+    if (L.k == H->kc && i != 0) continue;
+    TPC_TRY(dalloc(H, &L.p, L.N));
+    TPC_TRY(dalloc(H, &L.q, L.N));
+    TPC_TRY(dalloc(H, &L.xi, L.N));
+    TPC_TRY(dalloc(H, &L.zeta, L.N));
+    TPC_CUDA(H, cudaMemcpyAsync(L.p, F.p.data(), L.N * sizeof(double), cudaMemcpyHostToDevice, H->stream));
+    TPC_CUDA(H, cudaMemcpyAsync(L.q, F.q.data(), L.N * sizeof(double), cudaMemcpyHostToDevice, H->stream));
+    TPC_CUDA(H, cudaMemcpyAsync(L.xi, F.xi.data(), L.N * sizeof(double), cudaMemcpyHostToDevice, H->stream));
+    TPC_CUDA(H, cudaMemcpyAsync(L.zeta, F.zeta.data(), L.N * sizeof(double), cudaMemcpyHostToDevice, H->stream));
+    if (L.logR1) {
+      std::vector<double> twm;
+      twiddles(L.m, L.m, twm);
+      TPC_TRY(dalloc(H, &L.twm, L.m));
+      TPC_CUDA(H, cudaMemcpyAsync(L.twm, twm.data(), twm.size() * sizeof(double),
+                                  cudaMemcpyHostToDevice, H->stream));
+      TPC_CUDA(H, cudaStreamSynchronize(H->stream));
+    }
+  }
+  TPC_TRY(dalloc(H, &H->z, max_m));
+  TPC_TRY(dalloc(H, &H->partials, max_parts));
+  double* staging = nullptr;
+  TPC_TRY(dalloc(H, &staging, max_m));
+  // spectra of the Toeplitz blocks, divided by 2m (the 1/m of the inverse transform and the
+  // 1/2 of the two-real-in-one-complex unpacking)
+  std::vector<double> col;
+  for (int i = 0; i < nlev; ++i) {
+    const LevelForm& F = HH.lev[i];
+    DevLevel<double>& L = H->lev[i];
+    if (L.k == H->kc && i != 0) continue;
+    TPC_TRY(dalloc(H, &L.sA, L.m));
+    TPC_TRY(dalloc(H, &L.sD, L.m));
+    TPC_TRY(dalloc(H, &L.sB, L.m));
+    if (H->prm.variant == TPC_NONSYM) TPC_TRY(dalloc(H, &L.sC, L.m));
+    const double scale = 1.0 / (2.0 * (double)L.m);
+    const int g = (int)((L.m + 255) / 256);
+    const std::vector<double>* gens[4] = {&F.tA, &F.tB, &F.tC, &F.tD};
+    for (int blk = 0; blk < 4; ++blk) {
+      if (blk == 2 && !L.sC) continue;
+      circulant_column(*gens[blk], L.N, L.m, col);
+      TPC_CUDA(H, cudaMemcpyAsync(staging, col.data(), L.m * sizeof(double),
+                                  cudaMemcpyHostToDevice, H->stream));
+      TPC_TRY(forward_real(H, L, staging));
+      if (blk == 0) k_extract_real<double><<<g, 256, 0, H->stream>>>(H->z, L.sA, L.m, scale);
+      if (blk == 3) k_extract_real<double><<<g, 256, 0, H->stream>>>(H->z, L.sD, L.m, scale);
+      if (blk == 1) k_extract_cplx<double><<<g, 256, 0, H->stream>>>(H->z, L.sB, L.m, scale);
+      if (blk == 2) k_extract_cplx<double><<<g, 256, 0, H->stream>>>(H->z, L.sC, L.m, scale);
+      TPC_CUDA(H, cudaGetLastError());
+      TPC_CUDA(H, cudaStreamSynchronize(H->stream));  // col is reused
+    }
+  }
+  // coarsest inverse
+  const long long nc = 2 * HH.lev.back().N + 1;
+  TPC_TRY(dalloc(H, &H->coarse_inv, (size_t)(nc * nc)));
+  TPC_CUDA(H, cudaMemcpyAsync(H->coarse_inv, HH.coarse_inv.data(), nc * nc * sizeof(double),
+                              cudaMemcpyHostToDevice, H->stream));
+  // vectors
+  H->f.resize(nlev);
+  H->e.resize(nlev);
+  H->t.resize(nlev);
+  for (int i = 0; i < nlev; ++i) {
+    TPC_TRY(dalloc(H, &H->f[i], H->lev[i].n));
+    TPC_TRY(dalloc(H, &H->e[i], H->lev[i].n));
+    TPC_TRY(dalloc(H, &H->t[i], H->lev[i].n));
+  }
+  const long long nK = H->lev[0].n;
+  TPC_TRY(dalloc(H, &H->u, nK));
+  TPC_TRY(dalloc(H, &H->b, nK));
+  TPC_TRY(dalloc(H, &H->r0, nK));
+  TPC_TRY(dalloc(H, &H->sumsq_part, NORM_BLOCKS));
+  TPC_TRY(dalloc(H, &H->sumsq, 1));
+  TPC_CUDA(H, cudaMallocHost(&H->sumsq_host, sizeof(double)));
+  TPC_CUDA(H, cudaStreamSynchronize(H->stream));
+  // one outer iteration as a CUDA graph
+  cudaGraph_t graph = nullptr;
+  TPC_CUDA(H, cudaStreamBeginCapture(H->stream, cudaStreamCaptureModeThreadLocal));
+  const long long before = H->launches;
+  enqueue_iteration(H);
+  H->iter_nodes = H->launches - before;
+  H->launches = before;
+  cudaError_t ce = cudaStreamEndCapture(H->stream, &graph);
+  if (ce != cudaSuccess) return cuda_fail(H, ce, "cudaStreamEndCapture");
+  ce = cudaGraphInstantiate(&H->iter_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) return cuda_fail(H, ce, "cudaGraphInstantiate");
+  return TPC_OK;
+}
+
+void release(tpc_handle* H) {
+  if (!H) return;
+  if (H->iter_exec) cudaGraphExecDestroy(H->iter_exec);
+  if (H->stream) cudaStreamSynchronize(H->stream);
+  for (void* p : H->dev_allocs) cudaFree(p);
+  if (H->sumsq_host) cudaFreeHost(H->sumsq_host);
+  if (H->own_stream && H->stream) cudaStreamDestroy(H->stream);
+  (void)cudaGetLastError();
+  delete H;
+}
+
+int level_index(const tpc_handle* H, int level) {
+  if (!H || level < H->kc || level > H->K) return -1;
+  return H->K - level;
+}
+
+int solve_impl(tpc_handle* H, const double* b_dev, double* x_dev, double tol, int use_x0,
+               int* iters_out, double* relres_out) {
+  const long long n = H->lev[0].n;
+  const size_t bytes = (size_t)n * sizeof(double);
+  cudaStream_t s = H->stream;
+  TPC_CUDA(H, cudaMemcpyAsync(H->b, b_dev, bytes, cudaMemcpyDeviceToDevice, s));
+  if (use_x0) {
+    TPC_CUDA(H, cudaMemcpyAsync(H->u, x_dev, bytes, cudaMemcpyDeviceToDevice, s));
+    matvec(H, 0, H->u, H->b, H->r0, EPI_RESID, false);
+  } else {
+    TPC_CUDA(H, cudaMemsetAsync(H->u, 0, bytes, s));
+    TPC_CUDA(H, cudaMemcpyAsync(H->r0, H->b, bytes, cudaMemcpyDeviceToDevice, s));
+  }
+  enqueue_sumsq(H, H->r0, n);
+  TPC_CUDA(H, cudaGetLastError());
+  TPC_CUDA(H, cudaMemcpyAsync(H->sumsq_host, H->sumsq, sizeof(double), cudaMemcpyDeviceToHost, s));
+  TPC_CUDA(H, cudaStreamSynchronize(s));
+  const double r0 = std::sqrt(*H->sumsq_host);
+  double rel = (r0 > 0.0) ? 1.0 : 0.0;
+  int it = 0;
+  int status = TPC_OK;
+  while (rel >= tol && r0 > 0.0) {
+    if (it >= H->prm.max_iters) {
+      status = TPC_ENOTCONV;
+      break;
+    }
+    TPC_CUDA(H, cudaGraphLaunch(H->iter_exec, s));
+    H->launches += H->iter_nodes;
+    TPC_CUDA(H, cudaMemcpyAsync(H->sumsq_host, H->sumsq, sizeof(double), cudaMemcpyDeviceToHost, s));
+    TPC_CUDA(H, cudaStreamSynchronize(s));
+    ++it;
+    rel = std::sqrt(*H->sumsq_host) / r0;
+    if (!std::isfinite(rel)) {
+      status = TPC_EDIVERGED;
+      H->err = "residual became non-finite";
+      break;
+    }
+  }
+  TPC_CUDA(H, cudaMemcpyAsync(x_dev, H->u, bytes, cudaMemcpyDeviceToDevice, s));
+  TPC_CUDA(H, cudaStreamSynchronize(s));
+  if (iters_out) *iters_out = it;
+  if (relres_out) *relres_out = rel;
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tpc_setup(const tpc_params* p, double delta, double h, int levels, void* cuda_stream,
+              tpc_handle** out) {
+  if (!out || !p) {
+    set_host_error("NULL argument");
+    return TPC_EINVAL;
+  }
+  *out = nullptr;
+  tpc_handle* H = new (std::nothrow) tpc_handle();
+  if (!H) {
+    set_host_error("host allocation failed");
+    return TPC_ENOMEM;
+  }
+  H->prm = *p;
+  if (H->prm.max_iters < 0) H->prm.max_iters = 0;
+  if (p->precision != TPC_FP64) {
+    set_host_error("only precision = TPC_FP64 is implemented in this build");
+    delete H;
+    return TPC_ENOTSUP;
+  }
+  std::string err;
+  int rc = build_host_hierarchy(*p, delta, h, levels, H->host, err);
+  if (rc != TPC_OK) {
+    set_host_error(err);
+    delete H;
+    return rc;
+  }
+  H->K = H->host.K;
+  H->kc = H->host.kc;
+  H->r = H->host.r;
+  H->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  int dev_count = 0;
+  cudaError_t ce = cudaGetDeviceCount(&dev_count);
+  if (ce != cudaSuccess || dev_count == 0) {
+    (void)cudaGetLastError();
+    set_host_error(std::string("no CUDA device: ") + cudaGetErrorString(ce));
+    delete H;
+    return TPC_ECUDA;
+  }
+  if (!H->stream) {
+    // Work is captured into CUDA graphs, which the legacy default stream does not allow; a
+    // blocking stream keeps the default stream's ordering with the caller's other work.
+    ce = cudaStreamCreate(&H->stream);
+    if (ce != cudaSuccess) {
+      set_host_error(std::string("cudaStreamCreate: ") + cudaGetErrorString(ce));
+      delete H;
+      return TPC_ECUDA;
+    }
+    H->own_stream = true;
+  }
+  rc = setup_device(H);
+  if (rc != TPC_OK) {
+    set_host_error(H->err);
+    release(H);
+    return rc;
+  }
+  *out = H;
+  return TPC_OK;
+}
+
+int tpc_solve(tpc_handle* H, const double* b_dev, double* x_dev, double tol, int use_x0,
+              int* iters_out, double* relres_out) {
+  if (!H || !b_dev || !x_dev || !(tol >= 0.0)) {
+    if (H) H->err = "bad argument to tpc_solve";
+    return TPC_EINVAL;
+  }
+  return solve_impl(H, b_dev, x_dev, tol, use_x0, iters_out, relres_out);
+}
+
+int tpc_solve_host(tpc_handle* H, const double* b_host, double* x_host, double tol, int use_x0,
+                   int* iters_out, double* relres_out) {
+  if (!H || !b_host || !x_host || !(tol >= 0.0)) {
+    if (H) H->err = "bad argument to tpc_solve_host";
+    return TPC_EINVAL;
+  }
+  const long long n = H->lev[0].n;
+  const size_t bytes = (size_t)n * sizeof(double);
+  if (!H->hb) {
+    TPC_TRY(dalloc(H, &H->hb, n));
+    TPC_TRY(dalloc(H, &H->hx, n));
+  }
+  TPC_CUDA(H, cudaMemcpyAsync(H->hb, b_host, bytes, cudaMemcpyHostToDevice, H->stream));
+  if (use_x0) TPC_CUDA(H, cudaMemcpyAsync(H->hx, x_host, bytes, cudaMemcpyHostToDevice, H->stream));
+  const int rc = solve_impl(H, H->hb, H->hx, tol, use_x0, iters_out, relres_out);
+  if (rc < 0) return rc;
+  TPC_CUDA(H, cudaMemcpyAsync(x_host, H->hx, bytes, cudaMemcpyDeviceToHost, H->stream));
+  TPC_CUDA(H, cudaStreamSynchronize(H->stream));
+  return rc;
+}
+
+int tpc_apply(tpc_handle* H, int level, const double* x_dev, double* y_dev) {
+  const int li = level_index(H, level);
+  if (li < 0 || !x_dev || !y_dev || x_dev == y_dev) {
+    if (H) H->err = "bad argument to tpc_apply";
+    return TPC_EINVAL;
+  }
+  if (!H->lev[li].sA) {
+    H->err = "tpc_apply is not available on the coarsest level (held as an inverse)";
+    return TPC_EINVAL;
+  }
+  matvec(H, li, x_dev, nullptr, y_dev, EPI_APPLY, false);
+  TPC_CUDA(H, cudaGetLastError());
+  return TPC_OK;
+}
+
+int tpc_vcycle(tpc_handle* H, const double* r_dev, double* e_dev) {
+  if (!H || !r_dev || !e_dev || r_dev == e_dev) {
+    if (H) H->err = "bad argument to tpc_vcycle";
+    return TPC_EINVAL;
+  }
+  const double* res = enqueue_vcycle(H, 0, r_dev);
+  TPC_CUDA(H, cudaMemcpyAsync(e_dev, res, (size_t)H->lev[0].n * sizeof(double),
+                              cudaMemcpyDeviceToDevice, H->stream));
+  TPC_CUDA(H, cudaGetLastError());
+  return TPC_OK;
+}
+
+long long tpc_level_size(const tpc_handle* H, int level) {
+  const int li = level_index(H, level);
+  return li < 0 ? 0 : H->lev[li].n;
+}
+int tpc_finest_level(const tpc_handle* H) { return H ? H->K : -1; }
+int tpc_coarsest_level(const tpc_handle* H) { return H ? H->kc : -1; }
+
+int tpc_export_level(const tpc_handle* H, int level, double* host_buf, size_t cap,
+                     size_t* need) {
+  const int li = level_index(H, level);
+  if (li < 0 || !need) return TPC_EINVAL;
+  const LevelForm& F = H->host.lev[li];
+  *need = export_count(F.N);
+  if (!host_buf) return TPC_OK;
+  if (cap < *need) return TPC_EINVAL;
+  export_level(F, host_buf);
+  return TPC_OK;
+}
+
+int tpc_time_level_kernels(tpc_handle* H, int level, int reps, const double* x_dev,
+                           const double* f_dev, double* y_dev, double* ms_out) {
+  const int li = level_index(H, level);
+  if (li < 0 || reps < 1 || !x_dev || !f_dev || !y_dev || !ms_out || x_dev == y_dev ||
+      !H->lev[li].sA) {
+    if (H) H->err = "bad argument to tpc_time_level_kernels";
+    return TPC_EINVAL;
+  }
+  const DevLevel<double>& L = H->lev[li];
+  const bool ns = H->prm.variant == TPC_NONSYM;
+  LevelArgs<double> a = level_args<double>(H, L, H->twL, H->z, H->partials);
+  a.x = x_dev;
+  a.f = f_dev;
+  a.y = y_dev;
+  a.epi = EPI_RESID;
+  cudaStream_t s = H->stream;
+  cudaEvent_t ev[2];
+  TPC_CUDA(H, cudaEventCreate(&ev[0]));
+  TPC_CUDA(H, cudaEventCreate(&ev[1]));
+  for (int which = 0; which < 3; ++which) {
+    ms_out[which] = 0.0;
+    if (L.logR1 == 0 && which != 1) continue;
+    for (int rep = 0; rep <= reps; ++rep) {
+      if (rep == 1) cudaEventRecord(ev[0], s);
+      if (which == 0) {
+        k_fwd_strided<double, IN_PACK><<<L.fwd_blocks, NTHREADS, L.smem_strided, s>>>(a);
+      } else if (which == 2) {
+        k_inv_strided<double><<<L.fwd_blocks, NTHREADS, L.smem_strided, s>>>(a);
+      } else if (L.logR1 == 0) {
+        if (ns) k_mid<double, MID_WHOLE, true><<<1, NTHREADS, L.smem_mid, s>>>(a);
+        else k_mid<double, MID_WHOLE, false><<<1, NTHREADS, L.smem_mid, s>>>(a);
+      } else {
+        if (ns) k_mid<double, MID_PAIR, true><<<L.mid_blocks, NTHREADS, L.smem_mid, s>>>(a);
+        else k_mid<double, MID_PAIR, false><<<L.mid_blocks, NTHREADS, L.smem_mid, s>>>(a);
+      }
+      H->launches += 1;
+    }
+    cudaEventRecord(ev[1], s);
+    TPC_CUDA(H, cudaEventSynchronize(ev[1]));
+    float ms = 0.0f;
+    TPC_CUDA(H, cudaEventElapsedTime(&ms, ev[0], ev[1]));
+    ms_out[which] = (double)ms / reps;
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  TPC_CUDA(H, cudaGetLastError());
+  return TPC_OK;
+}
+
+long long tpc_kernel_launches(const tpc_handle* H) { return H ? H->launches : 0; }
+
+void tpc_destroy(tpc_handle* H) { release(H); }
+
+const char* tpc_last_error(const tpc_handle* H) {
+  if (H) return H->err.c_str();
+  return host_error();
+}
+
+}  // extern "C"

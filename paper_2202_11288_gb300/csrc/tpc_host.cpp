@@ -1,0 +1,399 @@
+// Host-side setup of the level hierarchy in generator-plus-Cross form (FP64).
+//
+// * Finest level: the printed coefficients of section 2.2 (a_m, a_{m+1/2}, c_m, d_m), read as
+//   functions of the distance between a collocation point and a grid point, give the
+//   generators of the four Toeplitz blocks of eq. (nonsym system) / eq. (system1). The Cross
+//   splitting of eq. (split01) then peels off the first midpoint unknown w_o:
+//   B = [p B_bar], C = [q; C_bar], D = [o zeta; xi D_bar].
+// * Coarse levels: the Galerkin product A_{k-1} = R A_k P (eq. block Galerkin) with
+//   R = 1/4 [1 2 1] on the concatenated vector and P = 2 R^T (section 3.1). Every coarse entry
+//   is (1/8) sum_{a,b in {-1,0,1}} w_a w_b A_k(2I+a, 2J+b), w = (1,2,1). Inside a segment
+//   this is the Toeplitz rule of Lemma 3.1; rows/columns through the middle unknown give the
+//   Cross formulas of Lemma 3.1, here with the fine indices written out from the definition
+//   (the printed Cross indices are read as shifted by one).
+// * Coarsest level: the dense matrix assembled from its form, inverted through an LU
+//   factorisation with partial pivoting (Algorithm 2: B_1 = A_1^{-1}).
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tpc_internal.h"
+
+namespace tpc {
+
+namespace {
+
+// Coefficient of the printed stencils at twice the distance dist2 (in units of h).
+// Node rows and all rows of the SPD system: a_m at integer distance m, a_{m+1/2} at m + 1/2.
+double coef_a(long long dist2, int r) {
+  if (dist2 < 0) dist2 = -dist2;
+  const long long m = dist2 / 2;
+  if (dist2 & 1) return (m <= r - 1) ? -4.0 : 0.0;  // a_{m+1/2}, 0 <= m <= r-1
+  if (m == 0) return 12.0 * r - 2.0;                // a_0
+  if (m < r) return -2.0;                           // a_m, 1 <= m <= r-1
+  if (m == r) return -1.0;                          // a_r
+  return 0.0;
+}
+// Midpoint rows of the nonsymmetric system: c_m for nodes at distance m + 1/2.
+double coef_c(long long dist2, int r) {
+  if (dist2 < 0) dist2 = -dist2;
+  if (!(dist2 & 1)) return 0.0;
+  const long long m = dist2 / 2;
+  if (m <= r - 2) return -2.0;
+  if (m == r - 1) return -9.0 / 4.0;
+  if (m == r) return 1.0 / 4.0;
+  return 0.0;
+}
+// ... and d_m for midpoints at integer distance m.
+double coef_d(long long dist2, int r) {
+  if (dist2 < 0) dist2 = -dist2;
+  if (dist2 & 1) return 0.0;
+  const long long m = dist2 / 2;
+  if (m == 0) return 12.0 * r - 4.0;
+  if (m < r) return -4.0;
+  if (m == r) return -2.0;
+  return 0.0;
+}
+
+thread_local std::string g_host_err;
+
+LevelForm finest_form(int variant, int K, int r, double shift) {
+  const long long Nint = 1LL << K;  // intervals
+  LevelForm L;
+  L.k = K;
+  L.N = Nint - 1;
+  const long long N = L.N;
+  // Generators of the full blocks as functions of d = i - j (rows i, columns j, 1-based):
+  //   A (nodes x nodes):      distance |d|                -> a
+  //   B (nodes x midpoints):  x_i - x_{j-1/2} = d + 1/2   -> a
+  //   C (midpoints x nodes):  x_{i-1/2} - x_j = d - 1/2   -> a (SPD) or c (nonsym)
+  //   D (midpoints x mids):   distance |d|                -> a (SPD) or d (nonsym)
+  auto fA = [&](long long d) { return coef_a(2 * d, r); };
+  auto fB = [&](long long d) { return coef_a(2 * d + 1, r); };
+  auto fC = [&](long long d) {
+    return variant == TPC_SPD ? coef_a(2 * d - 1, r) : coef_c(2 * d - 1, r);
+  };
+  auto fD = [&](long long d) {
+    return variant == TPC_SPD ? coef_a(2 * d, r) : coef_d(2 * d, r);
+  };
+  const size_t G = (size_t)(2 * N - 1);
+  L.tA.assign(G, 0.0);
+  L.tB.assign(G, 0.0);
+  L.tC.assign(G, 0.0);
+  L.tD.assign(G, 0.0);
+  for (long long d = -(N - 1); d <= N - 1; ++d) {
+    L.tA[d + N - 1] = fA(d);
+    L.tB[d + N - 1] = fB(d - 1);  // B_bar(i, j) = B(i, j + 1)
+    L.tC[d + N - 1] = fC(d + 1);  // C_bar(i, j) = C(i + 1, j)
+    L.tD[d + N - 1] = fD(d);      // D_bar(i, j) = D(i + 1, j + 1)
+  }
+  L.p.assign(N, 0.0);
+  L.q.assign(N, 0.0);
+  L.xi.assign(N, 0.0);
+  L.zeta.assign(N, 0.0);
+  for (long long i = 1; i <= N; ++i) {
+    L.p[i - 1] = fB(i - 1);     // B(i, 1)
+    L.q[i - 1] = fC(1 - i);     // C(1, i)
+    L.zeta[i - 1] = fD(-i);     // D(1, i + 1)
+    L.xi[i - 1] = fD(i);        // D(i + 1, 1)
+  }
+  L.o = fD(0);
+  L.tA[N - 1] += shift;
+  L.tD[N - 1] += shift;
+  L.o += shift;
+  return L;
+}
+
+LevelForm coarsen(const LevelForm& F) {
+  const long long N = F.N;
+  LevelForm Cc;
+  Cc.k = F.k - 1;
+  Cc.N = (N - 1) / 2;
+  const long long Nc = Cc.N;
+  const double w[3] = {1.0, 2.0, 1.0};  // weights of a = -1, 0, 1
+  auto tA = [&](long long d) { return F.tA[d + N - 1]; };
+  auto tB = [&](long long d) { return F.tB[d + N - 1]; };
+  auto tC = [&](long long d) { return F.tC[d + N - 1]; };
+  auto tD = [&](long long d) { return F.tD[d + N - 1]; };
+  auto p = [&](long long i) { return F.p[i - 1]; };
+  auto q = [&](long long i) { return F.q[i - 1]; };
+  auto xi = [&](long long i) { return F.xi[i - 1]; };
+  auto zeta = [&](long long i) { return F.zeta[i - 1]; };
+
+  const size_t G = (size_t)(2 * Nc - 1);
+  Cc.tA.assign(G, 0.0);
+  Cc.tB.assign(G, 0.0);
+  Cc.tC.assign(G, 0.0);
+  Cc.tD.assign(G, 0.0);
+  const std::vector<double>* fin[4] = {&F.tA, &F.tB, &F.tC, &F.tD};
+  std::vector<double>* cout_[4] = {&Cc.tA, &Cc.tB, &Cc.tC, &Cc.tD};
+  for (int b = 0; b < 4; ++b) {
+    const std::vector<double>& t = *fin[b];
+    std::vector<double>& tc = *cout_[b];
+    for (long long dl = -(Nc - 1); dl <= Nc - 1; ++dl) {
+      const long long c = 2 * dl + N - 1;  // index of fine d = 2 dl
+      tc[dl + Nc - 1] =
+          (t[c - 2] + 4.0 * t[c - 1] + 6.0 * t[c] + 4.0 * t[c + 1] + t[c + 2]) / 8.0;
+    }
+  }
+  Cc.p.assign(Nc, 0.0);
+  Cc.q.assign(Nc, 0.0);
+  Cc.xi.assign(Nc, 0.0);
+  Cc.zeta.assign(Nc, 0.0);
+  for (long long I = 1; I <= Nc; ++I) {
+    double sp = 0.0, sq = 0.0, sx = 0.0, sz = 0.0;
+    for (int a = -1; a <= 1; ++a) {
+      const long long i = 2 * I + a;  // fine index inside a segment, 1..N
+      // column through the fine middle (cols N, N+1, N+2) for coarse row I of v
+      sp += w[a + 1] * (tA(i - N) + 2.0 * p(i) + tB(i - 1));
+      // row through the fine middle (rows N, N+1, N+2) for coarse column I of v
+      sq += w[a + 1] * (tA(N - i) + 2.0 * q(i) + tC(1 - i));
+      // column through the middle for coarse row I of w_bar
+      sx += w[a + 1] * (tC(i - N) + 2.0 * xi(i) + tD(i - 1));
+      // row through the middle for coarse column I of w_bar
+      sz += w[a + 1] * (tB(N - i) + 2.0 * zeta(i) + tD(1 - i));
+    }
+    Cc.p[I - 1] = sp / 8.0;
+    Cc.q[I - 1] = sq / 8.0;
+    Cc.xi[I - 1] = sx / 8.0;
+    Cc.zeta[I - 1] = sz / 8.0;
+  }
+  // 3 x 3 block of fine rows/cols N, N+1, N+2 around the middle
+  Cc.o = (tA(0) + 2.0 * p(N) + tB(N - 1) + 2.0 * q(N) + 4.0 * F.o + 2.0 * zeta(1) +
+          tC(1 - N) + 2.0 * xi(1) + tD(0)) /
+         8.0;
+  return Cc;
+}
+
+// Dense entry (i, j), 1-based, of a level in generator-plus-Cross form.
+double dense_entry(const LevelForm& L, long long i, long long j) {
+  const long long N = L.N;
+  const bool iv = i <= N, im = i == N + 1, jv = j <= N, jm = j == N + 1;
+  if (im && jm) return L.o;
+  if (im) return jv ? L.q[j - 1] : L.zeta[j - N - 2];
+  if (jm) return iv ? L.p[i - 1] : L.xi[i - N - 2];
+  const long long ii = iv ? i : i - N - 1, jj = jv ? j : j - N - 1;
+  const std::vector<double>& t = iv ? (jv ? L.tA : L.tB) : (jv ? L.tC : L.tD);
+  return t[ii - jj + N - 1];
+}
+
+int invert_dense(std::vector<double>& A, long long n, std::vector<double>& inv) {
+  std::vector<long long> piv(n);
+  double amax = 0.0;
+  for (double v : A) amax = std::fmax(amax, std::fabs(v));
+  for (long long c = 0; c < n; ++c) {
+    long long pr = c;
+    for (long long r = c + 1; r < n; ++r)
+      if (std::fabs(A[r * n + c]) > std::fabs(A[pr * n + c])) pr = r;
+    if (!(std::fabs(A[pr * n + c]) > 1e-14 * amax)) return TPC_ESINGULAR;
+    piv[c] = pr;
+    if (pr != c)
+      for (long long k = 0; k < n; ++k) std::swap(A[c * n + k], A[pr * n + k]);
+    for (long long r = c + 1; r < n; ++r) {
+      const double l = A[r * n + c] / A[c * n + c];
+      A[r * n + c] = l;
+      for (long long k = c + 1; k < n; ++k) A[r * n + k] -= l * A[c * n + k];
+    }
+  }
+  inv.assign((size_t)(n * n), 0.0);
+  std::vector<double> col(n);
+  for (long long e = 0; e < n; ++e) {
+    for (long long i = 0; i < n; ++i) col[i] = (i == e) ? 1.0 : 0.0;
+    for (long long c = 0; c < n; ++c) std::swap(col[c], col[piv[c]]);
+    for (long long i = 0; i < n; ++i)
+      for (long long k = 0; k < i; ++k) col[i] -= A[i * n + k] * col[k];
+    for (long long i = n - 1; i >= 0; --i) {
+      for (long long k = i + 1; k < n; ++k) col[i] -= A[i * n + k] * col[k];
+      col[i] /= A[i * n + i];
+    }
+    for (long long i = 0; i < n; ++i) inv[i * n + e] = col[i];
+  }
+  return TPC_OK;
+}
+
+}  // namespace
+
+int build_host_hierarchy(const tpc_params& p, double delta, double h, int levels,
+                         HostHierarchy& out, std::string& err) {
+  if (!(h > 0.0) || !(h < 1.0) || !std::isfinite(delta) || !(delta > 0.0)) {
+    err = "need 0 < h < 1 and delta > 0";
+    return TPC_EINVAL;
+  }
+  const double Kd = std::log2(1.0 / h);
+  const int K = (int)std::lround(Kd);
+  if (K < 1 || K > 30 || std::ldexp(1.0, -K) != h) {
+    err = "h must be 2^-K with 1 <= K <= 30";
+    return TPC_EINVAL;
+  }
+  if (p.variant != TPC_SPD && p.variant != TPC_NONSYM) {
+    err = "variant must be TPC_SPD or TPC_NONSYM";
+    return TPC_EINVAL;
+  }
+  if (p.kernel != 0) {
+    err = "only the constant kernel (kernel = 0) is implemented";
+    return TPC_ENOTSUP;
+  }
+  if (p.m1 < 1 || p.m2 < 0 || p.m1 > 8 || p.m2 > 8) {
+    err = "need 1 <= m1 <= 8 and 0 <= m2 <= 8";
+    return TPC_EINVAL;
+  }
+  if (!(p.omega_pre > 0.0 && p.omega_pre < 2.0) || !(p.omega_post > 0.0 && p.omega_post < 2.0)) {
+    err = "damping weights must lie in (0, 2)";
+    return TPC_EINVAL;
+  }
+  if (!std::isfinite(p.shift)) {
+    err = "shift must be finite";
+    return TPC_EINVAL;
+  }
+  int kc = p.coarsest_level;
+  if (kc < 1 || kc > K || kc > 7) {
+    err = "coarsest level must satisfy 1 <= kc <= min(K, 7)";
+    return TPC_EINVAL;
+  }
+  if (levels < 0 || levels > K - kc + 1) {
+    err = "levels must be 0 (all) or in 1..K-kc+1";
+    return TPC_EINVAL;
+  }
+  if (levels > 0) kc = K - levels + 1;
+  if (kc > 7) {
+    err = "the coarsest level kept by 'levels' must be <= 7 (dense solve of <= 255 unknowns)";
+    return TPC_EINVAL;
+  }
+  // horizon ratio (section 2.2): r = floor(delta/h) >= 1, or 1 when delta <= h
+  const double ratio = delta / h;
+  int r = 1;
+  if (delta > h) {
+    const double fr = std::floor(ratio);
+    if (fr > 1e9) {
+      err = "delta/h too large";
+      return TPC_EINVAL;
+    }
+    r = (int)fr;
+  }
+  out.K = K;
+  out.kc = kc;
+  out.r = r;
+  out.lev.clear();
+  out.lev.reserve(K - kc + 1);
+  out.lev.push_back(finest_form(p.variant, K, r, p.shift));
+  for (int k = K; k > kc; --k) out.lev.push_back(coarsen(out.lev.back()));
+  const LevelForm& Lc = out.lev.back();
+  const long long n = 2 * Lc.N + 1;
+  std::vector<double> A((size_t)(n * n));
+  for (long long i = 1; i <= n; ++i)
+    for (long long j = 1; j <= n; ++j) A[(i - 1) * n + (j - 1)] = dense_entry(Lc, i, j);
+  if (invert_dense(A, n, out.coarse_inv) != TPC_OK) {
+    err = "coarsest matrix is singular";
+    return TPC_ESINGULAR;
+  }
+  return TPC_OK;
+}
+
+size_t export_count(long long N) { return (size_t)(2 + 4 * (2 * N - 1) + 4 * N); }
+
+void export_level(const LevelForm& L, double* dst) {
+  dst[0] = (double)L.N;
+  dst[1] = L.o;
+  size_t o = 2;
+  for (const std::vector<double>* v : {&L.tA, &L.tB, &L.tC, &L.tD, &L.p, &L.q, &L.xi, &L.zeta}) {
+    std::memcpy(dst + o, v->data(), v->size() * sizeof(double));
+    o += v->size();
+  }
+}
+
+// exp(-2 pi i j / m) for j < count. Angles are reduced to [0, pi/4] by the quadrant and
+// octant symmetries of sine and cosine before calling the C library's sin / cos, so each
+// value is within about one ulp.
+void twiddles(long long m, long long count, std::vector<double>& out) {
+  out.resize((size_t)(2 * count));
+  const double two_pi = 6.283185307179586476925286766559;
+  for (long long j = 0; j < count; ++j) {
+    double c, s;
+    const long long jj = j % m;
+    if (m % 8 != 0) {
+      const double th = two_pi * (double)jj / (double)m;
+      c = std::cos(th);
+      s = std::sin(th);
+    } else {
+      const long long q4 = m / 4, q8 = m / 8;
+      const long long quad = jj / q4, a = jj % q4;
+      double ca, sa;  // cos / sin of 2 pi a / m, a in [0, m/4)
+      if (a <= q8) {
+        const double th = two_pi * (double)a / (double)m;
+        ca = std::cos(th);
+        sa = std::sin(th);
+      } else {
+        const double th = two_pi * (double)(q4 - a) / (double)m;
+        ca = std::sin(th);
+        sa = std::cos(th);
+      }
+      switch (quad) {
+        case 0: c = ca; s = sa; break;
+        case 1: c = -sa; s = ca; break;
+        case 2: c = -ca; s = -sa; break;
+        default: c = sa; s = -ca; break;
+      }
+    }
+    out[2 * j] = c;
+    out[2 * j + 1] = -s;
+  }
+}
+
+}  // namespace tpc
+
+extern "C" {
+
+void tpc_default_params(tpc_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->variant = TPC_SPD;
+  p->kernel = 0;
+  p->kernel_a = 0.0;
+  p->gamma0 = 0.0;
+  p->shift = 0.0;
+  p->m1 = 1;
+  p->m2 = 1;
+  p->omega_pre = 2.0 / 3.0;
+  p->omega_post = 2.0 / 3.0;
+  p->coarsest_level = 3;
+  p->precision = TPC_FP64;
+  p->max_iters = 100;
+  p->inner_cycles = 4;
+}
+
+int tpc_host_hierarchy(const tpc_params* p, double delta, double h, int levels,
+                       double* host_buf, size_t cap, size_t* need) {
+  if (!p || !need) {
+    tpc::g_host_err = "NULL argument";
+    return TPC_EINVAL;
+  }
+  tpc::HostHierarchy H;
+  std::string err;
+  const int rc = tpc::build_host_hierarchy(*p, delta, h, levels, H, err);
+  if (rc != TPC_OK) {
+    tpc::g_host_err = err;
+    return rc;
+  }
+  size_t total = 0;
+  for (const auto& L : H.lev) total += tpc::export_count(L.N);
+  *need = total;
+  if (!host_buf || cap < total) {
+    tpc::g_host_err = "buffer too small";
+    return host_buf ? TPC_EINVAL : TPC_OK;
+  }
+  size_t o = 0;
+  for (const auto& L : H.lev) {
+    tpc::export_level(L, host_buf + o);
+    o += tpc::export_count(L.N);
+  }
+  return TPC_OK;
+}
+
+}  // extern "C"
+
+// Shared by the handle-less error path of the device code.
+namespace tpc {
+void set_host_error(const std::string& s) { g_host_err = s; }
+const char* host_error() { return g_host_err.c_str(); }
+}  // namespace tpc

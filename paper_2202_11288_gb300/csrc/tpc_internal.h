@@ -1,0 +1,42 @@
+// Internal declarations shared by the host setup (tpc_host.cpp) and the device code.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "../../include/tpcamg.h"
+
+namespace tpc {
+
+// One level in generator-plus-Cross form (eq. split01).
+//   Toeplitz blocks A, B_bar, C_bar, D_bar (N x N) as generators t[d + N - 1] = T(i, j),
+//   d = i - j in [-(N-1), N-1]; Cross vectors p (column), q (row), xi (column), zeta (row),
+//   each N long, 0-based; o the middle diagonal entry.
+struct LevelForm {
+  int k = 0;
+  long long N = 0;  // N_k = 2^k - 1
+  std::vector<double> tA, tB, tC, tD;
+  std::vector<double> p, q, xi, zeta;
+  double o = 0.0;
+  double gen(const std::vector<double>& t, long long d) const { return t[d + N - 1]; }
+};
+
+struct HostHierarchy {
+  int K = 0, kc = 0, r = 0;
+  std::vector<LevelForm> lev;          // lev[0] = finest (K), lev.back() = coarsest (kc)
+  std::vector<double> coarse_inv;      // n_kc x n_kc inverse of the coarsest matrix, row major
+};
+
+// Validate parameters and build the hierarchy on the host (FP64). Returns a TPC_* code and
+// writes a message into err on failure.
+int build_host_hierarchy(const tpc_params& p, double delta, double h, int levels,
+                         HostHierarchy& out, std::string& err);
+
+// Export layout of one level (see tpc_export_level).
+size_t export_count(long long N);
+void export_level(const LevelForm& L, double* dst);
+
+// exp(-2 pi i j / m) for j in [0, count), written as interleaved (re, im) pairs.
+void twiddles(long long m, long long count, std::vector<double>& out);
+
+}  // namespace tpc

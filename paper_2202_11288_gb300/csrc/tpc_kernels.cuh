@@ -1,0 +1,407 @@
+// Kernels of one Toeplitz-plus-Cross level and of the V-cycle (Algorithm 2).
+//
+// Level k (section 3.2.2): u = [v (N); w_o (1); w_bar (N)], N = N_k = 2^k - 1, m = 2N + 2.
+// y = A_k u is computed as (eq. split01 and the product formula after it)
+//   [A v + B_bar w_bar ; q.v + o w_o + zeta.w_bar ; C_bar v + D_bar w_bar]
+//   + [p w_o ; 0 ; xi w_o],
+// with the four Toeplitz products done through one circulant embedding of length m
+// (eq. ccs3.4): z = pad(v) + i pad(w_bar) is transformed once, the 2x2 block product
+// [Y1; Y2] = [A^ B^; C^ D^] [V^; W^] is formed per frequency pair (j, m-j) (V^, W^ are the
+// transforms of v and w_bar, unpacked from Z_j and conj(Z_{m-j})), and Y1 + i Y2 is
+// transformed back: the real part is A v + B_bar w_bar, the imaginary part C_bar v + D_bar w_bar.
+//
+// Pipelines for one product (forward DIF, inverse DIT, see tpc_fft.cuh):
+//   m <= 2^LOG_WHOLE : k_mid<MID_WHOLE>: one CTA does pack, FFT, spectral product, inverse
+//                      FFT and the epilogue.
+//   larger m         : m = R1 * L. k_fwd_strided (R1-point DIF on each of the L columns of
+//                      stride L, then the twiddle W_m^{c k}: the first log2 R1 stages),
+//                      k_mid<MID_PAIR> (remaining log2 L stages on contiguous blocks, the
+//                      spectral product across the mirror block, the first log2 L inverse
+//                      stages), k_inv_strided (twiddle, R1-point DIT, epilogue).
+// Bit-reversed position p holds frequency j = bitrev(p); its partner m - j sits at
+// p' = 3 * 2^h - 1 - p inside the same octave [2^h, 2^{h+1}) (p' = p for p = 0, 1). In
+// blocks of L positions, block b >= 2 pairs with b' = 3 * 2^g - 1 - b (g = octave of b);
+// blocks 0 and 1 pair with themselves.
+#pragma once
+
+#include "tpc_fft.cuh"
+
+namespace tpc {
+
+constexpr int LOG_LMAX = 12;        // longest in-shared-memory sub-transform (4096 points)
+constexpr int NTHREADS = 256;
+
+enum Epi { EPI_APPLY = 0, EPI_RESID = 1, EPI_JACOBI = 2 };
+enum MidMode { MID_PAIR = 0, MID_WHOLE = 1, MID_FWD = 2, MID_FWD_REAL = 3 };
+enum InMode { IN_PACK = 0, IN_REAL = 1 };
+
+template <typename T> struct LevelArgs {
+  long long N;           // N_k
+  int logm, logR1, logL, logC;
+  const T* sA;           // spectra at bit-reversed positions, already divided by 2m
+  const T* sD;
+  const c2<T>* sB;
+  const c2<T>* sC;       // nullptr for the SPD system (C_bar = B_bar^T, C^ = conj B^)
+  const T* p;
+  const T* q;
+  const T* xi;
+  const T* zeta;
+  T o;
+  T wA, wO, wD;          // omega / diagonal, per segment (damped Jacobi, eq. 7)
+  const c2<T>* twm;      // W_m^j, j < m (strided pipelines only)
+  const c2<T>* twL;      // W_{4096}^j, j < 2048
+  // per call
+  const T* x;            // operand u (n_k)
+  const T* f;            // right-hand side for EPI_RESID / EPI_JACOBI
+  T* y;                  // result (n_k); must not alias x
+  const T* real_in;      // IN_REAL / MID_FWD_REAL input (m reals)
+  int epi;
+  c2<T>* z;              // complex work array (m)
+  T* partials;           // per-CTA partial dots of the forward strided pass
+  int nparts;
+};
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  T s = 0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) s += red[i];
+  }
+  return s;  // valid in thread 0
+}
+
+// Epilogue for output index i < N: ax_v, ax_w are the Toeplitz parts of (A u)_v[i] and
+// (A u)_{w_bar}[i]; the Cross column p, xi times w_o is added here.
+template <typename T>
+__device__ __forceinline__ void epi_pair(const LevelArgs<T>& a, long long i, T ax_v, T ax_w,
+                                         T w_o) {
+  const T yv = fma(a.p[i], w_o, ax_v);
+  const T yw = fma(a.xi[i], w_o, ax_w);
+  const long long iw = a.N + 1 + i;
+  if (a.epi == EPI_APPLY) {
+    a.y[i] = yv;
+    a.y[iw] = yw;
+  } else if (a.epi == EPI_RESID) {
+    a.y[i] = a.f[i] - yv;
+    a.y[iw] = a.f[iw] - yw;
+  } else {
+    a.y[i] = fma(a.wA, a.f[i] - yv, a.x[i]);
+    a.y[iw] = fma(a.wD, a.f[iw] - yw, a.x[iw]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void epi_middle(const LevelArgs<T>& a, T dot, T w_o) {
+  const T ym = fma(a.o, w_o, dot);
+  const long long im = a.N;
+  if (a.epi == EPI_APPLY)
+    a.y[im] = ym;
+  else if (a.epi == EPI_RESID)
+    a.y[im] = a.f[im] - ym;
+  else
+    a.y[im] = fma(a.wO, a.f[im] - ym, a.x[im]);
+}
+
+// Spectral 2x2 block product for the frequency pair held at positions (lower, upper).
+// P = bit-reversed position of the lower member (index of the stored spectra).
+template <typename T, bool NS>
+__device__ __forceinline__ void mac_pair(const LevelArgs<T>& a, long long P, c2<T>* zl,
+                                         c2<T>* zu) {
+  const c2<T> Zp = *zl, Zq = *zu;
+  // 2 V^ = Z_p + conj Z_q ; 2 W^ = (Z_p - conj Z_q) / i
+  const T vr = Zp.x + Zq.x, vi = Zp.y - Zq.y;
+  const T wr = Zp.y + Zq.y, wi = Zq.x - Zp.x;
+  const T sa = a.sA[P], sd = a.sD[P];
+  const c2<T> sb = a.sB[P];
+  c2<T> sc;
+  if (NS) {
+    sc = a.sC[P];
+  } else {
+    sc.x = sb.x;
+    sc.y = -sb.y;
+  }
+  const T y1r = fma(sa, vr, fma(sb.x, wr, -sb.y * wi));
+  const T y1i = fma(sa, vi, fma(sb.x, wi, sb.y * wr));
+  const T y2r = fma(sd, wr, fma(sc.x, vr, -sc.y * vi));
+  const T y2i = fma(sd, wi, fma(sc.x, vi, sc.y * vr));
+  *zl = mk<T>(y1r - y2i, y1i + y2r);
+  if (zu != zl) *zu = mk<T>(y1r + y2i, y2r - y1i);
+}
+
+// Pair tasks of the self-paired block 0 (positions [0, L)): task q -> (p, p').
+__device__ __forceinline__ void block0_pair(int q, int& p, int& pp) {
+  if (q < 2) {
+    p = pp = q;
+    return;
+  }
+  const int qq = q - 1;
+  const int g = 31 - __clz(qq);
+  p = qq + (1 << g);
+  pp = 3 * (2 << g) - 1 - p;
+}
+
+// ------------------------------------------------------------------------------------
+// Forward strided pass: the first log2(R1) DIF stages as R1-point transforms of the L
+// columns (stride L), each followed by the twiddle W_m^{c k}. One CTA: 2^logC columns.
+// ------------------------------------------------------------------------------------
+template <typename T, int IN>
+__global__ void __launch_bounds__(NTHREADS) k_fwd_strided(LevelArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  c2<T>* s = reinterpret_cast<c2<T>*>(smem_raw);
+  __shared__ T red[NTHREADS / 32];
+  const int logR1 = a.logR1, logC = a.logC, logL = a.logL;
+  const int C = 1 << logC;
+  const int tile = 1 << (logR1 + logC);
+  const long long c0 = (long long)blockIdx.x << logC;
+  const int half = 1 << (logR1 - 1);
+  T dot = 0;
+  for (int e = threadIdx.x; e < tile; e += blockDim.x) {
+    const int t = e >> logC, cc = e & (C - 1);
+    const long long P = c0 + cc + ((long long)t << logL);
+    c2<T> v = mk<T>(0, 0);
+    if (IN == IN_PACK) {
+      if (t < half && P < a.N) {
+        const T xv = a.x[P], xw = a.x[a.N + 1 + P];
+        v = mk<T>(xv, xw);
+        dot = fma(a.q[P], xv, fma(a.zeta[P], xw, dot));
+      }
+    } else {
+      v = mk<T>(a.real_in[P], 0);
+    }
+    s[e] = v;
+  }
+  __syncthreads();
+  smem_dif<T, true>(s, logR1, logC, C, 1, a.twL, LOG_LMAX);
+  for (int e = threadIdx.x; e < tile; e += blockDim.x) {
+    const int t = e >> logC, cc = e & (C - 1);
+    const long long c = c0 + cc;
+    const long long P = c + ((long long)t << logL);
+    const long long kb = (long long)brev_bits((unsigned)t, logR1);
+    a.z[P] = cmul<T>(s[e], __ldg(a.twm + c * kb));
+  }
+  if (IN == IN_PACK) {
+    const T tot = block_sum<T>(dot, red);
+    if (threadIdx.x == 0) a.partials[blockIdx.x] = tot;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Contiguous blocks of L points: DIF, spectral product with the mirror block, DIT.
+// ------------------------------------------------------------------------------------
+template <typename T, int MODE, bool NS>
+__global__ void __launch_bounds__(NTHREADS) k_mid(LevelArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  c2<T>* s = reinterpret_cast<c2<T>*>(smem_raw);
+  __shared__ T red[NTHREADS / 32];
+  const int logL = a.logL;
+  const int L = 1 << logL;
+  long long b, b2;
+  if (MODE == MID_FWD || MODE == MID_FWD_REAL || MODE == MID_WHOLE) {
+    b = b2 = blockIdx.x;
+  } else {
+    const int cta = blockIdx.x;
+    if (cta < 2) {
+      b = b2 = cta;
+    } else {
+      const long long j = cta - 1;
+      const int g = 63 - __clzll(j);
+      b = j + (1LL << g);
+      b2 = 3 * (2LL << g) - 1 - b;
+    }
+  }
+  const int nseq = (b != b2) ? 2 : 1;
+  T dot = 0;
+  for (int e = threadIdx.x; e < (nseq << logL); e += blockDim.x) {
+    const int sq = e >> logL, i = e & (L - 1);
+    const long long P = (sq ? b2 : b) * (long long)L + i;
+    c2<T> v;
+    if (MODE == MID_WHOLE) {
+      v = mk<T>(0, 0);
+      if (i < a.N) {
+        const T xv = a.x[i], xw = a.x[a.N + 1 + i];
+        v = mk<T>(xv, xw);
+        dot = fma(a.q[i], xv, fma(a.zeta[i], xw, dot));
+      }
+    } else if (MODE == MID_FWD_REAL) {
+      v = mk<T>(a.real_in[P], 0);
+    } else {
+      v = a.z[P];
+    }
+    s[e] = v;
+  }
+  T dot_total = 0;
+  if (MODE == MID_WHOLE) dot_total = block_sum<T>(dot, red);
+  __syncthreads();
+  smem_dif<T, false>(s, logL, nseq - 1, 1, L, a.twL, LOG_LMAX);
+  if constexpr (MODE == MID_FWD || MODE == MID_FWD_REAL) {
+    for (int e = threadIdx.x; e < L; e += blockDim.x) a.z[b * (long long)L + e] = s[e];
+    return;
+  }
+  // spectral product
+  if (b != b2) {
+    for (int i = threadIdx.x; i < L; i += blockDim.x)
+      mac_pair<T, NS>(a, b * (long long)L + i, s + i, s + L + (L - 1 - i));
+  } else if (b == 1) {
+    for (int i = threadIdx.x; i < (L >> 1); i += blockDim.x)
+      mac_pair<T, NS>(a, (long long)L + i, s + i, s + (L - 1 - i));
+  } else {
+    for (int q = threadIdx.x; q <= (L >> 1); q += blockDim.x) {
+      int p, pp;
+      block0_pair(q, p, pp);
+      mac_pair<T, NS>(a, p, s + p, s + pp);
+    }
+  }
+  __syncthreads();
+  smem_dit<T, false>(s, logL, nseq - 1, 1, L, a.twL, LOG_LMAX);
+  if constexpr (MODE == MID_WHOLE) {
+    const T w_o = a.x[a.N];
+    for (int i = threadIdx.x; i < a.N; i += blockDim.x) epi_pair<T>(a, i, s[i].x, s[i].y, w_o);
+    if (threadIdx.x == 0) epi_middle<T>(a, dot_total, w_o);
+  } else {
+    for (int e = threadIdx.x; e < (nseq << logL); e += blockDim.x) {
+      const int sq = e >> logL, i = e & (L - 1);
+      a.z[(sq ? b2 : b) * (long long)L + i] = s[e];
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Inverse strided pass: twiddle conj(W_m^{c k}), R1-point DIT per column, epilogue.
+// ------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_inv_strided(LevelArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  c2<T>* s = reinterpret_cast<c2<T>*>(smem_raw);
+  const int logR1 = a.logR1, logC = a.logC, logL = a.logL;
+  const int C = 1 << logC;
+  const int tile = 1 << (logR1 + logC);
+  const long long c0 = (long long)blockIdx.x << logC;
+  for (int e = threadIdx.x; e < tile; e += blockDim.x) {
+    const int t = e >> logC, cc = e & (C - 1);
+    const long long c = c0 + cc;
+    const long long P = c + ((long long)t << logL);
+    const long long kb = (long long)brev_bits((unsigned)t, logR1);
+    s[e] = cmulc<T>(a.z[P], __ldg(a.twm + c * kb));
+  }
+  __syncthreads();
+  smem_dit<T, true>(s, logR1, logC, C, 1, a.twL, LOG_LMAX);
+  const T w_o = a.x[a.N];
+  const int half = 1 << (logR1 - 1);
+  for (int e = threadIdx.x; e < (half << logC); e += blockDim.x) {
+    const int t = e >> logC, cc = e & (C - 1);
+    const long long P = c0 + cc + ((long long)t << logL);
+    if (P < a.N) epi_pair<T>(a, P, s[e].x, s[e].y, w_o);
+  }
+  if (blockIdx.x == 0 && threadIdx.x < 32) {
+    T acc = 0;
+    for (int i = threadIdx.x; i < a.nparts; i += 32) acc += a.partials[i];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) epi_middle<T>(a, acc, w_o);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Spectra: stored value = (transform of the circulant column) / (2m) at every position.
+// ------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_extract_real(const c2<T>* z, T* out, long long m, T scale) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < m) out[i] = z[i].x * scale;
+}
+template <typename T>
+__global__ void k_extract_cplx(const c2<T>* z, c2<T>* out, long long m, T scale) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < m) out[i] = mk<T>(z[i].x * scale, z[i].y * scale);
+}
+
+// ------------------------------------------------------------------------------------
+// V-cycle pieces (Algorithm 2)
+// ------------------------------------------------------------------------------------
+// First pre-smoothing sweep from u = 0: u = omega D^{-1} f.
+template <typename T>
+__global__ void k_smooth_init(const T* f, T* e, long long N, T wA, T wO, T wD) {
+  const long long n = 2 * N + 1;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T w = (i < N) ? wA : ((i == N) ? wO : wD);
+    e[i] = w * f[i];
+  }
+}
+
+// Restriction I_k^{k-1}: fc[I] = (r[2I] + 2 r[2I+1] + r[2I+2]) / 4 (0-based, section 3.1).
+template <typename T>
+__global__ void k_restrict(const T* r, T* fc, long long nc) {
+  for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < nc;
+       I += (long long)gridDim.x * blockDim.x) {
+    const T a = r[2 * I], b = r[2 * I + 1], c = r[2 * I + 2];
+    fc[I] = (T)0.25 * a + (T)0.5 * b + (T)0.25 * c;
+  }
+}
+
+// Correction with P = 2 (I_k^{k-1})^T: e[2I+1] += ec[I], e[2I], e[2I+2] += ec[I] / 2.
+template <typename T>
+__global__ void k_prolong_add(T* e, const T* ec, long long nf) {
+  const long long nc = (nf - 1) / 2;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nf;
+       j += (long long)gridDim.x * blockDim.x) {
+    T add;
+    if (j & 1) {
+      add = ec[(j - 1) / 2];
+    } else {
+      const long long I = j / 2;
+      const T lo = (I - 1 >= 0) ? ec[I - 1] : (T)0;
+      const T hi = (I < nc) ? ec[I] : (T)0;
+      add = (T)0.5 * (lo + hi);
+    }
+    e[j] += add;
+  }
+}
+
+// Coarsest level: e = A_kc^{-1} f with the inverse formed on the host (n <= 255).
+template <typename T>
+__global__ void k_coarse_solve(const T* inv, const T* f, T* e, int n) {
+  __shared__ T fs[256];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) fs[i] = f[i];
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    T acc = 0;
+    for (int j = 0; j < n; ++j) acc = fma(inv[(long long)i * n + j], fs[j], acc);
+    e[i] = acc;
+  }
+}
+
+template <typename T>
+__global__ void k_axpy(T* u, const T* e, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    u[i] += e[i];
+}
+
+// Deterministic two-stage sum of squares: fixed grid, fixed order.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_sumsq_partial(const T* r, long long n,
+                                                            double* part) {
+  __shared__ double red[NTHREADS / 32];
+  double acc = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = (double)r[i];
+    acc = fma(v, v, acc);
+  }
+  const double s = block_sum<double>(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+__global__ void k_sumsq_final(const double* part, int np, double* out) {
+  double acc = 0;
+  for (int i = threadIdx.x; i < np; i += 32) acc += part[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (threadIdx.x == 0) out[0] = acc;
+}
+
+}  // namespace tpc
