@@ -34,6 +34,9 @@ METRIC = "solves/s to rel-res 1e-10 (1D SPD peridynamic system, FP64 GPU V-cycle
 UNIT = "solves/s"
 FP64_FLOP_PER_CLK_PER_SM = 4      # 2 DFMA per clock per SM (FMA-loop probe: 1.19 TFLOP/s at 1995 MHz)
 N_SMS = 152
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_mid_pair<double> launch at the finest
+# level, from ncu (profiles/k_mid_pair_fp64_N2e22.md); unknown for other sizes
+MID_TRAFFIC = {22: 268507136 + 88600832}
 
 
 def parse():
@@ -46,6 +49,8 @@ def parse():
     ap.add_argument("--delta", type=float, default=0.05)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="profiling case: set up, then 3 finest-level products, nothing timed")
     return ap.parse_args()
 
 
@@ -261,7 +266,7 @@ def run_ours(args, rank, world, local_rank):
     sm_max = clk.get("sm_max_mhz") or 2070.0
     peak = N_SMS * FP64_FLOP_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": MID_TRAFFIC.get(args.K),
                 "kernel": "k_mid<double,MID_PAIR> (finest level)",
                 "peak_source": "FP64: 152 SMs x 4 flop/clk x max SM clock (unit counts and "
                                "clocks; FMA-loop probe 1.19 TFLOP/s)",
@@ -284,8 +289,28 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_profile_case(args):
+    """A short, fixed launch sequence for profilers: setup, then three finest-level products."""
+    import torch
+
+    import paper_2202_11288_gb300 as tpc
+    n = 2 ** (args.K + 1) - 1
+    S = tpc.Solver(args.delta, 2.0 ** -args.K)
+    x = torch.tensor(uniform_pm1(n, 5), device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(3):
+        S.apply(args.K, x, y)
+    torch.cuda.synchronize()
+    assert torch.isfinite(y).all()
+    S.close()
+    print(json.dumps({"profile_case": f"N=2^{args.K}", "unknowns": n}))
+
+
 def main():
     args = parse()
+    if args.profile:
+        run_profile_case(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -21,7 +21,8 @@
  * dense factorisation (Algorithm 2: B_1 = A_1^{-1}).
  *
  * Threading: a handle is used by one host thread at a time. All device work is ordered on
- * the stream given to tpc_setup (NULL = the legacy default stream).
+ * the stream given to tpc_setup; for NULL the handle creates its own blocking stream (which
+ * is ordered with the legacy default stream), because its iterations are CUDA graphs.
  *
  * Errors: every int-returning call returns TPC_OK (0) on success, a positive status for a
  * completed call whose result is not what was asked (TPC_ENOTCONV), or a negative error.
@@ -85,7 +86,9 @@ int tpc_setup(const tpc_params* p, double delta, double h, int levels, void* cud
               tpc_handle** out);
 
 /* Solve A_K x = b to ||b - A x||_2 / ||b - A x0||_2 < tol (section 5 stopping rule) with
- * repeated V-cycles (Algorithm 2). b_dev, x_dev: device pointers to n_K doubles (caller
+ * repeated V-cycles (Algorithm 2). With precision TPC_MIXED each outer iteration runs
+ * inner_cycles FP32 V-cycle iterations on the FP64 residual (scaled to unit RMS) and adds the
+ * correction in FP64; the residual and the stopping test are always FP64. b_dev, x_dev: device pointers to n_K doubles (caller
  * owned; they may not alias). use_x0 != 0 starts from the values in x_dev, else from 0.
  * iters_out / relres_out (host pointers, may be NULL) receive the number of outer
  * iterations and the final relative residual. Blocks the host until the result is in
@@ -103,6 +106,11 @@ int tpc_solve_host(tpc_handle* H, const double* b_host, double* x_host, double t
  * matrix-vector formula after it). level in [kc, K]; x_dev, y_dev: device pointers to
  * n_level doubles, not aliasing. Stream ordered, does not block. */
 int tpc_apply(tpc_handle* H, int level, const double* x_dev, double* y_dev);
+
+/* y = A_level x in FP32 with the FP32 hierarchy of a TPC_MIXED handle (the spectra and Cross
+ * vectors are the FP64 ones rounded to FP32). Same layout and rules as tpc_apply; returns
+ * TPC_EINVAL on an FP64-only handle. */
+int tpc_apply_f32(tpc_handle* H, int level, const float* x_dev, float* y_dev);
 
 /* e = B_K r: one FP64 V-cycle of Algorithm 2 with zero initial guess on the finest level.
  * r_dev, e_dev: device pointers to n_K doubles, not aliasing. Stream ordered. */

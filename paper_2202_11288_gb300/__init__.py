@@ -24,6 +24,7 @@ TPC_SPD, TPC_NONSYM = 0, 1
 TPC_FP64, TPC_MIXED = 0, 1
 
 EXPORTED = ["tpc_default_params", "tpc_setup", "tpc_solve", "tpc_solve_host", "tpc_apply",
+            "tpc_apply_f32",
             "tpc_vcycle", "tpc_level_size", "tpc_finest_level", "tpc_coarsest_level",
             "tpc_export_level", "tpc_host_hierarchy", "tpc_time_level_kernels",
             "tpc_kernel_launches", "tpc_destroy", "tpc_last_error"]
@@ -67,6 +68,8 @@ def lib() -> ctypes.CDLL:
     L.tpc_solve_host.restype = I
     L.tpc_apply.argtypes = [P, I, P, P]
     L.tpc_apply.restype = I
+    L.tpc_apply_f32.argtypes = [P, I, P, P]
+    L.tpc_apply_f32.restype = I
     L.tpc_vcycle.argtypes = [P, P, P]
     L.tpc_vcycle.restype = I
     L.tpc_level_size.argtypes = [P, I]
@@ -183,6 +186,10 @@ def tpc_apply(H, level: int, x, y) -> None:
     _check(lib().tpc_apply(H, level, _ptr(x), _ptr(y)), H)
 
 
+def tpc_apply_f32(H, level: int, x, y) -> None:
+    _check(lib().tpc_apply_f32(H, level, _ptr(x), _ptr(y)), H)
+
+
 def tpc_vcycle(H, r, e) -> None:
     _check(lib().tpc_vcycle(H, _ptr(r), _ptr(e)), H)
 
@@ -242,6 +249,9 @@ class Solver:
 
     def apply(self, level: int, x, y) -> None:
         tpc_apply(self.handle, level, x, y)
+
+    def apply_f32(self, level: int, x, y) -> None:
+        tpc_apply_f32(self.handle, level, x, y)
 
     def vcycle(self, r, e) -> None:
         tpc_vcycle(self.handle, r, e)

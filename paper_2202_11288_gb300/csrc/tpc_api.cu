@@ -1,4 +1,8 @@
 // C ABI (include/tpcamg.h): device hierarchy, launch plans, V-cycle and solve loop.
+//
+// Two device hierarchies may exist per handle: FP64 (always; the outer residual, tpc_apply,
+// tpc_vcycle) and FP32 (precision = TPC_MIXED: the inner V-cycles). The FP32 spectra are the
+// FP64 spectra rounded once.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -16,7 +20,7 @@ const char* host_error();
 
 constexpr int LOG_WHOLE = 9;      // m <= 2^9: one CTA per product
 constexpr int LOG_R1_MAX = 11;    // strided pass: at most 2048 rows
-constexpr int LOG_TILE_MAX = 13;  // strided tile: at most 8192 complex entries (128 KB FP64)
+constexpr int LOG_TILE_MAX = 13;  // strided tile: at most 8192 complex entries
 constexpr int NORM_BLOCKS = 304;  // 2 x 152 SMs
 
 template <typename T> struct DevLevel {
@@ -37,6 +41,16 @@ template <typename T> struct DevLevel {
   c2<T>* twm = nullptr;
 };
 
+// Device hierarchy in one precision.
+template <typename T> struct Hier {
+  std::vector<DevLevel<T>> lev;  // lev[i] = level K - i
+  std::vector<T*> f, e, t;       // per level vectors (n_k)
+  c2<T>* z = nullptr;            // complex work array (m_K)
+  T* partials = nullptr;
+  c2<T>* twL = nullptr;          // W_4096^j, j < 2048
+  T* coarse_inv = nullptr;
+};
+
 }  // namespace tpc
 
 using namespace tpc;
@@ -47,18 +61,16 @@ struct tpc_handle {
   cudaStream_t stream = nullptr;
   bool own_stream = false;            // created here when the caller passed NULL
   HostHierarchy host;
-  std::vector<DevLevel<double>> lev;  // lev[i] = level K - i
-  std::vector<double*> f, e, t;       // per level vectors (n_k)
+  Hier<double> d;                     // FP64 hierarchy
+  Hier<float> s;                      // FP32 hierarchy (TPC_MIXED only)
   double* u = nullptr;                // finest solution
   double* b = nullptr;                // finest right-hand side (copy)
   double* r0 = nullptr;               // finest residual
-  c2<double>* z = nullptr;            // complex work array (m_K)
-  double* partials = nullptr;
+  float* res32 = nullptr;             // TPC_MIXED: inner residual and accumulated correction
+  float* acc32 = nullptr;
   double* sumsq_part = nullptr;
-  double* sumsq = nullptr;            // device scalar
+  double* sumsq = nullptr;            // device scalar ||r||^2
   double* sumsq_host = nullptr;       // pinned
-  c2<double>* twL = nullptr;
-  double* coarse_inv = nullptr;
   double* hb = nullptr;               // device staging for tpc_solve_host (b, x)
   double* hx = nullptr;
   cudaGraphExec_t iter_exec = nullptr;
@@ -69,8 +81,6 @@ struct tpc_handle {
 };
 
 namespace {
-
-thread_local std::string g_setup_err;
 
 int cuda_fail(tpc_handle* H, cudaError_t e, const char* what) {
   std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
@@ -83,6 +93,12 @@ int cuda_fail(tpc_handle* H, cudaError_t e, const char* what) {
   do {                                                      \
     cudaError_t e_ = (call);                                \
     if (e_ != cudaSuccess) return cuda_fail(H, e_, #call);  \
+  } while (0)
+
+#define TPC_TRY(x)                   \
+  do {                               \
+    int rc_ = (x);                   \
+    if (rc_ != TPC_OK) return rc_;   \
   } while (0)
 
 template <typename P>
@@ -100,11 +116,20 @@ int dalloc(tpc_handle* H, P** ptr, size_t count) {
   return TPC_OK;
 }
 
-#define TPC_TRY(x)                   \
-  do {                               \
-    int rc_ = (x);                   \
-    if (rc_ != TPC_OK) return rc_;   \
-  } while (0)
+// Copy FP64 host values to a device array of T (rounded once when T is float).
+template <typename T>
+int upload(tpc_handle* H, T* dst, const std::vector<double>& src) {
+  if (sizeof(T) == sizeof(double)) {
+    TPC_CUDA(H, cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(double),
+                                cudaMemcpyHostToDevice, H->stream));
+  } else {
+    std::vector<T> tmp(src.begin(), src.end());
+    TPC_CUDA(H, cudaMemcpyAsync(dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice,
+                                H->stream));
+  }
+  TPC_CUDA(H, cudaStreamSynchronize(H->stream));  // the source may go out of scope
+  return TPC_OK;
+}
 
 int grid_for(long long n) {
   long long g = (n + NTHREADS - 1) / NTHREADS;
@@ -142,8 +167,7 @@ void plan_level(DevLevel<T>& L) {
 }
 
 template <typename T>
-LevelArgs<T> level_args(const tpc_handle* H, const DevLevel<T>& L, const c2<T>* twL, c2<T>* z,
-                        T* partials) {
+LevelArgs<T> level_args(const Hier<T>& G, const DevLevel<T>& L) {
   LevelArgs<T> a{};
   a.N = L.N;
   a.logm = L.logm;
@@ -160,19 +184,18 @@ LevelArgs<T> level_args(const tpc_handle* H, const DevLevel<T>& L, const c2<T>* 
   a.zeta = L.zeta;
   a.o = L.o;
   a.twm = L.twm;
-  a.twL = twL;
-  a.z = z;
-  a.partials = partials;
+  a.twL = G.twL;
+  a.z = G.z;
+  a.partials = G.partials;
   a.nparts = L.fwd_blocks;
-  (void)H;
   return a;
 }
 
 // y = epilogue(A_k x) for one level on the handle's stream.
-template <bool NS>
-void launch_matvec(tpc_handle* H, const DevLevel<double>& L, const double* x, const double* f,
-                   double* y, int epi, bool post) {
-  LevelArgs<double> a = level_args<double>(H, L, H->twL, H->z, H->partials);
+template <typename T, bool NS>
+void launch_matvec(tpc_handle* H, const Hier<T>& G, const DevLevel<T>& L, const T* x,
+                   const T* f, T* y, int epi, bool post) {
+  LevelArgs<T> a = level_args<T>(G, L);
   a.x = x;
   a.f = f;
   a.y = y;
@@ -182,50 +205,52 @@ void launch_matvec(tpc_handle* H, const DevLevel<double>& L, const double* x, co
   a.wD = post ? L.wD_post : L.wD_pre;
   cudaStream_t s = H->stream;
   if (L.logR1 == 0) {
-    k_mid<double, MID_WHOLE, NS><<<1, NTHREADS, L.smem_mid, s>>>(a);
+    k_mid_whole<T, NS><<<1, NTHREADS, L.smem_mid, s>>>(a);
     H->launches += 1;
     return;
   }
   H->launches += 3;
-  k_fwd_strided<double, IN_PACK><<<L.fwd_blocks, NTHREADS, L.smem_strided, s>>>(a);
-  k_mid<double, MID_PAIR, NS><<<L.mid_blocks, NTHREADS, L.smem_mid, s>>>(a);
-  k_inv_strided<double><<<L.fwd_blocks, NTHREADS, L.smem_strided, s>>>(a);
+  k_fwd_strided<T, IN_PACK><<<L.fwd_blocks, NTHREADS, L.smem_strided, s>>>(a);
+  k_mid_pair<T, NS><<<L.mid_blocks, NTHREADS, L.smem_mid, s>>>(a);
+  k_inv_strided<T><<<L.fwd_blocks, NTHREADS, L.smem_strided, s>>>(a);
 }
 
-void matvec(tpc_handle* H, int li, const double* x, const double* f, double* y, int epi,
+template <typename T>
+void matvec(tpc_handle* H, const Hier<T>& G, int li, const T* x, const T* f, T* y, int epi,
             bool post) {
   if (H->prm.variant == TPC_NONSYM)
-    launch_matvec<true>(H, H->lev[li], x, f, y, epi, post);
+    launch_matvec<T, true>(H, G, G.lev[li], x, f, y, epi, post);
   else
-    launch_matvec<false>(H, H->lev[li], x, f, y, epi, post);
+    launch_matvec<T, false>(H, G, G.lev[li], x, f, y, epi, post);
 }
 
 // Algorithm 2 on level index li (level K - li) with right-hand side f (not modified).
-// Returns the buffer that holds B_k f: e[li] or t[li].
-double* enqueue_vcycle(tpc_handle* H, int li, const double* f) {
-  const DevLevel<double>& L = H->lev[li];
+// Returns the buffer that holds B_k f: G.e[li] or G.t[li].
+template <typename T>
+T* enqueue_vcycle(tpc_handle* H, Hier<T>& G, int li, const T* f) {
+  const DevLevel<T>& L = G.lev[li];
   cudaStream_t s = H->stream;
-  double* e = H->e[li];
-  double* t = H->t[li];
+  T* e = G.e[li];
+  T* t = G.t[li];
   if (L.k == H->kc) {
-    k_coarse_solve<double><<<1, 256, 0, s>>>(H->coarse_inv, f, e, (int)L.n);
+    k_coarse_solve<T><<<1, 256, 0, s>>>(G.coarse_inv, f, e, (int)L.n);
     H->launches += 1;
     return e;
   }
   H->launches += 3;  // smooth_init, restrict, prolong_add
   const int g = grid_for(L.n);
-  k_smooth_init<double><<<g, NTHREADS, 0, s>>>(f, e, L.N, L.wA_pre, L.wO_pre, L.wD_pre);
+  k_smooth_init<T><<<g, NTHREADS, 0, s>>>(f, e, L.N, L.wA_pre, L.wO_pre, L.wD_pre);
   for (int l = 1; l < H->prm.m1; ++l) {
-    matvec(H, li, e, f, t, EPI_JACOBI, false);
+    matvec<T>(H, G, li, e, f, t, EPI_JACOBI, false);
     std::swap(e, t);
   }
-  matvec(H, li, e, f, t, EPI_RESID, false);
-  const DevLevel<double>& Lc = H->lev[li + 1];
-  k_restrict<double><<<grid_for(Lc.n), NTHREADS, 0, s>>>(t, H->f[li + 1], Lc.n);
-  const double* ec = enqueue_vcycle(H, li + 1, H->f[li + 1]);
-  k_prolong_add<double><<<g, NTHREADS, 0, s>>>(e, ec, L.n);
+  matvec<T>(H, G, li, e, f, t, EPI_RESID, false);
+  const DevLevel<T>& Lc = G.lev[li + 1];
+  k_restrict<T><<<grid_for(Lc.n), NTHREADS, 0, s>>>(t, G.f[li + 1], Lc.n);
+  const T* ec = enqueue_vcycle<T>(H, G, li + 1, G.f[li + 1]);
+  k_prolong_add<T><<<g, NTHREADS, 0, s>>>(e, ec, L.n);
   for (int l = 0; l < H->prm.m2; ++l) {
-    matvec(H, li, e, f, t, EPI_JACOBI, true);
+    matvec<T>(H, G, li, e, f, t, EPI_JACOBI, true);
     std::swap(e, t);
   }
   return e;
@@ -237,34 +262,49 @@ void enqueue_sumsq(tpc_handle* H, const double* r, long long n) {
   k_sumsq_final<<<1, 32, 0, H->stream>>>(H->sumsq_part, NORM_BLOCKS, H->sumsq);
 }
 
-// One outer iteration: u += B_K r; r = b - A u; ||r||^2.
+// One outer iteration.
+//   FP64:  u += B_K r; r = b - A u; ||r||^2.
+//   mixed: f = s r in FP32 (s = sqrt(n) / ||r||); inner_cycles FP32 iterations
+//          e <- e + B_K (f - A e) from e = 0; u += e / s; then the FP64 residual and norm.
 void enqueue_iteration(tpc_handle* H) {
-  const DevLevel<double>& L = H->lev[0];
-  double* e = enqueue_vcycle(H, 0, H->r0);
-  H->launches += 1;
-  k_axpy<double><<<grid_for(L.n), NTHREADS, 0, H->stream>>>(H->u, e, L.n);
-  matvec(H, 0, H->u, H->b, H->r0, EPI_RESID, false);
-  enqueue_sumsq(H, H->r0, L.n);
+  const long long n = H->d.lev[0].n;
+  const int g = grid_for(n);
+  if (H->prm.precision == TPC_MIXED) {
+    Hier<float>& S = H->s;
+    k_to_f32_scaled<<<g, NTHREADS, 0, H->stream>>>(H->r0, S.f[0], n, H->sumsq);
+    H->launches += 1;
+    const float* ec = enqueue_vcycle<float>(H, S, 0, S.f[0]);
+    k_copy<float><<<g, NTHREADS, 0, H->stream>>>(ec, H->acc32, n);
+    H->launches += 1;
+    for (int c = 1; c < H->prm.inner_cycles; ++c) {
+      matvec<float>(H, S, 0, H->acc32, S.f[0], H->res32, EPI_RESID, false);
+      ec = enqueue_vcycle<float>(H, S, 0, H->res32);
+      k_axpy<float><<<g, NTHREADS, 0, H->stream>>>(H->acc32, ec, n);
+      H->launches += 1;
+    }
+    k_axpy_f32_scaled<<<g, NTHREADS, 0, H->stream>>>(H->u, H->acc32, n, H->sumsq);
+    H->launches += 1;
+  } else {
+    double* e = enqueue_vcycle<double>(H, H->d, 0, H->r0);
+    k_axpy<double><<<g, NTHREADS, 0, H->stream>>>(H->u, e, n);
+    H->launches += 1;
+  }
+  matvec<double>(H, H->d, 0, H->u, H->b, H->r0, EPI_RESID, false);
+  enqueue_sumsq(H, H->r0, n);
 }
 
 template <typename T, bool NS>
-int set_smem_attrs() {
+cudaError_t set_smem_attrs() {
   const int big = 1 << 17;  // 128 KB (largest tile)
+  const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e;
-  e = cudaFuncSetAttribute(k_fwd_strided<T, IN_PACK>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e != cudaSuccess) return (int)e;
-  e = cudaFuncSetAttribute(k_fwd_strided<T, IN_REAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e != cudaSuccess) return (int)e;
-  e = cudaFuncSetAttribute(k_mid<T, MID_PAIR, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e != cudaSuccess) return (int)e;
-  e = cudaFuncSetAttribute(k_mid<T, MID_WHOLE, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e != cudaSuccess) return (int)e;
-  e = cudaFuncSetAttribute(k_mid<T, MID_FWD, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e != cudaSuccess) return (int)e;
-  e = cudaFuncSetAttribute(k_mid<T, MID_FWD_REAL, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e != cudaSuccess) return (int)e;
-  e = cudaFuncSetAttribute(k_inv_strided<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  return (int)e;
+  if ((e = cudaFuncSetAttribute(k_fwd_strided<T, IN_PACK>, A, big)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_fwd_strided<T, IN_REAL>, A, big)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_mid_pair<T, NS>, A, big)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_mid_whole<T, NS>, A, big)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_mid_fwd<T>, A, big)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_mid_fwd_real<T>, A, big)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_inv_strided<T>, A, big);
 }
 
 // Circulant first column of an N x N Toeplitz generator, embedded in length m (eq. ccs3.4):
@@ -279,39 +319,38 @@ void circulant_column(const std::vector<double>& t, long long N, long long m,
   }
 }
 
-// Forward transform of a real length-m column into H->z (bit-reversed order).
-int forward_real(tpc_handle* H, const DevLevel<double>& L, const double* real_dev) {
-  LevelArgs<double> a = level_args<double>(H, L, H->twL, H->z, H->partials);
+// Forward transform (FP64) of a real length-m column into G.z (bit-reversed order).
+int forward_real(tpc_handle* H, const Hier<double>& G, const DevLevel<double>& L,
+                 const double* real_dev) {
+  LevelArgs<double> a = level_args<double>(G, L);
   a.real_in = real_dev;
   cudaStream_t s = H->stream;
   H->launches += L.logR1 ? 2 : 1;
   if (L.logR1 == 0) {
-    k_mid<double, MID_FWD_REAL, false><<<1, NTHREADS, L.smem_mid, s>>>(a);
+    k_mid_fwd_real<double><<<1, NTHREADS, L.smem_mid, s>>>(a);
   } else {
     k_fwd_strided<double, IN_REAL><<<L.fwd_blocks, NTHREADS, L.smem_strided, s>>>(a);
-    k_mid<double, MID_FWD, false><<<1 << L.logR1, NTHREADS, (size_t)sizeof(double2) << L.logL, s>>>(a);
+    k_mid_fwd<double><<<1 << L.logR1, NTHREADS, (size_t)sizeof(double2) << L.logL, s>>>(a);
   }
   TPC_CUDA(H, cudaGetLastError());
   return TPC_OK;
 }
 
-int setup_device(tpc_handle* H) {
+// Level data (plan, Cross, diagonal weights, twiddles, vectors) of hierarchy G.
+template <typename T>
+int alloc_levels(tpc_handle* H, Hier<T>& G) {
   const HostHierarchy& HH = H->host;
   const int nlev = (int)HH.lev.size();
-  H->lev.resize(nlev);
-  if (int rc = set_smem_attrs<double, false>()) return cuda_fail(H, (cudaError_t)rc, "cudaFuncSetAttribute");
-  if (int rc = set_smem_attrs<double, true>()) return cuda_fail(H, (cudaError_t)rc, "cudaFuncSetAttribute");
-  // twiddles for in-shared-memory sub-transforms
+  G.lev.resize(nlev);
   std::vector<double> tw;
   twiddles(1LL << LOG_LMAX, 1LL << (LOG_LMAX - 1), tw);
-  TPC_TRY(dalloc(H, &H->twL, (size_t)1 << (LOG_LMAX - 1)));
-  TPC_CUDA(H, cudaMemcpyAsync(H->twL, tw.data(), tw.size() * sizeof(double),
-                              cudaMemcpyHostToDevice, H->stream));
+  TPC_TRY(dalloc(H, &G.twL, (size_t)1 << (LOG_LMAX - 1)));
+  TPC_TRY(upload<T>(H, reinterpret_cast<T*>(G.twL), tw));
   long long max_m = 0;
   int max_parts = 1;
   for (int i = 0; i < nlev; ++i) {
     const LevelForm& F = HH.lev[i];
-    DevLevel<double>& L = H->lev[i];
+    DevLevel<T>& L = G.lev[i];
     L.k = F.k;
     L.N = F.N;
     L.n = 2 * F.N + 1;
@@ -325,13 +364,13 @@ int setup_device(tpc_handle* H) {
     if (L.fwd_blocks > max_parts) max_parts = L.fwd_blocks;
     const double dA = F.tA[F.N - 1], dO = F.o, dD = F.tD[F.N - 1];
     const double wpre = H->prm.omega_pre, wpost = H->prm.omega_post;
-    L.o = F.o;
-    L.wA_pre = wpre / dA;
-    L.wO_pre = wpre / dO;
-    L.wD_pre = wpre / dD;
-    L.wA_post = wpost / dA;
-    L.wO_post = wpost / dO;
-    L.wD_post = wpost / dD;
+    L.o = (T)F.o;
+    L.wA_pre = (T)(wpre / dA);
+    L.wO_pre = (T)(wpre / dO);
+    L.wD_pre = (T)(wpre / dD);
+    L.wA_post = (T)(wpost / dA);
+    L.wO_post = (T)(wpost / dO);
+    L.wD_post = (T)(wpost / dD);
     // the coarsest level only needs its inverse, unless it is also the finest (its product
     // then gives the outer residual)
     if (L.k == H->kc && i != 0) continue;
@@ -339,34 +378,57 @@ int setup_device(tpc_handle* H) {
     TPC_TRY(dalloc(H, &L.q, L.N));
     TPC_TRY(dalloc(H, &L.xi, L.N));
     TPC_TRY(dalloc(H, &L.zeta, L.N));
-    TPC_CUDA(H, cudaMemcpyAsync(L.p, F.p.data(), L.N * sizeof(double), cudaMemcpyHostToDevice, H->stream));
-    TPC_CUDA(H, cudaMemcpyAsync(L.q, F.q.data(), L.N * sizeof(double), cudaMemcpyHostToDevice, H->stream));
-    TPC_CUDA(H, cudaMemcpyAsync(L.xi, F.xi.data(), L.N * sizeof(double), cudaMemcpyHostToDevice, H->stream));
-    TPC_CUDA(H, cudaMemcpyAsync(L.zeta, F.zeta.data(), L.N * sizeof(double), cudaMemcpyHostToDevice, H->stream));
+    TPC_TRY(upload<T>(H, L.p, F.p));
+    TPC_TRY(upload<T>(H, L.q, F.q));
+    TPC_TRY(upload<T>(H, L.xi, F.xi));
+    TPC_TRY(upload<T>(H, L.zeta, F.zeta));
     if (L.logR1) {
       std::vector<double> twm;
       twiddles(L.m, L.m, twm);
       TPC_TRY(dalloc(H, &L.twm, L.m));
-      TPC_CUDA(H, cudaMemcpyAsync(L.twm, twm.data(), twm.size() * sizeof(double),
-                                  cudaMemcpyHostToDevice, H->stream));
-      TPC_CUDA(H, cudaStreamSynchronize(H->stream));
+      TPC_TRY(upload<T>(H, reinterpret_cast<T*>(L.twm), twm));
     }
-  }
-  TPC_TRY(dalloc(H, &H->z, max_m));
-  TPC_TRY(dalloc(H, &H->partials, max_parts));
-  double* staging = nullptr;
-  TPC_TRY(dalloc(H, &staging, max_m));
-  // spectra of the Toeplitz blocks, divided by 2m (the 1/m of the inverse transform and the
-  // 1/2 of the two-real-in-one-complex unpacking)
-  std::vector<double> col;
-  for (int i = 0; i < nlev; ++i) {
-    const LevelForm& F = HH.lev[i];
-    DevLevel<double>& L = H->lev[i];
-    if (L.k == H->kc && i != 0) continue;
     TPC_TRY(dalloc(H, &L.sA, L.m));
     TPC_TRY(dalloc(H, &L.sD, L.m));
     TPC_TRY(dalloc(H, &L.sB, L.m));
     if (H->prm.variant == TPC_NONSYM) TPC_TRY(dalloc(H, &L.sC, L.m));
+  }
+  TPC_TRY(dalloc(H, &G.z, max_m));
+  TPC_TRY(dalloc(H, &G.partials, max_parts));
+  const long long nc = 2 * HH.lev.back().N + 1;
+  TPC_TRY(dalloc(H, &G.coarse_inv, (size_t)(nc * nc)));
+  TPC_TRY(upload<T>(H, G.coarse_inv, HH.coarse_inv));
+  G.f.resize(nlev);
+  G.e.resize(nlev);
+  G.t.resize(nlev);
+  for (int i = 0; i < nlev; ++i) {
+    TPC_TRY(dalloc(H, &G.f[i], G.lev[i].n));
+    TPC_TRY(dalloc(H, &G.e[i], G.lev[i].n));
+    TPC_TRY(dalloc(H, &G.t[i], G.lev[i].n));
+  }
+  return TPC_OK;
+}
+
+int setup_device(tpc_handle* H) {
+  const HostHierarchy& HH = H->host;
+  const int nlev = (int)HH.lev.size();
+  const bool mixed = H->prm.precision == TPC_MIXED;
+  cudaError_t ae;
+  if ((ae = set_smem_attrs<double, false>()) != cudaSuccess) return cuda_fail(H, ae, "cudaFuncSetAttribute");
+  if ((ae = set_smem_attrs<double, true>()) != cudaSuccess) return cuda_fail(H, ae, "cudaFuncSetAttribute");
+  if ((ae = set_smem_attrs<float, false>()) != cudaSuccess) return cuda_fail(H, ae, "cudaFuncSetAttribute");
+  if ((ae = set_smem_attrs<float, true>()) != cudaSuccess) return cuda_fail(H, ae, "cudaFuncSetAttribute");
+  TPC_TRY(alloc_levels<double>(H, H->d));
+  if (mixed) TPC_TRY(alloc_levels<float>(H, H->s));
+  double* staging = nullptr;
+  TPC_TRY(dalloc(H, &staging, (size_t)H->d.lev[0].m));
+  // spectra of the Toeplitz blocks, divided by 2m (the 1/m of the inverse transform and the
+  // 1/2 of the two-real-in-one-complex unpacking); FP32 copies are the FP64 values rounded
+  std::vector<double> col;
+  for (int i = 0; i < nlev; ++i) {
+    const LevelForm& F = HH.lev[i];
+    DevLevel<double>& L = H->d.lev[i];
+    if (!L.sA) continue;
     const double scale = 1.0 / (2.0 * (double)L.m);
     const int g = (int)((L.m + 255) / 256);
     const std::vector<double>* gens[4] = {&F.tA, &F.tB, &F.tC, &F.tD};
@@ -375,33 +437,39 @@ int setup_device(tpc_handle* H) {
       circulant_column(*gens[blk], L.N, L.m, col);
       TPC_CUDA(H, cudaMemcpyAsync(staging, col.data(), L.m * sizeof(double),
                                   cudaMemcpyHostToDevice, H->stream));
-      TPC_TRY(forward_real(H, L, staging));
-      if (blk == 0) k_extract_real<double><<<g, 256, 0, H->stream>>>(H->z, L.sA, L.m, scale);
-      if (blk == 3) k_extract_real<double><<<g, 256, 0, H->stream>>>(H->z, L.sD, L.m, scale);
-      if (blk == 1) k_extract_cplx<double><<<g, 256, 0, H->stream>>>(H->z, L.sB, L.m, scale);
-      if (blk == 2) k_extract_cplx<double><<<g, 256, 0, H->stream>>>(H->z, L.sC, L.m, scale);
+      TPC_TRY(forward_real(H, H->d, L, staging));
+      if (blk == 0) k_extract_real<double><<<g, 256, 0, H->stream>>>(H->d.z, L.sA, L.m, scale);
+      if (blk == 3) k_extract_real<double><<<g, 256, 0, H->stream>>>(H->d.z, L.sD, L.m, scale);
+      if (blk == 1) k_extract_cplx<double><<<g, 256, 0, H->stream>>>(H->d.z, L.sB, L.m, scale);
+      if (blk == 2) k_extract_cplx<double><<<g, 256, 0, H->stream>>>(H->d.z, L.sC, L.m, scale);
+      H->launches += 1;
       TPC_CUDA(H, cudaGetLastError());
       TPC_CUDA(H, cudaStreamSynchronize(H->stream));  // col is reused
     }
+    if (mixed) {
+      DevLevel<float>& Ls = H->s.lev[i];
+      const int g2 = (int)((2 * L.m + 255) / 256);
+      k_round_f32<<<g, 256, 0, H->stream>>>(L.sA, Ls.sA, L.m);
+      k_round_f32<<<g, 256, 0, H->stream>>>(L.sD, Ls.sD, L.m);
+      k_round_f32<<<g2, 256, 0, H->stream>>>(reinterpret_cast<const double*>(L.sB),
+                                             reinterpret_cast<float*>(Ls.sB), 2 * L.m);
+      H->launches += 3;
+      if (L.sC) {
+        k_round_f32<<<g2, 256, 0, H->stream>>>(reinterpret_cast<const double*>(L.sC),
+                                               reinterpret_cast<float*>(Ls.sC), 2 * L.m);
+        H->launches += 1;
+      }
+      TPC_CUDA(H, cudaGetLastError());
+    }
   }
-  // coarsest inverse
-  const long long nc = 2 * HH.lev.back().N + 1;
-  TPC_TRY(dalloc(H, &H->coarse_inv, (size_t)(nc * nc)));
-  TPC_CUDA(H, cudaMemcpyAsync(H->coarse_inv, HH.coarse_inv.data(), nc * nc * sizeof(double),
-                              cudaMemcpyHostToDevice, H->stream));
-  // vectors
-  H->f.resize(nlev);
-  H->e.resize(nlev);
-  H->t.resize(nlev);
-  for (int i = 0; i < nlev; ++i) {
-    TPC_TRY(dalloc(H, &H->f[i], H->lev[i].n));
-    TPC_TRY(dalloc(H, &H->e[i], H->lev[i].n));
-    TPC_TRY(dalloc(H, &H->t[i], H->lev[i].n));
-  }
-  const long long nK = H->lev[0].n;
+  const long long nK = H->d.lev[0].n;
   TPC_TRY(dalloc(H, &H->u, nK));
   TPC_TRY(dalloc(H, &H->b, nK));
   TPC_TRY(dalloc(H, &H->r0, nK));
+  if (mixed) {
+    TPC_TRY(dalloc(H, &H->res32, nK));
+    TPC_TRY(dalloc(H, &H->acc32, nK));
+  }
   TPC_TRY(dalloc(H, &H->sumsq_part, NORM_BLOCKS));
   TPC_TRY(dalloc(H, &H->sumsq, 1));
   TPC_CUDA(H, cudaMallocHost(&H->sumsq_host, sizeof(double)));
@@ -439,13 +507,13 @@ int level_index(const tpc_handle* H, int level) {
 
 int solve_impl(tpc_handle* H, const double* b_dev, double* x_dev, double tol, int use_x0,
                int* iters_out, double* relres_out) {
-  const long long n = H->lev[0].n;
+  const long long n = H->d.lev[0].n;
   const size_t bytes = (size_t)n * sizeof(double);
   cudaStream_t s = H->stream;
   TPC_CUDA(H, cudaMemcpyAsync(H->b, b_dev, bytes, cudaMemcpyDeviceToDevice, s));
   if (use_x0) {
     TPC_CUDA(H, cudaMemcpyAsync(H->u, x_dev, bytes, cudaMemcpyDeviceToDevice, s));
-    matvec(H, 0, H->u, H->b, H->r0, EPI_RESID, false);
+    matvec<double>(H, H->d, 0, H->u, H->b, H->r0, EPI_RESID, false);
   } else {
     TPC_CUDA(H, cudaMemsetAsync(H->u, 0, bytes, s));
     TPC_CUDA(H, cudaMemcpyAsync(H->r0, H->b, bytes, cudaMemcpyDeviceToDevice, s));
@@ -458,6 +526,10 @@ int solve_impl(tpc_handle* H, const double* b_dev, double* x_dev, double tol, in
   double rel = (r0 > 0.0) ? 1.0 : 0.0;
   int it = 0;
   int status = TPC_OK;
+  if (!std::isfinite(r0)) {
+    H->err = "right-hand side or initial residual is not finite";
+    return TPC_EINVAL;
+  }
   while (rel >= tol && r0 > 0.0) {
     if (it >= H->prm.max_iters) {
       status = TPC_ENOTCONV;
@@ -482,6 +554,23 @@ int solve_impl(tpc_handle* H, const double* b_dev, double* x_dev, double tol, in
   return status;
 }
 
+template <typename T>
+int apply_impl(tpc_handle* H, Hier<T>& G, int level, const T* x_dev, T* y_dev) {
+  const int li = level_index(H, level);
+  if (li < 0 || !x_dev || !y_dev || (const void*)x_dev == (const void*)y_dev) {
+    H->err = "bad argument to tpc_apply";
+    return TPC_EINVAL;
+  }
+  if (G.lev.empty() || !G.lev[li].sA) {
+    H->err = "no product on this level (the coarsest level is held as an inverse, or the "
+             "FP32 hierarchy was not built)";
+    return TPC_EINVAL;
+  }
+  matvec<T>(H, G, li, x_dev, nullptr, y_dev, EPI_APPLY, false);
+  TPC_CUDA(H, cudaGetLastError());
+  return TPC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -493,6 +582,14 @@ int tpc_setup(const tpc_params* p, double delta, double h, int levels, void* cud
     return TPC_EINVAL;
   }
   *out = nullptr;
+  if (p->precision != TPC_FP64 && p->precision != TPC_MIXED) {
+    set_host_error("precision must be TPC_FP64 or TPC_MIXED");
+    return TPC_EINVAL;
+  }
+  if (p->precision == TPC_MIXED && (p->inner_cycles < 1 || p->inner_cycles > 32)) {
+    set_host_error("inner_cycles must be in 1..32");
+    return TPC_EINVAL;
+  }
   tpc_handle* H = new (std::nothrow) tpc_handle();
   if (!H) {
     set_host_error("host allocation failed");
@@ -500,11 +597,6 @@ int tpc_setup(const tpc_params* p, double delta, double h, int levels, void* cud
   }
   H->prm = *p;
   if (H->prm.max_iters < 0) H->prm.max_iters = 0;
-  if (p->precision != TPC_FP64) {
-    set_host_error("only precision = TPC_FP64 is implemented in this build");
-    delete H;
-    return TPC_ENOTSUP;
-  }
   std::string err;
   int rc = build_host_hierarchy(*p, delta, h, levels, H->host, err);
   if (rc != TPC_OK) {
@@ -560,7 +652,7 @@ int tpc_solve_host(tpc_handle* H, const double* b_host, double* x_host, double t
     if (H) H->err = "bad argument to tpc_solve_host";
     return TPC_EINVAL;
   }
-  const long long n = H->lev[0].n;
+  const long long n = H->d.lev[0].n;
   const size_t bytes = (size_t)n * sizeof(double);
   if (!H->hb) {
     TPC_TRY(dalloc(H, &H->hb, n));
@@ -576,18 +668,13 @@ int tpc_solve_host(tpc_handle* H, const double* b_host, double* x_host, double t
 }
 
 int tpc_apply(tpc_handle* H, int level, const double* x_dev, double* y_dev) {
-  const int li = level_index(H, level);
-  if (li < 0 || !x_dev || !y_dev || x_dev == y_dev) {
-    if (H) H->err = "bad argument to tpc_apply";
-    return TPC_EINVAL;
-  }
-  if (!H->lev[li].sA) {
-    H->err = "tpc_apply is not available on the coarsest level (held as an inverse)";
-    return TPC_EINVAL;
-  }
-  matvec(H, li, x_dev, nullptr, y_dev, EPI_APPLY, false);
-  TPC_CUDA(H, cudaGetLastError());
-  return TPC_OK;
+  if (!H) return TPC_EINVAL;
+  return apply_impl<double>(H, H->d, level, x_dev, y_dev);
+}
+
+int tpc_apply_f32(tpc_handle* H, int level, const float* x_dev, float* y_dev) {
+  if (!H) return TPC_EINVAL;
+  return apply_impl<float>(H, H->s, level, x_dev, y_dev);
 }
 
 int tpc_vcycle(tpc_handle* H, const double* r_dev, double* e_dev) {
@@ -595,8 +682,8 @@ int tpc_vcycle(tpc_handle* H, const double* r_dev, double* e_dev) {
     if (H) H->err = "bad argument to tpc_vcycle";
     return TPC_EINVAL;
   }
-  const double* res = enqueue_vcycle(H, 0, r_dev);
-  TPC_CUDA(H, cudaMemcpyAsync(e_dev, res, (size_t)H->lev[0].n * sizeof(double),
+  const double* res = enqueue_vcycle<double>(H, H->d, 0, r_dev);
+  TPC_CUDA(H, cudaMemcpyAsync(e_dev, res, (size_t)H->d.lev[0].n * sizeof(double),
                               cudaMemcpyDeviceToDevice, H->stream));
   TPC_CUDA(H, cudaGetLastError());
   return TPC_OK;
@@ -604,7 +691,7 @@ int tpc_vcycle(tpc_handle* H, const double* r_dev, double* e_dev) {
 
 long long tpc_level_size(const tpc_handle* H, int level) {
   const int li = level_index(H, level);
-  return li < 0 ? 0 : H->lev[li].n;
+  return li < 0 ? 0 : H->d.lev[li].n;
 }
 int tpc_finest_level(const tpc_handle* H) { return H ? H->K : -1; }
 int tpc_coarsest_level(const tpc_handle* H) { return H ? H->kc : -1; }
@@ -625,13 +712,13 @@ int tpc_time_level_kernels(tpc_handle* H, int level, int reps, const double* x_d
                            const double* f_dev, double* y_dev, double* ms_out) {
   const int li = level_index(H, level);
   if (li < 0 || reps < 1 || !x_dev || !f_dev || !y_dev || !ms_out || x_dev == y_dev ||
-      !H->lev[li].sA) {
+      !H->d.lev[li].sA) {
     if (H) H->err = "bad argument to tpc_time_level_kernels";
     return TPC_EINVAL;
   }
-  const DevLevel<double>& L = H->lev[li];
+  const DevLevel<double>& L = H->d.lev[li];
   const bool ns = H->prm.variant == TPC_NONSYM;
-  LevelArgs<double> a = level_args<double>(H, L, H->twL, H->z, H->partials);
+  LevelArgs<double> a = level_args<double>(H->d, L);
   a.x = x_dev;
   a.f = f_dev;
   a.y = y_dev;
@@ -650,11 +737,11 @@ int tpc_time_level_kernels(tpc_handle* H, int level, int reps, const double* x_d
       } else if (which == 2) {
         k_inv_strided<double><<<L.fwd_blocks, NTHREADS, L.smem_strided, s>>>(a);
       } else if (L.logR1 == 0) {
-        if (ns) k_mid<double, MID_WHOLE, true><<<1, NTHREADS, L.smem_mid, s>>>(a);
-        else k_mid<double, MID_WHOLE, false><<<1, NTHREADS, L.smem_mid, s>>>(a);
+        if (ns) k_mid_whole<double, true><<<1, NTHREADS, L.smem_mid, s>>>(a);
+        else k_mid_whole<double, false><<<1, NTHREADS, L.smem_mid, s>>>(a);
       } else {
-        if (ns) k_mid<double, MID_PAIR, true><<<L.mid_blocks, NTHREADS, L.smem_mid, s>>>(a);
-        else k_mid<double, MID_PAIR, false><<<L.mid_blocks, NTHREADS, L.smem_mid, s>>>(a);
+        if (ns) k_mid_pair<double, true><<<L.mid_blocks, NTHREADS, L.smem_mid, s>>>(a);
+        else k_mid_pair<double, false><<<L.mid_blocks, NTHREADS, L.smem_mid, s>>>(a);
       }
       H->launches += 1;
     }

@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(NTHREADS) k_fwd_strided(LevelArgs<T> a) {
 // Contiguous blocks of L points: DIF, spectral product with the mirror block, DIT.
 // ------------------------------------------------------------------------------------
 template <typename T, int MODE, bool NS>
-__global__ void __launch_bounds__(NTHREADS) k_mid(LevelArgs<T> a) {
+__device__ __forceinline__ void mid_body(const LevelArgs<T>& a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2<T>* s = reinterpret_cast<c2<T>*>(smem_raw);
   __shared__ T red[NTHREADS / 32];
@@ -269,6 +269,24 @@ __global__ void __launch_bounds__(NTHREADS) k_mid(LevelArgs<T> a) {
       a.z[(sq ? b2 : b) * (long long)L + i] = s[e];
     }
   }
+}
+
+// One kernel name per mode (so profilers can select them).
+template <typename T, bool NS>
+__global__ void __launch_bounds__(NTHREADS) k_mid_pair(LevelArgs<T> a) {
+  mid_body<T, MID_PAIR, NS>(a);
+}
+template <typename T, bool NS>
+__global__ void __launch_bounds__(NTHREADS) k_mid_whole(LevelArgs<T> a) {
+  mid_body<T, MID_WHOLE, NS>(a);
+}
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_mid_fwd(LevelArgs<T> a) {
+  mid_body<T, MID_FWD, false>(a);
+}
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_mid_fwd_real(LevelArgs<T> a) {
+  mid_body<T, MID_FWD_REAL, false>(a);
 }
 
 // ------------------------------------------------------------------------------------
@@ -381,6 +399,33 @@ __global__ void k_axpy(T* u, const T* e, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     u[i] += e[i];
+}
+
+template <typename T>
+__global__ void k_copy(const T* src, T* dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+// Mixed precision: the FP64 residual r enters the FP32 V-cycles scaled to unit RMS,
+// f = r * sqrt(n / ||r||^2), and the FP32 correction e comes back as u += e / that scale.
+__global__ void k_to_f32_scaled(const double* r, float* f, long long n, const double* sumsq) {
+  const double ss = sumsq[0];
+  const double s = (ss > 0.0) ? sqrt((double)n / ss) : 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    f[i] = (float)(r[i] * s);
+}
+__global__ void k_axpy_f32_scaled(double* u, const float* e, long long n, const double* sumsq) {
+  const double inv = sqrt(sumsq[0] / (double)n);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    u[i] = fma((double)e[i], inv, u[i]);
+}
+__global__ void k_round_f32(const double* in, float* out, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)in[i];
 }
 
 // Deterministic two-stage sum of squares: fixed grid, fixed order.
