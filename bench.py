@@ -39,7 +39,7 @@ FP64_FLOP_PER_CLK_PER_SM = 4      # 2 DFMA per clock per SM (FMA-loop probe: 1.1
 N_SMS = 152
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_mid_pair<double> launch at the finest
 # level, from ncu (profiles/k_mid_pair_fp64_N2e22.md); unknown for other sizes
-MID_TRAFFIC = {22: 268507136 + 88600832}
+MID_TRAFFIC = {}
 
 
 def parse():
@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="profiling case: set up, then 3 finest-level products, nothing timed")
+    ap.add_argument("--profile-solve", choices=["fp64", "mixed"], default=None,
+                    help="profiling case: set up, then one solve, nothing timed")
     return ap.parse_args()
 
 
@@ -335,10 +337,30 @@ def run_profile_case(args):
     print(json.dumps({"profile_case": f"N=2^{args.K}", "unknowns": n}))
 
 
+def run_profile_solve(args):
+    """A fixed launch sequence for profilers: setup, then one solve."""
+    import torch
+
+    import paper_2202_11288_gb300 as tpc
+    n = 2 ** (args.K + 1) - 1
+    prec = tpc.TPC_MIXED if args.profile_solve == "mixed" else tpc.TPC_FP64
+    S = tpc.Solver(args.delta, 2.0 ** -args.K, precision=prec, inner_cycles=args.inner)
+    b = torch.tensor(uniform_pm1(n, 0), device="cuda")
+    x = torch.zeros_like(b)
+    rc, it, rel = S.solve(b, x, tol=args.tol)
+    torch.cuda.synchronize()
+    S.close()
+    print(json.dumps({"profile_solve": args.profile_solve, "K": args.K, "rc": rc, "iters": it,
+                      "relres": rel}))
+
+
 def main():
     args = parse()
     if args.profile:
         run_profile_case(args)
+        return
+    if args.profile_solve:
+        run_profile_solve(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

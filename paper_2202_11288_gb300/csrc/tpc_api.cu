@@ -47,7 +47,7 @@ template <typename T> struct Hier {
   std::vector<T*> f, e, t;       // per level vectors (n_k)
   c2<T>* z = nullptr;            // complex work array (m_K)
   T* partials = nullptr;
-  c2<T>* twL = nullptr;          // W_4096^j, j < 2048
+  c2<T>* twL = nullptr;          // W_4096^j, j < 4096
   T* coarse_inv = nullptr;
 };
 
@@ -162,8 +162,8 @@ void plan_level(DevLevel<T>& L) {
     L.fwd_blocks = 1 << (logL - logC);
     L.mid_blocks = (1 << (L.logm - logL - 1)) + 1;
   }
-  L.smem_strided = L.logR1 ? ((size_t)sizeof(c2<T>) << (L.logR1 + L.logC)) : 0;
-  L.smem_mid = (size_t)sizeof(c2<T>) << (L.logL + (L.logR1 ? 1 : 0));
+  L.smem_strided = L.logR1 ? sizeof(c2<T>) * (size_t)padded_size(1 << (L.logR1 + L.logC)) : 0;
+  L.smem_mid = sizeof(c2<T>) * (size_t)padded_size(1 << (L.logL + (L.logR1 ? 1 : 0)));
 }
 
 template <typename T>
@@ -205,14 +205,14 @@ void launch_matvec(tpc_handle* H, const Hier<T>& G, const DevLevel<T>& L, const 
   a.wD = post ? L.wD_post : L.wD_pre;
   cudaStream_t s = H->stream;
   if (L.logR1 == 0) {
-    k_mid_whole<T, NS><<<1, NTHREADS, L.smem_mid, s>>>(a);
+    k_mid_whole<T, NS><<<1, FFT_THREADS, L.smem_mid, s>>>(a);
     H->launches += 1;
     return;
   }
   H->launches += 3;
-  k_fwd_strided<T, IN_PACK><<<L.fwd_blocks, NTHREADS, L.smem_strided, s>>>(a);
-  k_mid_pair<T, NS><<<L.mid_blocks, NTHREADS, L.smem_mid, s>>>(a);
-  k_inv_strided<T><<<L.fwd_blocks, NTHREADS, L.smem_strided, s>>>(a);
+  k_fwd_strided<T, IN_PACK><<<L.fwd_blocks, FFT_THREADS, L.smem_strided, s>>>(a);
+  k_mid_pair<T, NS><<<L.mid_blocks, FFT_THREADS, L.smem_mid, s>>>(a);
+  k_inv_strided<T><<<L.fwd_blocks, FFT_THREADS, L.smem_strided, s>>>(a);
 }
 
 template <typename T>
@@ -295,7 +295,7 @@ void enqueue_iteration(tpc_handle* H) {
 
 template <typename T, bool NS>
 cudaError_t set_smem_attrs() {
-  const int big = 1 << 17;  // 128 KB (largest tile)
+  const int big = 144 * 1024;  // largest padded tile: 8704 x 16 B = 136 KB
   const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_fwd_strided<T, IN_PACK>, A, big)) != cudaSuccess) return e;
@@ -327,10 +327,11 @@ int forward_real(tpc_handle* H, const Hier<double>& G, const DevLevel<double>& L
   cudaStream_t s = H->stream;
   H->launches += L.logR1 ? 2 : 1;
   if (L.logR1 == 0) {
-    k_mid_fwd_real<double><<<1, NTHREADS, L.smem_mid, s>>>(a);
+    k_mid_fwd_real<double><<<1, FFT_THREADS, L.smem_mid, s>>>(a);
   } else {
-    k_fwd_strided<double, IN_REAL><<<L.fwd_blocks, NTHREADS, L.smem_strided, s>>>(a);
-    k_mid_fwd<double><<<1 << L.logR1, NTHREADS, (size_t)sizeof(double2) << L.logL, s>>>(a);
+    k_fwd_strided<double, IN_REAL><<<L.fwd_blocks, FFT_THREADS, L.smem_strided, s>>>(a);
+    k_mid_fwd<double><<<1 << L.logR1, FFT_THREADS,
+                        sizeof(double2) * (size_t)padded_size(1 << L.logL), s>>>(a);
   }
   TPC_CUDA(H, cudaGetLastError());
   return TPC_OK;
@@ -343,8 +344,8 @@ int alloc_levels(tpc_handle* H, Hier<T>& G) {
   const int nlev = (int)HH.lev.size();
   G.lev.resize(nlev);
   std::vector<double> tw;
-  twiddles(1LL << LOG_LMAX, 1LL << (LOG_LMAX - 1), tw);
-  TPC_TRY(dalloc(H, &G.twL, (size_t)1 << (LOG_LMAX - 1)));
+  twiddles(1LL << LOG_LMAX, 1LL << LOG_LMAX, tw);
+  TPC_TRY(dalloc(H, &G.twL, (size_t)1 << LOG_LMAX));
   TPC_TRY(upload<T>(H, reinterpret_cast<T*>(G.twL), tw));
   long long max_m = 0;
   int max_parts = 1;
@@ -733,15 +734,15 @@ int tpc_time_level_kernels(tpc_handle* H, int level, int reps, const double* x_d
     for (int rep = 0; rep <= reps; ++rep) {
       if (rep == 1) cudaEventRecord(ev[0], s);
       if (which == 0) {
-        k_fwd_strided<double, IN_PACK><<<L.fwd_blocks, NTHREADS, L.smem_strided, s>>>(a);
+        k_fwd_strided<double, IN_PACK><<<L.fwd_blocks, FFT_THREADS, L.smem_strided, s>>>(a);
       } else if (which == 2) {
-        k_inv_strided<double><<<L.fwd_blocks, NTHREADS, L.smem_strided, s>>>(a);
+        k_inv_strided<double><<<L.fwd_blocks, FFT_THREADS, L.smem_strided, s>>>(a);
       } else if (L.logR1 == 0) {
-        if (ns) k_mid_whole<double, true><<<1, NTHREADS, L.smem_mid, s>>>(a);
-        else k_mid_whole<double, false><<<1, NTHREADS, L.smem_mid, s>>>(a);
+        if (ns) k_mid_whole<double, true><<<1, FFT_THREADS, L.smem_mid, s>>>(a);
+        else k_mid_whole<double, false><<<1, FFT_THREADS, L.smem_mid, s>>>(a);
       } else {
-        if (ns) k_mid_pair<double, true><<<L.mid_blocks, NTHREADS, L.smem_mid, s>>>(a);
-        else k_mid_pair<double, false><<<L.mid_blocks, NTHREADS, L.smem_mid, s>>>(a);
+        if (ns) k_mid_pair<double, true><<<L.mid_blocks, FFT_THREADS, L.smem_mid, s>>>(a);
+        else k_mid_pair<double, false><<<L.mid_blocks, FFT_THREADS, L.smem_mid, s>>>(a);
       }
       H->launches += 1;
     }

@@ -1,4 +1,5 @@
-// Device building blocks: complex arithmetic and in-shared-memory radix-2 FFT stages.
+// Device building blocks: complex arithmetic and in-shared-memory FFTs built from radix-16
+// (and smaller) register butterflies.
 //
 // Transform convention (section 3.2): forward F x = sum_j x_j W^{jk}, W = exp(-2 pi i / m),
 // computed decimation-in-frequency (natural order in, bit-reversed order out); the inverse is
@@ -6,6 +7,11 @@
 // (the 1/m is folded into the stored spectra). The product C x = ifft(fft(c) .* fft(x)) of a
 // circulant embedding (eq. ccs3.4) never needs the bit-reversal permutation: spectra are
 // stored in the same bit-reversed order as the forward output.
+//
+// A DIF step of radix R on sub-blocks of length S treats each sub-block as R rows of S/R
+// columns: for column c it takes the R entries c + t S/R, applies the R-point DIF network
+// (result slot t holds frequency bitrev_R(t)) and multiplies slot t by W_S^{c bitrev_R(t)};
+// this equals log2(R) consecutive radix-2 DIF stages. The DIT step is its exact transpose.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -38,73 +44,185 @@ template <typename T> __device__ __forceinline__ c2<T> cmulc(c2<T> a, c2<T> b) {
   return mk<T>(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
 }
 
-// Radix-2 DIF stages of length 2^logL on 2^logCount independent sequences held in shared
-// memory: element t of sequence q lives at s[q * qs + t * ts]. tw[j] = exp(-2 pi i j / Lmax),
-// j < Lmax / 2, Lmax = 2^logLmax >= 2^logL. QFAST: consecutive threads take consecutive
-// sequences (for tiles whose sequences are interleaved columns); otherwise consecutive
-// butterflies of one sequence. Ends with __syncthreads().
-template <typename T, bool QFAST>
-__device__ __forceinline__ void smem_dif(c2<T>* s, int logL, int logCount, int ts, int qs,
-                                         const c2<T>* __restrict__ tw, int logLmax) {
-  if (logL == 0) return;
-  const int nbf = 1 << (logL - 1 + logCount);
-  const int qmask = (1 << logCount) - 1;
-  const int bmask = (1 << (logL - 1)) - 1;
-  for (int logh = logL - 1; logh >= 0; --logh) {
-    const int hh = 1 << logh;
-    const int tsh = logLmax - logh - 1;
-    for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
-      int q, bb;
-      if (QFAST) {
-        q = b & qmask;
-        bb = b >> logCount;
-      } else {
-        bb = b & bmask;
-        q = b >> (logL - 1);
-      }
-      const int i = bb & (hh - 1);
-      const int t0 = ((bb >> logh) << (logh + 1)) + i;
-      c2<T>* p0 = s + q * qs + t0 * ts;
-      c2<T>* p1 = p0 + hh * ts;
-      const c2<T> u = *p0, v = *p1;
-      const c2<T> w = __ldg(tw + (i << tsh));
-      *p0 = cadd<T>(u, v);
-      *p1 = cmul<T>(csub<T>(u, v), w);
-    }
-    __syncthreads();
+// Shared-memory index with one padding slot every 16 entries (keeps the strided accesses of
+// the butterfly steps on distinct banks).
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int padded_size(int n) { return n + (n >> 4); }
+
+// x * exp(-2 pi i e / 16) for a compile-time e in [0, 16). The constants are cos and sin of
+// multiples of pi/8: cos(pi/8) = sqrt(2 + sqrt 2) / 2, sin(pi/8) = sqrt(2 - sqrt 2) / 2,
+// cos(pi/4) = sqrt(2) / 2.
+template <typename T, int E>
+__device__ __forceinline__ c2<T> mul_w16(c2<T> x) {
+  constexpr double C1 = 0.92387953251128675613, S1 = 0.38268343236508977173;
+  constexpr double H = 0.70710678118654752440;
+  if constexpr (E == 0) return x;
+  else if constexpr (E == 4) return mk<T>(x.y, -x.x);           // * (-i)
+  else if constexpr (E == 8) return mk<T>(-x.x, -x.y);          // * (-1)
+  else if constexpr (E == 12) return mk<T>(-x.y, x.x);          // * (+i)
+  else if constexpr (E == 2) return mk<T>((T)H * (x.x + x.y), (T)H * (x.y - x.x));
+  else if constexpr (E == 6) return mk<T>((T)H * (x.y - x.x), -(T)H * (x.x + x.y));
+  else if constexpr (E == 10) return mk<T>(-(T)H * (x.x + x.y), (T)H * (x.x - x.y));
+  else if constexpr (E == 14) return mk<T>((T)H * (x.x - x.y), (T)H * (x.x + x.y));
+  else {
+    // general angle: w = (cos, -sin) of 2 pi E / 16
+    constexpr double wr = (E == 1) ? C1 : (E == 3) ? S1 : (E == 5) ? -S1 : (E == 7) ? -C1
+                        : (E == 9) ? -C1 : (E == 11) ? -S1 : (E == 13) ? S1 : C1;
+    constexpr double wi = (E == 1) ? -S1 : (E == 3) ? -C1 : (E == 5) ? -C1 : (E == 7) ? -S1
+                        : (E == 9) ? S1 : (E == 11) ? C1 : (E == 13) ? C1 : S1;
+    return cmul<T>(x, mk<T>((T)wr, (T)wi));
   }
 }
 
-// The transposed (inverse) network: radix-2 DIT stages with conjugate twiddles,
-// bit-reversed in, natural out, unnormalised. Ends with __syncthreads().
+// R-point DIF network on registers: natural order in, slot t = frequency bitrev_R(t) out.
+// Butterfly (B + I, B + I + H) of the stage with half-size H uses W_{2H}^I = W_16^{8 I / H}.
+template <typename T, int H, int B, int I>
+__device__ __forceinline__ void dif_bfly(c2<T>* v) {
+  if constexpr (I < H) {
+    const c2<T> u = v[B + I], w = v[B + I + H];
+    v[B + I] = cadd<T>(u, w);
+    v[B + I + H] = mul_w16<T, (8 * I) / H>(csub<T>(u, w));
+    dif_bfly<T, H, B, I + 1>(v);
+  }
+}
+template <typename T, int R, int H, int B>
+__device__ __forceinline__ void dif_blocks(c2<T>* v) {
+  if constexpr (B < R) {
+    dif_bfly<T, H, B, 0>(v);
+    dif_blocks<T, R, H, B + 2 * H>(v);
+  }
+}
+template <typename T, int R, int H = R / 2>
+__device__ __forceinline__ void reg_dif_stage(c2<T>* v) {
+  if constexpr (H >= 1) {
+    dif_blocks<T, R, H, 0>(v);
+    reg_dif_stage<T, R, H / 2>(v);
+  }
+}
+
+// Transposed network: slot t = frequency bitrev_R(t) in, natural order out, conjugate
+// twiddles (the inverse up to a factor R).
+template <typename T, int H, int B, int I>
+__device__ __forceinline__ void dit_bfly(c2<T>* v) {
+  if constexpr (I < H) {
+    const c2<T> u = v[B + I];
+    const c2<T> w = mul_w16<T, (16 - (8 * I) / H) % 16>(v[B + I + H]);
+    v[B + I] = cadd<T>(u, w);
+    v[B + I + H] = csub<T>(u, w);
+    dit_bfly<T, H, B, I + 1>(v);
+  }
+}
+template <typename T, int R, int H, int B>
+__device__ __forceinline__ void dit_blocks(c2<T>* v) {
+  if constexpr (B < R) {
+    dit_bfly<T, H, B, 0>(v);
+    dit_blocks<T, R, H, B + 2 * H>(v);
+  }
+}
+template <typename T, int R, int H = 1>
+__device__ __forceinline__ void reg_dit_stage(c2<T>* v) {
+  if constexpr (H < R) {
+    dit_blocks<T, R, H, 0>(v);
+    reg_dit_stage<T, R, H * 2>(v);
+  }
+}
+
+template <int R> __device__ __forceinline__ int brev_r(int t) {
+  return (int)(__brev((unsigned)t) >> (32 - (R == 16 ? 4 : R == 8 ? 3 : R == 4 ? 2 : 1)));
+}
+
+// One radix-R step on all sub-blocks of length 2^logS of 2^logCount sequences of length
+// 2^logL held in shared memory (element t of sequence q at pad16(q * qs + t * ts)).
+// tw[j] = exp(-2 pi i j / Lmax), j < Lmax = 2^logLmax. QFAST: consecutive threads take
+// consecutive sequences first (interleaved column tiles), else consecutive columns.
+template <typename T, int R, bool QFAST, bool INV>
+__device__ __forceinline__ void fft_step(c2<T>* s, int logS, int logL, int logCount, int ts,
+                                         int qs, const c2<T>* __restrict__ tw, int logLmax) {
+  constexpr int logR = (R == 16) ? 4 : (R == 8) ? 3 : (R == 4) ? 2 : 1;
+  const int logCols = logS - logR;
+  const int logSb = logL - logS;
+  const int ntask = 1 << (logCount + logSb + logCols);
+  const int twsh = logLmax - logS;
+  for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
+    int q, c, sb;
+    if (QFAST) {
+      q = task & ((1 << logCount) - 1);
+      const int rest = task >> logCount;
+      c = rest & ((1 << logCols) - 1);
+      sb = rest >> logCols;
+    } else {
+      c = task & ((1 << logCols) - 1);
+      const int rest = task >> logCols;
+      sb = rest & ((1 << logSb) - 1);
+      q = rest >> logSb;
+    }
+    const int base = q * qs + ((sb << logS) + c) * ts;
+    const int step = ts << logCols;
+    c2<T> v[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) v[t] = s[pad16(base + t * step)];
+    if (INV) {
+      if (logCols > 0) {
+#pragma unroll
+        for (int t = 1; t < R; ++t) v[t] = cmulc<T>(v[t], __ldg(tw + ((c * brev_r<R>(t)) << twsh)));
+      }
+      reg_dit_stage<T, R>(v);
+    } else {
+      reg_dif_stage<T, R>(v);
+      if (logCols > 0) {
+#pragma unroll
+        for (int t = 1; t < R; ++t) v[t] = cmul<T>(v[t], __ldg(tw + ((c * brev_r<R>(t)) << twsh)));
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < R; ++t) s[pad16(base + t * step)] = v[t];
+  }
+}
+
+// Radices of the steps of a 2^logL transform: as many 16s as fit, then the remainder.
+__device__ __forceinline__ int step_radix_log(int logL, int idx) {
+  const int n16 = logL >> 2;
+  return idx < n16 ? 4 : (logL & 3);
+}
+__device__ __forceinline__ int num_steps(int logL) { return (logL >> 2) + ((logL & 3) ? 1 : 0); }
+
+template <typename T, bool QFAST, bool INV>
+__device__ __forceinline__ void dispatch_step(int r, c2<T>* s, int logS, int logL, int logCount,
+                                              int ts, int qs, const c2<T>* tw, int logLmax) {
+  switch (r) {
+    case 4: fft_step<T, 16, QFAST, INV>(s, logS, logL, logCount, ts, qs, tw, logLmax); break;
+    case 3: fft_step<T, 8, QFAST, INV>(s, logS, logL, logCount, ts, qs, tw, logLmax); break;
+    case 2: fft_step<T, 4, QFAST, INV>(s, logS, logL, logCount, ts, qs, tw, logLmax); break;
+    default: fft_step<T, 2, QFAST, INV>(s, logS, logL, logCount, ts, qs, tw, logLmax); break;
+  }
+}
+
+// Forward DIF of length 2^logL on 2^logCount sequences in shared memory (natural in,
+// bit-reversed out). Ends with __syncthreads().
+template <typename T, bool QFAST>
+__device__ __forceinline__ void smem_dif(c2<T>* s, int logL, int logCount, int ts, int qs,
+                                         const c2<T>* __restrict__ tw, int logLmax) {
+  int logS = logL;
+  const int ns = num_steps(logL);
+  for (int k = 0; k < ns; ++k) {
+    const int r = step_radix_log(logL, k);
+    dispatch_step<T, QFAST, false>(r, s, logS, logL, logCount, ts, qs, tw, logLmax);
+    __syncthreads();
+    logS -= r;
+  }
+}
+
+// Inverse: the DIF steps transposed, in reverse order (bit-reversed in, natural out,
+// unnormalised). Ends with __syncthreads().
 template <typename T, bool QFAST>
 __device__ __forceinline__ void smem_dit(c2<T>* s, int logL, int logCount, int ts, int qs,
                                          const c2<T>* __restrict__ tw, int logLmax) {
-  if (logL == 0) return;
-  const int nbf = 1 << (logL - 1 + logCount);
-  const int qmask = (1 << logCount) - 1;
-  const int bmask = (1 << (logL - 1)) - 1;
-  for (int logh = 0; logh < logL; ++logh) {
-    const int hh = 1 << logh;
-    const int tsh = logLmax - logh - 1;
-    for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
-      int q, bb;
-      if (QFAST) {
-        q = b & qmask;
-        bb = b >> logCount;
-      } else {
-        bb = b & bmask;
-        q = b >> (logL - 1);
-      }
-      const int i = bb & (hh - 1);
-      const int t0 = ((bb >> logh) << (logh + 1)) + i;
-      c2<T>* p0 = s + q * qs + t0 * ts;
-      c2<T>* p1 = p0 + hh * ts;
-      const c2<T> u = *p0;
-      const c2<T> v = cmulc<T>(*p1, __ldg(tw + (i << tsh)));
-      *p0 = cadd<T>(u, v);
-      *p1 = csub<T>(u, v);
-    }
+  const int ns = num_steps(logL);
+  int logS = 0;
+  for (int k = ns - 1; k >= 0; --k) {
+    const int r = step_radix_log(logL, k);
+    logS += r;
+    dispatch_step<T, QFAST, true>(r, s, logS, logL, logCount, ts, qs, tw, logLmax);
     __syncthreads();
   }
 }

@@ -29,7 +29,8 @@
 namespace tpc {
 
 constexpr int LOG_LMAX = 12;        // longest in-shared-memory sub-transform (4096 points)
-constexpr int NTHREADS = 256;
+constexpr int NTHREADS = 256;       // elementwise kernels
+constexpr int FFT_THREADS = 512;    // transform kernels (one radix-16 task per thread at 8192)
 
 enum Epi { EPI_APPLY = 0, EPI_RESID = 1, EPI_JACOBI = 2 };
 enum MidMode { MID_PAIR = 0, MID_WHOLE = 1, MID_FWD = 2, MID_FWD_REAL = 3 };
@@ -49,7 +50,7 @@ template <typename T> struct LevelArgs {
   T o;
   T wA, wO, wD;          // omega / diagonal, per segment (damped Jacobi, eq. 7)
   const c2<T>* twm;      // W_m^j, j < m (strided pipelines only)
-  const c2<T>* twL;      // W_{4096}^j, j < 2048
+  const c2<T>* twL;      // W_{4096}^j, j < 4096
   // per call
   const T* x;            // operand u (n_k)
   const T* f;            // right-hand side for EPI_RESID / EPI_JACOBI
@@ -151,10 +152,10 @@ __device__ __forceinline__ void block0_pair(int q, int& p, int& pp) {
 // columns (stride L), each followed by the twiddle W_m^{c k}. One CTA: 2^logC columns.
 // ------------------------------------------------------------------------------------
 template <typename T, int IN>
-__global__ void __launch_bounds__(NTHREADS) k_fwd_strided(LevelArgs<T> a) {
+__global__ void __launch_bounds__(FFT_THREADS) k_fwd_strided(LevelArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2<T>* s = reinterpret_cast<c2<T>*>(smem_raw);
-  __shared__ T red[NTHREADS / 32];
+  __shared__ T red[FFT_THREADS / 32];
   const int logR1 = a.logR1, logC = a.logC, logL = a.logL;
   const int C = 1 << logC;
   const int tile = 1 << (logR1 + logC);
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(NTHREADS) k_fwd_strided(LevelArgs<T> a) {
     } else {
       v = mk<T>(a.real_in[P], 0);
     }
-    s[e] = v;
+    s[pad16(e)] = v;
   }
   __syncthreads();
   smem_dif<T, true>(s, logR1, logC, C, 1, a.twL, LOG_LMAX);
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(NTHREADS) k_fwd_strided(LevelArgs<T> a) {
     const long long c = c0 + cc;
     const long long P = c + ((long long)t << logL);
     const long long kb = (long long)brev_bits((unsigned)t, logR1);
-    a.z[P] = cmul<T>(s[e], __ldg(a.twm + c * kb));
+    a.z[P] = cmul<T>(s[pad16(e)], __ldg(a.twm + c * kb));
   }
   if (IN == IN_PACK) {
     const T tot = block_sum<T>(dot, red);
@@ -198,7 +199,7 @@ template <typename T, int MODE, bool NS>
 __device__ __forceinline__ void mid_body(const LevelArgs<T>& a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2<T>* s = reinterpret_cast<c2<T>*>(smem_raw);
-  __shared__ T red[NTHREADS / 32];
+  __shared__ T red[FFT_THREADS / 32];
   const int logL = a.logL;
   const int L = 1 << logL;
   long long b, b2;
@@ -233,59 +234,62 @@ __device__ __forceinline__ void mid_body(const LevelArgs<T>& a) {
     } else {
       v = a.z[P];
     }
-    s[e] = v;
+    s[pad16(e)] = v;
   }
   T dot_total = 0;
   if (MODE == MID_WHOLE) dot_total = block_sum<T>(dot, red);
   __syncthreads();
   smem_dif<T, false>(s, logL, nseq - 1, 1, L, a.twL, LOG_LMAX);
   if constexpr (MODE == MID_FWD || MODE == MID_FWD_REAL) {
-    for (int e = threadIdx.x; e < L; e += blockDim.x) a.z[b * (long long)L + e] = s[e];
+    for (int e = threadIdx.x; e < L; e += blockDim.x) a.z[b * (long long)L + e] = s[pad16(e)];
     return;
   }
   // spectral product
   if (b != b2) {
     for (int i = threadIdx.x; i < L; i += blockDim.x)
-      mac_pair<T, NS>(a, b * (long long)L + i, s + i, s + L + (L - 1 - i));
+      mac_pair<T, NS>(a, b * (long long)L + i, s + pad16(i), s + pad16(L + (L - 1 - i)));
   } else if (b == 1) {
     for (int i = threadIdx.x; i < (L >> 1); i += blockDim.x)
-      mac_pair<T, NS>(a, (long long)L + i, s + i, s + (L - 1 - i));
+      mac_pair<T, NS>(a, (long long)L + i, s + pad16(i), s + pad16(L - 1 - i));
   } else {
     for (int q = threadIdx.x; q <= (L >> 1); q += blockDim.x) {
       int p, pp;
       block0_pair(q, p, pp);
-      mac_pair<T, NS>(a, p, s + p, s + pp);
+      mac_pair<T, NS>(a, p, s + pad16(p), s + pad16(pp));
     }
   }
   __syncthreads();
   smem_dit<T, false>(s, logL, nseq - 1, 1, L, a.twL, LOG_LMAX);
   if constexpr (MODE == MID_WHOLE) {
     const T w_o = a.x[a.N];
-    for (int i = threadIdx.x; i < a.N; i += blockDim.x) epi_pair<T>(a, i, s[i].x, s[i].y, w_o);
+    for (int i = threadIdx.x; i < a.N; i += blockDim.x) {
+      const c2<T> y = s[pad16(i)];
+      epi_pair<T>(a, i, y.x, y.y, w_o);
+    }
     if (threadIdx.x == 0) epi_middle<T>(a, dot_total, w_o);
   } else {
     for (int e = threadIdx.x; e < (nseq << logL); e += blockDim.x) {
       const int sq = e >> logL, i = e & (L - 1);
-      a.z[(sq ? b2 : b) * (long long)L + i] = s[e];
+      a.z[(sq ? b2 : b) * (long long)L + i] = s[pad16(e)];
     }
   }
 }
 
 // One kernel name per mode (so profilers can select them).
 template <typename T, bool NS>
-__global__ void __launch_bounds__(NTHREADS) k_mid_pair(LevelArgs<T> a) {
+__global__ void __launch_bounds__(FFT_THREADS) k_mid_pair(LevelArgs<T> a) {
   mid_body<T, MID_PAIR, NS>(a);
 }
 template <typename T, bool NS>
-__global__ void __launch_bounds__(NTHREADS) k_mid_whole(LevelArgs<T> a) {
+__global__ void __launch_bounds__(FFT_THREADS) k_mid_whole(LevelArgs<T> a) {
   mid_body<T, MID_WHOLE, NS>(a);
 }
 template <typename T>
-__global__ void __launch_bounds__(NTHREADS) k_mid_fwd(LevelArgs<T> a) {
+__global__ void __launch_bounds__(FFT_THREADS) k_mid_fwd(LevelArgs<T> a) {
   mid_body<T, MID_FWD, false>(a);
 }
 template <typename T>
-__global__ void __launch_bounds__(NTHREADS) k_mid_fwd_real(LevelArgs<T> a) {
+__global__ void __launch_bounds__(FFT_THREADS) k_mid_fwd_real(LevelArgs<T> a) {
   mid_body<T, MID_FWD_REAL, false>(a);
 }
 
@@ -293,7 +297,7 @@ __global__ void __launch_bounds__(NTHREADS) k_mid_fwd_real(LevelArgs<T> a) {
 // Inverse strided pass: twiddle conj(W_m^{c k}), R1-point DIT per column, epilogue.
 // ------------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(NTHREADS) k_inv_strided(LevelArgs<T> a) {
+__global__ void __launch_bounds__(FFT_THREADS) k_inv_strided(LevelArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2<T>* s = reinterpret_cast<c2<T>*>(smem_raw);
   const int logR1 = a.logR1, logC = a.logC, logL = a.logL;
@@ -305,7 +309,7 @@ __global__ void __launch_bounds__(NTHREADS) k_inv_strided(LevelArgs<T> a) {
     const long long c = c0 + cc;
     const long long P = c + ((long long)t << logL);
     const long long kb = (long long)brev_bits((unsigned)t, logR1);
-    s[e] = cmulc<T>(a.z[P], __ldg(a.twm + c * kb));
+    s[pad16(e)] = cmulc<T>(a.z[P], __ldg(a.twm + c * kb));
   }
   __syncthreads();
   smem_dit<T, true>(s, logR1, logC, C, 1, a.twL, LOG_LMAX);
@@ -314,7 +318,10 @@ __global__ void __launch_bounds__(NTHREADS) k_inv_strided(LevelArgs<T> a) {
   for (int e = threadIdx.x; e < (half << logC); e += blockDim.x) {
     const int t = e >> logC, cc = e & (C - 1);
     const long long P = c0 + cc + ((long long)t << logL);
-    if (P < a.N) epi_pair<T>(a, P, s[e].x, s[e].y, w_o);
+    if (P < a.N) {
+      const c2<T> y = s[pad16(e)];
+      epi_pair<T>(a, P, y.x, y.y, w_o);
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x < 32) {
     T acc = 0;
