@@ -191,10 +191,19 @@ LevelArgs<T> level_args(const Hier<T>& G, const DevLevel<T>& L) {
   return a;
 }
 
-// y = epilogue(A_k x) for one level on the handle's stream.
+// How the operand of a product is formed while it is loaded (see Pro in tpc_kernels.cuh).
+template <typename T> struct Prologue {
+  int mode = PRO_NONE;
+  T* xout = nullptr;        // operand stored here (PRO_SMOOTH / RESTRICT / PROLONG)
+  T* fout = nullptr;        // restricted right-hand side stored here (PRO_RESTRICT)
+  const T* rfine = nullptr;
+  const T* ec = nullptr;
+};
+
+// y = epilogue(A_k u) for one level on the handle's stream, u = x or formed by the prologue.
 template <typename T, bool NS>
 void launch_matvec(tpc_handle* H, const Hier<T>& G, const DevLevel<T>& L, const T* x,
-                   const T* f, T* y, int epi, bool post) {
+                   const T* f, T* y, int epi, bool post, const Prologue<T>& pro) {
   LevelArgs<T> a = level_args<T>(G, L);
   a.x = x;
   a.f = f;
@@ -203,54 +212,84 @@ void launch_matvec(tpc_handle* H, const Hier<T>& G, const DevLevel<T>& L, const 
   a.wA = post ? L.wA_post : L.wA_pre;
   a.wO = post ? L.wO_post : L.wO_pre;
   a.wD = post ? L.wD_post : L.wD_pre;
+  a.pro = pro.mode;
+  a.pA = L.wA_pre;
+  a.pO = L.wO_pre;
+  a.pD = L.wD_pre;
+  a.xout = pro.xout;
+  a.fout = pro.fout;
+  a.rfine = pro.rfine;
+  a.ec = pro.ec;
   cudaStream_t s = H->stream;
   if (L.logR1 == 0) {
-    k_mid_whole<T, NS><<<1, FFT_THREADS, L.smem_mid, s>>>(a);
+    k_mid_whole<T, NS><<<1, fft_threads<T>(), L.smem_mid, s>>>(a);
     H->launches += 1;
     return;
   }
   H->launches += 3;
-  k_fwd_strided<T, IN_PACK><<<L.fwd_blocks, FFT_THREADS, L.smem_strided, s>>>(a);
-  k_mid_pair<T, NS><<<L.mid_blocks, FFT_THREADS, L.smem_mid, s>>>(a);
-  k_inv_strided<T><<<L.fwd_blocks, FFT_THREADS, L.smem_strided, s>>>(a);
+  k_fwd_strided<T, IN_PACK><<<L.fwd_blocks, fft_threads<T>(), L.smem_strided, s>>>(a);
+  k_mid_pair<T, NS><<<L.mid_blocks, fft_threads<T>(), L.smem_mid, s>>>(a);
+  k_inv_strided<T><<<L.fwd_blocks, fft_threads<T>(), L.smem_strided, s>>>(a);
 }
 
 template <typename T>
 void matvec(tpc_handle* H, const Hier<T>& G, int li, const T* x, const T* f, T* y, int epi,
-            bool post) {
+            bool post, const Prologue<T>& pro = Prologue<T>()) {
   if (H->prm.variant == TPC_NONSYM)
-    launch_matvec<T, true>(H, G, G.lev[li], x, f, y, epi, post);
+    launch_matvec<T, true>(H, G, G.lev[li], x, f, y, epi, post, pro);
   else
-    launch_matvec<T, false>(H, G, G.lev[li], x, f, y, epi, post);
+    launch_matvec<T, false>(H, G, G.lev[li], x, f, y, epi, post, pro);
 }
 
-// Algorithm 2 on level index li (level K - li) with right-hand side f (not modified).
+// Algorithm 2 on level index li (level K - li). The right-hand side is f_top (top level) or
+// the restriction of rfine, the residual of the finer level (stored in G.f[li] on the way).
 // Returns the buffer that holds B_k f: G.e[li] or G.t[li].
+//   pre-smoothing:  the first sweep from 0 is the prologue of the first product
+//                   (u = omega D^{-1} f, after restricting f when the level is not the top);
+//   residual:       epilogue of the last pre-smoothing product (f - A u), restricted by the
+//                   next level's prologue;
+//   correction:     prologue of the first post-smoothing product (u + I_{k-1}^k e_c).
 template <typename T>
-T* enqueue_vcycle(tpc_handle* H, Hier<T>& G, int li, const T* f) {
+T* enqueue_vcycle(tpc_handle* H, Hier<T>& G, int li, const T* f_top, const T* rfine) {
   const DevLevel<T>& L = G.lev[li];
   cudaStream_t s = H->stream;
   T* e = G.e[li];
   T* t = G.t[li];
+  const T* f = rfine ? G.f[li] : f_top;
   if (L.k == H->kc) {
-    k_coarse_solve<T><<<1, 256, 0, s>>>(G.coarse_inv, f, e, (int)L.n);
+    if (rfine) {
+      k_coarse_solve<T><<<1, 256, 0, s>>>(G.coarse_inv, G.f[li], rfine, e, (int)L.n);
+    } else {
+      k_coarse_solve<T><<<1, 256, 0, s>>>(G.coarse_inv, const_cast<T*>(f_top), nullptr, e,
+                                         (int)L.n);
+    }
     H->launches += 1;
     return e;
   }
-  H->launches += 3;  // smooth_init, restrict, prolong_add
-  const int g = grid_for(L.n);
-  k_smooth_init<T><<<g, NTHREADS, 0, s>>>(f, e, L.N, L.wA_pre, L.wO_pre, L.wD_pre);
+  Prologue<T> first;
+  first.mode = rfine ? PRO_RESTRICT : PRO_SMOOTH;
+  first.xout = e;
+  first.fout = G.f[li];
+  first.rfine = rfine;
   for (int l = 1; l < H->prm.m1; ++l) {
-    matvec<T>(H, G, li, e, f, t, EPI_JACOBI, false);
+    matvec<T>(H, G, li, e, f, t, EPI_JACOBI, false, first);
+    first = Prologue<T>();
     std::swap(e, t);
   }
-  matvec<T>(H, G, li, e, f, t, EPI_RESID, false);
-  const DevLevel<T>& Lc = G.lev[li + 1];
-  k_restrict<T><<<grid_for(Lc.n), NTHREADS, 0, s>>>(t, G.f[li + 1], Lc.n);
-  const T* ec = enqueue_vcycle<T>(H, G, li + 1, G.f[li + 1]);
-  k_prolong_add<T><<<g, NTHREADS, 0, s>>>(e, ec, L.n);
+  matvec<T>(H, G, li, e, f, t, EPI_RESID, false, first);
+  const T* ec = enqueue_vcycle<T>(H, G, li + 1, nullptr, t);
+  if (H->prm.m2 == 0) {
+    k_prolong_add<T><<<grid_for(L.n), NTHREADS, 0, s>>>(e, ec, L.n);
+    H->launches += 1;
+    return e;
+  }
+  Prologue<T> corr;
+  corr.mode = PRO_PROLONG;
+  corr.xout = e;
+  corr.ec = ec;
   for (int l = 0; l < H->prm.m2; ++l) {
-    matvec<T>(H, G, li, e, f, t, EPI_JACOBI, true);
+    matvec<T>(H, G, li, e, f, t, EPI_JACOBI, true, corr);
+    corr = Prologue<T>();
     std::swap(e, t);
   }
   return e;
@@ -273,19 +312,19 @@ void enqueue_iteration(tpc_handle* H) {
     Hier<float>& S = H->s;
     k_to_f32_scaled<<<g, NTHREADS, 0, H->stream>>>(H->r0, S.f[0], n, H->sumsq);
     H->launches += 1;
-    const float* ec = enqueue_vcycle<float>(H, S, 0, S.f[0]);
+    const float* ec = enqueue_vcycle<float>(H, S, 0, S.f[0], nullptr);
     k_copy<float><<<g, NTHREADS, 0, H->stream>>>(ec, H->acc32, n);
     H->launches += 1;
     for (int c = 1; c < H->prm.inner_cycles; ++c) {
       matvec<float>(H, S, 0, H->acc32, S.f[0], H->res32, EPI_RESID, false);
-      ec = enqueue_vcycle<float>(H, S, 0, H->res32);
+      ec = enqueue_vcycle<float>(H, S, 0, H->res32, nullptr);
       k_axpy<float><<<g, NTHREADS, 0, H->stream>>>(H->acc32, ec, n);
       H->launches += 1;
     }
     k_axpy_f32_scaled<<<g, NTHREADS, 0, H->stream>>>(H->u, H->acc32, n, H->sumsq);
     H->launches += 1;
   } else {
-    double* e = enqueue_vcycle<double>(H, H->d, 0, H->r0);
+    double* e = enqueue_vcycle<double>(H, H->d, 0, H->r0, nullptr);
     k_axpy<double><<<g, NTHREADS, 0, H->stream>>>(H->u, e, n);
     H->launches += 1;
   }
@@ -385,8 +424,17 @@ int alloc_levels(tpc_handle* H, Hier<T>& G) {
     TPC_TRY(upload<T>(H, L.zeta, F.zeta));
     if (L.logR1) {
       std::vector<double> twm;
-      twiddles(L.m, L.m, twm);
-      TPC_TRY(dalloc(H, &L.twm, L.m));
+      if (sizeof(T) == sizeof(double)) {
+        twiddles(L.m, L.m, twm);  // W_m^j, j < m
+      } else {
+        // W_m^j for j < 4096, then W_m^{4096 j} = W_{m/4096}^j for j < max(1, m / 4096)
+        std::vector<double> hi;
+        twiddles(L.m, TW_LO, twm);
+        if (L.m > TW_LO) twiddles(L.m / TW_LO, L.m / TW_LO, hi);
+        else hi = {1.0, 0.0};
+        twm.insert(twm.end(), hi.begin(), hi.end());
+      }
+      TPC_TRY(dalloc(H, &L.twm, twm.size() / 2));
       TPC_TRY(upload<T>(H, reinterpret_cast<T*>(L.twm), twm));
     }
     TPC_TRY(dalloc(H, &L.sA, L.m));
@@ -683,7 +731,7 @@ int tpc_vcycle(tpc_handle* H, const double* r_dev, double* e_dev) {
     if (H) H->err = "bad argument to tpc_vcycle";
     return TPC_EINVAL;
   }
-  const double* res = enqueue_vcycle<double>(H, H->d, 0, r_dev);
+  const double* res = enqueue_vcycle<double>(H, H->d, 0, r_dev, nullptr);
   TPC_CUDA(H, cudaMemcpyAsync(e_dev, res, (size_t)H->d.lev[0].n * sizeof(double),
                               cudaMemcpyDeviceToDevice, H->stream));
   TPC_CUDA(H, cudaGetLastError());

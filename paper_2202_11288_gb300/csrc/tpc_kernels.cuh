@@ -30,9 +30,21 @@ namespace tpc {
 
 constexpr int LOG_LMAX = 12;        // longest in-shared-memory sub-transform (4096 points)
 constexpr int NTHREADS = 256;       // elementwise kernels
-constexpr int FFT_THREADS = 512;    // transform kernels (one radix-16 task per thread at 8192)
+constexpr int FFT_THREADS = 512;    // upper bound of the transform kernels' block size
+// Transform kernels: FP64 is bound by the FP64 pipe -> 512 threads (one radix-16 task per
+// thread for 8192 points, 16 warps on the SM's single resident block); FP32 is bound by memory
+// latency -> 256 threads and 3 resident blocks per SM so load, compute and store phases of
+// different blocks overlap.
+template <typename T> constexpr int fft_threads() { return sizeof(T) == 8 ? 512 : 256; }
+template <typename T> constexpr int fft_min_blocks() { return sizeof(T) == 8 ? 1 : 3; }
 
 enum Epi { EPI_APPLY = 0, EPI_RESID = 1, EPI_JACOBI = 2 };
+// Prologue: how the operand u of the product is formed while it is loaded.
+//   PRO_NONE:     u = x
+//   PRO_SMOOTH:   u = omega D^{-1} f                  (first pre-smoothing sweep from 0), stored
+//   PRO_RESTRICT: f = I_k^{k-1} r_fine, u = omega D^{-1} f (restriction + first sweep), both stored
+//   PRO_PROLONG:  u = x + I_{k-1}^k e_coarse          (coarse-grid correction), stored
+enum Pro { PRO_NONE = 0, PRO_SMOOTH = 1, PRO_RESTRICT = 2, PRO_PROLONG = 3 };
 enum MidMode { MID_PAIR = 0, MID_WHOLE = 1, MID_FWD = 2, MID_FWD_REAL = 3 };
 enum InMode { IN_PACK = 0, IN_REAL = 1 };
 
@@ -49,9 +61,15 @@ template <typename T> struct LevelArgs {
   const T* zeta;
   T o;
   T wA, wO, wD;          // omega / diagonal, per segment (damped Jacobi, eq. 7)
-  const c2<T>* twm;      // W_m^j, j < m (strided pipelines only)
+  const c2<T>* twm;      // strided pipelines only: W_m^j, j < m (FP64); two-level (FP32)
   const c2<T>* twL;      // W_{4096}^j, j < 4096
   // per call
+  int pro;               // Pro
+  T pA, pO, pD;          // pre-smoothing omega / diagonal per segment (PRO_SMOOTH, PRO_RESTRICT)
+  T* xout;               // where the formed operand is stored (PRO_SMOOTH/RESTRICT/PROLONG)
+  T* fout;               // where the restricted right-hand side is stored (PRO_RESTRICT)
+  const T* rfine;        // residual of the finer level (PRO_RESTRICT)
+  const T* ec;           // correction from the coarser level (PRO_PROLONG)
   const T* x;            // operand u (n_k)
   const T* f;            // right-hand side for EPI_RESID / EPI_JACOBI
   T* y;                  // result (n_k); must not alias x
@@ -61,6 +79,57 @@ template <typename T> struct LevelArgs {
   T* partials;           // per-CTA partial dots of the forward strided pass
   int nparts;
 };
+
+// Twiddle W_m^e of the strided passes, e < m. FP64 (whose kernels are bound by the FP64 pipe)
+// reads one table of m entries; FP32 (bound by memory traffic) multiplies two small cached
+// tables: W_m^e = W_m^{e mod 4096} * W_m^{4096 floor(e / 4096)}.
+constexpr int TW_LO = 4096;
+template <typename T>
+__device__ __forceinline__ c2<T> inter_tw(const c2<T>* __restrict__ twm, long long e) {
+  if constexpr (sizeof(T) == 8) {
+    return __ldg(twm + e);
+  } else {
+    const c2<T> lo = __ldg(twm + (e & (TW_LO - 1)));
+    const c2<T> hi = __ldg(twm + TW_LO + (e >> 12));
+    return cmul<T>(lo, hi);
+  }
+}
+
+// Restriction I_k^{k-1} (section 3.1) at coarse index I: (r[2I] + 2 r[2I+1] + r[2I+2]) / 4.
+template <typename T>
+__device__ __forceinline__ T restrict_at(const T* __restrict__ r, long long I) {
+  return (T)0.25 * r[2 * I] + (T)0.5 * r[2 * I + 1] + (T)0.25 * r[2 * I + 2];
+}
+// Prolongation I_{k-1}^k = 2 (I_k^{k-1})^T at fine index j (nc coarse entries).
+template <typename T>
+__device__ __forceinline__ T prolong_at(const T* __restrict__ ec, long long j, long long nc) {
+  if (j & 1) return ec[(j - 1) / 2];
+  const long long I = j / 2;
+  const T lo = (I >= 1) ? ec[I - 1] : (T)0;
+  const T hi = (I < nc) ? ec[I] : (T)0;
+  return (T)0.5 * (lo + hi);
+}
+// Operand entry j of the product (concatenated index), formed by the prologue; w is the
+// pre-smoothing weight of j's segment.
+template <typename T>
+__device__ __forceinline__ T operand(const LevelArgs<T>& a, long long j, T w) {
+  if (a.pro == PRO_NONE) return a.x[j];
+  if (a.pro == PRO_SMOOTH) {
+    const T v = w * a.f[j];
+    a.xout[j] = v;
+    return v;
+  }
+  if (a.pro == PRO_RESTRICT) {
+    const T fv = restrict_at<T>(a.rfine, j);
+    a.fout[j] = fv;
+    const T v = w * fv;
+    a.xout[j] = v;
+    return v;
+  }
+  const T v = a.x[j] + prolong_at<T>(a.ec, j, a.N);  // coarse size n_{k-1} = N_k
+  a.xout[j] = v;
+  return v;
+}
 
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, T* red) {
@@ -152,7 +221,7 @@ __device__ __forceinline__ void block0_pair(int q, int& p, int& pp) {
 // columns (stride L), each followed by the twiddle W_m^{c k}. One CTA: 2^logC columns.
 // ------------------------------------------------------------------------------------
 template <typename T, int IN>
-__global__ void __launch_bounds__(FFT_THREADS) k_fwd_strided(LevelArgs<T> a) {
+__global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_fwd_strided(LevelArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2<T>* s = reinterpret_cast<c2<T>*>(smem_raw);
   __shared__ T red[FFT_THREADS / 32];
@@ -168,7 +237,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fwd_strided(LevelArgs<T> a) {
     c2<T> v = mk<T>(0, 0);
     if (IN == IN_PACK) {
       if (t < half && P < a.N) {
-        const T xv = a.x[P], xw = a.x[a.N + 1 + P];
+        const T xv = operand<T>(a, P, a.pA), xw = operand<T>(a, a.N + 1 + P, a.pD);
         v = mk<T>(xv, xw);
         dot = fma(a.q[P], xv, fma(a.zeta[P], xw, dot));
       }
@@ -184,11 +253,14 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fwd_strided(LevelArgs<T> a) {
     const long long c = c0 + cc;
     const long long P = c + ((long long)t << logL);
     const long long kb = (long long)brev_bits((unsigned)t, logR1);
-    a.z[P] = cmul<T>(s[pad16(e)], __ldg(a.twm + c * kb));
+    a.z[P] = cmul<T>(s[pad16(e)], inter_tw<T>(a.twm, c * kb));
   }
   if (IN == IN_PACK) {
     const T tot = block_sum<T>(dot, red);
-    if (threadIdx.x == 0) a.partials[blockIdx.x] = tot;
+    if (threadIdx.x == 0) {
+      a.partials[blockIdx.x] = tot;
+      if (blockIdx.x == 0 && a.pro != PRO_NONE) (void)operand<T>(a, a.N, a.pO);  // middle w_o
+    }
   }
 }
 
@@ -225,7 +297,7 @@ __device__ __forceinline__ void mid_body(const LevelArgs<T>& a) {
     if (MODE == MID_WHOLE) {
       v = mk<T>(0, 0);
       if (i < a.N) {
-        const T xv = a.x[i], xw = a.x[a.N + 1 + i];
+        const T xv = operand<T>(a, i, a.pA), xw = operand<T>(a, a.N + 1 + i, a.pD);
         v = mk<T>(xv, xw);
         dot = fma(a.q[i], xv, fma(a.zeta[i], xw, dot));
       }
@@ -237,7 +309,10 @@ __device__ __forceinline__ void mid_body(const LevelArgs<T>& a) {
     s[pad16(e)] = v;
   }
   T dot_total = 0;
-  if (MODE == MID_WHOLE) dot_total = block_sum<T>(dot, red);
+  if (MODE == MID_WHOLE) {
+    if (threadIdx.x == 0 && a.pro != PRO_NONE) (void)operand<T>(a, a.N, a.pO);  // middle w_o
+    dot_total = block_sum<T>(dot, red);
+  }
   __syncthreads();
   smem_dif<T, false>(s, logL, nseq - 1, 1, L, a.twL, LOG_LMAX);
   if constexpr (MODE == MID_FWD || MODE == MID_FWD_REAL) {
@@ -277,19 +352,19 @@ __device__ __forceinline__ void mid_body(const LevelArgs<T>& a) {
 
 // One kernel name per mode (so profilers can select them).
 template <typename T, bool NS>
-__global__ void __launch_bounds__(FFT_THREADS) k_mid_pair(LevelArgs<T> a) {
+__global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_mid_pair(LevelArgs<T> a) {
   mid_body<T, MID_PAIR, NS>(a);
 }
 template <typename T, bool NS>
-__global__ void __launch_bounds__(FFT_THREADS) k_mid_whole(LevelArgs<T> a) {
+__global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_mid_whole(LevelArgs<T> a) {
   mid_body<T, MID_WHOLE, NS>(a);
 }
 template <typename T>
-__global__ void __launch_bounds__(FFT_THREADS) k_mid_fwd(LevelArgs<T> a) {
+__global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_mid_fwd(LevelArgs<T> a) {
   mid_body<T, MID_FWD, false>(a);
 }
 template <typename T>
-__global__ void __launch_bounds__(FFT_THREADS) k_mid_fwd_real(LevelArgs<T> a) {
+__global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_mid_fwd_real(LevelArgs<T> a) {
   mid_body<T, MID_FWD_REAL, false>(a);
 }
 
@@ -297,7 +372,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_mid_fwd_real(LevelArgs<T> a) {
 // Inverse strided pass: twiddle conj(W_m^{c k}), R1-point DIT per column, epilogue.
 // ------------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(FFT_THREADS) k_inv_strided(LevelArgs<T> a) {
+__global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_inv_strided(LevelArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2<T>* s = reinterpret_cast<c2<T>*>(smem_raw);
   const int logR1 = a.logR1, logC = a.logC, logL = a.logL;
@@ -309,7 +384,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_inv_strided(LevelArgs<T> a) {
     const long long c = c0 + cc;
     const long long P = c + ((long long)t << logL);
     const long long kb = (long long)brev_bits((unsigned)t, logR1);
-    s[pad16(e)] = cmulc<T>(a.z[P], __ldg(a.twm + c * kb));
+    s[pad16(e)] = cmulc<T>(a.z[P], inter_tw<T>(a.twm, c * kb));
   }
   __syncthreads();
   smem_dit<T, true>(s, logR1, logC, C, 1, a.twL, LOG_LMAX);
@@ -388,11 +463,20 @@ __global__ void k_prolong_add(T* e, const T* ec, long long nf) {
   }
 }
 
-// Coarsest level: e = A_kc^{-1} f with the inverse formed on the host (n <= 255).
+// Coarsest level: e = A_kc^{-1} f with the inverse formed on the host (n <= 255). With
+// rfine != nullptr the right-hand side is first restricted from the finer residual (and
+// stored in f).
 template <typename T>
-__global__ void k_coarse_solve(const T* inv, const T* f, T* e, int n) {
+__global__ void k_coarse_solve(const T* inv, T* f, const T* rfine, T* e, int n) {
   __shared__ T fs[256];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) fs[i] = f[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    if (rfine) {
+      fs[i] = restrict_at<T>(rfine, i);
+      f[i] = fs[i];
+    } else {
+      fs[i] = f[i];
+    }
+  }
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     T acc = 0;
