@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="profiling case: set up, then 3 finest-level products, nothing timed")
+    ap.add_argument("--profile-f32", action="store_true",
+                    help="profiling case: mixed-precision setup, then 3 FP32 finest-level products")
     ap.add_argument("--profile-solve", choices=["fp64", "mixed"], default=None,
                     help="profiling case: set up, then one solve, nothing timed")
     return ap.parse_args()
@@ -337,6 +339,23 @@ def run_profile_case(args):
     print(json.dumps({"profile_case": f"N=2^{args.K}", "unknowns": n}))
 
 
+def run_profile_f32(args):
+    """A fixed launch sequence for profilers: mixed setup, then three FP32 finest products."""
+    import torch
+
+    import paper_2202_11288_gb300 as tpc
+    n = 2 ** (args.K + 1) - 1
+    S = tpc.Solver(args.delta, 2.0 ** -args.K, precision=tpc.TPC_MIXED)
+    x = torch.tensor(uniform_pm1(n, 5), dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(3):
+        S.apply_f32(args.K, x, y)
+    torch.cuda.synchronize()
+    assert torch.isfinite(y).all()
+    S.close()
+    print(json.dumps({"profile_f32": f"N=2^{args.K}", "unknowns": n}))
+
+
 def run_profile_solve(args):
     """A fixed launch sequence for profilers: setup, then one solve."""
     import torch
@@ -361,6 +380,9 @@ def main():
         return
     if args.profile_solve:
         run_profile_solve(args)
+        return
+    if args.profile_f32:
+        run_profile_f32(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

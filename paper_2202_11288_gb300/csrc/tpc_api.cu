@@ -47,7 +47,7 @@ template <typename T> struct Hier {
   std::vector<T*> f, e, t;       // per level vectors (n_k)
   c2<T>* z = nullptr;            // complex work array (m_K)
   T* partials = nullptr;
-  c2<T>* twL = nullptr;          // W_4096^j, j < 4096
+  c2<T>* twL = nullptr;          // W_4096^j, j < 4096 (FP32 kernels copy j <= 512)
   T* coarse_inv = nullptr;
 };
 
@@ -162,8 +162,9 @@ void plan_level(DevLevel<T>& L) {
     L.fwd_blocks = 1 << (logL - logC);
     L.mid_blocks = (1 << (L.logm - logL - 1)) + 1;
   }
-  L.smem_strided = L.logR1 ? sizeof(c2<T>) * (size_t)padded_size(1 << (L.logR1 + L.logC)) : 0;
-  L.smem_mid = sizeof(c2<T>) * (size_t)padded_size(1 << (L.logL + (L.logR1 ? 1 : 0)));
+  L.smem_strided =
+      L.logR1 ? sizeof(c2<T>) * (size_t)(TW_TAB + padded_size(1 << (L.logR1 + L.logC))) : 0;
+  L.smem_mid = sizeof(c2<T>) * (size_t)(TW_TAB + padded_size(1 << (L.logL + (L.logR1 ? 1 : 0))));
 }
 
 template <typename T>
@@ -334,7 +335,7 @@ void enqueue_iteration(tpc_handle* H) {
 
 template <typename T, bool NS>
 cudaError_t set_smem_attrs() {
-  const int big = 144 * 1024;  // largest padded tile: 8704 x 16 B = 136 KB
+  const int big = 150 * 1024;  // largest: (520 + 8704) x 16 B = 144 KB
   const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_fwd_strided<T, IN_PACK>, A, big)) != cudaSuccess) return e;
@@ -370,7 +371,7 @@ int forward_real(tpc_handle* H, const Hier<double>& G, const DevLevel<double>& L
   } else {
     k_fwd_strided<double, IN_REAL><<<L.fwd_blocks, FFT_THREADS, L.smem_strided, s>>>(a);
     k_mid_fwd<double><<<1 << L.logR1, FFT_THREADS,
-                        sizeof(double2) * (size_t)padded_size(1 << L.logL), s>>>(a);
+                        sizeof(double2) * (size_t)(TW_TAB + padded_size(1 << L.logL)), s>>>(a);
   }
   TPC_CUDA(H, cudaGetLastError());
   return TPC_OK;
@@ -383,7 +384,7 @@ int alloc_levels(tpc_handle* H, Hier<T>& G) {
   const int nlev = (int)HH.lev.size();
   G.lev.resize(nlev);
   std::vector<double> tw;
-  twiddles(1LL << LOG_LMAX, 1LL << LOG_LMAX, tw);
+  twiddles(1LL << LOG_LMAX, 1LL << LOG_LMAX, tw);  // W_4096^j, j < 4096
   TPC_TRY(dalloc(H, &G.twL, (size_t)1 << LOG_LMAX));
   TPC_TRY(upload<T>(H, reinterpret_cast<T*>(G.twL), tw));
   long long max_m = 0;
@@ -422,19 +423,10 @@ int alloc_levels(tpc_handle* H, Hier<T>& G) {
     TPC_TRY(upload<T>(H, L.q, F.q));
     TPC_TRY(upload<T>(H, L.xi, F.xi));
     TPC_TRY(upload<T>(H, L.zeta, F.zeta));
-    if (L.logR1) {
+    if (L.logR1 && sizeof(T) == sizeof(double)) {  // FP32 computes these (inter_tw)
       std::vector<double> twm;
-      if (sizeof(T) == sizeof(double)) {
-        twiddles(L.m, L.m, twm);  // W_m^j, j < m
-      } else {
-        // W_m^j for j < 4096, then W_m^{4096 j} = W_{m/4096}^j for j < max(1, m / 4096)
-        std::vector<double> hi;
-        twiddles(L.m, TW_LO, twm);
-        if (L.m > TW_LO) twiddles(L.m / TW_LO, L.m / TW_LO, hi);
-        else hi = {1.0, 0.0};
-        twm.insert(twm.end(), hi.begin(), hi.end());
-      }
-      TPC_TRY(dalloc(H, &L.twm, twm.size() / 2));
+      twiddles(L.m, L.m, twm);  // W_m^j, j < m
+      TPC_TRY(dalloc(H, &L.twm, L.m));
       TPC_TRY(upload<T>(H, reinterpret_cast<T*>(L.twm), twm));
     }
     TPC_TRY(dalloc(H, &L.sA, L.m));

@@ -127,14 +127,58 @@ __device__ __forceinline__ void reg_dit_stage(c2<T>* v) {
   }
 }
 
+// Twiddles of the in-shared-memory steps: W_4096^e = exp(-2 pi i e / 4096) for e < 4096 from
+// an octant table tab[j] = W_4096^j, j <= 512, held in shared memory, using the exact
+// symmetries W^{1024 q + r} = (-i)^q W^r and W^r = -i conj(W^{1024 - r}).
+constexpr int TW_TAB = 520;  // 513 entries, rounded up to keep the data after it aligned
+template <typename T>
+__device__ __forceinline__ c2<T> tw4096(const c2<T>* __restrict__ tab, int e) {
+  const int q = (e >> 10) & 3, r = e & 1023;
+  c2<T> w;
+  if (r <= 512) {
+    w = tab[r];
+  } else {
+    const c2<T> t = tab[1024 - r];
+    w = mk<T>(-t.y, -t.x);
+  }
+  switch (q) {
+    case 0: return w;
+    case 1: return mk<T>(w.y, -w.x);
+    case 2: return mk<T>(-w.x, -w.y);
+    default: return mk<T>(-w.y, w.x);
+  }
+}
+// The twiddle table the steps use: FP32 copies the octant of the global table into shared
+// memory (all threads; ends with a barrier); FP64 uses the global table directly.
+template <typename T>
+__device__ __forceinline__ const c2<T>* step_table(c2<T>* tab, const c2<T>* __restrict__ g) {
+  if constexpr (sizeof(T) == 8) {
+    return g;
+  } else {
+    for (int j = threadIdx.x; j <= 512; j += blockDim.x) tab[j] = g[j];
+    __syncthreads();
+    return tab;
+  }
+}
+
 template <int R> __device__ __forceinline__ int brev_r(int t) {
   return (int)(__brev((unsigned)t) >> (32 - (R == 16 ? 4 : R == 8 ? 3 : R == 4 ? 2 : 1)));
 }
 
 // One radix-R step on all sub-blocks of length 2^logS of 2^logCount sequences of length
 // 2^logL held in shared memory (element t of sequence q at pad16(q * qs + t * ts)).
-// tw[j] = exp(-2 pi i j / Lmax), j < Lmax = 2^logLmax. QFAST: consecutive threads take
+// tw: the full W_4096 table in global memory (FP64) or the octant table in shared memory
+// (FP32), see step_tw; 2^logLmax = 4096. QFAST: consecutive threads take
 // consecutive sequences first (interleaved column tiles), else consecutive columns.
+// W_4096^e for the in-shared-memory steps: FP64 (bound by the FP64 pipe, L1 mostly free)
+// reads the full 4096-entry table from global memory; FP32 (bound by memory latency, L1
+// mostly taken by shared memory) reads the octant table in shared memory.
+template <typename T>
+__device__ __forceinline__ c2<T> step_tw(const c2<T>* __restrict__ tw, int e) {
+  if constexpr (sizeof(T) == 8) return __ldg(tw + e);
+  else return tw4096<T>(tw, e);
+}
+
 template <typename T, int R, bool QFAST, bool INV>
 __device__ __forceinline__ void fft_step(c2<T>* s, int logS, int logL, int logCount, int ts,
                                          int qs, const c2<T>* __restrict__ tw, int logLmax) {
@@ -164,14 +208,14 @@ __device__ __forceinline__ void fft_step(c2<T>* s, int logS, int logL, int logCo
     if (INV) {
       if (logCols > 0) {
 #pragma unroll
-        for (int t = 1; t < R; ++t) v[t] = cmulc<T>(v[t], __ldg(tw + ((c * brev_r<R>(t)) << twsh)));
+        for (int t = 1; t < R; ++t) v[t] = cmulc<T>(v[t], step_tw<T>(tw, (c * brev_r<R>(t)) << twsh));
       }
       reg_dit_stage<T, R>(v);
     } else {
       reg_dif_stage<T, R>(v);
       if (logCols > 0) {
 #pragma unroll
-        for (int t = 1; t < R; ++t) v[t] = cmul<T>(v[t], __ldg(tw + ((c * brev_r<R>(t)) << twsh)));
+        for (int t = 1; t < R; ++t) v[t] = cmul<T>(v[t], step_tw<T>(tw, (c * brev_r<R>(t)) << twsh));
       }
     }
 #pragma unroll

@@ -62,7 +62,7 @@ template <typename T> struct LevelArgs {
   T o;
   T wA, wO, wD;          // omega / diagonal, per segment (damped Jacobi, eq. 7)
   const c2<T>* twm;      // strided pipelines only: W_m^j, j < m (FP64); two-level (FP32)
-  const c2<T>* twL;      // W_{4096}^j, j < 4096
+  const c2<T>* twL;      // W_{4096}^j, j < 4096 (FP32 copies the octant j <= 512 to shared)
   // per call
   int pro;               // Pro
   T pA, pO, pD;          // pre-smoothing omega / diagonal per segment (PRO_SMOOTH, PRO_RESTRICT)
@@ -81,17 +81,16 @@ template <typename T> struct LevelArgs {
 };
 
 // Twiddle W_m^e of the strided passes, e < m. FP64 (whose kernels are bound by the FP64 pipe)
-// reads one table of m entries; FP32 (bound by memory traffic) multiplies two small cached
-// tables: W_m^e = W_m^{e mod 4096} * W_m^{4096 floor(e / 4096)}.
-constexpr int TW_LO = 4096;
+// reads one table of m entries; FP32 (bound by memory latency) computes it with sincospif.
 template <typename T>
-__device__ __forceinline__ c2<T> inter_tw(const c2<T>* __restrict__ twm, long long e) {
+__device__ __forceinline__ c2<T> inter_tw(const c2<T>* __restrict__ twm, long long e, int logm) {
   if constexpr (sizeof(T) == 8) {
     return __ldg(twm + e);
   } else {
-    const c2<T> lo = __ldg(twm + (e & (TW_LO - 1)));
-    const c2<T> hi = __ldg(twm + TW_LO + (e >> 12));
-    return cmul<T>(lo, hi);
+    // FP32: W_m^e = (cospi(x), -sinpi(x)) with x = 2e/m, exact in FP32 for m <= 2^24
+    float sn, cs;
+    sincospif(ldexpf((float)e, 1 - logm), &sn, &cs);
+    return mk<T>(cs, -sn);
   }
 }
 
@@ -110,26 +109,60 @@ __device__ __forceinline__ T prolong_at(const T* __restrict__ ec, long long j, l
   return (T)0.5 * (lo + hi);
 }
 // Operand entry j of the product (concatenated index), formed by the prologue; w is the
-// pre-smoothing weight of j's segment.
+// pre-smoothing weight of j's segment. Split into the loads (issued in batches, so that many
+// loads are in flight per thread) and the arithmetic and stores that follow them.
+template <typename T> struct Raw {
+  T a0, a1, a2;
+};
 template <typename T>
-__device__ __forceinline__ T operand(const LevelArgs<T>& a, long long j, T w) {
-  if (a.pro == PRO_NONE) return a.x[j];
+__device__ __forceinline__ Raw<T> operand_load(const LevelArgs<T>& a, long long j) {
+  Raw<T> r{0, 0, 0};
+  if (a.pro == PRO_NONE) {
+    r.a0 = a.x[j];
+  } else if (a.pro == PRO_SMOOTH) {
+    r.a0 = a.f[j];
+  } else if (a.pro == PRO_RESTRICT) {
+    r.a0 = a.rfine[2 * j];
+    r.a1 = a.rfine[2 * j + 1];
+    r.a2 = a.rfine[2 * j + 2];
+  } else {
+    r.a0 = a.x[j];
+    if (j & 1) {
+      r.a1 = a.ec[(j - 1) / 2];
+    } else {
+      const long long I = j / 2;
+      r.a1 = (I >= 1) ? a.ec[I - 1] : (T)0;
+      r.a2 = (I < a.N) ? a.ec[I] : (T)0;  // coarse size n_{k-1} = N_k
+    }
+  }
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ T operand_finish(const LevelArgs<T>& a, long long j, const Raw<T>& r,
+                                            T w) {
+  if (a.pro == PRO_NONE) return r.a0;
   if (a.pro == PRO_SMOOTH) {
-    const T v = w * a.f[j];
+    const T v = w * r.a0;
     a.xout[j] = v;
     return v;
   }
   if (a.pro == PRO_RESTRICT) {
-    const T fv = restrict_at<T>(a.rfine, j);
+    const T fv = (T)0.25 * r.a0 + (T)0.5 * r.a1 + (T)0.25 * r.a2;  // restriction, section 3.1
     a.fout[j] = fv;
     const T v = w * fv;
     a.xout[j] = v;
     return v;
   }
-  const T v = a.x[j] + prolong_at<T>(a.ec, j, a.N);  // coarse size n_{k-1} = N_k
+  const T v = r.a0 + ((j & 1) ? r.a1 : (T)0.5 * (r.a1 + r.a2));  // prolongation, P = 2 R^T
   a.xout[j] = v;
   return v;
 }
+template <typename T>
+__device__ __forceinline__ T operand(const LevelArgs<T>& a, long long j, T w) {
+  return operand_finish<T>(a, j, operand_load<T>(a, j), w);
+}
+
+constexpr int UNROLL = 4;  // elements per thread whose loads are issued together
 
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, T* red) {
@@ -147,22 +180,42 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
 }
 
 // Epilogue for output index i < N: ax_v, ax_w are the Toeplitz parts of (A u)_v[i] and
-// (A u)_{w_bar}[i]; the Cross column p, xi times w_o is added here.
+// (A u)_{w_bar}[i]; the Cross column p, xi times w_o is added here. Loads first (batched by
+// the callers), then arithmetic and stores.
+template <typename T> struct EpiRaw {
+  T p, xi, fv, fw, xv, xw;
+};
 template <typename T>
-__device__ __forceinline__ void epi_pair(const LevelArgs<T>& a, long long i, T ax_v, T ax_w,
-                                         T w_o) {
-  const T yv = fma(a.p[i], w_o, ax_v);
-  const T yw = fma(a.xi[i], w_o, ax_w);
+__device__ __forceinline__ EpiRaw<T> epi_load(const LevelArgs<T>& a, long long i) {
+  EpiRaw<T> r{0, 0, 0, 0, 0, 0};
+  const long long iw = a.N + 1 + i;
+  r.p = a.p[i];
+  r.xi = a.xi[i];
+  if (a.epi != EPI_APPLY) {
+    r.fv = a.f[i];
+    r.fw = a.f[iw];
+  }
+  if (a.epi == EPI_JACOBI) {
+    r.xv = a.x[i];
+    r.xw = a.x[iw];
+  }
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ void epi_store(const LevelArgs<T>& a, long long i, const EpiRaw<T>& r,
+                                          T ax_v, T ax_w, T w_o) {
+  const T yv = fma(r.p, w_o, ax_v);
+  const T yw = fma(r.xi, w_o, ax_w);
   const long long iw = a.N + 1 + i;
   if (a.epi == EPI_APPLY) {
     a.y[i] = yv;
     a.y[iw] = yw;
   } else if (a.epi == EPI_RESID) {
-    a.y[i] = a.f[i] - yv;
-    a.y[iw] = a.f[iw] - yw;
+    a.y[i] = r.fv - yv;
+    a.y[iw] = r.fw - yw;
   } else {
-    a.y[i] = fma(a.wA, a.f[i] - yv, a.x[i]);
-    a.y[iw] = fma(a.wD, a.f[iw] - yw, a.x[iw]);
+    a.y[i] = fma(a.wA, r.fv - yv, r.xv);
+    a.y[iw] = fma(a.wD, r.fw - yw, r.xw);
   }
 }
 
@@ -179,27 +232,35 @@ __device__ __forceinline__ void epi_middle(const LevelArgs<T>& a, T dot, T w_o) 
 }
 
 // Spectral 2x2 block product for the frequency pair held at positions (lower, upper).
-// P = bit-reversed position of the lower member (index of the stored spectra).
+// Spectra of the lower member (bit-reversed position P): loaded first, applied after.
+template <typename T> struct Spec {
+  T sa, sd;
+  c2<T> sb, sc;
+};
 template <typename T, bool NS>
-__device__ __forceinline__ void mac_pair(const LevelArgs<T>& a, long long P, c2<T>* zl,
-                                         c2<T>* zu) {
+__device__ __forceinline__ Spec<T> spec_load(const LevelArgs<T>& a, long long P) {
+  Spec<T> r;
+  r.sa = a.sA[P];
+  r.sd = a.sD[P];
+  r.sb = a.sB[P];
+  if (NS) {
+    r.sc = a.sC[P];
+  } else {
+    r.sc.x = r.sb.x;
+    r.sc.y = -r.sb.y;
+  }
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ void mac_pair(const Spec<T>& sp, c2<T>* zl, c2<T>* zu) {
   const c2<T> Zp = *zl, Zq = *zu;
   // 2 V^ = Z_p + conj Z_q ; 2 W^ = (Z_p - conj Z_q) / i
   const T vr = Zp.x + Zq.x, vi = Zp.y - Zq.y;
   const T wr = Zp.y + Zq.y, wi = Zq.x - Zp.x;
-  const T sa = a.sA[P], sd = a.sD[P];
-  const c2<T> sb = a.sB[P];
-  c2<T> sc;
-  if (NS) {
-    sc = a.sC[P];
-  } else {
-    sc.x = sb.x;
-    sc.y = -sb.y;
-  }
-  const T y1r = fma(sa, vr, fma(sb.x, wr, -sb.y * wi));
-  const T y1i = fma(sa, vi, fma(sb.x, wi, sb.y * wr));
-  const T y2r = fma(sd, wr, fma(sc.x, vr, -sc.y * vi));
-  const T y2i = fma(sd, wi, fma(sc.x, vi, sc.y * vr));
+  const T y1r = fma(sp.sa, vr, fma(sp.sb.x, wr, -sp.sb.y * wi));
+  const T y1i = fma(sp.sa, vi, fma(sp.sb.x, wi, sp.sb.y * wr));
+  const T y2r = fma(sp.sd, wr, fma(sp.sc.x, vr, -sp.sc.y * vi));
+  const T y2i = fma(sp.sd, wi, fma(sp.sc.x, vi, sp.sc.y * vr));
   *zl = mk<T>(y1r - y2i, y1i + y2r);
   if (zu != zl) *zu = mk<T>(y1r + y2i, y2r - y1i);
 }
@@ -223,37 +284,77 @@ __device__ __forceinline__ void block0_pair(int q, int& p, int& pp) {
 template <typename T, int IN>
 __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_fwd_strided(LevelArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  c2<T>* s = reinterpret_cast<c2<T>*>(smem_raw);
+  c2<T>* tab = reinterpret_cast<c2<T>*>(smem_raw);
+  c2<T>* s = tab + TW_TAB;
   __shared__ T red[FFT_THREADS / 32];
   const int logR1 = a.logR1, logC = a.logC, logL = a.logL;
+  const c2<T>* tw = step_table<T>(tab, a.twL);
   const int C = 1 << logC;
   const int tile = 1 << (logR1 + logC);
   const long long c0 = (long long)blockIdx.x << logC;
   const int half = 1 << (logR1 - 1);
   T dot = 0;
-  for (int e = threadIdx.x; e < tile; e += blockDim.x) {
-    const int t = e >> logC, cc = e & (C - 1);
-    const long long P = c0 + cc + ((long long)t << logL);
-    c2<T> v = mk<T>(0, 0);
-    if (IN == IN_PACK) {
-      if (t < half && P < a.N) {
-        const T xv = operand<T>(a, P, a.pA), xw = operand<T>(a, a.N + 1 + P, a.pD);
-        v = mk<T>(xv, xw);
-        dot = fma(a.q[P], xv, fma(a.zeta[P], xw, dot));
+  if (IN == IN_PACK) {
+    // rows t >= R1/2 are the zero padding of the embedding
+    for (int e = threadIdx.x + (tile >> 1); e < tile; e += blockDim.x) s[pad16(e)] = mk<T>(0, 0);
+    for (int e0 = threadIdx.x; e0 < (tile >> 1); e0 += UNROLL * blockDim.x) {
+      Raw<T> rv[UNROLL], rw[UNROLL];
+      T qv[UNROLL], zv[UNROLL];
+      bool ok[UNROLL];
+#pragma unroll
+      for (int u = 0; u < UNROLL; ++u) {
+        const int e = e0 + u * blockDim.x;
+        const int t = e >> logC, cc = e & (C - 1);
+        const long long P = c0 + cc + ((long long)t << logL);
+        ok[u] = (e < (tile >> 1)) && P < a.N;
+        if (ok[u]) {
+          rv[u] = operand_load<T>(a, P);
+          rw[u] = operand_load<T>(a, a.N + 1 + P);
+          qv[u] = a.q[P];
+          zv[u] = a.zeta[P];
+        }
       }
-    } else {
-      v = mk<T>(a.real_in[P], 0);
+#pragma unroll
+      for (int u = 0; u < UNROLL; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e >= (tile >> 1)) continue;
+        const int t = e >> logC, cc = e & (C - 1);
+        const long long P = c0 + cc + ((long long)t << logL);
+        c2<T> v = mk<T>(0, 0);
+        if (ok[u]) {
+          const T xv = operand_finish<T>(a, P, rv[u], a.pA);
+          const T xw = operand_finish<T>(a, a.N + 1 + P, rw[u], a.pD);
+          v = mk<T>(xv, xw);
+          dot = fma(qv[u], xv, fma(zv[u], xw, dot));
+        }
+        s[pad16(e)] = v;
+      }
     }
-    s[pad16(e)] = v;
+  } else {
+    for (int e0 = threadIdx.x; e0 < tile; e0 += UNROLL * blockDim.x) {
+      T rv[UNROLL];
+#pragma unroll
+      for (int u = 0; u < UNROLL; ++u) {
+        const int e = e0 + u * blockDim.x;
+        const int t = e >> logC, cc = e & (C - 1);
+        if (e < tile) rv[u] = a.real_in[c0 + cc + ((long long)t << logL)];
+      }
+#pragma unroll
+      for (int u = 0; u < UNROLL; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < tile) s[pad16(e)] = mk<T>(rv[u], 0);
+      }
+    }
   }
+  (void)half;
   __syncthreads();
-  smem_dif<T, true>(s, logR1, logC, C, 1, a.twL, LOG_LMAX);
+  smem_dif<T, true>(s, logR1, logC, C, 1, tw, LOG_LMAX);
   for (int e = threadIdx.x; e < tile; e += blockDim.x) {
     const int t = e >> logC, cc = e & (C - 1);
     const long long c = c0 + cc;
     const long long P = c + ((long long)t << logL);
     const long long kb = (long long)brev_bits((unsigned)t, logR1);
-    a.z[P] = cmul<T>(s[pad16(e)], inter_tw<T>(a.twm, c * kb));
+    a.z[P] = cmul<T>(s[pad16(e)], inter_tw<T>(a.twm, c * kb, a.logm));
   }
   if (IN == IN_PACK) {
     const T tot = block_sum<T>(dot, red);
@@ -270,9 +371,11 @@ __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_fwd_s
 template <typename T, int MODE, bool NS>
 __device__ __forceinline__ void mid_body(const LevelArgs<T>& a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  c2<T>* s = reinterpret_cast<c2<T>*>(smem_raw);
+  c2<T>* tab = reinterpret_cast<c2<T>*>(smem_raw);
+  c2<T>* s = tab + TW_TAB;
   __shared__ T red[FFT_THREADS / 32];
   const int logL = a.logL;
+  const c2<T>* tw = step_table<T>(tab, a.twL);
   const int L = 1 << logL;
   long long b, b2;
   if (MODE == MID_FWD || MODE == MID_FWD_REAL || MODE == MID_WHOLE) {
@@ -289,24 +392,55 @@ __device__ __forceinline__ void mid_body(const LevelArgs<T>& a) {
     }
   }
   const int nseq = (b != b2) ? 2 : 1;
+  const int total = nseq << logL;
   T dot = 0;
-  for (int e = threadIdx.x; e < (nseq << logL); e += blockDim.x) {
-    const int sq = e >> logL, i = e & (L - 1);
-    const long long P = (sq ? b2 : b) * (long long)L + i;
-    c2<T> v;
-    if (MODE == MID_WHOLE) {
-      v = mk<T>(0, 0);
-      if (i < a.N) {
-        const T xv = operand<T>(a, i, a.pA), xw = operand<T>(a, a.N + 1 + i, a.pD);
-        v = mk<T>(xv, xw);
-        dot = fma(a.q[i], xv, fma(a.zeta[i], xw, dot));
+  if constexpr (MODE == MID_WHOLE) {
+    for (int e0 = threadIdx.x; e0 < total; e0 += UNROLL * blockDim.x) {
+      Raw<T> rv[UNROLL], rw[UNROLL];
+      T qv[UNROLL], zv[UNROLL];
+#pragma unroll
+      for (int u = 0; u < UNROLL; ++u) {
+        const int i = e0 + u * blockDim.x;
+        if (i < a.N) {
+          rv[u] = operand_load<T>(a, i);
+          rw[u] = operand_load<T>(a, a.N + 1 + i);
+          qv[u] = a.q[i];
+          zv[u] = a.zeta[i];
+        }
       }
-    } else if (MODE == MID_FWD_REAL) {
-      v = mk<T>(a.real_in[P], 0);
-    } else {
-      v = a.z[P];
+#pragma unroll
+      for (int u = 0; u < UNROLL; ++u) {
+        const int i = e0 + u * blockDim.x;
+        if (i >= total) continue;
+        c2<T> v = mk<T>(0, 0);
+        if (i < a.N) {
+          const T xv = operand_finish<T>(a, i, rv[u], a.pA);
+          const T xw = operand_finish<T>(a, a.N + 1 + i, rw[u], a.pD);
+          v = mk<T>(xv, xw);
+          dot = fma(qv[u], xv, fma(zv[u], xw, dot));
+        }
+        s[pad16(i)] = v;
+      }
     }
-    s[pad16(e)] = v;
+  } else {
+    for (int e0 = threadIdx.x; e0 < total; e0 += 2 * UNROLL * blockDim.x) {
+      c2<T> v[2 * UNROLL];
+#pragma unroll
+      for (int u = 0; u < 2 * UNROLL; ++u) {
+        const int e = e0 + u * blockDim.x;
+        const int sq = e >> logL, i = e & (L - 1);
+        const long long P = (sq ? b2 : b) * (long long)L + i;
+        if (e < total) {
+          if constexpr (MODE == MID_FWD_REAL) v[u] = mk<T>(a.real_in[P], 0);
+          else v[u] = a.z[P];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2 * UNROLL; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < total) s[pad16(e)] = v[u];
+      }
+    }
   }
   T dot_total = 0;
   if (MODE == MID_WHOLE) {
@@ -314,36 +448,65 @@ __device__ __forceinline__ void mid_body(const LevelArgs<T>& a) {
     dot_total = block_sum<T>(dot, red);
   }
   __syncthreads();
-  smem_dif<T, false>(s, logL, nseq - 1, 1, L, a.twL, LOG_LMAX);
+  smem_dif<T, false>(s, logL, nseq - 1, 1, L, tw, LOG_LMAX);
   if constexpr (MODE == MID_FWD || MODE == MID_FWD_REAL) {
     for (int e = threadIdx.x; e < L; e += blockDim.x) a.z[b * (long long)L + e] = s[pad16(e)];
     return;
   }
-  // spectral product
-  if (b != b2) {
-    for (int i = threadIdx.x; i < L; i += blockDim.x)
-      mac_pair<T, NS>(a, b * (long long)L + i, s + pad16(i), s + pad16(L + (L - 1 - i)));
-  } else if (b == 1) {
-    for (int i = threadIdx.x; i < (L >> 1); i += blockDim.x)
-      mac_pair<T, NS>(a, (long long)L + i, s + pad16(i), s + pad16(L - 1 - i));
-  } else {
-    for (int q = threadIdx.x; q <= (L >> 1); q += blockDim.x) {
-      int p, pp;
-      block0_pair(q, p, pp);
-      mac_pair<T, NS>(a, p, s + pad16(p), s + pad16(pp));
+  // spectral product: ntask frequency pairs; task i -> (lower, upper) shared-memory slots and
+  // the bit-reversed position of the lower member
+  const int ntask = (b != b2) ? L : ((b == 1) ? (L >> 1) : (L >> 1) + 1);
+  for (int i0 = threadIdx.x; i0 < ntask; i0 += UNROLL * blockDim.x) {
+    Spec<T> sp[UNROLL];
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i < ntask) {
+        int p = i, pp;
+        if (b == 0) block0_pair(i, p, pp);
+        sp[u] = spec_load<T, NS>(a, b * (long long)L + p);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i >= ntask) continue;
+      int lo, hi;
+      if (b != b2) {
+        lo = i;
+        hi = L + (L - 1 - i);
+      } else if (b == 1) {
+        lo = i;
+        hi = L - 1 - i;
+      } else {
+        block0_pair(i, lo, hi);
+      }
+      mac_pair<T>(sp[u], s + pad16(lo), s + pad16(hi));
     }
   }
   __syncthreads();
-  smem_dit<T, false>(s, logL, nseq - 1, 1, L, a.twL, LOG_LMAX);
+  smem_dit<T, false>(s, logL, nseq - 1, 1, L, tw, LOG_LMAX);
   if constexpr (MODE == MID_WHOLE) {
     const T w_o = a.x[a.N];
-    for (int i = threadIdx.x; i < a.N; i += blockDim.x) {
-      const c2<T> y = s[pad16(i)];
-      epi_pair<T>(a, i, y.x, y.y, w_o);
+    for (int i0 = threadIdx.x; i0 < a.N; i0 += UNROLL * blockDim.x) {
+      EpiRaw<T> er[UNROLL];
+#pragma unroll
+      for (int u = 0; u < UNROLL; ++u) {
+        const int i = i0 + u * blockDim.x;
+        if (i < a.N) er[u] = epi_load<T>(a, i);
+      }
+#pragma unroll
+      for (int u = 0; u < UNROLL; ++u) {
+        const int i = i0 + u * blockDim.x;
+        if (i < a.N) {
+          const c2<T> y = s[pad16(i)];
+          epi_store<T>(a, i, er[u], y.x, y.y, w_o);
+        }
+      }
     }
     if (threadIdx.x == 0) epi_middle<T>(a, dot_total, w_o);
   } else {
-    for (int e = threadIdx.x; e < (nseq << logL); e += blockDim.x) {
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
       const int sq = e >> logL, i = e & (L - 1);
       a.z[(sq ? b2 : b) * (long long)L + i] = s[pad16(e)];
     }
@@ -374,28 +537,53 @@ __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_mid_f
 template <typename T>
 __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_inv_strided(LevelArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  c2<T>* s = reinterpret_cast<c2<T>*>(smem_raw);
+  c2<T>* tab = reinterpret_cast<c2<T>*>(smem_raw);
+  c2<T>* s = tab + TW_TAB;
   const int logR1 = a.logR1, logC = a.logC, logL = a.logL;
+  const c2<T>* tw = step_table<T>(tab, a.twL);
   const int C = 1 << logC;
   const int tile = 1 << (logR1 + logC);
   const long long c0 = (long long)blockIdx.x << logC;
-  for (int e = threadIdx.x; e < tile; e += blockDim.x) {
-    const int t = e >> logC, cc = e & (C - 1);
-    const long long c = c0 + cc;
-    const long long P = c + ((long long)t << logL);
-    const long long kb = (long long)brev_bits((unsigned)t, logR1);
-    s[pad16(e)] = cmulc<T>(a.z[P], inter_tw<T>(a.twm, c * kb));
+  for (int e0 = threadIdx.x; e0 < tile; e0 += 2 * UNROLL * blockDim.x) {
+    c2<T> v[2 * UNROLL];
+#pragma unroll
+    for (int u = 0; u < 2 * UNROLL; ++u) {
+      const int e = e0 + u * blockDim.x;
+      const int t = e >> logC, cc = e & (C - 1);
+      if (e < tile) v[u] = a.z[c0 + cc + ((long long)t << logL)];
+    }
+#pragma unroll
+    for (int u = 0; u < 2 * UNROLL; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e >= tile) continue;
+      const int t = e >> logC, cc = e & (C - 1);
+      const long long kb = (long long)brev_bits((unsigned)t, logR1);
+      s[pad16(e)] = cmulc<T>(v[u], inter_tw<T>(a.twm, (c0 + cc) * kb, a.logm));
+    }
   }
   __syncthreads();
-  smem_dit<T, true>(s, logR1, logC, C, 1, a.twL, LOG_LMAX);
+  smem_dit<T, true>(s, logR1, logC, C, 1, tw, LOG_LMAX);
   const T w_o = a.x[a.N];
   const int half = 1 << (logR1 - 1);
-  for (int e = threadIdx.x; e < (half << logC); e += blockDim.x) {
-    const int t = e >> logC, cc = e & (C - 1);
-    const long long P = c0 + cc + ((long long)t << logL);
-    if (P < a.N) {
-      const c2<T> y = s[pad16(e)];
-      epi_pair<T>(a, P, y.x, y.y, w_o);
+  const int nout = half << logC;
+  for (int e0 = threadIdx.x; e0 < nout; e0 += UNROLL * blockDim.x) {
+    EpiRaw<T> er[UNROLL];
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) {
+      const int e = e0 + u * blockDim.x;
+      const int t = e >> logC, cc = e & (C - 1);
+      const long long P = c0 + cc + ((long long)t << logL);
+      if (e < nout && P < a.N) er[u] = epi_load<T>(a, P);
+    }
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) {
+      const int e = e0 + u * blockDim.x;
+      const int t = e >> logC, cc = e & (C - 1);
+      const long long P = c0 + cc + ((long long)t << logL);
+      if (e < nout && P < a.N) {
+        const c2<T> y = s[pad16(e)];
+        epi_store<T>(a, P, er[u], y.x, y.y, w_o);
+      }
     }
   }
   if (blockIdx.x == 0 && threadIdx.x < 32) {
