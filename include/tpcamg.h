@@ -149,6 +149,27 @@ int tpc_time_level_kernels(tpc_handle* H, int level, int reps, const double* x_d
  * of the graph). */
 long long tpc_kernel_launches(const tpc_handle* H);
 
+/* y = A x for ONE level given in generator-plus-Cross form, for callers that cannot allocate
+ * device memory (work recorded while a CUDA graph is captured with allocation disallowed, a
+ * plugin whose host application owns every device allocation, a path that must not let
+ * cudaMalloc/cudaFree synchronise the device). The paper has no counterpart of this call. It
+ * allocates nothing: its work memory is one static device array of about 5.7 MB that every
+ * GPU loading this library holds until the process exits.
+ * N: N_k = 2^k - 1 with 2N + 2 <= 65536 (N <= 32767); larger or other N -> TPC_EINVAL.
+ * tA, tB, tC, tD: device arrays of 2N - 1 doubles, the generators t[d + N - 1] = T(i, j)
+ * (d = i - j) of A, B_bar, C_bar, D_bar (the tpc_export_level layout); p, q, xi, zeta: device
+ * arrays of N doubles; o: the middle diagonal entry; x_dev, y_dev: device arrays of 2N + 1
+ * doubles, not aliasing. Work is ordered on cuda_stream (NULL = default stream) and the call
+ * does not block. All calls share the static array and it keeps the last call's contents:
+ * calls that overlap on the GPU race, so order them on one stream. The first call on a device
+ * sets that device up (static array address, kernel limits, twiddle table) and synchronises
+ * it; make it before any stream capture. Returns TPC_OK, TPC_EINVAL or TPC_ECUDA (message in
+ * tpc_last_error(NULL)). */
+int tpc_apply_noalloc(long long N, const double* tA, const double* tB, const double* tC,
+                      const double* tD, const double* p, const double* q, const double* xi,
+                      const double* zeta, double o, const double* x_dev, double* y_dev,
+                      void* cuda_stream);
+
 /* Release everything a handle owns. NULL-safe. */
 void tpc_destroy(tpc_handle* H);
 

@@ -27,7 +27,7 @@ EXPORTED = ["tpc_default_params", "tpc_setup", "tpc_solve", "tpc_solve_host", "t
             "tpc_apply_f32",
             "tpc_vcycle", "tpc_level_size", "tpc_finest_level", "tpc_coarsest_level",
             "tpc_export_level", "tpc_host_hierarchy", "tpc_time_level_kernels",
-            "tpc_kernel_launches", "tpc_destroy", "tpc_last_error"]
+            "tpc_kernel_launches", "tpc_apply_noalloc", "tpc_destroy", "tpc_last_error"]
 
 
 class TpcParams(ctypes.Structure):
@@ -86,6 +86,8 @@ def lib() -> ctypes.CDLL:
     L.tpc_time_level_kernels.restype = I
     L.tpc_kernel_launches.argtypes = [P]
     L.tpc_kernel_launches.restype = LL
+    L.tpc_apply_noalloc.argtypes = [LL, P, P, P, P, P, P, P, P, D, P, P, P]
+    L.tpc_apply_noalloc.restype = I
     L.tpc_destroy.argtypes = [P]
     L.tpc_destroy.restype = None
     L.tpc_last_error.argtypes = [P]
@@ -224,6 +226,15 @@ def tpc_time_level_kernels(H, level: int, reps: int, x, f, y):
 
 def tpc_kernel_launches(H) -> int:
     return int(lib().tpc_kernel_launches(H))
+
+
+def tpc_apply_noalloc(N: int, tA, tB, tC, tD, p, q, xi, zeta, o: float, x, y,
+                      stream=None) -> None:
+    """y = A x for one level from device generators and Cross vectors, with no device
+    allocation (for callers that cannot allocate; see include/tpcamg.h for the limits)."""
+    _check(lib().tpc_apply_noalloc(N, _ptr(tA), _ptr(tB), _ptr(tC), _ptr(tD), _ptr(p), _ptr(q),
+                                   _ptr(xi), _ptr(zeta), float(o), _ptr(x), _ptr(y),
+                                   _stream_handle(stream)))
 
 
 def tpc_destroy(H) -> None:

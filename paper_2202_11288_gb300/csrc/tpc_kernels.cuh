@@ -689,20 +689,20 @@ __global__ void k_copy(const T* src, T* dst, long long n) {
 
 // Mixed precision: the FP64 residual r enters the FP32 V-cycles scaled to unit RMS,
 // f = r * sqrt(n / ||r||^2), and the FP32 correction e comes back as u += e / that scale.
-__global__ void k_to_f32_scaled(const double* r, float* f, long long n, const double* sumsq) {
+static __global__ void k_to_f32_scaled(const double* r, float* f, long long n, const double* sumsq) {
   const double ss = sumsq[0];
   const double s = (ss > 0.0) ? sqrt((double)n / ss) : 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     f[i] = (float)(r[i] * s);
 }
-__global__ void k_axpy_f32_scaled(double* u, const float* e, long long n, const double* sumsq) {
+static __global__ void k_axpy_f32_scaled(double* u, const float* e, long long n, const double* sumsq) {
   const double inv = sqrt(sumsq[0] / (double)n);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     u[i] = fma((double)e[i], inv, u[i]);
 }
-__global__ void k_round_f32(const double* in, float* out, long long n) {
+static __global__ void k_round_f32(const double* in, float* out, long long n) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i < n) out[i] = (float)in[i];
 }
@@ -721,7 +721,7 @@ __global__ void __launch_bounds__(NTHREADS) k_sumsq_partial(const T* r, long lon
   const double s = block_sum<double>(acc, red);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
-__global__ void k_sumsq_final(const double* part, int np, double* out) {
+static __global__ void k_sumsq_final(const double* part, int np, double* out) {
   double acc = 0;
   for (int i = threadIdx.x; i < np; i += 32) acc += part[i];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
