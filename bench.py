@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--K", type=int, default=22)
     ap.add_argument("--delta", type=float, default=0.05)
     ap.add_argument("--tol", type=float, default=1e-10)
-    ap.add_argument("--inner", type=int, default=4, help="FP32 V-cycles per FP64 residual")
+    ap.add_argument("--inner", type=int, default=6, help="FP32 V-cycles per FP64 residual")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="profiling case: set up, then 3 finest-level products, nothing timed")

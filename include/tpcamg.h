@@ -64,7 +64,7 @@ typedef struct tpc_params {
   int coarsest_level; /* kc, 1 <= kc <= K (default 3)                                      */
   int precision;      /* TPC_FP64, or TPC_MIXED: FP32 V-cycles inside FP64 refinement      */
   int max_iters;      /* outer iterations of tpc_solve (default 100)                       */
-  int inner_cycles;   /* TPC_MIXED: FP32 V-cycles per FP64 residual (default 4)            */
+  int inner_cycles;   /* TPC_MIXED: FP32 V-cycles per FP64 residual (default 6)            */
 } tpc_params;
 
 typedef struct tpc_handle tpc_handle;

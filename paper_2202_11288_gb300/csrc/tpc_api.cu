@@ -18,7 +18,9 @@ namespace tpc {
 void set_host_error(const std::string& s);
 const char* host_error();
 
-constexpr int LOG_WHOLE = 9;      // m <= 2^9: one CTA per product
+// One block does the whole product for m <= 2^LOG_WHOLE: FP64 (bound by the FP64 pipe, one
+// SM is slow) only for small m; FP32 up to the 4096 points one block holds.
+template <typename T> constexpr int log_whole() { return sizeof(T) == 8 ? 9 : 12; }
 constexpr int LOG_R1_MAX = 11;    // strided pass: at most 2048 rows
 constexpr int LOG_TILE_MAX = 13;  // strided tile: at most 8192 complex entries
 constexpr int NORM_BLOCKS = 304;  // 2 x 152 SMs
@@ -49,6 +51,9 @@ template <typename T> struct Hier {
   T* partials = nullptr;
   c2<T>* twL = nullptr;          // W_4096^j, j < 4096 (FP32 kernels copy j <= 512)
   T* coarse_inv = nullptr;
+  BottomPlan<T>* bottom = nullptr;  // single-block V-cycle bottom (FP32, V(1,1)), or null
+  int bottom_li = -1;               // level index where it takes over
+  size_t bottom_smem = 0;
 };
 
 }  // namespace tpc
@@ -141,7 +146,7 @@ int grid_for(long long n) {
 template <typename T>
 void plan_level(DevLevel<T>& L) {
   L.logm = L.k + 1;
-  if (L.logm <= LOG_WHOLE) {
+  if (L.logm <= log_whole<T>()) {
     L.logR1 = 0;
     L.logL = L.logm;
     L.logC = 0;
@@ -163,8 +168,9 @@ void plan_level(DevLevel<T>& L) {
     L.mid_blocks = (1 << (L.logm - logL - 1)) + 1;
   }
   L.smem_strided =
-      L.logR1 ? sizeof(c2<T>) * (size_t)(TW_TAB + padded_size(1 << (L.logR1 + L.logC))) : 0;
-  L.smem_mid = sizeof(c2<T>) * (size_t)(TW_TAB + padded_size(1 << (L.logL + (L.logR1 ? 1 : 0))));
+      L.logR1 ? sizeof(c2<T>) * (size_t)(tw_slots<T>() + padded_size(1 << (L.logR1 + L.logC))) : 0;
+  L.smem_mid =
+      sizeof(c2<T>) * (size_t)(tw_slots<T>() + padded_size(1 << (L.logL + (L.logR1 ? 1 : 0))));
 }
 
 template <typename T>
@@ -257,6 +263,14 @@ T* enqueue_vcycle(tpc_handle* H, Hier<T>& G, int li, const T* f_top, const T* rf
   T* e = G.e[li];
   T* t = G.t[li];
   const T* f = rfine ? G.f[li] : f_top;
+  if (G.bottom && li == G.bottom_li && rfine) {
+    if (H->prm.variant == TPC_NONSYM)
+      k_vcycle_bottom<T, true><<<1, fft_threads<T>(), G.bottom_smem, s>>>(G.bottom);
+    else
+      k_vcycle_bottom<T, false><<<1, fft_threads<T>(), G.bottom_smem, s>>>(G.bottom);
+    H->launches += 1;
+    return t;  // the last post-smoothing product of level li writes G.t[li]
+  }
   if (L.k == H->kc) {
     if (rfine) {
       k_coarse_solve<T><<<1, 256, 0, s>>>(G.coarse_inv, G.f[li], rfine, e, (int)L.n);
@@ -344,6 +358,9 @@ cudaError_t set_smem_attrs() {
   if ((e = cudaFuncSetAttribute(k_mid_whole<T, NS>, A, big)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_mid_fwd<T>, A, big)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_mid_fwd_real<T>, A, big)) != cudaSuccess) return e;
+  if constexpr (sizeof(T) == 4) {
+    if ((e = cudaFuncSetAttribute(k_vcycle_bottom<T, NS>, A, big)) != cudaSuccess) return e;
+  }
   return cudaFuncSetAttribute(k_inv_strided<T>, A, big);
 }
 
@@ -371,7 +388,7 @@ int forward_real(tpc_handle* H, const Hier<double>& G, const DevLevel<double>& L
   } else {
     k_fwd_strided<double, IN_REAL><<<L.fwd_blocks, FFT_THREADS, L.smem_strided, s>>>(a);
     k_mid_fwd<double><<<1 << L.logR1, FFT_THREADS,
-                        sizeof(double2) * (size_t)(TW_TAB + padded_size(1 << L.logL)), s>>>(a);
+                        sizeof(double2) * (size_t)(tw_slots<double>() + padded_size(1 << L.logL)), s>>>(a);
   }
   TPC_CUDA(H, cudaGetLastError());
   return TPC_OK;
@@ -450,6 +467,64 @@ int alloc_levels(tpc_handle* H, Hier<T>& G) {
   return TPC_OK;
 }
 
+// The single-block bottom of the FP32 V(1,1) cycle: levels li0..(coarsest-1) all use the
+// one-block plan; li0 > 0 (the level above passes its residual down).
+template <typename T>
+int build_bottom(tpc_handle* H, Hier<T>& G) {
+  const int nlev = (int)G.lev.size();
+  const int ic = nlev - 1;  // coarsest
+  if (H->prm.m1 != 1 || H->prm.m2 != 1 || nlev < 3) return TPC_OK;
+  int li0 = ic;
+  while (li0 - 1 >= 1 && G.lev[li0 - 1].logR1 == 0) --li0;
+  const int np = ic - li0;  // product levels in the bottom
+  if (np < 1 || np > BOTTOM_MAX_LEVELS) return TPC_OK;
+  BottomPlan<T> bp;
+  std::memset(&bp, 0, sizeof(bp));
+  bp.nlev = np;
+  for (int j = 0; j < np; ++j) {
+    const int li = li0 + j;
+    const DevLevel<T>& L = G.lev[li];
+    LevelArgs<T> a = level_args<T>(G, L);
+    a.pA = L.wA_pre;
+    a.pO = L.wO_pre;
+    a.pD = L.wD_pre;
+    // descent: restriction of the finer residual + first sweep, residual
+    a.pro = PRO_RESTRICT;
+    a.rfine = G.t[li - 1];
+    a.fout = G.f[li];
+    a.xout = G.e[li];
+    a.x = G.e[li];
+    a.f = G.f[li];
+    a.y = G.t[li];
+    a.epi = EPI_RESID;
+    a.wA = L.wA_pre;
+    a.wO = L.wO_pre;
+    a.wD = L.wD_pre;
+    bp.pre[j] = a;
+    // ascent: coarse correction + one post-smoothing sweep, result in t
+    a.pro = PRO_PROLONG;
+    a.rfine = nullptr;
+    a.fout = nullptr;
+    a.ec = (li + 1 == ic) ? G.e[ic] : G.t[li + 1];
+    a.epi = EPI_JACOBI;
+    a.wA = L.wA_post;
+    a.wO = L.wO_post;
+    a.wD = L.wD_post;
+    bp.post[j] = a;
+  }
+  bp.cinv = G.coarse_inv;
+  bp.rc = G.t[ic - 1];
+  bp.fc = G.f[ic];
+  bp.ec = G.e[ic];
+  bp.nc = (int)G.lev[ic].n;
+  TPC_TRY(dalloc(H, &G.bottom, 1));
+  TPC_CUDA(H, cudaMemcpyAsync(G.bottom, &bp, sizeof(bp), cudaMemcpyHostToDevice, H->stream));
+  TPC_CUDA(H, cudaStreamSynchronize(H->stream));
+  G.bottom_li = li0;
+  G.bottom_smem = sizeof(c2<T>) * (size_t)(tw_slots<T>() + padded_size(1 << G.lev[li0].logm));
+  return TPC_OK;
+}
+
 int setup_device(tpc_handle* H) {
   const HostHierarchy& HH = H->host;
   const int nlev = (int)HH.lev.size();
@@ -460,7 +535,10 @@ int setup_device(tpc_handle* H) {
   if ((ae = set_smem_attrs<float, false>()) != cudaSuccess) return cuda_fail(H, ae, "cudaFuncSetAttribute");
   if ((ae = set_smem_attrs<float, true>()) != cudaSuccess) return cuda_fail(H, ae, "cudaFuncSetAttribute");
   TPC_TRY(alloc_levels<double>(H, H->d));
-  if (mixed) TPC_TRY(alloc_levels<float>(H, H->s));
+  if (mixed) {
+    TPC_TRY(alloc_levels<float>(H, H->s));
+    TPC_TRY(build_bottom<float>(H, H->s));
+  }
   double* staging = nullptr;
   TPC_TRY(dalloc(H, &staging, (size_t)H->d.lev[0].m));
   // spectra of the Toeplitz blocks, divided by 2m (the 1/m of the inverse transform and the

@@ -130,26 +130,25 @@ __device__ __forceinline__ void reg_dit_stage(c2<T>* v) {
 // Twiddles of the in-shared-memory steps: W_4096^e = exp(-2 pi i e / 4096) for e < 4096 from
 // an octant table tab[j] = W_4096^j, j <= 512, held in shared memory, using the exact
 // symmetries W^{1024 q + r} = (-i)^q W^r and W^r = -i conj(W^{1024 - r}).
-constexpr int TW_TAB = 520;  // 513 entries, rounded up to keep the data after it aligned
+constexpr int TW_TAB = 520;  // octant table slots (513 entries, rounded for alignment)
+// Shared-memory slots reserved for the step twiddles ahead of the data: FP32 keeps the octant
+// table there; FP64 reads its table from global memory and reserves nothing.
+template <typename T> __host__ __device__ constexpr int tw_slots() {
+  return sizeof(T) == 8 ? 0 : TW_TAB;
+}
 template <typename T>
 __device__ __forceinline__ c2<T> tw4096(const c2<T>* __restrict__ tab, int e) {
   const int q = (e >> 10) & 3, r = e & 1023;
-  c2<T> w;
-  if (r <= 512) {
-    w = tab[r];
-  } else {
-    const c2<T> t = tab[1024 - r];
-    w = mk<T>(-t.y, -t.x);
-  }
-  switch (q) {
-    case 0: return w;
-    case 1: return mk<T>(w.y, -w.x);
-    case 2: return mk<T>(-w.x, -w.y);
-    default: return mk<T>(-w.y, w.x);
-  }
+  const bool flip = r > 512;
+  const c2<T> t = tab[flip ? 1024 - r : r];
+  const T a = flip ? -t.y : t.x, b = flip ? -t.x : t.y;  // W^r
+  // times (-i)^q
+  const T re = (q == 0) ? a : (q == 1) ? b : (q == 2) ? -a : -b;
+  const T im = (q == 0) ? b : (q == 1) ? -a : (q == 2) ? -b : a;
+  return mk<T>(re, im);
 }
-// The twiddle table the steps use: FP32 copies the octant of the global table into shared
-// memory (all threads; ends with a barrier); FP64 uses the global table directly.
+// The twiddle table the steps use: FP32 copies the octant of the global W_4096 table into
+// shared memory (all threads; ends with a barrier); FP64 uses the global table directly.
 template <typename T>
 __device__ __forceinline__ const c2<T>* step_table(c2<T>* tab, const c2<T>* __restrict__ g) {
   if constexpr (sizeof(T) == 8) {
@@ -171,12 +170,35 @@ template <int R> __device__ __forceinline__ int brev_r(int t) {
 // (FP32), see step_tw; 2^logLmax = 4096. QFAST: consecutive threads take
 // consecutive sequences first (interleaved column tiles), else consecutive columns.
 // W_4096^e for the in-shared-memory steps: FP64 (bound by the FP64 pipe, L1 mostly free)
-// reads the full 4096-entry table from global memory; FP32 (bound by memory latency, L1
-// mostly taken by shared memory) reads the octant table in shared memory.
+// reads the full 4096-entry table from global memory through L1; FP32 reads the octant table
+// in shared memory (a full table there is read at bank-conflicting strides, W^{c k} with c
+// varying across the lanes).
 template <typename T>
 __device__ __forceinline__ c2<T> step_tw(const c2<T>* __restrict__ tw, int e) {
   if constexpr (sizeof(T) == 8) return __ldg(tw + e);
-  else return tw4096<T>(tw, e);
+  else return tw4096<T>(tw, e);  // octant table in shared memory
+}
+
+// Twiddles W^{c k}, k = 1..R-1, of one task. FP64: one exact table read each. FP32: exact
+// reads of W^c, W^{2c}, W^{4c}, W^{8c} and the other powers as products of those (at most three
+// roundings), which keeps the FP32 steps' instruction count and table reads low.
+template <typename T, int R>
+__device__ __forceinline__ void task_twiddles(const c2<T>* __restrict__ tw, int c, int twsh,
+                                              c2<T>* pw) {
+  const int ec = c << twsh;
+  if constexpr (sizeof(T) == 8) {
+#pragma unroll
+    for (int k = 1; k < R; ++k) pw[k] = step_tw<T>(tw, ec * k);
+  } else {
+#pragma unroll
+    for (int k = 1; k < R; k <<= 1) pw[k] = step_tw<T>(tw, ec * k);
+#pragma unroll
+    for (int k = 3; k < R; ++k) {
+      if ((k & (k - 1)) == 0) continue;
+      const int hb = 1 << (31 - __clz(k));
+      pw[k] = cmul<T>(pw[k - hb], pw[hb]);
+    }
+  }
 }
 
 template <typename T, int R, bool QFAST, bool INV>
@@ -202,24 +224,31 @@ __device__ __forceinline__ void fft_step(c2<T>* s, int logS, int logL, int logCo
     }
     const int base = q * qs + ((sb << logS) + c) * ts;
     const int step = ts << logCols;
+    // pad16(base + t step) = pad16(base) + t pstep when step is a multiple of 16
+    const bool uni = (step & 15) == 0;
+    const int pb = pad16(base), pstep = step + (step >> 4);
     c2<T> v[R];
 #pragma unroll
-    for (int t = 0; t < R; ++t) v[t] = s[pad16(base + t * step)];
+    for (int t = 0; t < R; ++t) v[t] = s[uni ? pb + t * pstep : pad16(base + t * step)];
     if (INV) {
       if (logCols > 0) {
+        c2<T> pw[R];
+        task_twiddles<T, R>(tw, c, twsh, pw);
 #pragma unroll
-        for (int t = 1; t < R; ++t) v[t] = cmulc<T>(v[t], step_tw<T>(tw, (c * brev_r<R>(t)) << twsh));
+        for (int t = 1; t < R; ++t) v[t] = cmulc<T>(v[t], pw[brev_r<R>(t)]);
       }
       reg_dit_stage<T, R>(v);
     } else {
       reg_dif_stage<T, R>(v);
       if (logCols > 0) {
+        c2<T> pw[R];
+        task_twiddles<T, R>(tw, c, twsh, pw);
 #pragma unroll
-        for (int t = 1; t < R; ++t) v[t] = cmul<T>(v[t], step_tw<T>(tw, (c * brev_r<R>(t)) << twsh));
+        for (int t = 1; t < R; ++t) v[t] = cmul<T>(v[t], pw[brev_r<R>(t)]);
       }
     }
 #pragma unroll
-    for (int t = 0; t < R; ++t) s[pad16(base + t * step)] = v[t];
+    for (int t = 0; t < R; ++t) s[uni ? pb + t * pstep : pad16(base + t * step)] = v[t];
   }
 }
 

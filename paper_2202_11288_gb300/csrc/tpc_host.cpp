@@ -359,7 +359,7 @@ void tpc_default_params(tpc_params* p) {
   p->coarsest_level = 3;
   p->precision = TPC_FP64;
   p->max_iters = 100;
-  p->inner_cycles = 4;
+  p->inner_cycles = 6;
 }
 
 int tpc_host_hierarchy(const tpc_params* p, double delta, double h, int levels,

@@ -32,11 +32,27 @@ constexpr int LOG_LMAX = 12;        // longest in-shared-memory sub-transform (4
 constexpr int NTHREADS = 256;       // elementwise kernels
 constexpr int FFT_THREADS = 512;    // upper bound of the transform kernels' block size
 // Transform kernels: FP64 is bound by the FP64 pipe -> 512 threads (one radix-16 task per
-// thread for 8192 points, 16 warps on the SM's single resident block); FP32 is bound by memory
-// latency -> 256 threads and 3 resident blocks per SM so load, compute and store phases of
-// different blocks overlap.
-template <typename T> constexpr int fft_threads() { return sizeof(T) == 8 ? 512 : 256; }
-template <typename T> constexpr int fft_min_blocks() { return sizeof(T) == 8 ? 1 : 3; }
+// thread for 8192 points, 16 warps on the SM's single resident block); FP32 -> 256 threads,
+// 2 resident blocks per SM for the strided passes (their prologue / epilogue need the
+// registers) and 3 for the contiguous-block kernels (measured best for each).
+#ifndef TPC_F32_THREADS
+#define TPC_F32_THREADS 256
+#endif
+#ifndef TPC_F32_MIN_BLOCKS
+#define TPC_F32_MIN_BLOCKS 2
+#endif
+#ifndef TPC_F32_MID_MIN_BLOCKS
+#define TPC_F32_MID_MIN_BLOCKS 3
+#endif
+template <typename T> constexpr int fft_threads() { return sizeof(T) == 8 ? 512 : TPC_F32_THREADS; }
+// strided passes (register-heavier prologue / epilogue)
+template <typename T> constexpr int fft_min_blocks() {
+  return sizeof(T) == 8 ? 1 : TPC_F32_MIN_BLOCKS;
+}
+// contiguous-block kernels
+template <typename T> constexpr int mid_min_blocks() {
+  return sizeof(T) == 8 ? 1 : TPC_F32_MID_MIN_BLOCKS;
+}
 
 enum Epi { EPI_APPLY = 0, EPI_RESID = 1, EPI_JACOBI = 2 };
 // Prologue: how the operand u of the product is formed while it is loaded.
@@ -81,16 +97,38 @@ template <typename T> struct LevelArgs {
 };
 
 // Twiddle W_m^e of the strided passes, e < m. FP64 (whose kernels are bound by the FP64 pipe)
-// reads one table of m entries; FP32 (bound by memory latency) computes it with sincospif.
+// reads one table of m entries; FP32 (bound by memory latency) computes it (w_f32).
+// FP32 W_m^e = exp(-2 pi i e / m) without tables or FP64: the exact quadrant / octant symmetries
+// of sine and cosine reduce the angle to theta = 2 pi s / m in [0, pi/4] (s integer), then the
+// Taylor series of sin and cos, truncated after the x^9 / x^10 terms (remainder below 2e-9 for
+// |x| <= pi/4, far under the FP32 epsilon), are evaluated by Horner's rule.
+__device__ __forceinline__ float2 w_f32(int e, int logm) {
+  const int q4 = 1 << (logm - 2), q8 = q4 >> 1;
+  const int quad = e >> (logm - 2);
+  int r = e & (q4 - 1);
+  const bool swap = r > q8;
+  if (swap) r = q4 - r;
+  // 32-bit integer conversions only (64-bit ones would run on the FP64 pipe); 2^-logm exactly
+  const float x = (float)r * (6.283185307179586f * __int_as_float((127 - logm) << 23));
+  const float x2 = x * x;
+  const float sn = x * fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.0f / 362880.0f, -1.0f / 5040.0f),
+                                              1.0f / 120.0f), -1.0f / 6.0f), 1.0f);
+  const float cs = fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, -1.0f / 3628800.0f,
+                                                             1.0f / 40320.0f), -1.0f / 720.0f),
+                                          1.0f / 24.0f), -0.5f), 1.0f);
+  const float c0 = swap ? sn : cs, s0 = swap ? cs : sn;  // cos, sin of 2 pi (e mod m/4) / m
+  // exp(-i (quad pi/2 + phi)) = (-i)^quad (c0 - i s0)
+  const float re = (quad == 0) ? c0 : (quad == 1) ? -s0 : (quad == 2) ? -c0 : s0;
+  const float im = (quad == 0) ? -s0 : (quad == 1) ? -c0 : (quad == 2) ? s0 : c0;
+  return make_float2(re, im);
+}
+
 template <typename T>
 __device__ __forceinline__ c2<T> inter_tw(const c2<T>* __restrict__ twm, long long e, int logm) {
   if constexpr (sizeof(T) == 8) {
     return __ldg(twm + e);
   } else {
-    // FP32: W_m^e = (cospi(x), -sinpi(x)) with x = 2e/m, exact in FP32 for m <= 2^24
-    float sn, cs;
-    sincospif(ldexpf((float)e, 1 - logm), &sn, &cs);
-    return mk<T>(cs, -sn);
+    return w_f32((int)e, logm);  // e < m <= 2^24
   }
 }
 
@@ -162,7 +200,10 @@ __device__ __forceinline__ T operand(const LevelArgs<T>& a, long long j, T w) {
   return operand_finish<T>(a, j, operand_load<T>(a, j), w);
 }
 
-constexpr int UNROLL = 4;  // elements per thread whose loads are issued together
+#ifndef TPC_UNROLL
+#define TPC_UNROLL 4
+#endif
+constexpr int UNROLL = TPC_UNROLL;  // elements per thread whose loads are issued together
 
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, T* red) {
@@ -285,7 +326,7 @@ template <typename T, int IN>
 __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_fwd_strided(LevelArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2<T>* tab = reinterpret_cast<c2<T>*>(smem_raw);
-  c2<T>* s = tab + TW_TAB;
+  c2<T>* s = tab + tw_slots<T>();
   __shared__ T red[FFT_THREADS / 32];
   const int logR1 = a.logR1, logC = a.logC, logL = a.logL;
   const c2<T>* tw = step_table<T>(tab, a.twL);
@@ -368,29 +409,13 @@ __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_fwd_s
 // ------------------------------------------------------------------------------------
 // Contiguous blocks of L points: DIF, spectral product with the mirror block, DIT.
 // ------------------------------------------------------------------------------------
+// Body of the contiguous-block kernels on blocks (b, b2) with the step twiddles tw, the padded
+// data area s and the reduction scratch red in shared memory.
 template <typename T, int MODE, bool NS>
-__device__ __forceinline__ void mid_body(const LevelArgs<T>& a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  c2<T>* tab = reinterpret_cast<c2<T>*>(smem_raw);
-  c2<T>* s = tab + TW_TAB;
-  __shared__ T red[FFT_THREADS / 32];
+__device__ __forceinline__ void mid_core(const LevelArgs<T>& a, const c2<T>* tw, c2<T>* s,
+                                         T* red, long long b, long long b2) {
   const int logL = a.logL;
-  const c2<T>* tw = step_table<T>(tab, a.twL);
   const int L = 1 << logL;
-  long long b, b2;
-  if (MODE == MID_FWD || MODE == MID_FWD_REAL || MODE == MID_WHOLE) {
-    b = b2 = blockIdx.x;
-  } else {
-    const int cta = blockIdx.x;
-    if (cta < 2) {
-      b = b2 = cta;
-    } else {
-      const long long j = cta - 1;
-      const int g = 63 - __clzll(j);
-      b = j + (1LL << g);
-      b2 = 3 * (2LL << g) - 1 - b;
-    }
-  }
   const int nseq = (b != b2) ? 2 : 1;
   const int total = nseq << logL;
   T dot = 0;
@@ -513,21 +538,45 @@ __device__ __forceinline__ void mid_body(const LevelArgs<T>& a) {
   }
 }
 
+template <typename T, int MODE, bool NS>
+__device__ __forceinline__ void mid_body(const LevelArgs<T>& a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  c2<T>* tab = reinterpret_cast<c2<T>*>(smem_raw);
+  c2<T>* s = tab + tw_slots<T>();
+  __shared__ T red[FFT_THREADS / 32];
+  const c2<T>* tw = step_table<T>(tab, a.twL);
+  long long b, b2;
+  if (MODE == MID_FWD || MODE == MID_FWD_REAL || MODE == MID_WHOLE) {
+    b = b2 = blockIdx.x;
+  } else {
+    const int cta = blockIdx.x;
+    if (cta < 2) {
+      b = b2 = cta;
+    } else {
+      const long long j = cta - 1;
+      const int g = 63 - __clzll(j);
+      b = j + (1LL << g);
+      b2 = 3 * (2LL << g) - 1 - b;
+    }
+  }
+  mid_core<T, MODE, NS>(a, tw, s, red, b, b2);
+}
+
 // One kernel name per mode (so profilers can select them).
 template <typename T, bool NS>
-__global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_mid_pair(LevelArgs<T> a) {
+__global__ void __launch_bounds__(fft_threads<T>(), mid_min_blocks<T>()) k_mid_pair(LevelArgs<T> a) {
   mid_body<T, MID_PAIR, NS>(a);
 }
 template <typename T, bool NS>
-__global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_mid_whole(LevelArgs<T> a) {
+__global__ void __launch_bounds__(fft_threads<T>(), mid_min_blocks<T>()) k_mid_whole(LevelArgs<T> a) {
   mid_body<T, MID_WHOLE, NS>(a);
 }
 template <typename T>
-__global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_mid_fwd(LevelArgs<T> a) {
+__global__ void __launch_bounds__(fft_threads<T>(), mid_min_blocks<T>()) k_mid_fwd(LevelArgs<T> a) {
   mid_body<T, MID_FWD, false>(a);
 }
 template <typename T>
-__global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_mid_fwd_real(LevelArgs<T> a) {
+__global__ void __launch_bounds__(fft_threads<T>(), mid_min_blocks<T>()) k_mid_fwd_real(LevelArgs<T> a) {
   mid_body<T, MID_FWD_REAL, false>(a);
 }
 
@@ -538,7 +587,7 @@ template <typename T>
 __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_inv_strided(LevelArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2<T>* tab = reinterpret_cast<c2<T>*>(smem_raw);
-  c2<T>* s = tab + TW_TAB;
+  c2<T>* s = tab + tw_slots<T>();
   const int logR1 = a.logR1, logC = a.logC, logL = a.logL;
   const c2<T>* tw = step_table<T>(tab, a.twL);
   const int C = 1 << logC;
@@ -591,6 +640,70 @@ __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_inv_s
     for (int i = threadIdx.x; i < a.nparts; i += 32) acc += a.partials[i];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if (threadIdx.x == 0) epi_middle<T>(a, acc, w_o);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// The bottom of a V(1,1) cycle in one block: every level whose product fits one block
+// (m <= 4096), from the level below the strided ones down to the coarsest and back up.
+// Descent, level i: u = omega D^{-1} (restriction of the finer residual), r = f - A u
+// (PRO_RESTRICT + EPI_RESID); coarsest: f = restriction, e = A^{-1} f; ascent: u + P e_c then
+// one damped Jacobi sweep (PRO_PROLONG + EPI_JACOBI). Same arithmetic, buffers and order as
+// the per-level launches, without one launch per product.
+// ------------------------------------------------------------------------------------
+constexpr int BOTTOM_MAX_LEVELS = 12;
+template <typename T> struct BottomPlan {
+  int nlev;                              // product levels, finest first
+  LevelArgs<T> pre[BOTTOM_MAX_LEVELS];
+  LevelArgs<T> post[BOTTOM_MAX_LEVELS];
+  const T* cinv;                         // coarsest inverse (nc x nc)
+  const T* rc;                           // residual of the level above the coarsest
+  T* fc;                                 // coarsest right-hand side
+  T* ec;                                 // coarsest solution
+  int nc;
+};
+
+template <typename T>
+__device__ __forceinline__ void copy_args(LevelArgs<T>* dst, const LevelArgs<T>* src) {
+  const int n = (int)(sizeof(LevelArgs<T>) / sizeof(int));
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    reinterpret_cast<int*>(dst)[i] = reinterpret_cast<const int*>(src)[i];
+  __syncthreads();
+}
+
+template <typename T, bool NS>
+__global__ void __launch_bounds__(fft_threads<T>(), 1) k_vcycle_bottom(const BottomPlan<T>* bp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  c2<T>* tab = reinterpret_cast<c2<T>*>(smem_raw);
+  c2<T>* s = tab + tw_slots<T>();
+  __shared__ T red[FFT_THREADS / 32];
+  __shared__ __align__(16) LevelArgs<T> la;
+  const int nlev = bp->nlev;
+  const c2<T>* tw = step_table<T>(tab, bp->pre[0].twL);
+  for (int i = 0; i < nlev; ++i) {
+    copy_args<T>(&la, &bp->pre[i]);
+    mid_core<T, MID_WHOLE, NS>(la, tw, s, red, 0, 0);
+    __syncthreads();
+  }
+  {
+    T* fs = reinterpret_cast<T*>(s);
+    const int nc = bp->nc;
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+      fs[i] = restrict_at<T>(bp->rc, i);
+      bp->fc[i] = fs[i];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+      T acc = 0;
+      for (int j = 0; j < nc; ++j) acc = fma(bp->cinv[(long long)i * nc + j], fs[j], acc);
+      bp->ec[i] = acc;
+    }
+    __syncthreads();
+  }
+  for (int i = nlev - 1; i >= 0; --i) {
+    copy_args<T>(&la, &bp->post[i]);
+    mid_core<T, MID_WHOLE, NS>(la, tw, s, red, 0, 0);
+    __syncthreads();
   }
 }
 

@@ -162,9 +162,9 @@ extern "C" int tpc_apply_noalloc(long long N, const double* tA, const double* tB
     mid_blocks = (1 << (logm - logL - 1)) + 1;
   }
   const size_t smem_strided =
-      logR1 ? sizeof(double2) * (size_t)(TW_TAB + padded_size(1 << (logR1 + logC))) : 0;
-  const size_t smem_mid = sizeof(double2) * (size_t)(TW_TAB + padded_size(1 << (logL + (logR1 ? 1 : 0))));
-  const size_t smem_fwd_blk = sizeof(double2) * (size_t)(TW_TAB + padded_size(1 << logL));
+      logR1 ? sizeof(double2) * (size_t)(tw_slots<double>() + padded_size(1 << (logR1 + logC))) : 0;
+  const size_t smem_mid = sizeof(double2) * (size_t)(tw_slots<double>() + padded_size(1 << (logL + (logR1 ? 1 : 0))));
+  const size_t smem_fwd_blk = sizeof(double2) * (size_t)(tw_slots<double>() + padded_size(1 << logL));
 
   double* stage = reinterpret_cast<double*>(base + OFF_STAGE);
   double2* z = reinterpret_cast<double2*>(base + OFF_Z);
