@@ -53,6 +53,12 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--inner", type=int, default=6, help="FP32 V-cycles per FP64 residual")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=512,
+                    help="instances of the batched-uneven measurement (0 = skip it)")
+    ap.add_argument("--serve-rates", default="50,200,1000,2000",
+                    help="Poisson arrival rates (req/s) of the serving measurement ('' = skip)")
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="arrival window per rate of the serving measurement")
     ap.add_argument("--profile", action="store_true",
                     help="profiling case: set up, then 3 finest-level products, nothing timed")
     ap.add_argument("--profile-f32", action="store_true",
@@ -221,6 +227,137 @@ def time_solves(tpc, torch, S, stream, rhs, x, args, clocks=None):
     return ev0.elapsed_time(ev1), iters, tpc.tpc_kernel_launches(S.handle) - l0, clk
 
 
+def batch_workload(count, seed=0):
+    """Uneven 1-D instances: N = 2^K with K uniform in 9..17 (1023 .. 262143 unknowns), delta
+    uniform in [0.02, 0.25] (redrawn until r >= 1), SPD / nonsymmetric alternating, constant
+    kernel, uniform[-1,1) right-hand sides."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for i in range(count):
+        K = int(rng.integers(9, 18))
+        while True:
+            delta = float(rng.uniform(0.02, 0.25))
+            if delta * (1 << K) >= 1.0:
+                break
+        specs.append((K, delta, i % 2))
+    return specs
+
+
+def time_batch(tpc, torch, args, rank):
+    """One step = one tpc_solve_batch call over all instances (mixed precision)."""
+    specs = batch_workload(args.batch)
+    solvers = [tpc.Solver(d, 2.0 ** -K, variant=v, precision=tpc.TPC_MIXED) for K, d, v in specs]
+    bs = [torch.tensor(uniform_pm1(S.n, 5000 + i), device="cuda") for i, S in enumerate(solvers)]
+    xs = [torch.zeros_like(b) for b in bs]
+    handles = [S.handle for S in solvers]
+    for _ in range(2):
+        rc, its, rels, sts = tpc.tpc_solve_batch(handles, bs, xs, tol=args.tol)
+        assert rc == tpc.TPC_OK, rc
+    torch.cuda.synchronize()
+    steps = max(1, args.steps)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        rc, its, rels, sts = tpc.tpc_solve_batch(handles, bs, xs, tol=args.tol)
+        assert rc == tpc.TPC_OK and max(rels) < args.tol
+    torch.cuda.synchronize()
+    sec = (time.perf_counter() - t0) / steps
+    dof = sum(S.n for S in solvers)
+    for S in solvers:
+        S.close()
+    return {"instances": len(specs), "solves_per_s": len(specs) / sec, "dof_per_s": dof / sec,
+            "ms_per_batch": 1000.0 * sec, "unknowns_total": dof,
+            "workload": "N=2^K, K uniform in 9..17, delta uniform in [0.02,0.25], SPD/nonsym, "
+                        "mixed precision, tol 1e-10, one tpc_solve_batch per step (host clock)"}
+
+
+def serve_keys():
+    """Problems of the serving measurement: N = 2^K, K in 9..21 (1023 .. 4,194,303 unknowns,
+    log-uniform when K is uniform), delta in {0.05, 0.1, 0.2}, SPD or nonsymmetric."""
+    return [(v, d, K) for K in range(9, 22) for d in (0.05, 0.1, 0.2) for v in (0, 1)]
+
+
+def time_serving(tpc, torch, args):
+    """Poisson arrivals into the request server; p50 / p99 latency and throughput per rate."""
+    rates = [float(r) for r in args.serve_rates.split(",") if r.strip()]
+    keys = serve_keys()
+    rng = np.random.default_rng(17)
+    rhs = {K: torch.tensor(uniform_pm1((1 << (K + 1)) - 1, 900 + K)).pin_memory()
+           for K in range(9, 22)}
+    pool = {K: [] for K in rhs}
+
+    def xbuf(K):
+        return pool[K].pop() if pool[K] else torch.empty(rhs[K].numel(), dtype=torch.float64).pin_memory()
+
+    srv = tpc.Server(hbm_budget_bytes=150 << 30, max_inflight=32, precision=tpc.TPC_MIXED)
+    out = {"workload": "Poisson arrivals; N=2^K, K uniform in 9..21 (1023..4,194,303 unknowns), "
+                       "delta in {0.05,0.1,0.2}, SPD/nonsym, mixed precision, tol 1e-10, host "
+                       "buffers (pinned); hierarchies resident (HBM budget 150 GB, 32 slots)",
+           "rates": []}
+    try:
+        owner = {}
+        t0 = time.perf_counter()
+        for v, d, K in keys:                           # prewarm: build every hierarchy once
+            x = xbuf(K)
+            owner[srv.submit(v, d, 2.0 ** -K, rhs[K], x, args.tol)] = (K, x)
+        got = 0
+        while got < len(keys):
+            for r in srv.poll(256, wait_ms=20):
+                K, x = owner.pop(r["ticket"])
+                pool[K].append(x)
+                got += 1
+        out["prewarm_s"] = time.perf_counter() - t0
+        for rate in rates:
+            n_req = max(1, int(rate * args.serve_seconds))
+            gaps = rng.exponential(1.0 / rate, n_req)
+            picks = rng.integers(len(keys), size=n_req)
+            lat, bad = [], 0
+            start = time.perf_counter()
+            t_next = start
+            for i in range(n_req):
+                t_next += gaps[i]
+                while True:
+                    for r in srv.poll(256, wait_ms=0):
+                        K, x = owner.pop(r["ticket"])
+                        pool[K].append(x)
+                        lat.append(r["latency_s"])
+                        bad += r["status"] != tpc.TPC_OK
+                    dt = t_next - time.perf_counter()
+                    if dt <= 0:
+                        break
+                    time.sleep(min(dt, 0.0005))
+                v, d, K = keys[picks[i]]
+                x = xbuf(K)
+                owner[srv.submit(v, d, 2.0 ** -K, rhs[K], x, args.tol)] = (K, x)
+            while owner:
+                for r in srv.poll(256, wait_ms=20):
+                    K, x = owner.pop(r["ticket"])
+                    pool[K].append(x)
+                    lat.append(r["latency_s"])
+                    bad += r["status"] != tpc.TPC_OK
+            wall = time.perf_counter() - start
+            lat_ms = np.array(lat) * 1000.0
+            out["rates"].append({"rate_req_s": rate, "requests": n_req,
+                                 "throughput_req_s": n_req / wall,
+                                 "p50_ms": float(np.percentile(lat_ms, 50)),
+                                 "p99_ms": float(np.percentile(lat_ms, 99)),
+                                 "failed": int(bad)})
+    finally:
+        srv.close()
+    return out
+
+
+def replica_throughput(local_ms, steps, world, dist=None, device=None):
+    """Whole-job throughput of N replicas: every rank times `steps` of its own solves; the
+    job's time is the maximum over ranks (all_reduce MAX), and the value counts the solves of
+    all ranks: world * steps / max_ms. Returns (value per second, max ms)."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if dist is not None and world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return world * steps / (ms_max / 1000.0), ms_max
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -233,10 +370,7 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl")
 
     def max_over_ranks(v):
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        if dist:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replica_throughput(v, 1, world, dist, "cuda")[1]
 
     def barrier():
         if dist:
@@ -300,6 +434,10 @@ def run_ours(args, rank, world, local_rank):
                 "peak_source": "FP64: 152 SMs x 4 flop/clk x max SM clock (unit counts and "
                                "clocks; FMA-loop probe 1.19 TFLOP/s)",
                 "ms_per_launch": {"fwd_strided": ms3[0], "mid": ms3[1], "inv_strided": ms3[2]}}
+    # the batched and served measurements run on one GPU (rank 0 of a single-rank job)
+    batch = time_batch(tpc, torch, args, rank) if (args.batch > 0 and world == 1) else None
+    serving = (time_serving(tpc, torch, args)
+               if (args.serve_rates.strip() and world == 1) else None)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -315,6 +453,10 @@ def run_ours(args, rank, world, local_rank):
                 "roofline": roofline, "clocks": clk,
                 "gpu_launches": int(launches)}
         line["speedup_mixed_vs_fp64"] = line["value"] / line["fp64"]["value"]
+        if batch:
+            line["batch_uneven"] = batch
+        if serving:
+            line["serving"] = serving
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(line), flush=True)

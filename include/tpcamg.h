@@ -97,6 +97,21 @@ int tpc_setup(const tpc_params* p, double delta, double h, int levels, void* cud
 int tpc_solve(tpc_handle* H, const double* b_dev, double* x_dev, double tol, int use_x0,
               int* iters_out, double* relres_out);
 
+/* Solve count independent systems at once (instances of any sizes, variants and precisions):
+ * instance i solves hs[i]'s system A x_dev[i] = b_dev[i] to tol (zero initial guess). Each
+ * instance runs on its own handle's stream and the host services the instances round-robin,
+ * so their iterations overlap on the GPU; every instance does exactly the arithmetic of
+ * tpc_solve on its handle (results are bitwise those of solving it alone). The handles must be
+ * distinct; b_dev[i], x_dev[i] are device arrays of that handle's n_K doubles. iters_out,
+ * relres_out, status_out (host arrays of count entries, may be NULL) receive each instance's
+ * outer iterations, final relative residual and status (TPC_OK / TPC_ENOTCONV / ...).
+ * Returns TPC_OK if every instance converged, else the most severe instance status or an
+ * error. Blocks until every x_dev[i] holds its result. This is the batched-instances mode of
+ * the solver (not in the paper, which solves one system at a time). */
+int tpc_solve_batch(tpc_handle* const* hs, int count, const double* const* b_dev,
+                    double* const* x_dev, double tol, int* iters_out, double* relres_out,
+                    int* status_out);
+
 /* Same as tpc_solve with host buffers b_host / x_host (n_K doubles each): the call copies
  * b to the device, solves and copies x back before returning. */
 int tpc_solve_host(tpc_handle* H, const double* b_host, double* x_host, double tol,
@@ -169,6 +184,53 @@ int tpc_apply_noalloc(long long N, const double* tA, const double* tB, const dou
                       const double* tD, const double* p, const double* q, const double* xi,
                       const double* zeta, double o, const double* x_dev, double* y_dev,
                       void* cuda_stream);
+
+/* ---- Request server: continuous batching of independent solves (not in the paper) ----
+ * A worker thread admits submitted requests while a slot (max_inflight) and device memory
+ * (hbm_budget_bytes) are free, keeps level hierarchies resident keyed by (variant, delta, h,
+ * precision) and reuses an idle one when a key repeats (evicting idle ones least recently used
+ * first), and runs every admitted solve on its own stream exactly as tpc_solve would (the
+ * result is bitwise that of solving it alone). Requests that arrive while others are on the
+ * GPU start as soon as a slot and memory free up. */
+typedef struct tpc_server tpc_server;
+typedef struct tpc_server_config {
+  size_t hbm_budget_bytes; /* device memory the resident hierarchies may hold (default 150 GiB) */
+  int max_inflight;        /* solves on the GPU at once (default 32)                        */
+  int precision;           /* TPC_FP64 or TPC_MIXED (default)                                */
+  int max_handles_per_key; /* hierarchies of one key (default 1: same-key requests queue, no
+                              duplicate set-up); requests of other keys pass a waiting one  */
+} tpc_server_config;
+typedef struct tpc_request {
+  int variant;             /* TPC_SPD or TPC_NONSYM                                          */
+  double delta, h;         /* horizon and mesh size (h = 2^-K), as for tpc_setup             */
+  long long n;             /* 2/h - 1 unknowns: the length of b_host and x_host              */
+  const double* b_host;    /* right-hand side, host memory (pinned for speed), read once     */
+  double* x_host;          /* solution, host memory; valid when the result is polled         */
+  double tol;              /* relative residual target                                       */
+} tpc_request;
+typedef struct tpc_server_result {
+  long long ticket;        /* as returned by tpc_server_submit                               */
+  int status;              /* TPC_OK, TPC_ENOTCONV or a negative error                       */
+  int iters;               /* outer iterations                                               */
+  double relres;           /* final relative residual                                        */
+  double latency_s;        /* submit to result in x_host, seconds                            */
+  double queue_s;          /* submit to admission, seconds                                   */
+} tpc_server_result;
+
+/* Fill *c with the defaults above. */
+void tpc_server_default_config(tpc_server_config* c);
+/* Start a server on the current device. p: solver parameters for its handles (NULL = the
+ * defaults; precision is taken from cfg). *out owns the worker thread and every hierarchy. */
+int tpc_server_create(const tpc_server_config* cfg, const tpc_params* p, tpc_server** out);
+/* Queue one request (the buffers must stay valid until its result is polled). Thread-safe. */
+int tpc_server_submit(tpc_server* S, const tpc_request* r, long long* ticket);
+/* Move up to cap finished results into out (waiting up to wait_ms for the first); returns
+ * their number. Thread-safe. */
+int tpc_server_poll(tpc_server* S, tpc_server_result* out, int cap, int wait_ms);
+/* Requests submitted and not yet finished. */
+long long tpc_server_outstanding(tpc_server* S);
+/* Finish every outstanding request, free everything, stop the worker. NULL-safe. */
+void tpc_server_destroy(tpc_server* S);
 
 /* Release everything a handle owns. NULL-safe. */
 void tpc_destroy(tpc_handle* H);

@@ -23,11 +23,14 @@ TPC_EINVAL, TPC_ENOMEM, TPC_ECUDA, TPC_ESINGULAR, TPC_ENOTSUP, TPC_EDIVERGED = -
 TPC_SPD, TPC_NONSYM = 0, 1
 TPC_FP64, TPC_MIXED = 0, 1
 
-EXPORTED = ["tpc_default_params", "tpc_setup", "tpc_solve", "tpc_solve_host", "tpc_apply",
+EXPORTED = ["tpc_default_params", "tpc_setup", "tpc_solve", "tpc_solve_batch", "tpc_solve_host",
+            "tpc_apply",
             "tpc_apply_f32",
             "tpc_vcycle", "tpc_level_size", "tpc_finest_level", "tpc_coarsest_level",
             "tpc_export_level", "tpc_host_hierarchy", "tpc_time_level_kernels",
-            "tpc_kernel_launches", "tpc_apply_noalloc", "tpc_destroy", "tpc_last_error"]
+            "tpc_kernel_launches", "tpc_apply_noalloc", "tpc_destroy", "tpc_last_error",
+            "tpc_server_default_config", "tpc_server_create", "tpc_server_submit",
+            "tpc_server_poll", "tpc_server_outstanding", "tpc_server_destroy"]
 
 
 class TpcParams(ctypes.Structure):
@@ -37,6 +40,23 @@ class TpcParams(ctypes.Structure):
                 ("omega_pre", ctypes.c_double), ("omega_post", ctypes.c_double),
                 ("coarsest_level", ctypes.c_int), ("precision", ctypes.c_int),
                 ("max_iters", ctypes.c_int), ("inner_cycles", ctypes.c_int)]
+
+
+class TpcServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int),
+                ("precision", ctypes.c_int), ("max_handles_per_key", ctypes.c_int)]
+
+
+class TpcRequest(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("delta", ctypes.c_double), ("h", ctypes.c_double),
+                ("n", ctypes.c_longlong), ("b_host", ctypes.c_void_p), ("x_host", ctypes.c_void_p),
+                ("tol", ctypes.c_double)]
+
+
+class TpcServerResult(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_longlong), ("status", ctypes.c_int), ("iters", ctypes.c_int),
+                ("relres", ctypes.c_double), ("latency_s", ctypes.c_double),
+                ("queue_s", ctypes.c_double)]
 
 
 class TpcError(RuntimeError):
@@ -64,6 +84,8 @@ def lib() -> ctypes.CDLL:
     L.tpc_setup.restype = I
     L.tpc_solve.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]
     L.tpc_solve.restype = I
+    L.tpc_solve_batch.argtypes = [P, I, P, P, D, P, P, P]
+    L.tpc_solve_batch.restype = I
     L.tpc_solve_host.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]
     L.tpc_solve_host.restype = I
     L.tpc_apply.argtypes = [P, I, P, P]
@@ -88,6 +110,18 @@ def lib() -> ctypes.CDLL:
     L.tpc_kernel_launches.restype = LL
     L.tpc_apply_noalloc.argtypes = [LL, P, P, P, P, P, P, P, P, D, P, P, P]
     L.tpc_apply_noalloc.restype = I
+    L.tpc_server_default_config.argtypes = [ctypes.POINTER(TpcServerConfig)]
+    L.tpc_server_default_config.restype = None
+    L.tpc_server_create.argtypes = [ctypes.POINTER(TpcServerConfig), pp, ctypes.POINTER(P)]
+    L.tpc_server_create.restype = I
+    L.tpc_server_submit.argtypes = [P, ctypes.POINTER(TpcRequest), ctypes.POINTER(LL)]
+    L.tpc_server_submit.restype = I
+    L.tpc_server_poll.argtypes = [P, ctypes.POINTER(TpcServerResult), I, I]
+    L.tpc_server_poll.restype = I
+    L.tpc_server_outstanding.argtypes = [P]
+    L.tpc_server_outstanding.restype = LL
+    L.tpc_server_destroy.argtypes = [P]
+    L.tpc_server_destroy.restype = None
     L.tpc_destroy.argtypes = [P]
     L.tpc_destroy.restype = None
     L.tpc_last_error.argtypes = [P]
@@ -171,6 +205,22 @@ def tpc_solve(H, b, x, tol: float = 1e-10, use_x0: bool = False):
     rc = _check(lib().tpc_solve(H, _ptr(b), _ptr(x), tol, int(use_x0), ctypes.byref(it),
                                 ctypes.byref(rel)), H, allow=(TPC_OK, TPC_ENOTCONV))
     return rc, it.value, rel.value
+
+
+def tpc_solve_batch(handles, bs, xs, tol: float = 1e-10):
+    """Solve len(handles) independent systems concurrently; returns (rc, iters, relres, status)
+    lists. handles: tpc handles (distinct); bs, xs: device tensors (or pointers)."""
+    n = len(handles)
+    HA = (ctypes.c_void_p * n)(*[h.value if hasattr(h, "value") else h for h in handles])
+    BA = (ctypes.c_void_p * n)(*[_ptr(b) for b in bs])
+    XA = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+    it = (ctypes.c_int * n)()
+    rel = (ctypes.c_double * n)()
+    stt = (ctypes.c_int * n)()
+    rc = lib().tpc_solve_batch(HA, n, BA, XA, tol, it, rel, stt)
+    if rc < 0 and rc not in (TPC_EDIVERGED,):
+        raise TpcError(rc, tpc_last_error(None))
+    return rc, list(it), list(rel), list(stt)
 
 
 def tpc_solve_host(H, b: np.ndarray, x: np.ndarray, tol: float = 1e-10, use_x0: bool = False):
@@ -276,6 +326,63 @@ class Solver:
     def close(self) -> None:
         if self.handle:
             tpc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Request server (continuous batching): ``submit`` queues a solve on host buffers,
+    ``poll`` returns finished results. Buffers must stay alive until their result is polled."""
+
+    def __init__(self, hbm_budget_bytes: int | None = None, max_inflight: int | None = None,
+                 precision: int = TPC_MIXED, max_handles_per_key: int | None = None, **params):
+        cfg = TpcServerConfig()
+        lib().tpc_server_default_config(ctypes.byref(cfg))
+        if hbm_budget_bytes is not None:
+            cfg.hbm_budget_bytes = int(hbm_budget_bytes)
+        if max_inflight is not None:
+            cfg.max_inflight = int(max_inflight)
+        if max_handles_per_key is not None:
+            cfg.max_handles_per_key = int(max_handles_per_key)
+        cfg.precision = precision
+        p = tpc_default_params(**params)
+        self.handle = ctypes.c_void_p()
+        _check(lib().tpc_server_create(ctypes.byref(cfg), ctypes.byref(p), ctypes.byref(self.handle)))
+        self._keep = {}
+
+    def submit(self, variant: int, delta: float, h: float, b, x, tol: float = 1e-10) -> int:
+        """b, x: contiguous float64 host arrays (numpy, or pinned torch CPU tensors)."""
+        n = b.numel() if hasattr(b, "numel") else b.size
+        bp = b.data_ptr() if hasattr(b, "data_ptr") else b.ctypes.data
+        xp = x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
+        r = TpcRequest(variant, delta, h, n, bp, xp, tol)
+        t = ctypes.c_longlong(0)
+        _check(lib().tpc_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)))
+        self._keep[t.value] = (b, x)
+        return t.value
+
+    def poll(self, cap: int = 256, wait_ms: int = 0) -> list:
+        out = (TpcServerResult * cap)()
+        k = lib().tpc_server_poll(self.handle, out, cap, wait_ms)
+        res = []
+        for i in range(max(k, 0)):
+            r = out[i]
+            self._keep.pop(r.ticket, None)
+            res.append({"ticket": r.ticket, "status": r.status, "iters": r.iters,
+                        "relres": r.relres, "latency_s": r.latency_s, "queue_s": r.queue_s})
+        return res
+
+    def outstanding(self) -> int:
+        return int(lib().tpc_server_outstanding(self.handle))
+
+    def close(self) -> None:
+        if self.handle:
+            lib().tpc_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):  # pragma: no cover

@@ -13,7 +13,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libtpcamg.so")
-SOURCES = ["tpc_host.cpp", "tpc_api.cu", "tpc_noalloc.cu"]
+SOURCES = ["tpc_host.cpp", "tpc_api.cu", "tpc_noalloc.cu", "tpc_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -5,6 +5,7 @@
 // FP64 spectra rounded once.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -79,10 +80,12 @@ struct tpc_handle {
   double* hb = nullptr;               // device staging for tpc_solve_host (b, x)
   double* hx = nullptr;
   cudaGraphExec_t iter_exec = nullptr;
+  cudaEvent_t ev = nullptr;           // marks the latest ||r||^2 read-back
   long long iter_nodes = 0;           // kernel nodes of iter_exec
   long long launches = 0;             // kernels launched so far (see tpc_kernel_launches)
   std::string err;
   std::vector<void*> dev_allocs;
+  size_t dev_bytes = 0;               // device memory held by the handle
 };
 
 namespace {
@@ -106,17 +109,20 @@ int cuda_fail(tpc_handle* H, cudaError_t e, const char* what) {
     if (rc_ != TPC_OK) return rc_;   \
   } while (0)
 
+// Device allocations of a handle come from the device's stream-ordered memory pool (fast to
+// take and return when many handles are set up and destroyed, e.g. by a batch or a server).
 template <typename P>
 int dalloc(tpc_handle* H, P** ptr, size_t count) {
   void* v = nullptr;
-  cudaError_t e = cudaMalloc(&v, count * sizeof(P) + 16);
+  cudaError_t e = cudaMallocAsync(&v, count * sizeof(P) + 16, H->stream);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
-    H->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    H->err = std::string("cudaMallocAsync: ") + cudaGetErrorString(e);
     set_host_error(H->err);
     return (e == cudaErrorMemoryAllocation) ? TPC_ENOMEM : TPC_ECUDA;
   }
   H->dev_allocs.push_back(v);
+  H->dev_bytes += count * sizeof(P) + 16;
   *ptr = reinterpret_cast<P*>(v);
   return TPC_OK;
 }
@@ -592,6 +598,7 @@ int setup_device(tpc_handle* H) {
   TPC_TRY(dalloc(H, &H->sumsq_part, NORM_BLOCKS));
   TPC_TRY(dalloc(H, &H->sumsq, 1));
   TPC_CUDA(H, cudaMallocHost(&H->sumsq_host, sizeof(double)));
+  TPC_CUDA(H, cudaEventCreateWithFlags(&H->ev, cudaEventDisableTiming));
   TPC_CUDA(H, cudaStreamSynchronize(H->stream));
   // one outer iteration as a CUDA graph
   cudaGraph_t graph = nullptr;
@@ -612,7 +619,9 @@ void release(tpc_handle* H) {
   if (!H) return;
   if (H->iter_exec) cudaGraphExecDestroy(H->iter_exec);
   if (H->stream) cudaStreamSynchronize(H->stream);
-  for (void* p : H->dev_allocs) cudaFree(p);
+  if (H->ev) cudaEventDestroy(H->ev);
+  for (void* p : H->dev_allocs) cudaFreeAsync(p, H->stream);
+  if (H->stream) cudaStreamSynchronize(H->stream);
   if (H->sumsq_host) cudaFreeHost(H->sumsq_host);
   if (H->own_stream && H->stream) cudaStreamDestroy(H->stream);
   (void)cudaGetLastError();
@@ -624,11 +633,31 @@ int level_index(const tpc_handle* H, int level) {
   return H->K - level;
 }
 
-int solve_impl(tpc_handle* H, const double* b_dev, double* x_dev, double tol, int use_x0,
-               int* iters_out, double* relres_out) {
+// One solve as a small state machine, so that tpc_solve (one instance) and tpc_solve_batch
+// (several instances, each on its handle's stream, serviced round-robin) run the same steps:
+//   begin:   b copied in, u = 0 (or x0), r = b - A u, ||r||^2 read back asynchronously;
+//   step:    after the read-back arrives: test the stopping rule, else launch one iteration
+//            graph and read ||r||^2 back again;
+//   finish:  u copied to x.
+struct SolveState {
+  tpc_handle* H = nullptr;
+  double* x_dev = nullptr;
+  double tol = 0.0, r0 = 0.0, rel = 0.0;
+  int it = 0, status = TPC_OK;
+  bool started = false, done = false;
+};
+
+int solve_begin(SolveState& st, const double* b_dev, double* x_dev, double tol, int use_x0) {
+  tpc_handle* H = st.H;
   const long long n = H->d.lev[0].n;
   const size_t bytes = (size_t)n * sizeof(double);
   cudaStream_t s = H->stream;
+  st.x_dev = x_dev;
+  st.tol = tol;
+  st.it = 0;
+  st.status = TPC_OK;
+  st.started = false;
+  st.done = false;
   TPC_CUDA(H, cudaMemcpyAsync(H->b, b_dev, bytes, cudaMemcpyDeviceToDevice, s));
   if (use_x0) {
     TPC_CUDA(H, cudaMemcpyAsync(H->u, x_dev, bytes, cudaMemcpyDeviceToDevice, s));
@@ -640,37 +669,73 @@ int solve_impl(tpc_handle* H, const double* b_dev, double* x_dev, double tol, in
   enqueue_sumsq(H, H->r0, n);
   TPC_CUDA(H, cudaGetLastError());
   TPC_CUDA(H, cudaMemcpyAsync(H->sumsq_host, H->sumsq, sizeof(double), cudaMemcpyDeviceToHost, s));
-  TPC_CUDA(H, cudaStreamSynchronize(s));
-  const double r0 = std::sqrt(*H->sumsq_host);
-  double rel = (r0 > 0.0) ? 1.0 : 0.0;
-  int it = 0;
-  int status = TPC_OK;
-  if (!std::isfinite(r0)) {
-    H->err = "right-hand side or initial residual is not finite";
-    return TPC_EINVAL;
-  }
-  while (rel >= tol && r0 > 0.0) {
-    if (it >= H->prm.max_iters) {
-      status = TPC_ENOTCONV;
-      break;
+  TPC_CUDA(H, cudaEventRecord(H->ev, s));
+  return TPC_OK;
+}
+
+// Call when H->ev has completed. Decides and, if the solve goes on, enqueues one iteration.
+int solve_step(SolveState& st) {
+  tpc_handle* H = st.H;
+  cudaStream_t s = H->stream;
+  const double ss = *H->sumsq_host;
+  if (!st.started) {
+    st.started = true;
+    st.r0 = std::sqrt(ss);
+    st.rel = (st.r0 > 0.0) ? 1.0 : 0.0;
+    if (!std::isfinite(st.r0)) {
+      H->err = "right-hand side or initial residual is not finite";
+      st.status = TPC_EINVAL;
+      st.done = true;
+      return TPC_OK;
     }
-    TPC_CUDA(H, cudaGraphLaunch(H->iter_exec, s));
-    H->launches += H->iter_nodes;
-    TPC_CUDA(H, cudaMemcpyAsync(H->sumsq_host, H->sumsq, sizeof(double), cudaMemcpyDeviceToHost, s));
-    TPC_CUDA(H, cudaStreamSynchronize(s));
-    ++it;
-    rel = std::sqrt(*H->sumsq_host) / r0;
-    if (!std::isfinite(rel)) {
-      status = TPC_EDIVERGED;
+  } else {
+    ++st.it;
+    st.rel = std::sqrt(ss) / st.r0;
+    if (!std::isfinite(st.rel)) {
       H->err = "residual became non-finite";
-      break;
+      st.status = TPC_EDIVERGED;
+      st.done = true;
+      return TPC_OK;
     }
   }
-  TPC_CUDA(H, cudaMemcpyAsync(x_dev, H->u, bytes, cudaMemcpyDeviceToDevice, s));
-  TPC_CUDA(H, cudaStreamSynchronize(s));
-  if (iters_out) *iters_out = it;
-  if (relres_out) *relres_out = rel;
-  return status;
+  if (!(st.rel >= st.tol && st.r0 > 0.0)) {
+    st.done = true;
+    return TPC_OK;
+  }
+  if (st.it >= H->prm.max_iters) {
+    st.status = TPC_ENOTCONV;
+    st.done = true;
+    return TPC_OK;
+  }
+  TPC_CUDA(H, cudaGraphLaunch(H->iter_exec, s));
+  H->launches += H->iter_nodes;
+  TPC_CUDA(H, cudaMemcpyAsync(H->sumsq_host, H->sumsq, sizeof(double), cudaMemcpyDeviceToHost, s));
+  TPC_CUDA(H, cudaEventRecord(H->ev, s));
+  return TPC_OK;
+}
+
+int solve_finish(SolveState& st) {
+  tpc_handle* H = st.H;
+  const size_t bytes = (size_t)H->d.lev[0].n * sizeof(double);
+  if (st.status != TPC_EINVAL)
+    TPC_CUDA(H, cudaMemcpyAsync(st.x_dev, H->u, bytes, cudaMemcpyDeviceToDevice, H->stream));
+  return TPC_OK;
+}
+
+int solve_impl(tpc_handle* H, const double* b_dev, double* x_dev, double tol, int use_x0,
+               int* iters_out, double* relres_out) {
+  SolveState st;
+  st.H = H;
+  TPC_TRY(solve_begin(st, b_dev, x_dev, tol, use_x0));
+  while (!st.done) {
+    TPC_CUDA(H, cudaEventSynchronize(H->ev));
+    TPC_TRY(solve_step(st));
+  }
+  TPC_TRY(solve_finish(st));
+  TPC_CUDA(H, cudaStreamSynchronize(H->stream));
+  if (iters_out) *iters_out = st.it;
+  if (relres_out) *relres_out = st.rel;
+  return st.status;
 }
 
 template <typename T>
@@ -691,6 +756,84 @@ int apply_impl(tpc_handle* H, Hier<T>& G, int level, const T* x_dev, T* y_dev) {
 }
 
 }  // namespace
+
+// Asynchronous solve with host buffers, driven by polling (used by the request server):
+// the right-hand side is copied to the handle's staging buffer, the solve runs as in
+// tpc_solve, and the solution is copied back into the caller's host buffer.
+namespace tpc {
+struct AsyncSolve {
+  SolveState st;
+  double* x_host = nullptr;
+  bool copying_out = false;
+  bool complete = false;
+};
+
+int async_begin_host(tpc_handle* H, const double* b_host, double* x_host, double tol,
+                     AsyncSolve** out) {
+  const long long n = H->d.lev[0].n;
+  const size_t bytes = (size_t)n * sizeof(double);
+  if (!H->hb) {
+    TPC_TRY(dalloc(H, &H->hb, n));
+    TPC_TRY(dalloc(H, &H->hx, n));
+  }
+  AsyncSolve* a = new (std::nothrow) AsyncSolve();
+  if (!a) return TPC_ENOMEM;
+  a->st.H = H;
+  a->x_host = x_host;
+  cudaError_t e = cudaMemcpyAsync(H->hb, b_host, bytes, cudaMemcpyHostToDevice, H->stream);
+  if (e != cudaSuccess) {
+    delete a;
+    return cuda_fail(H, e, "cudaMemcpyAsync");
+  }
+  const int rc = solve_begin(a->st, H->hb, H->hx, tol, 0);
+  if (rc != TPC_OK) {
+    delete a;
+    return rc;
+  }
+  *out = a;
+  return TPC_OK;
+}
+
+// Non-blocking: advances the solve if its last read-back arrived. *done = 1 once the
+// solution is in the caller's host buffer.
+int async_poll(AsyncSolve* a, int* done) {
+  tpc_handle* H = a->st.H;
+  *done = 0;
+  if (a->complete) {
+    *done = 1;
+    return TPC_OK;
+  }
+  const cudaError_t q = cudaEventQuery(H->ev);
+  if (q == cudaErrorNotReady) return TPC_OK;
+  if (q != cudaSuccess) return cuda_fail(H, q, "cudaEventQuery");
+  if (a->copying_out) {
+    a->complete = true;
+    *done = 1;
+    return TPC_OK;
+  }
+  TPC_TRY(solve_step(a->st));
+  if (a->st.done) {
+    TPC_TRY(solve_finish(a->st));
+    const size_t bytes = (size_t)H->d.lev[0].n * sizeof(double);
+    if (a->st.status != TPC_EINVAL)
+      TPC_CUDA(H, cudaMemcpyAsync(a->x_host, H->hx, bytes, cudaMemcpyDeviceToHost, H->stream));
+    TPC_CUDA(H, cudaEventRecord(H->ev, H->stream));
+    a->copying_out = true;
+  }
+  return TPC_OK;
+}
+
+void async_result(const AsyncSolve* a, int* status, int* iters, double* relres) {
+  *status = a->st.status;
+  *iters = a->st.it;
+  *relres = a->st.rel;
+}
+
+void async_free(AsyncSolve* a) { delete a; }
+
+size_t handle_device_bytes(const tpc_handle* H) { return H ? H->dev_bytes : 0; }
+
+}  // namespace tpc
 
 extern "C" {
 
@@ -763,6 +906,63 @@ int tpc_solve(tpc_handle* H, const double* b_dev, double* x_dev, double tol, int
     return TPC_EINVAL;
   }
   return solve_impl(H, b_dev, x_dev, tol, use_x0, iters_out, relres_out);
+}
+
+int tpc_solve_batch(tpc_handle* const* hs, int count, const double* const* b_dev,
+                    double* const* x_dev, double tol, int* iters_out, double* relres_out,
+                    int* status_out) {
+  if (count < 0 || (count > 0 && (!hs || !b_dev || !x_dev)) || !(tol >= 0.0)) {
+    set_host_error("bad argument to tpc_solve_batch");
+    return TPC_EINVAL;
+  }
+  std::vector<tpc_handle*> sorted(hs, hs + count);
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i] || !b_dev[i] || !x_dev[i]) {
+      set_host_error("tpc_solve_batch: NULL handle or vector");
+      return TPC_EINVAL;
+    }
+  }
+  std::sort(sorted.begin(), sorted.end());
+  if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) {
+    set_host_error("tpc_solve_batch: a handle appears twice (each instance needs its own)");
+    return TPC_EINVAL;
+  }
+  std::vector<SolveState> st(count);
+  for (int i = 0; i < count; ++i) {
+    st[i].H = hs[i];
+    const int rc = solve_begin(st[i], b_dev[i], x_dev[i], tol, 0);
+    if (rc != TPC_OK) {
+      set_host_error(hs[i]->err);
+      return rc;
+    }
+  }
+  int active = count;
+  while (active > 0) {
+    for (int i = 0; i < count; ++i) {
+      if (st[i].done) continue;
+      tpc_handle* H = st[i].H;
+      TPC_CUDA(H, cudaEventSynchronize(H->ev));
+      const int rc = solve_step(st[i]);
+      if (rc != TPC_OK) {
+        set_host_error(H->err);
+        return rc;
+      }
+      if (st[i].done) {
+        TPC_TRY(solve_finish(st[i]));
+        --active;
+      }
+    }
+  }
+  int worst = TPC_OK;
+  for (int i = 0; i < count; ++i) {
+    tpc_handle* H = st[i].H;
+    TPC_CUDA(H, cudaStreamSynchronize(H->stream));
+    if (iters_out) iters_out[i] = st[i].it;
+    if (relres_out) relres_out[i] = st[i].rel;
+    if (status_out) status_out[i] = st[i].status;
+    if (st[i].status < worst || (worst == TPC_OK && st[i].status != TPC_OK)) worst = st[i].status;
+  }
+  return worst;
 }
 
 int tpc_solve_host(tpc_handle* H, const double* b_host, double* x_host, double tol, int use_x0,

@@ -39,4 +39,13 @@ void export_level(const LevelForm& L, double* dst);
 // exp(-2 pi i j / m) for j in [0, count), written as interleaved (re, im) pairs.
 void twiddles(long long m, long long count, std::vector<double>& out);
 
+// Polled solve with host buffers (tpc_api.cu), used by the request server (tpc_server.cu).
+struct AsyncSolve;
+int async_begin_host(tpc_handle* H, const double* b_host, double* x_host, double tol,
+                     AsyncSolve** out);
+int async_poll(AsyncSolve* a, int* done);
+void async_result(const AsyncSolve* a, int* status, int* iters, double* relres);
+void async_free(AsyncSolve* a);
+size_t handle_device_bytes(const tpc_handle* H);
+
 }  // namespace tpc

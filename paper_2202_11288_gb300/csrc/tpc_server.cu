@@ -1,0 +1,323 @@
+// Request server: continuous batching of independent solves on one GPU.
+//
+// A worker thread owns every handle. Requests (problem description + host buffers) are queued
+// by tpc_server_submit; the worker admits them while a slot (max_inflight) and device memory
+// (the HBM budget) are free, keeps level hierarchies resident keyed by the problem (variant,
+// horizon, mesh size, precision) and reuses an idle one when the key repeats (a request whose
+// key's hierarchies are all busy waits for one, unless the key may have another; later
+// requests of other keys go ahead), evicting idle hierarchies least-recently-used first when
+// the budget requires. Every admitted solve runs on
+// its handle's own stream as an ordinary tpc_solve (same arithmetic, same result as solving it
+// alone); the worker polls them without blocking, so requests that arrive while others are on
+// the GPU start as soon as a slot and memory free up and their work overlaps on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "tpc_internal.h"
+
+namespace tpc {
+void set_host_error(const std::string& s);
+}
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  long long ticket = 0;
+  tpc_request r{};
+  Clock::time_point t_submit;
+};
+
+struct Entry {
+  int variant = 0, precision = 0;
+  double delta = 0.0, h = 0.0;
+  tpc_handle* H = nullptr;
+  size_t bytes = 0;
+  bool busy = false;
+  unsigned long long last_use = 0;
+};
+
+struct Active {
+  Entry* entry = nullptr;
+  Request req;
+  tpc::AsyncSolve* a = nullptr;
+  Clock::time_point t_start;
+};
+
+}  // namespace
+
+struct tpc_server {
+  tpc_server_config cfg{};
+  tpc_params prm{};
+  int device = 0;
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv;
+  bool stop = false;
+  std::deque<Request> pending;           // guarded by mu
+  std::vector<tpc_server_result> done;   // guarded by mu
+  long long next_ticket = 1;             // guarded by mu
+  std::atomic<long long> outstanding{0};  // submitted and not yet finished
+  // worker-owned (entries are heap objects so that active solves keep valid pointers)
+  std::vector<Entry*> cache;
+  std::vector<Active> active;
+  size_t used_bytes = 0;
+  unsigned long long tick = 0;
+  std::string worker_err;
+};
+
+namespace {
+
+bool same_key(const Entry& e, const tpc_request& r, int precision) {
+  return e.variant == r.variant && e.precision == precision && e.delta == r.delta && e.h == r.h;
+}
+
+// Device bytes a hierarchy of this key needs: the size of a resident one with the same mesh
+// size, variant and precision if there is one, else an estimate from the level sizes (spectra,
+// twiddles, vectors over all levels: about 220 bytes per unknown in FP64, 320 with the FP32
+// copy, plus the fixed tables).
+size_t estimate_bytes(const tpc_server* S, const tpc_request& r) {
+  for (const Entry* e : S->cache)
+    if (e->h == r.h && e->precision == S->cfg.precision && e->variant == r.variant) return e->bytes;
+  const double n = 2.0 / r.h;
+  return (size_t)(n * (S->cfg.precision == TPC_MIXED ? 320.0 : 220.0)) + (size_t(256) << 10);
+}
+
+void finish_request(tpc_server* S, Active& act, int status, int iters, double relres) {
+  tpc_server_result res{};
+  res.ticket = act.req.ticket;
+  res.status = status;
+  res.iters = iters;
+  res.relres = relres;
+  res.latency_s = std::chrono::duration<double>(Clock::now() - act.req.t_submit).count();
+  res.queue_s = std::chrono::duration<double>(act.t_start - act.req.t_submit).count();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->done.push_back(res);
+  }
+  S->outstanding.fetch_sub(1);
+  S->cv.notify_all();
+}
+
+// Try to start the request; returns false if it must wait (for a slot, for memory, or for
+// a busy hierarchy of its key when the key already has max_handles_per_key of them).
+bool admit(tpc_server* S, Request& req) {
+  if ((int)S->active.size() >= S->cfg.max_inflight) return false;
+  const int prec = S->cfg.precision;
+  Entry* ent = nullptr;
+  int same = 0;
+  for (Entry* e : S->cache) {
+    if (!same_key(*e, req.r, prec)) continue;
+    ++same;
+    if (!e->busy) {
+      ent = e;
+      break;
+    }
+  }
+  if (!ent && same >= S->cfg.max_handles_per_key) return false;
+  Active act;
+  act.req = req;
+  act.t_start = Clock::now();
+  if (!ent) {
+    const size_t need = estimate_bytes(S, req.r);
+    // evict idle hierarchies, least recently used first, until the new one fits
+    while (S->used_bytes + need > S->cfg.hbm_budget_bytes) {
+      int lru = -1;
+      for (size_t i = 0; i < S->cache.size(); ++i)
+        if (!S->cache[i]->busy &&
+            (lru < 0 || S->cache[i]->last_use < S->cache[lru]->last_use))
+          lru = (int)i;
+      if (lru < 0) break;
+      S->used_bytes -= S->cache[lru]->bytes;
+      tpc_destroy(S->cache[lru]->H);
+      delete S->cache[lru];
+      S->cache.erase(S->cache.begin() + lru);
+    }
+    if (S->used_bytes + need > S->cfg.hbm_budget_bytes) {
+      if (!S->active.empty()) return false;  // wait for memory to free up
+      finish_request(S, act, TPC_ENOMEM, 0, 0.0);  // larger than the whole budget
+      return true;
+    }
+    tpc_params p = S->prm;
+    p.variant = req.r.variant;
+    tpc_handle* H = nullptr;
+    const int rc = tpc_setup(&p, req.r.delta, req.r.h, 0, nullptr, &H);
+    if (rc != TPC_OK) {
+      finish_request(S, act, rc, 0, 0.0);
+      return true;
+    }
+    ent = new Entry();
+    ent->variant = req.r.variant;
+    ent->precision = prec;
+    ent->delta = req.r.delta;
+    ent->h = req.r.h;
+    ent->H = H;
+    ent->bytes = tpc::handle_device_bytes(H);
+    S->used_bytes += ent->bytes;
+    S->cache.push_back(ent);
+  }
+  act.entry = ent;
+  const long long n = tpc_level_size(ent->H, tpc_finest_level(ent->H));
+  if (req.r.n != n) {
+    finish_request(S, act, TPC_EINVAL, 0, 0.0);
+    return true;
+  }
+  const int rc = tpc::async_begin_host(ent->H, req.r.b_host, req.r.x_host, req.r.tol, &act.a);
+  if (rc != TPC_OK) {
+    finish_request(S, act, rc, 0, 0.0);
+    return true;
+  }
+  // the staging buffers of the first host solve are allocated then: count them
+  S->used_bytes += tpc::handle_device_bytes(ent->H) - ent->bytes;
+  ent->bytes = tpc::handle_device_bytes(ent->H);
+  ent->busy = true;
+  S->active.push_back(act);
+  return true;
+}
+
+void worker_main(tpc_server* S) {
+  cudaSetDevice(S->device);
+  std::deque<Request> queue;
+  for (;;) {
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      if (queue.empty() && S->active.empty() && S->pending.empty() && !S->stop)
+        S->cv.wait_for(lk, std::chrono::milliseconds(1));
+      if (S->stop && S->pending.empty() && queue.empty() && S->active.empty()) break;
+      while (!S->pending.empty()) {
+        queue.push_back(S->pending.front());
+        S->pending.pop_front();
+      }
+    }
+    // admit in arrival order, passing over requests that must wait for their key, while
+    // slots and memory allow
+    for (auto it = queue.begin(); it != queue.end() && (int)S->active.size() < S->cfg.max_inflight;) {
+      if (admit(S, *it))
+        it = queue.erase(it);
+      else
+        ++it;
+    }
+    // advance the solves on the GPU
+    bool progressed = false;
+    for (size_t i = 0; i < S->active.size();) {
+      Active& act = S->active[i];
+      int fin = 0;
+      const int rc = tpc::async_poll(act.a, &fin);
+      if (rc != TPC_OK || fin) {
+        int status = rc, iters = 0;
+        double rel = 0.0;
+        if (rc == TPC_OK) tpc::async_result(act.a, &status, &iters, &rel);
+        tpc::async_free(act.a);
+        act.entry->busy = false;
+        act.entry->last_use = ++S->tick;
+        finish_request(S, act, status, iters, rel);
+        S->active.erase(S->active.begin() + i);
+        progressed = true;
+        continue;
+      }
+      ++i;
+    }
+    if (!progressed && !S->active.empty()) std::this_thread::yield();
+  }
+  for (Entry* e : S->cache) {
+    tpc_destroy(e->H);
+    delete e;
+  }
+  S->cache.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+void tpc_server_default_config(tpc_server_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->hbm_budget_bytes = (size_t)150 << 30;
+  c->max_inflight = 32;
+  c->precision = TPC_MIXED;
+  c->max_handles_per_key = 1;
+}
+
+int tpc_server_create(const tpc_server_config* cfg, const tpc_params* p, tpc_server** out) {
+  if (!cfg || !out || cfg->max_inflight < 1 || cfg->hbm_budget_bytes == 0 ||
+      cfg->max_handles_per_key < 1 ||
+      (cfg->precision != TPC_FP64 && cfg->precision != TPC_MIXED)) {
+    tpc::set_host_error("bad argument to tpc_server_create");
+    return TPC_EINVAL;
+  }
+  *out = nullptr;
+  tpc_server* S = new (std::nothrow) tpc_server();
+  if (!S) return TPC_ENOMEM;
+  S->cfg = *cfg;
+  if (p)
+    S->prm = *p;
+  else
+    tpc_default_params(&S->prm);
+  S->prm.precision = cfg->precision;
+  if (cudaGetDevice(&S->device) != cudaSuccess) {
+    (void)cudaGetLastError();
+    delete S;
+    tpc::set_host_error("tpc_server_create: no CUDA device");
+    return TPC_ECUDA;
+  }
+  S->worker = std::thread(worker_main, S);
+  *out = S;
+  return TPC_OK;
+}
+
+int tpc_server_submit(tpc_server* S, const tpc_request* r, long long* ticket) {
+  if (!S || !r || !r->b_host || !r->x_host || !(r->tol >= 0.0) || r->n <= 0) {
+    tpc::set_host_error("bad argument to tpc_server_submit");
+    return TPC_EINVAL;
+  }
+  Request q;
+  q.r = *r;
+  q.t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    q.ticket = S->next_ticket++;
+    S->pending.push_back(q);
+    S->outstanding.fetch_add(1);
+  }
+  S->cv.notify_all();
+  if (ticket) *ticket = q.ticket;
+  return TPC_OK;
+}
+
+int tpc_server_poll(tpc_server* S, tpc_server_result* out, int cap, int wait_ms) {
+  if (!S || (cap > 0 && !out) || cap < 0) return TPC_EINVAL;
+  std::unique_lock<std::mutex> lk(S->mu);
+  if (S->done.empty() && wait_ms > 0)
+    S->cv.wait_for(lk, std::chrono::milliseconds(wait_ms), [&] { return !S->done.empty(); });
+  const int k = std::min<int>(cap, (int)S->done.size());
+  for (int i = 0; i < k; ++i) out[i] = S->done[i];
+  S->done.erase(S->done.begin(), S->done.begin() + k);
+  return k;
+}
+
+long long tpc_server_outstanding(tpc_server* S) { return S ? S->outstanding.load() : 0; }
+
+void tpc_server_destroy(tpc_server* S) {
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv.notify_all();
+  if (S->worker.joinable()) S->worker.join();
+  delete S;
+}
+
+}  // extern "C"

@@ -1,0 +1,74 @@
+"""Request server (continuous batching): every result is the same alone and in the mix.
+
+Requests of several problems are submitted at once into a server with few slots and a tight
+device-memory budget (so hierarchies are evicted and rebuilt); each result must equal, bit for
+bit and with the same iteration count, the solve of the same request alone on its own handle.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import paper_2202_11288_gb300 as tpc
+from synth import uniform_pm1
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+KEYS = [(tpc.TPC_SPD, 0.05, 10), (tpc.TPC_NONSYM, 0.1, 11), (tpc.TPC_SPD, 0.2, 9),
+        (tpc.TPC_SPD, 0.125, 12), (tpc.TPC_NONSYM, 0.3, 10)]
+
+
+def _wait_all(srv, count, timeout_s=120.0):
+    got = []
+    t0 = time.time()
+    while len(got) < count and time.time() - t0 < timeout_s:
+        got += srv.poll(64, wait_ms=50)
+    return got
+
+
+def test_server_results_equal_alone_with_eviction():
+    rng = np.random.default_rng(3)
+    reqs = []
+    for i in range(20):
+        v, d, K = KEYS[int(rng.integers(len(KEYS)))]
+        n = (1 << (K + 1)) - 1
+        b = torch.tensor(uniform_pm1(n, 700 + i)).pin_memory()
+        x = torch.zeros(n, dtype=torch.float64).pin_memory()
+        reqs.append((v, d, K, b, x))
+    # a budget below the five hierarchies' total (about 5 MB), so the LRU eviction runs
+    srv = tpc.Server(hbm_budget_bytes=4 << 20, max_inflight=4, precision=tpc.TPC_MIXED)
+    try:
+        tickets = {srv.submit(v, d, 2.0 ** -K, b, x): i for i, (v, d, K, b, x) in enumerate(reqs)}
+        res = _wait_all(srv, len(reqs))
+        assert len(res) == len(reqs)
+        assert srv.outstanding() == 0
+    finally:
+        srv.close()
+    for r in res:
+        i = tickets[r["ticket"]]
+        v, d, K, b, x = reqs[i]
+        assert r["status"] == tpc.TPC_OK and r["relres"] < 1e-10
+        assert r["latency_s"] >= r["queue_s"] >= 0.0
+        S = tpc.Solver(d, 2.0 ** -K, variant=v, precision=tpc.TPC_MIXED)
+        try:
+            xa = np.zeros(b.numel())
+            rc, it, rel = S.solve_host(b.numpy(), xa, tol=1e-10)
+        finally:
+            S.close()
+        assert it == r["iters"] and rel == r["relres"]
+        assert np.array_equal(xa, x.numpy())
+
+
+def test_server_rejects_a_problem_larger_than_its_budget():
+    srv = tpc.Server(hbm_budget_bytes=1 << 20, max_inflight=2)
+    try:
+        K = 12
+        n = (1 << (K + 1)) - 1
+        b, x = np.ones(n), np.zeros(n)
+        srv.submit(tpc.TPC_SPD, 0.1, 2.0 ** -K, b, x)
+        res = _wait_all(srv, 1)
+        assert len(res) == 1 and res[0]["status"] == tpc.TPC_ENOMEM
+    finally:
+        srv.close()
