@@ -40,6 +40,26 @@ N_SMS = 152
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_mid_pair<double> launch at the finest
 # level, from ncu (profiles/k_mid_pair_fp64_N2e22.md); unknown for other sizes
 MID_TRAFFIC = {}
+# Algorithmic bytes of the FP32 finest-level kernels per point of the FFT length m = 2N + 2
+# (residual epilogue, no prologue; x, f, y hold about m floats, q, zeta and p, xi about m/2 each):
+#   forward pass:           reads x (4m), q and zeta (4m); writes z (8m)               -> 16m
+#   contiguous-block kernel: reads z (8m) and 16 B of spectra per pair (8m); writes z -> 24m
+#   inverse pass:           reads z (8m), p and xi (4m), f (4m); writes y (4m)         -> 20m
+F32_BYTES_PER_POINT = (16, 24, 20)
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP32 finest kernels, from ncu,
+# keyed by (K, kernel index); unknown for other sizes
+F32_TRAFFIC = {}
+
+
+def measured_hbm_gbs():
+    """The measured copy bandwidth of this GPU type, else the stated fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return {"gbs": float(json.load(fh)["hbm_gbs"]),
+                    "source": "measured STREAM-style copy (MEASURED_PEAKS.json hbm_gbs)"}
+    except (OSError, KeyError, ValueError):
+        return {"gbs": 6800.0, "source": "fallback 6.8 TB/s (no measured peak file)"}
 
 
 def parse():
@@ -419,8 +439,13 @@ def run_ours(args, rank, world, local_rank):
         assert rc == tpc.TPC_OK
     torch.cuda.synchronize()
     e2e_value = world * args.steps / max_over_ranks(time.perf_counter() - t0)
+    # the FP32 kernels of the finest level, which the FP32 V-cycles run most
+    x32 = x.float()
+    f32 = rhs[0].float()
+    y32 = torch.empty_like(x32)
+    ms3_32 = tpc.tpc_time_level_kernels_f32(S.handle, args.K, 5, x32, f32, y32)
     S.close()
-    del x_last
+    del x_last, x32, f32, y32
 
     m = 2 ** (args.K + 1)
     logL = min(12, (args.K + 2) // 2)
@@ -428,12 +453,28 @@ def run_ours(args, rank, world, local_rank):
     achieved = flops_mid / (ms3[1] * 1e-3) / 1e12
     sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
     peak = N_SMS * FP64_FLOP_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": MID_TRAFFIC.get(args.K),
-                "kernel": "k_mid_pair<double> (finest level; the FP64 residual product)",
-                "peak_source": "FP64: 152 SMs x 4 flop/clk x max SM clock (unit counts and "
-                               "clocks; FMA-loop probe 1.19 TFLOP/s)",
-                "ms_per_launch": {"fwd_strided": ms3[0], "mid": ms3[1], "inv_strided": ms3[2]}}
+    roofline_fp64 = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": MID_TRAFFIC.get(args.K),
+                     "kernel": "k_mid_pair<double> (finest level; the FP64 residual product)",
+                     "peak_source": "FP64: 152 SMs x 4 flop/clk x max SM clock (unit counts "
+                                    "and clocks; FMA-loop probe 1.19 TFLOP/s)",
+                     "ms_per_launch": {"fwd_strided": ms3[0], "mid": ms3[1],
+                                       "inv_strided": ms3[2]}}
+    # headline path: the FP32 finest-level kernels, each launched once per FP32 product; the
+    # dominant one is the slowest of the three
+    names = ("k_fwd_strided<float>", "k_mid_pair<float>", "k_inv_strided<float>")
+    dom = max(range(3), key=lambda i: ms3_32[i])
+    nbytes = [b * m for b in F32_BYTES_PER_POINT]
+    hbm = measured_hbm_gbs()
+    ach32 = nbytes[dom] / (ms3_32[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": ach32, "peak": hbm["gbs"], "unit": "GB/s",
+                "frac": ach32 / hbm["gbs"], "traffic": F32_TRAFFIC.get((args.K, dom)),
+                "kernel": names[dom] + " (finest level of the FP32 V-cycles)",
+                "algorithmic_bytes_per_launch": nbytes[dom],
+                "peak_source": hbm["source"],
+                "ms_per_launch": dict(zip(("fwd_strided", "mid", "inv_strided"), ms3_32)),
+                "achieved_all": {names[i]: nbytes[i] / (ms3_32[i] * 1e-3) / 1e9
+                                 for i in range(3)}}
     # the batched and served measurements run on one GPU (rank 0 of a single-rank job)
     batch = time_batch(tpc, torch, args, rank) if (args.batch > 0 and world == 1) else None
     serving = (time_serving(tpc, torch, args)
@@ -450,7 +491,7 @@ def run_ours(args, rank, world, local_rank):
                          "gpu_launches": int(l64)},
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                         "d2h_bytes_per_step": 8 * n},
-                "roofline": roofline, "clocks": clk,
+                "roofline": roofline, "roofline_fp64": roofline_fp64, "clocks": clk,
                 "gpu_launches": int(launches)}
         line["speedup_mixed_vs_fp64"] = line["value"] / line["fp64"]["value"]
         if batch:

@@ -160,6 +160,12 @@ int tpc_host_hierarchy(const tpc_params* p, double delta, double h, int levels,
 int tpc_time_level_kernels(tpc_handle* H, int level, int reps, const double* x_dev,
                            const double* f_dev, double* y_dev, double* ms_out);
 
+/* The same timing for the FP32 copy of the level in a TPC_MIXED handle (the kernels the FP32
+ * V-cycles run); x_dev, f_dev, y_dev: n_level floats on the device. TPC_EINVAL on an FP64
+ * handle. */
+int tpc_time_level_kernels_f32(tpc_handle* H, int level, int reps, const float* x_dev,
+                               const float* f_dev, float* y_dev, double* ms_out);
+
 /* Number of kernels this handle has launched so far (graph launches count every kernel node
  * of the graph). */
 long long tpc_kernel_launches(const tpc_handle* H);

@@ -28,7 +28,7 @@ EXPORTED = ["tpc_default_params", "tpc_setup", "tpc_solve", "tpc_solve_batch", "
             "tpc_apply_f32",
             "tpc_vcycle", "tpc_level_size", "tpc_finest_level", "tpc_coarsest_level",
             "tpc_export_level", "tpc_host_hierarchy", "tpc_time_level_kernels",
-            "tpc_kernel_launches", "tpc_apply_noalloc", "tpc_destroy", "tpc_last_error",
+            "tpc_time_level_kernels_f32", "tpc_kernel_launches", "tpc_apply_noalloc", "tpc_destroy", "tpc_last_error",
             "tpc_server_default_config", "tpc_server_create", "tpc_server_submit",
             "tpc_server_poll", "tpc_server_outstanding", "tpc_server_destroy"]
 
@@ -106,6 +106,8 @@ def lib() -> ctypes.CDLL:
     L.tpc_host_hierarchy.restype = I
     L.tpc_time_level_kernels.argtypes = [P, I, I, P, P, P, ctypes.POINTER(D)]
     L.tpc_time_level_kernels.restype = I
+    L.tpc_time_level_kernels_f32.argtypes = [P, I, I, P, P, P, ctypes.POINTER(D)]
+    L.tpc_time_level_kernels_f32.restype = I
     L.tpc_kernel_launches.argtypes = [P]
     L.tpc_kernel_launches.restype = LL
     L.tpc_apply_noalloc.argtypes = [LL, P, P, P, P, P, P, P, P, D, P, P, P]
@@ -271,6 +273,13 @@ def tpc_time_level_kernels(H, level: int, reps: int, x, f, y):
     """Average ms per launch of [forward strided, contiguous-block, inverse strided] kernels."""
     out = (ctypes.c_double * 3)()
     _check(lib().tpc_time_level_kernels(H, level, reps, _ptr(x), _ptr(f), _ptr(y), out), H)
+    return [out[0], out[1], out[2]]
+
+
+def tpc_time_level_kernels_f32(H, level: int, reps: int, x, f, y):
+    """The same for the FP32 level copy of a mixed handle (float32 device tensors)."""
+    out = (ctypes.c_double * 3)()
+    _check(lib().tpc_time_level_kernels_f32(H, level, reps, _ptr(x), _ptr(f), _ptr(y), out), H)
     return [out[0], out[1], out[2]]
 
 

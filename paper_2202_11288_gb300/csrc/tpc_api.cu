@@ -240,9 +240,9 @@ void launch_matvec(tpc_handle* H, const Hier<T>& G, const DevLevel<T>& L, const 
     return;
   }
   H->launches += 3;
-  k_fwd_strided<T, IN_PACK><<<L.fwd_blocks, fft_threads<T>(), L.smem_strided, s>>>(a);
+  launch_fwd_strided<T>(a, L.fwd_blocks, L.smem_strided, s);
   k_mid_pair<T, NS><<<L.mid_blocks, fft_threads<T>(), L.smem_mid, s>>>(a);
-  k_inv_strided<T><<<L.fwd_blocks, fft_threads<T>(), L.smem_strided, s>>>(a);
+  launch_inv_strided<T>(a, L.fwd_blocks, L.smem_strided, s);
 }
 
 template <typename T>
@@ -358,8 +358,9 @@ cudaError_t set_smem_attrs() {
   const int big = 150 * 1024;  // largest: (520 + 8704) x 16 B = 144 KB
   const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_fwd_strided<T, IN_PACK>, A, big)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_fwd_strided<T, IN_REAL>, A, big)) != cudaSuccess) return e;
+  if ((e = strided_smem_attrs<T>(big)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_fwd_strided<T, IN_REAL, PRO_NONE>, A, big)) != cudaSuccess)
+    return e;
   if ((e = cudaFuncSetAttribute(k_mid_pair<T, NS>, A, big)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_mid_whole<T, NS>, A, big)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_mid_fwd<T>, A, big)) != cudaSuccess) return e;
@@ -367,7 +368,7 @@ cudaError_t set_smem_attrs() {
   if constexpr (sizeof(T) == 4) {
     if ((e = cudaFuncSetAttribute(k_vcycle_bottom<T, NS>, A, big)) != cudaSuccess) return e;
   }
-  return cudaFuncSetAttribute(k_inv_strided<T>, A, big);
+  return cudaSuccess;
 }
 
 // Circulant first column of an N x N Toeplitz generator, embedded in length m (eq. ccs3.4):
@@ -392,7 +393,7 @@ int forward_real(tpc_handle* H, const Hier<double>& G, const DevLevel<double>& L
   if (L.logR1 == 0) {
     k_mid_fwd_real<double><<<1, FFT_THREADS, L.smem_mid, s>>>(a);
   } else {
-    k_fwd_strided<double, IN_REAL><<<L.fwd_blocks, FFT_THREADS, L.smem_strided, s>>>(a);
+    k_fwd_strided<double, IN_REAL, PRO_NONE><<<L.fwd_blocks, FFT_THREADS, L.smem_strided, s>>>(a);
     k_mid_fwd<double><<<1 << L.logR1, FFT_THREADS,
                         sizeof(double2) * (size_t)(tw_slots<double>() + padded_size(1 << L.logL)), s>>>(a);
   }
@@ -835,6 +836,59 @@ size_t handle_device_bytes(const tpc_handle* H) { return H ? H->dev_bytes : 0; }
 
 }  // namespace tpc
 
+// Times the three transform kernels of one level (residual epilogue), reps launches each after
+// one warm-up launch, with CUDA events on the handle's stream.
+template <typename T>
+int time_level(tpc_handle* H, const Hier<T>& G, int level, int reps, const T* x_dev,
+               const T* f_dev, T* y_dev, double* ms_out) {
+  const int li = level_index(H, level);
+  if (li < 0 || reps < 1 || !x_dev || !f_dev || !y_dev || !ms_out || x_dev == y_dev ||
+      (int)G.lev.size() <= li || !G.lev[li].sA) {
+    H->err = "bad argument to tpc_time_level_kernels";
+    return TPC_EINVAL;
+  }
+  const DevLevel<T>& L = G.lev[li];
+  const bool ns = H->prm.variant == TPC_NONSYM;
+  LevelArgs<T> a = level_args<T>(G, L);
+  a.x = x_dev;
+  a.f = f_dev;
+  a.y = y_dev;
+  a.epi = EPI_RESID;
+  const int nt = fft_threads<T>();
+  cudaStream_t s = H->stream;
+  cudaEvent_t ev[2];
+  TPC_CUDA(H, cudaEventCreate(&ev[0]));
+  TPC_CUDA(H, cudaEventCreate(&ev[1]));
+  for (int which = 0; which < 3; ++which) {
+    ms_out[which] = 0.0;
+    if (L.logR1 == 0 && which != 1) continue;
+    for (int rep = 0; rep <= reps; ++rep) {
+      if (rep == 1) cudaEventRecord(ev[0], s);
+      if (which == 0) {
+        launch_fwd_strided<T>(a, L.fwd_blocks, L.smem_strided, s);
+      } else if (which == 2) {
+        launch_inv_strided<T>(a, L.fwd_blocks, L.smem_strided, s);
+      } else if (L.logR1 == 0) {
+        if (ns) k_mid_whole<T, true><<<1, nt, L.smem_mid, s>>>(a);
+        else k_mid_whole<T, false><<<1, nt, L.smem_mid, s>>>(a);
+      } else {
+        if (ns) k_mid_pair<T, true><<<L.mid_blocks, nt, L.smem_mid, s>>>(a);
+        else k_mid_pair<T, false><<<L.mid_blocks, nt, L.smem_mid, s>>>(a);
+      }
+      H->launches += 1;
+    }
+    cudaEventRecord(ev[1], s);
+    TPC_CUDA(H, cudaEventSynchronize(ev[1]));
+    float ms = 0.0f;
+    TPC_CUDA(H, cudaEventElapsedTime(&ms, ev[0], ev[1]));
+    ms_out[which] = (double)ms / reps;
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  TPC_CUDA(H, cudaGetLastError());
+  return TPC_OK;
+}
+
 extern "C" {
 
 int tpc_setup(const tpc_params* p, double delta, double h, int levels, void* cuda_stream,
@@ -1029,51 +1083,14 @@ int tpc_export_level(const tpc_handle* H, int level, double* host_buf, size_t ca
 
 int tpc_time_level_kernels(tpc_handle* H, int level, int reps, const double* x_dev,
                            const double* f_dev, double* y_dev, double* ms_out) {
-  const int li = level_index(H, level);
-  if (li < 0 || reps < 1 || !x_dev || !f_dev || !y_dev || !ms_out || x_dev == y_dev ||
-      !H->d.lev[li].sA) {
-    if (H) H->err = "bad argument to tpc_time_level_kernels";
-    return TPC_EINVAL;
-  }
-  const DevLevel<double>& L = H->d.lev[li];
-  const bool ns = H->prm.variant == TPC_NONSYM;
-  LevelArgs<double> a = level_args<double>(H->d, L);
-  a.x = x_dev;
-  a.f = f_dev;
-  a.y = y_dev;
-  a.epi = EPI_RESID;
-  cudaStream_t s = H->stream;
-  cudaEvent_t ev[2];
-  TPC_CUDA(H, cudaEventCreate(&ev[0]));
-  TPC_CUDA(H, cudaEventCreate(&ev[1]));
-  for (int which = 0; which < 3; ++which) {
-    ms_out[which] = 0.0;
-    if (L.logR1 == 0 && which != 1) continue;
-    for (int rep = 0; rep <= reps; ++rep) {
-      if (rep == 1) cudaEventRecord(ev[0], s);
-      if (which == 0) {
-        k_fwd_strided<double, IN_PACK><<<L.fwd_blocks, FFT_THREADS, L.smem_strided, s>>>(a);
-      } else if (which == 2) {
-        k_inv_strided<double><<<L.fwd_blocks, FFT_THREADS, L.smem_strided, s>>>(a);
-      } else if (L.logR1 == 0) {
-        if (ns) k_mid_whole<double, true><<<1, FFT_THREADS, L.smem_mid, s>>>(a);
-        else k_mid_whole<double, false><<<1, FFT_THREADS, L.smem_mid, s>>>(a);
-      } else {
-        if (ns) k_mid_pair<double, true><<<L.mid_blocks, FFT_THREADS, L.smem_mid, s>>>(a);
-        else k_mid_pair<double, false><<<L.mid_blocks, FFT_THREADS, L.smem_mid, s>>>(a);
-      }
-      H->launches += 1;
-    }
-    cudaEventRecord(ev[1], s);
-    TPC_CUDA(H, cudaEventSynchronize(ev[1]));
-    float ms = 0.0f;
-    TPC_CUDA(H, cudaEventElapsedTime(&ms, ev[0], ev[1]));
-    ms_out[which] = (double)ms / reps;
-  }
-  cudaEventDestroy(ev[0]);
-  cudaEventDestroy(ev[1]);
-  TPC_CUDA(H, cudaGetLastError());
-  return TPC_OK;
+  if (!H) return TPC_EINVAL;
+  return time_level<double>(H, H->d, level, reps, x_dev, f_dev, y_dev, ms_out);
+}
+
+int tpc_time_level_kernels_f32(tpc_handle* H, int level, int reps, const float* x_dev,
+                               const float* f_dev, float* y_dev, double* ms_out) {
+  if (!H) return TPC_EINVAL;
+  return time_level<float>(H, H->s, level, reps, x_dev, f_dev, y_dev, ms_out);
 }
 
 long long tpc_kernel_launches(const tpc_handle* H) { return H ? H->launches : 0; }

@@ -29,11 +29,15 @@ template <typename T> __device__ __forceinline__ c2<T> mk(T a, T b) {
   r.y = b;
   return r;
 }
+// Complex add / subtract. FP32 uses the packed two-lane instructions (add and fma on a pair of
+// floats in one instruction; a - b is fma(b, -1, a), the same rounding as the subtraction).
 template <typename T> __device__ __forceinline__ c2<T> cadd(c2<T> a, c2<T> b) {
-  return mk<T>(a.x + b.x, a.y + b.y);
+  if constexpr (sizeof(T) == 4) return __fadd2_rn(a, b);
+  else return mk<T>(a.x + b.x, a.y + b.y);
 }
 template <typename T> __device__ __forceinline__ c2<T> csub(c2<T> a, c2<T> b) {
-  return mk<T>(a.x - b.x, a.y - b.y);
+  if constexpr (sizeof(T) == 4) return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+  else return mk<T>(a.x - b.x, a.y - b.y);
 }
 // a * b
 template <typename T> __device__ __forceinline__ c2<T> cmul(c2<T> a, c2<T> b) {
@@ -224,12 +228,22 @@ __device__ __forceinline__ void fft_step(c2<T>* s, int logS, int logL, int logCo
     }
     const int base = q * qs + ((sb << logS) + c) * ts;
     const int step = ts << logCols;
-    // pad16(base + t step) = pad16(base) + t pstep when step is a multiple of 16
-    const bool uni = (step & 15) == 0;
-    const int pb = pad16(base), pstep = step + (step >> 4);
+    // pad16(base + t step) = pad16(base) + t pstep when step is a multiple of 16 (pstep =
+    // step + step / 16) or when all R entries lie in one group of 16 slots (pstep = step);
+    // otherwise each index is padded on its own. The test is uniform over a step's tasks
+    // except in the last case, and the two loops keep the fast one free of the general form.
+    const int pb = pad16(base);
+    int pstep = -1;
+    if ((step & 15) == 0) pstep = step + (step >> 4);
+    else if ((base & 15) + (R - 1) * step < 16) pstep = step;
     c2<T> v[R];
+    if (pstep >= 0) {
 #pragma unroll
-    for (int t = 0; t < R; ++t) v[t] = s[uni ? pb + t * pstep : pad16(base + t * step)];
+      for (int t = 0; t < R; ++t) v[t] = s[pb + t * pstep];
+    } else {
+#pragma unroll
+      for (int t = 0; t < R; ++t) v[t] = s[pad16(base + t * step)];
+    }
     if (INV) {
       if (logCols > 0) {
         c2<T> pw[R];
@@ -247,17 +261,28 @@ __device__ __forceinline__ void fft_step(c2<T>* s, int logS, int logL, int logCo
         for (int t = 1; t < R; ++t) v[t] = cmul<T>(v[t], pw[brev_r<R>(t)]);
       }
     }
+    if (pstep >= 0) {
 #pragma unroll
-    for (int t = 0; t < R; ++t) s[uni ? pb + t * pstep : pad16(base + t * step)] = v[t];
+      for (int t = 0; t < R; ++t) s[pb + t * pstep] = v[t];
+    } else {
+#pragma unroll
+      for (int t = 0; t < R; ++t) s[pad16(base + t * step)] = v[t];
+    }
   }
 }
 
-// Radices of the steps of a 2^logL transform: as many 16s as fit, then the remainder.
+// Radices of the steps of a 2^logL transform: as many of the largest radix (2^TPC_LOG_RMAX,
+// default 16) as fit, then the remainder.
+#ifndef TPC_LOG_RMAX
+#define TPC_LOG_RMAX 4
+#endif
 __device__ __forceinline__ int step_radix_log(int logL, int idx) {
-  const int n16 = logL >> 2;
-  return idx < n16 ? 4 : (logL & 3);
+  const int nfull = logL / TPC_LOG_RMAX;
+  return idx < nfull ? TPC_LOG_RMAX : (logL % TPC_LOG_RMAX);
 }
-__device__ __forceinline__ int num_steps(int logL) { return (logL >> 2) + ((logL & 3) ? 1 : 0); }
+__device__ __forceinline__ int num_steps(int logL) {
+  return logL / TPC_LOG_RMAX + ((logL % TPC_LOG_RMAX) ? 1 : 0);
+}
 
 template <typename T, bool QFAST, bool INV>
 __device__ __forceinline__ void dispatch_step(int r, c2<T>* s, int logS, int logL, int logCount,

@@ -123,6 +123,36 @@ __device__ __forceinline__ float2 w_f32(int e, int logm) {
   return make_float2(re, im);
 }
 
+// FP32 twiddles of the strided passes, factored per thread. Thread tid of a block of nt
+// threads (C = 2^logC columns, tile = R1 C entries, tile >= 2 nt) holds the entries
+// e = tid + nt j, j < J = tile / nt: column c = c0 + (tid mod C) and row t = t0 + (nt / C) j with
+// t0 = tid / C < nt / C. The row bits of t0 and of (nt / C) j do not overlap, so
+// bitrev(t) = bitrev(t0) + bitrev_J(j) (bit reversal over log2 R1 and log2 J bits) and
+// W_m^{c bitrev(t)} = W_m^{c bitrev(t0)} * W_m^{c bitrev_J(j)}: one value per thread times an
+// entry of a C x J table built once per block (at most 512 entries).
+struct InterTw32 {
+  float2 base;   // W_m^{c bitrev(t0)}
+  int row;       // first table entry of this thread's column
+  int logJ;
+};
+__device__ __forceinline__ InterTw32 inter_tw32_setup(float2* tab, long long c0, int logC,
+                                                      int logR1, int logm) {
+  const int nt = blockDim.x, C = 1 << logC;
+  const int logJ = logR1 + logC - (31 - __clz(nt));
+  const int J = 1 << logJ;
+  for (int i = threadIdx.x; i < (C << logJ); i += nt)
+    tab[i] = w_f32((int)((c0 + (i >> logJ)) * (i & (J - 1))), logm);
+  InterTw32 r;
+  const int cc = threadIdx.x & (C - 1), t0 = threadIdx.x >> logC;
+  r.base = w_f32((int)((c0 + cc) * (long long)brev_bits((unsigned)t0, logR1)), logm);
+  r.row = cc << logJ;
+  r.logJ = logJ;
+  return r;
+}
+__device__ __forceinline__ float2 inter_tw32(const InterTw32& it, const float2* tab, int j) {
+  return cmul<float>(it.base, tab[it.row + (int)(__brev((unsigned)j) >> (32 - it.logJ))]);
+}
+
 template <typename T>
 __device__ __forceinline__ c2<T> inter_tw(const c2<T>* __restrict__ twm, long long e, int logm) {
   if constexpr (sizeof(T) == 8) {
@@ -152,39 +182,44 @@ __device__ __forceinline__ T prolong_at(const T* __restrict__ ec, long long j, l
 template <typename T> struct Raw {
   T a0, a1, a2;
 };
+// The coarse-correction values of PRO_PROLONG at fine index j (a1, a2 of Raw).
 template <typename T>
-__device__ __forceinline__ Raw<T> operand_load(const LevelArgs<T>& a, long long j) {
+__device__ __forceinline__ void prolong_load(const LevelArgs<T>& a, long long j, Raw<T>& r) {
+  if (j & 1) {
+    r.a1 = a.ec[(j - 1) / 2];
+  } else {
+    const long long I = j / 2;
+    r.a1 = (I >= 1) ? a.ec[I - 1] : (T)0;
+    r.a2 = (I < a.N) ? a.ec[I] : (T)0;  // coarse size n_{k-1} = N_k
+  }
+}
+template <typename T>
+__device__ __forceinline__ Raw<T> operand_load(const LevelArgs<T>& a, long long j, int pro) {
   Raw<T> r{0, 0, 0};
-  if (a.pro == PRO_NONE) {
+  if (pro == PRO_NONE) {
     r.a0 = a.x[j];
-  } else if (a.pro == PRO_SMOOTH) {
+  } else if (pro == PRO_SMOOTH) {
     r.a0 = a.f[j];
-  } else if (a.pro == PRO_RESTRICT) {
+  } else if (pro == PRO_RESTRICT) {
     r.a0 = a.rfine[2 * j];
     r.a1 = a.rfine[2 * j + 1];
     r.a2 = a.rfine[2 * j + 2];
   } else {
     r.a0 = a.x[j];
-    if (j & 1) {
-      r.a1 = a.ec[(j - 1) / 2];
-    } else {
-      const long long I = j / 2;
-      r.a1 = (I >= 1) ? a.ec[I - 1] : (T)0;
-      r.a2 = (I < a.N) ? a.ec[I] : (T)0;  // coarse size n_{k-1} = N_k
-    }
+    prolong_load<T>(a, j, r);
   }
   return r;
 }
 template <typename T>
 __device__ __forceinline__ T operand_finish(const LevelArgs<T>& a, long long j, const Raw<T>& r,
-                                            T w) {
-  if (a.pro == PRO_NONE) return r.a0;
-  if (a.pro == PRO_SMOOTH) {
+                                            T w, int pro) {
+  if (pro == PRO_NONE) return r.a0;
+  if (pro == PRO_SMOOTH) {
     const T v = w * r.a0;
     a.xout[j] = v;
     return v;
   }
-  if (a.pro == PRO_RESTRICT) {
+  if (pro == PRO_RESTRICT) {
     const T fv = (T)0.25 * r.a0 + (T)0.5 * r.a1 + (T)0.25 * r.a2;  // restriction, section 3.1
     a.fout[j] = fv;
     const T v = w * fv;
@@ -196,14 +231,31 @@ __device__ __forceinline__ T operand_finish(const LevelArgs<T>& a, long long j, 
   return v;
 }
 template <typename T>
-__device__ __forceinline__ T operand(const LevelArgs<T>& a, long long j, T w) {
-  return operand_finish<T>(a, j, operand_load<T>(a, j), w);
+__device__ __forceinline__ T operand(const LevelArgs<T>& a, long long j, T w, int pro) {
+  return operand_finish<T>(a, j, operand_load<T>(a, j, pro), w, pro);
 }
 
 #ifndef TPC_UNROLL
 #define TPC_UNROLL 4
 #endif
 constexpr int UNROLL = TPC_UNROLL;  // elements per thread whose loads are issued together
+
+// Asynchronous global -> shared copies (4 or 8 bytes, both addresses aligned to the size): a
+// thread issues all of its copies for a tile without holding registers for them, then waits.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d),
+               "l"(__cvta_generic_to_global(gmem))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d),
+               "l"(__cvta_generic_to_global(gmem))
+               : "memory");
+}
+// Waits for this thread's copies (others' copies need a barrier as well).
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, T* red) {
@@ -227,16 +279,16 @@ template <typename T> struct EpiRaw {
   T p, xi, fv, fw, xv, xw;
 };
 template <typename T>
-__device__ __forceinline__ EpiRaw<T> epi_load(const LevelArgs<T>& a, long long i) {
+__device__ __forceinline__ EpiRaw<T> epi_load(const LevelArgs<T>& a, long long i, int epi) {
   EpiRaw<T> r{0, 0, 0, 0, 0, 0};
   const long long iw = a.N + 1 + i;
   r.p = a.p[i];
   r.xi = a.xi[i];
-  if (a.epi != EPI_APPLY) {
+  if (epi != EPI_APPLY) {
     r.fv = a.f[i];
     r.fw = a.f[iw];
   }
-  if (a.epi == EPI_JACOBI) {
+  if (epi == EPI_JACOBI) {
     r.xv = a.x[i];
     r.xw = a.x[iw];
   }
@@ -244,14 +296,14 @@ __device__ __forceinline__ EpiRaw<T> epi_load(const LevelArgs<T>& a, long long i
 }
 template <typename T>
 __device__ __forceinline__ void epi_store(const LevelArgs<T>& a, long long i, const EpiRaw<T>& r,
-                                          T ax_v, T ax_w, T w_o) {
+                                          T ax_v, T ax_w, T w_o, int epi) {
   const T yv = fma(r.p, w_o, ax_v);
   const T yw = fma(r.xi, w_o, ax_w);
   const long long iw = a.N + 1 + i;
-  if (a.epi == EPI_APPLY) {
+  if (epi == EPI_APPLY) {
     a.y[i] = yv;
     a.y[iw] = yw;
-  } else if (a.epi == EPI_RESID) {
+  } else if (epi == EPI_RESID) {
     a.y[i] = r.fv - yv;
     a.y[iw] = r.fw - yw;
   } else {
@@ -261,12 +313,12 @@ __device__ __forceinline__ void epi_store(const LevelArgs<T>& a, long long i, co
 }
 
 template <typename T>
-__device__ __forceinline__ void epi_middle(const LevelArgs<T>& a, T dot, T w_o) {
+__device__ __forceinline__ void epi_middle(const LevelArgs<T>& a, T dot, T w_o, int epi) {
   const T ym = fma(a.o, w_o, dot);
   const long long im = a.N;
-  if (a.epi == EPI_APPLY)
+  if (epi == EPI_APPLY)
     a.y[im] = ym;
-  else if (a.epi == EPI_RESID)
+  else if (epi == EPI_RESID)
     a.y[im] = a.f[im] - ym;
   else
     a.y[im] = fma(a.wO, a.f[im] - ym, a.x[im]);
@@ -295,9 +347,10 @@ __device__ __forceinline__ Spec<T> spec_load(const LevelArgs<T>& a, long long P)
 template <typename T>
 __device__ __forceinline__ void mac_pair(const Spec<T>& sp, c2<T>* zl, c2<T>* zu) {
   const c2<T> Zp = *zl, Zq = *zu;
-  // 2 V^ = Z_p + conj Z_q ; 2 W^ = (Z_p - conj Z_q) / i
-  const T vr = Zp.x + Zq.x, vi = Zp.y - Zq.y;
-  const T wr = Zp.y + Zq.y, wi = Zq.x - Zp.x;
+  // 2 V^ = Z_p + conj Z_q ; 2 W^ = (Z_p - conj Z_q) / i, from Z_p + Z_q and Z_p - Z_q
+  const c2<T> S = cadd<T>(Zp, Zq), D = csub<T>(Zp, Zq);
+  const T vr = S.x, vi = D.y;
+  const T wr = S.y, wi = -D.x;
   const T y1r = fma(sp.sa, vr, fma(sp.sb.x, wr, -sp.sb.y * wi));
   const T y1i = fma(sp.sa, vi, fma(sp.sb.x, wi, sp.sb.y * wr));
   const T y2r = fma(sp.sd, wr, fma(sp.sc.x, vr, -sp.sc.y * vi));
@@ -322,8 +375,10 @@ __device__ __forceinline__ void block0_pair(int q, int& p, int& pp) {
 // Forward strided pass: the first log2(R1) DIF stages as R1-point transforms of the L
 // columns (stride L), each followed by the twiddle W_m^{c k}. One CTA: 2^logC columns.
 // ------------------------------------------------------------------------------------
-template <typename T, int IN>
+// PRO: the prologue, fixed at compile time (the launch selects the instance from a.pro).
+template <typename T, int IN, int PRO>
 __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_fwd_strided(LevelArgs<T> a) {
+  constexpr int pro = PRO;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2<T>* tab = reinterpret_cast<c2<T>*>(smem_raw);
   c2<T>* s = tab + tw_slots<T>();
@@ -335,7 +390,66 @@ __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_fwd_s
   const long long c0 = (long long)blockIdx.x << logC;
   const int half = 1 << (logR1 - 1);
   T dot = 0;
-  if (IN == IN_PACK) {
+  // FP32 (bound by memory latency): the raw operand values and the Cross rows q, zeta arrive by
+  // asynchronous copies, all of a thread's copies in flight at once: the operand pair (v, w_bar)
+  // into the slot of its row t < R1/2, (q, zeta) into the slot of row t + R1/2 (the zero
+  // padding, cleared once read). The restriction prologue (three fine values per entry) keeps
+  // the register path.
+  constexpr bool ASYNC = sizeof(T) == 4 && IN == IN_PACK && PRO != PRO_RESTRICT;
+  if constexpr (ASYNC) {
+    const int ht = tile >> 1;
+    const T* src = (PRO == PRO_SMOOTH) ? a.f : a.x;
+    for (int e = threadIdx.x; e < ht; e += blockDim.x) {
+      const int t = e >> logC, cc = e & (C - 1);
+      const long long P = c0 + cc + ((long long)t << logL);
+      c2<T>* lo = s + pad16(e);
+      c2<T>* hi = s + pad16(e + ht);
+      if (P < a.N) {
+        cp_async4(&lo->x, src + P);
+        cp_async4(&lo->y, src + a.N + 1 + P);
+        cp_async4(&hi->x, a.q + P);
+        cp_async4(&hi->y, a.zeta + P);
+      } else {
+        *lo = mk<T>(0, 0);
+        *hi = mk<T>(0, 0);
+      }
+    }
+    cp_async_wait_all();
+    for (int e0 = threadIdx.x; e0 < ht; e0 += UNROLL * blockDim.x) {
+      Raw<T> rv[UNROLL], rw[UNROLL];
+      if constexpr (PRO == PRO_PROLONG) {
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+          const int e = e0 + u * blockDim.x;
+          const int t = e >> logC, cc = e & (C - 1);
+          const long long P = c0 + cc + ((long long)t << logL);
+          if (e < ht && P < a.N) {
+            prolong_load<T>(a, P, rv[u]);
+            prolong_load<T>(a, a.N + 1 + P, rw[u]);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UNROLL; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e >= ht) continue;
+        const int t = e >> logC, cc = e & (C - 1);
+        const long long P = c0 + cc + ((long long)t << logL);
+        c2<T>* lo = s + pad16(e);
+        c2<T>* hi = s + pad16(e + ht);
+        if (P < a.N) {
+          const c2<T> raw = *lo, qz = *hi;
+          rv[u].a0 = raw.x;
+          rw[u].a0 = raw.y;
+          const T xv = operand_finish<T>(a, P, rv[u], a.pA, pro);
+          const T xw = operand_finish<T>(a, a.N + 1 + P, rw[u], a.pD, pro);
+          *lo = mk<T>(xv, xw);
+          dot = fma(qz.x, xv, fma(qz.y, xw, dot));
+        }
+        *hi = mk<T>(0, 0);
+      }
+    }
+  } else if (IN == IN_PACK) {
     // rows t >= R1/2 are the zero padding of the embedding
     for (int e = threadIdx.x + (tile >> 1); e < tile; e += blockDim.x) s[pad16(e)] = mk<T>(0, 0);
     for (int e0 = threadIdx.x; e0 < (tile >> 1); e0 += UNROLL * blockDim.x) {
@@ -349,8 +463,8 @@ __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_fwd_s
         const long long P = c0 + cc + ((long long)t << logL);
         ok[u] = (e < (tile >> 1)) && P < a.N;
         if (ok[u]) {
-          rv[u] = operand_load<T>(a, P);
-          rw[u] = operand_load<T>(a, a.N + 1 + P);
+          rv[u] = operand_load<T>(a, P, pro);
+          rw[u] = operand_load<T>(a, a.N + 1 + P, pro);
           qv[u] = a.q[P];
           zv[u] = a.zeta[P];
         }
@@ -363,8 +477,8 @@ __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_fwd_s
         const long long P = c0 + cc + ((long long)t << logL);
         c2<T> v = mk<T>(0, 0);
         if (ok[u]) {
-          const T xv = operand_finish<T>(a, P, rv[u], a.pA);
-          const T xw = operand_finish<T>(a, a.N + 1 + P, rw[u], a.pD);
+          const T xv = operand_finish<T>(a, P, rv[u], a.pA, pro);
+          const T xw = operand_finish<T>(a, a.N + 1 + P, rw[u], a.pD, pro);
           v = mk<T>(xv, xw);
           dot = fma(qv[u], xv, fma(zv[u], xw, dot));
         }
@@ -390,18 +504,33 @@ __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_fwd_s
   (void)half;
   __syncthreads();
   smem_dif<T, true>(s, logR1, logC, C, 1, tw, LOG_LMAX);
-  for (int e = threadIdx.x; e < tile; e += blockDim.x) {
-    const int t = e >> logC, cc = e & (C - 1);
-    const long long c = c0 + cc;
-    const long long P = c + ((long long)t << logL);
-    const long long kb = (long long)brev_bits((unsigned)t, logR1);
-    a.z[P] = cmul<T>(s[pad16(e)], inter_tw<T>(a.twm, c * kb, a.logm));
+  if (sizeof(T) == 4 && tile >= 2 * (int)blockDim.x &&
+      (long long)tile * C <= (long long)TW_TAB * blockDim.x) {
+    // the step-twiddle table is no longer needed: its slots take the factored twiddles
+    float2* t2 = reinterpret_cast<float2*>(tab);
+    const InterTw32 it = inter_tw32_setup(t2, c0, logC, logR1, a.logm);
+    __syncthreads();
+    int j = 0;
+    for (int e = threadIdx.x; e < tile; e += blockDim.x, ++j) {
+      const int t = e >> logC, cc = e & (C - 1);
+      const long long P = c0 + cc + ((long long)t << logL);
+      const float2 w = inter_tw32(it, t2, j);
+      a.z[P] = cmul<T>(s[pad16(e)], mk<T>((T)w.x, (T)w.y));
+    }
+  } else {
+    for (int e = threadIdx.x; e < tile; e += blockDim.x) {
+      const int t = e >> logC, cc = e & (C - 1);
+      const long long c = c0 + cc;
+      const long long P = c + ((long long)t << logL);
+      const long long kb = (long long)brev_bits((unsigned)t, logR1);
+      a.z[P] = cmul<T>(s[pad16(e)], inter_tw<T>(a.twm, c * kb, a.logm));
+    }
   }
   if (IN == IN_PACK) {
     const T tot = block_sum<T>(dot, red);
     if (threadIdx.x == 0) {
       a.partials[blockIdx.x] = tot;
-      if (blockIdx.x == 0 && a.pro != PRO_NONE) (void)operand<T>(a, a.N, a.pO);  // middle w_o
+      if (blockIdx.x == 0 && pro != PRO_NONE) (void)operand<T>(a, a.N, a.pO, pro);  // middle w_o
     }
   }
 }
@@ -427,8 +556,8 @@ __device__ __forceinline__ void mid_core(const LevelArgs<T>& a, const c2<T>* tw,
       for (int u = 0; u < UNROLL; ++u) {
         const int i = e0 + u * blockDim.x;
         if (i < a.N) {
-          rv[u] = operand_load<T>(a, i);
-          rw[u] = operand_load<T>(a, a.N + 1 + i);
+          rv[u] = operand_load<T>(a, i, a.pro);
+          rw[u] = operand_load<T>(a, a.N + 1 + i, a.pro);
           qv[u] = a.q[i];
           zv[u] = a.zeta[i];
         }
@@ -439,14 +568,21 @@ __device__ __forceinline__ void mid_core(const LevelArgs<T>& a, const c2<T>* tw,
         if (i >= total) continue;
         c2<T> v = mk<T>(0, 0);
         if (i < a.N) {
-          const T xv = operand_finish<T>(a, i, rv[u], a.pA);
-          const T xw = operand_finish<T>(a, a.N + 1 + i, rw[u], a.pD);
+          const T xv = operand_finish<T>(a, i, rv[u], a.pA, a.pro);
+          const T xw = operand_finish<T>(a, a.N + 1 + i, rw[u], a.pD, a.pro);
           v = mk<T>(xv, xw);
           dot = fma(qv[u], xv, fma(zv[u], xw, dot));
         }
         s[pad16(i)] = v;
       }
     }
+  } else if (sizeof(T) == 4 && MODE == MID_PAIR) {
+    // FP32: asynchronous copies, all of a thread's copies in flight at once
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+      const int sq = e >> logL, i = e & (L - 1);
+      cp_async8(s + pad16(e), a.z + (sq ? b2 : b) * (long long)L + i);
+    }
+    cp_async_wait_all();
   } else {
     for (int e0 = threadIdx.x; e0 < total; e0 += 2 * UNROLL * blockDim.x) {
       c2<T> v[2 * UNROLL];
@@ -469,7 +605,7 @@ __device__ __forceinline__ void mid_core(const LevelArgs<T>& a, const c2<T>* tw,
   }
   T dot_total = 0;
   if (MODE == MID_WHOLE) {
-    if (threadIdx.x == 0 && a.pro != PRO_NONE) (void)operand<T>(a, a.N, a.pO);  // middle w_o
+    if (threadIdx.x == 0 && a.pro != PRO_NONE) (void)operand<T>(a, a.N, a.pO, a.pro);  // middle w_o
     dot_total = block_sum<T>(dot, red);
   }
   __syncthreads();
@@ -518,18 +654,18 @@ __device__ __forceinline__ void mid_core(const LevelArgs<T>& a, const c2<T>* tw,
 #pragma unroll
       for (int u = 0; u < UNROLL; ++u) {
         const int i = i0 + u * blockDim.x;
-        if (i < a.N) er[u] = epi_load<T>(a, i);
+        if (i < a.N) er[u] = epi_load<T>(a, i, a.epi);
       }
 #pragma unroll
       for (int u = 0; u < UNROLL; ++u) {
         const int i = i0 + u * blockDim.x;
         if (i < a.N) {
           const c2<T> y = s[pad16(i)];
-          epi_store<T>(a, i, er[u], y.x, y.y, w_o);
+          epi_store<T>(a, i, er[u], y.x, y.y, w_o, a.epi);
         }
       }
     }
-    if (threadIdx.x == 0) epi_middle<T>(a, dot_total, w_o);
+    if (threadIdx.x == 0) epi_middle<T>(a, dot_total, w_o, a.epi);
   } else {
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
       const int sq = e >> logL, i = e & (L - 1);
@@ -583,34 +719,67 @@ __global__ void __launch_bounds__(fft_threads<T>(), mid_min_blocks<T>()) k_mid_f
 // ------------------------------------------------------------------------------------
 // Inverse strided pass: twiddle conj(W_m^{c k}), R1-point DIT per column, epilogue.
 // ------------------------------------------------------------------------------------
-template <typename T>
+// EPI: the epilogue, fixed at compile time (the launch selects the instance from a.epi).
+template <typename T, int EPI>
 __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_inv_strided(LevelArgs<T> a) {
+  constexpr int epi = EPI;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2<T>* tab = reinterpret_cast<c2<T>*>(smem_raw);
   c2<T>* s = tab + tw_slots<T>();
   const int logR1 = a.logR1, logC = a.logC, logL = a.logL;
-  const c2<T>* tw = step_table<T>(tab, a.twL);
   const int C = 1 << logC;
   const int tile = 1 << (logR1 + logC);
   const long long c0 = (long long)blockIdx.x << logC;
-  for (int e0 = threadIdx.x; e0 < tile; e0 += 2 * UNROLL * blockDim.x) {
-    c2<T> v[2 * UNROLL];
-#pragma unroll
-    for (int u = 0; u < 2 * UNROLL; ++u) {
-      const int e = e0 + u * blockDim.x;
+  const bool fact = sizeof(T) == 4 && tile >= 2 * (int)blockDim.x &&
+                    (long long)tile * C <= (long long)TW_TAB * blockDim.x;
+  InterTw32 it{};
+  const float2* t2 = reinterpret_cast<const float2*>(tab);
+  if (fact) {
+    // factored twiddles in the step-table slots until the transform needs them
+    it = inter_tw32_setup(reinterpret_cast<float2*>(tab), c0, logC, logR1, a.logm);
+    __syncthreads();
+  }
+  if constexpr (sizeof(T) == 4) {
+    // asynchronous copies of the tile, then the twiddle in place (each thread its own slots)
+    for (int e = threadIdx.x; e < tile; e += blockDim.x) {
       const int t = e >> logC, cc = e & (C - 1);
-      if (e < tile) v[u] = a.z[c0 + cc + ((long long)t << logL)];
+      cp_async8(s + pad16(e), a.z + c0 + cc + ((long long)t << logL));
     }
+    cp_async_wait_all();
+    int j = 0;
+    for (int e = threadIdx.x; e < tile; e += blockDim.x, ++j) {
+      c2<T> w;
+      if (fact) {
+        const float2 wf = inter_tw32(it, t2, j);
+        w = mk<T>((T)wf.x, (T)wf.y);
+      } else {
+        const int t = e >> logC, cc = e & (C - 1);
+        const long long kb = (long long)brev_bits((unsigned)t, logR1);
+        w = inter_tw<T>(a.twm, (c0 + cc) * kb, a.logm);
+      }
+      s[pad16(e)] = cmulc<T>(s[pad16(e)], w);
+    }
+  } else {
+    for (int e0 = threadIdx.x; e0 < tile; e0 += 2 * UNROLL * blockDim.x) {
+      c2<T> v[2 * UNROLL];
 #pragma unroll
-    for (int u = 0; u < 2 * UNROLL; ++u) {
-      const int e = e0 + u * blockDim.x;
-      if (e >= tile) continue;
-      const int t = e >> logC, cc = e & (C - 1);
-      const long long kb = (long long)brev_bits((unsigned)t, logR1);
-      s[pad16(e)] = cmulc<T>(v[u], inter_tw<T>(a.twm, (c0 + cc) * kb, a.logm));
+      for (int u = 0; u < 2 * UNROLL; ++u) {
+        const int e = e0 + u * blockDim.x;
+        const int t = e >> logC, cc = e & (C - 1);
+        if (e < tile) v[u] = a.z[c0 + cc + ((long long)t << logL)];
+      }
+#pragma unroll
+      for (int u = 0; u < 2 * UNROLL; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e >= tile) continue;
+        const int t = e >> logC, cc = e & (C - 1);
+        const long long kb = (long long)brev_bits((unsigned)t, logR1);
+        s[pad16(e)] = cmulc<T>(v[u], inter_tw<T>(a.twm, (c0 + cc) * kb, a.logm));
+      }
     }
   }
   __syncthreads();
+  const c2<T>* tw = step_table<T>(tab, a.twL);
   smem_dit<T, true>(s, logR1, logC, C, 1, tw, LOG_LMAX);
   const T w_o = a.x[a.N];
   const int half = 1 << (logR1 - 1);
@@ -622,7 +791,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_inv_s
       const int e = e0 + u * blockDim.x;
       const int t = e >> logC, cc = e & (C - 1);
       const long long P = c0 + cc + ((long long)t << logL);
-      if (e < nout && P < a.N) er[u] = epi_load<T>(a, P);
+      if (e < nout && P < a.N) er[u] = epi_load<T>(a, P, epi);
     }
 #pragma unroll
     for (int u = 0; u < UNROLL; ++u) {
@@ -631,7 +800,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_inv_s
       const long long P = c0 + cc + ((long long)t << logL);
       if (e < nout && P < a.N) {
         const c2<T> y = s[pad16(e)];
-        epi_store<T>(a, P, er[u], y.x, y.y, w_o);
+        epi_store<T>(a, P, er[u], y.x, y.y, w_o, epi);
       }
     }
   }
@@ -639,7 +808,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_inv_s
     T acc = 0;
     for (int i = threadIdx.x; i < a.nparts; i += 32) acc += a.partials[i];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (threadIdx.x == 0) epi_middle<T>(a, acc, w_o);
+    if (threadIdx.x == 0) epi_middle<T>(a, acc, w_o, epi);
   }
 }
 
@@ -839,6 +1008,41 @@ static __global__ void k_sumsq_final(const double* part, int np, double* out) {
   for (int i = threadIdx.x; i < np; i += 32) acc += part[i];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if (threadIdx.x == 0) out[0] = acc;
+}
+
+// Launches of the strided passes with the prologue / epilogue instance chosen from the
+// arguments' runtime mode.
+template <typename T>
+inline void launch_fwd_strided(const LevelArgs<T>& a, int blocks, size_t smem, cudaStream_t s) {
+  const int nt = fft_threads<T>();
+  switch (a.pro) {
+    case PRO_SMOOTH: k_fwd_strided<T, IN_PACK, PRO_SMOOTH><<<blocks, nt, smem, s>>>(a); break;
+    case PRO_RESTRICT: k_fwd_strided<T, IN_PACK, PRO_RESTRICT><<<blocks, nt, smem, s>>>(a); break;
+    case PRO_PROLONG: k_fwd_strided<T, IN_PACK, PRO_PROLONG><<<blocks, nt, smem, s>>>(a); break;
+    default: k_fwd_strided<T, IN_PACK, PRO_NONE><<<blocks, nt, smem, s>>>(a); break;
+  }
+}
+template <typename T>
+inline void launch_inv_strided(const LevelArgs<T>& a, int blocks, size_t smem, cudaStream_t s) {
+  const int nt = fft_threads<T>();
+  switch (a.epi) {
+    case EPI_RESID: k_inv_strided<T, EPI_RESID><<<blocks, nt, smem, s>>>(a); break;
+    case EPI_JACOBI: k_inv_strided<T, EPI_JACOBI><<<blocks, nt, smem, s>>>(a); break;
+    default: k_inv_strided<T, EPI_APPLY><<<blocks, nt, smem, s>>>(a); break;
+  }
+}
+// Raise the dynamic shared-memory limit of every strided-pass instance.
+template <typename T>
+inline cudaError_t strided_smem_attrs(int bytes) {
+  const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_fwd_strided<T, IN_PACK, PRO_NONE>, A, bytes)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_fwd_strided<T, IN_PACK, PRO_SMOOTH>, A, bytes)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_fwd_strided<T, IN_PACK, PRO_RESTRICT>, A, bytes)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_fwd_strided<T, IN_PACK, PRO_PROLONG>, A, bytes)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_inv_strided<T, EPI_APPLY>, A, bytes)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_inv_strided<T, EPI_RESID>, A, bytes)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_inv_strided<T, EPI_JACOBI>, A, bytes);
 }
 
 }  // namespace tpc

@@ -98,13 +98,13 @@ int setup_device(int dev, unsigned char** base) {
   }
   const int big = 150 * 1024;
   const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  if (cudaFuncSetAttribute(k_fwd_strided<double, IN_PACK>, A, big) != cudaSuccess ||
-      cudaFuncSetAttribute(k_fwd_strided<double, IN_REAL>, A, big) != cudaSuccess ||
+  if (cudaFuncSetAttribute(k_fwd_strided<double, IN_PACK, PRO_NONE>, A, big) != cudaSuccess ||
+      cudaFuncSetAttribute(k_fwd_strided<double, IN_REAL, PRO_NONE>, A, big) != cudaSuccess ||
       cudaFuncSetAttribute(k_mid_pair<double, true>, A, big) != cudaSuccess ||
       cudaFuncSetAttribute(k_mid_whole<double, true>, A, big) != cudaSuccess ||
       cudaFuncSetAttribute(k_mid_fwd<double>, A, big) != cudaSuccess ||
       cudaFuncSetAttribute(k_mid_fwd_real<double>, A, big) != cudaSuccess ||
-      cudaFuncSetAttribute(k_inv_strided<double>, A, big) != cudaSuccess) {
+      cudaFuncSetAttribute(k_inv_strided<double, EPI_APPLY>, A, big) != cudaSuccess) {
     (void)cudaGetLastError();
     return fail(TPC_ECUDA, "tpc_apply_noalloc: cudaFuncSetAttribute failed");
   }
@@ -208,7 +208,7 @@ extern "C" int tpc_apply_noalloc(long long N, const double* tA, const double* tB
     if (logR1 == 0) {
       k_mid_fwd_real<double><<<1, FFT_THREADS, smem_mid, s>>>(a);
     } else {
-      k_fwd_strided<double, IN_REAL><<<fwd_blocks, FFT_THREADS, smem_strided, s>>>(a);
+      k_fwd_strided<double, IN_REAL, PRO_NONE><<<fwd_blocks, FFT_THREADS, smem_strided, s>>>(a);
       k_mid_fwd<double><<<1 << logR1, FFT_THREADS, smem_fwd_blk, s>>>(a);
     }
     if (blk == 0) k_extract_real<double><<<gm, 256, 0, s>>>(z, sA, m, scale);
@@ -226,9 +226,9 @@ extern "C" int tpc_apply_noalloc(long long N, const double* tA, const double* tB
   if (logR1 == 0) {
     k_mid_whole<double, true><<<1, FFT_THREADS, smem_mid, s>>>(a);
   } else {
-    k_fwd_strided<double, IN_PACK><<<fwd_blocks, FFT_THREADS, smem_strided, s>>>(a);
+    k_fwd_strided<double, IN_PACK, PRO_NONE><<<fwd_blocks, FFT_THREADS, smem_strided, s>>>(a);
     k_mid_pair<double, true><<<mid_blocks, FFT_THREADS, smem_mid, s>>>(a);
-    k_inv_strided<double><<<fwd_blocks, FFT_THREADS, smem_strided, s>>>(a);
+    k_inv_strided<double, EPI_APPLY><<<fwd_blocks, FFT_THREADS, smem_strided, s>>>(a);
   }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(TPC_ECUDA, cudaGetErrorString(e));
