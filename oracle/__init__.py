@@ -17,11 +17,15 @@ Contents
              Algorithm 2 with a dense LU at the coarsest level, the outer iteration and the
              stopping rule of section 5; the Cross splitting of eq. (split01) read off a
              dense level matrix; the two-grid factor of Theorem 4.1.
+``timestep`` -- section 5: the time-dependent problem advanced by the BDF4 scheme of eq.
+             (bdf4) with the shifted system (sigma I + A) U^k = ..., for the exact solution
+             u = e^t (1 + x)^6 of Tables 2 and 3.
 ``large``  -- the same finest-level operator for sizes where a dense matrix does not fit:
              selected dense rows, and the product computed with numpy's FFT as the
              convolution step (section 3.2, eq. ccs3.4).
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py`` (printed
 coefficients vs quadrature, Example 3.1, Toeplitz closure, SPD and the two-grid bound of
-Theorem 4.1, LU agreement, order of accuracy). No function is "parity unpinned".
+Theorem 4.1, LU agreement, order of accuracy, the sixteen BDF4 errors of Tables 2 and 3).
+No function is "parity unpinned".
 """

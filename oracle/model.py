@@ -215,6 +215,46 @@ def manufactured(variant: int, N: int, r: int):
     with the same row stencil (eqs. rightside1-2, read row by row). delta = r h.
     Returns (b, u_exact) in the unknown ordering of the module docstring.
     """
+    return manufactured_rhs(variant, N, r, _u_poly, _u_antiderivative)
+
+
+def collocation_points(N: int) -> np.ndarray:
+    """Coordinates x_p of the unknowns (nodes, then midpoints), in [0, 1]."""
+    nodes, mids = grid_points(N)
+    return np.concatenate([nodes, mids]) / N
+
+
+def exterior_points(N: int, r: int):
+    """The constrained points of Omega_I within the horizon, at half steps: left x = -j h/2
+    and right x = 1 + j h/2 for j = 0..2r (x = 0 and x = 1 included)."""
+    h = 1.0 / N
+    j = np.arange(2 * r + 1)
+    return -j * 0.5 * h, 1.0 + j * 0.5 * h
+
+
+def exterior_rhs(variant: int, N: int, r: int, g_left, g_right) -> np.ndarray:
+    """Minus the couplings of each row to the constrained exterior values (eqs.
+    rightside1-2, read row by row with the row's own stencil): -sum_q entry(p, q) g(x_q).
+    g_left[j], g_right[j]: values at the points of :func:`exterior_points`."""
+    nodes, mids = grid_points(N)
+    rows = [(x, True) for x in nodes] + [(x, False) for x in mids]
+    out = np.zeros(len(rows))
+    for p, (xp, is_node) in enumerate(rows):
+        xp2 = int(round(2 * xp))
+        for j in range(2 * r + 1):
+            for q2, gv in ((-j, g_left[j]), (2 * N + j, g_right[j])):
+                dist2 = q2 - xp2
+                if abs(dist2) > 2 * r + 1:
+                    continue
+                w = stencil_entry(variant, is_node, dist2, r)
+                if w != 0.0:
+                    out[p] -= w * gv
+    return out
+
+
+def manufactured_rhs(variant: int, N: int, r: int, u, U):
+    """The right-hand side of :func:`manufactured` for any smooth u with antiderivative U
+    (callables of x): eta_h (-L_delta u)(x_p) minus the exterior couplings of g = u."""
     h = 1.0 / N
     delta = r * h
     nodes, mids = grid_points(N)
@@ -226,8 +266,8 @@ def manufactured(variant: int, N: int, r: int):
     ext2 = all2[(all2 <= 0) | (all2 >= 2 * N)]
     for p, (xp, is_node) in enumerate(rows):
         x = xp * h
-        integ = _u_antiderivative(x + delta) - _u_antiderivative(x - delta)
-        val = (6.0 / h) * (2.0 * delta * _u_poly(x) - integ)
+        integ = U(x + delta) - U(x - delta)
+        val = (6.0 / h) * (2.0 * delta * u(x) - integ)
         xp2 = int(round(2 * xp))
         for q2 in ext2:
             dist2 = q2 - xp2
@@ -235,7 +275,7 @@ def manufactured(variant: int, N: int, r: int):
                 continue
             w = stencil_entry(variant, is_node, dist2, r)
             if w != 0.0:
-                val -= w * _u_poly(q2 * 0.5 * h)
+                val -= w * u(q2 * 0.5 * h)
         b[p] = val
-        uex[p] = _u_poly(x)
+        uex[p] = u(x)
     return b, uex
