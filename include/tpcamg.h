@@ -97,6 +97,16 @@ int tpc_setup(const tpc_params* p, double delta, double h, int levels, void* cud
 int tpc_solve(tpc_handle* H, const double* b_dev, double* x_dev, double tol, int use_x0,
               int* iters_out, double* relres_out);
 
+/* One step of eq. (bdf4) on a handle set up with shift = sigma (tpc_bdf4_coefficients):
+ * forms b = hist_scale (4 u1 - 3 u2 + 4/3 u3 - 1/4 u4) + g_scale g on the device (u_j = U^{k-j};
+ * g may be NULL for no source term) and solves (sigma I + A) u_out = b from the initial guess
+ * u1, stopping as tpc_solve does (relative to the initial residual). Device pointers of n_K
+ * doubles; u_out may be any of u1..u4 (they are read first). Stream-ordered on the handle's
+ * stream; blocks the host like tpc_solve. Returns as tpc_solve. */
+int tpc_bdf4_step(tpc_handle* H, const double* u1, const double* u2, const double* u3,
+                  const double* u4, double hist_scale, const double* g, double g_scale,
+                  double tol, double* u_out, int* iters_out, double* relres_out);
+
 /* Solve count independent systems at once (instances of any sizes, variants and precisions):
  * instance i solves hs[i]'s system A x_dev[i] = b_dev[i] to tol (zero initial guess). Each
  * instance runs on its own handle's stream and the host services the instances round-robin,
@@ -149,6 +159,33 @@ int tpc_export_level(const tpc_handle* H, int level, double* host_buf, size_t ca
  * *need receives the total count; nothing is written if cap < *need. */
 int tpc_host_hierarchy(const tpc_params* p, double delta, double h, int levels,
                        double* host_buf, size_t cap, size_t* need);
+
+/* ---------------------------------------------------------------------------------------
+ * Time stepping (section 5): u_t = L_delta u + f on (0, 1), u = g on the interaction domain,
+ * advanced by the BDF4 scheme of eq. (bdf4),
+ *   (25/12 I - tau L_delta) U^k = 4 U^{k-1} - 3 U^{k-2} + 4/3 U^{k-3} - 1/4 U^{k-4} + tau F^k.
+ * The collocation system is A U = eta_h (-L_delta u)(x_p) - (exterior couplings of g) with
+ * eta_h = 6 / (gamma h) (gamma = gamma0, or the paper's 3 / delta^3 with delta = r h when
+ * gamma0 = 0), so a step is the shifted solve
+ *   (sigma I + A) U^k = (eta_h / tau) (4 U^{k-1} - 3 U^{k-2} + 4/3 U^{k-3} - 1/4 U^{k-4}) + b^k,
+ *   sigma = 25 eta_h / (12 tau),  b^k = eta_h F^k(x_p) - (exterior couplings of g^k).
+ * --------------------------------------------------------------------------------------- */
+
+/* sigma (the shift to set in tpc_params.shift before tpc_setup) and eta_h / tau for time step
+ * tau > 0. Host only. TPC_EINVAL on bad arguments (message in tpc_last_error(NULL)). */
+int tpc_bdf4_coefficients(const tpc_params* p, double delta, double h, double tau,
+                          double* shift_out, double* hist_scale_out);
+
+/* Collocation right-hand side of section 2.2 (eq. ccs2.5 with the constrained exterior values
+ * moved to the right, eqs. rightside1-2, each row with its own stencil):
+ *   rhs[p] = eta_h f_colloc[p] - sum over exterior points q within the horizon of A(p, q) g(x_q).
+ * f_colloc: n = 2/h - 1 values of f at the collocation points in unknown order (nodes h..1-h,
+ * then midpoints h/2..1-h/2), or NULL for f = 0. g_left[j] = g(-j h/2), g_right[j] =
+ * g(1 + j h/2) for j = 0..2r (r = floor(delta/h), at least 1), or NULL for zero exterior
+ * values. rhs_out: n doubles. Host memory, host work O(n + r^2). Returns TPC_OK or TPC_EINVAL.
+ * (SPD system: the midpoint rows use the integer-row stencil, as eq. (system1) does.) */
+int tpc_collocation_rhs(const tpc_params* p, double delta, double h, const double* f_colloc,
+                        const double* g_left, const double* g_right, double* rhs_out);
 
 /* Timing of the kernels of one level's product y = f - A_level x on the handle's stream:
  * each kernel of the pipeline is launched reps times (reps >= 1) between two CUDA events,

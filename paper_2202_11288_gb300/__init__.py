@@ -28,7 +28,9 @@ EXPORTED = ["tpc_default_params", "tpc_setup", "tpc_solve", "tpc_solve_batch", "
             "tpc_apply_f32",
             "tpc_vcycle", "tpc_level_size", "tpc_finest_level", "tpc_coarsest_level",
             "tpc_export_level", "tpc_host_hierarchy", "tpc_time_level_kernels",
-            "tpc_time_level_kernels_f32", "tpc_kernel_launches", "tpc_apply_noalloc", "tpc_destroy", "tpc_last_error",
+            "tpc_time_level_kernels_f32", "tpc_kernel_launches", "tpc_apply_noalloc",
+            "tpc_bdf4_coefficients", "tpc_collocation_rhs", "tpc_bdf4_step",
+            "tpc_destroy", "tpc_last_error",
             "tpc_server_default_config", "tpc_server_create", "tpc_server_submit",
             "tpc_server_poll", "tpc_server_outstanding", "tpc_server_destroy"]
 
@@ -104,6 +106,12 @@ def lib() -> ctypes.CDLL:
     L.tpc_export_level.restype = I
     L.tpc_host_hierarchy.argtypes = [pp, D, D, I, P, SZ, ctypes.POINTER(SZ)]
     L.tpc_host_hierarchy.restype = I
+    L.tpc_bdf4_coefficients.argtypes = [pp, D, D, D, ctypes.POINTER(D), ctypes.POINTER(D)]
+    L.tpc_bdf4_coefficients.restype = I
+    L.tpc_collocation_rhs.argtypes = [pp, D, D, P, P, P, P]
+    L.tpc_collocation_rhs.restype = I
+    L.tpc_bdf4_step.argtypes = [P, P, P, P, P, D, P, D, D, P, ctypes.POINTER(I), ctypes.POINTER(D)]
+    L.tpc_bdf4_step.restype = I
     L.tpc_time_level_kernels.argtypes = [P, I, I, P, P, P, ctypes.POINTER(D)]
     L.tpc_time_level_kernels.restype = I
     L.tpc_time_level_kernels_f32.argtypes = [P, I, I, P, P, P, ctypes.POINTER(D)]
@@ -182,7 +190,9 @@ def tpc_host_hierarchy(delta: float, h: float, levels: int = 0, params: TpcParam
     return _split_levels(buf)
 
 
-def _ptr(t) -> int:
+def _ptr(t):
+    if t is None:
+        return None  # NULL
     return t.data_ptr() if hasattr(t, "data_ptr") else int(t)
 
 
@@ -206,6 +216,41 @@ def tpc_solve(H, b, x, tol: float = 1e-10, use_x0: bool = False):
     it, rel = ctypes.c_int(0), ctypes.c_double(0.0)
     rc = _check(lib().tpc_solve(H, _ptr(b), _ptr(x), tol, int(use_x0), ctypes.byref(it),
                                 ctypes.byref(rel)), H, allow=(TPC_OK, TPC_ENOTCONV))
+    return rc, it.value, rel.value
+
+
+def tpc_bdf4_coefficients(delta: float, h: float, tau: float, params: TpcParams | None = None):
+    """(sigma, eta_h / tau) of one BDF4 step of size tau (host only)."""
+    p = params if params is not None else tpc_default_params()
+    sh, hs = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib().tpc_bdf4_coefficients(ctypes.byref(p), delta, h, tau, ctypes.byref(sh),
+                                       ctypes.byref(hs)))
+    return sh.value, hs.value
+
+
+def tpc_collocation_rhs(delta: float, h: float, f_colloc=None, g_left=None, g_right=None,
+                        params: TpcParams | None = None) -> np.ndarray:
+    """eta_h f - (exterior couplings of g) at the collocation points (host arrays; None = 0)."""
+    p = params if params is not None else tpc_default_params()
+    n = int(round(2.0 / h)) - 1
+    fa, gl, gr = (None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+                  for a in (f_colloc, g_left, g_right))
+    out = np.empty(n, dtype=np.float64)
+
+    def ptr(a):
+        return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+    _check(lib().tpc_collocation_rhs(ctypes.byref(p), delta, h, ptr(fa), ptr(gl), ptr(gr),
+                                     ptr(out)))
+    return out
+
+
+def tpc_bdf4_step(H, u1, u2, u3, u4, hist_scale: float, g, g_scale: float, tol: float, out):
+    it, rel = ctypes.c_int(0), ctypes.c_double(0.0)
+    rc = _check(lib().tpc_bdf4_step(H, _ptr(u1), _ptr(u2), _ptr(u3), _ptr(u4), hist_scale,
+                                    _ptr(g) if g is not None else None, g_scale, tol, _ptr(out),
+                                    ctypes.byref(it), ctypes.byref(rel)), H,
+                allow=(TPC_OK, TPC_ENOTCONV))
     return rc, it.value, rel.value
 
 
@@ -316,6 +361,11 @@ class Solver:
 
     def solve_host(self, b: np.ndarray, x: np.ndarray, tol: float = 1e-10, use_x0: bool = False):
         return tpc_solve_host(self.handle, b, x, tol, use_x0)
+
+    def bdf4_step(self, u1, u2, u3, u4, hist_scale: float, g, g_scale: float, out,
+                  tol: float = 1e-12):
+        """One step of eq. (bdf4) (the handle's shift must be sigma, tpc_bdf4_coefficients)."""
+        return tpc_bdf4_step(self.handle, u1, u2, u3, u4, hist_scale, g, g_scale, tol, out)
 
     def apply(self, level: int, x, y) -> None:
         tpc_apply(self.handle, level, x, y)

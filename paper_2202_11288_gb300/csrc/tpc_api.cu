@@ -962,6 +962,25 @@ int tpc_solve(tpc_handle* H, const double* b_dev, double* x_dev, double tol, int
   return solve_impl(H, b_dev, x_dev, tol, use_x0, iters_out, relres_out);
 }
 
+int tpc_bdf4_step(tpc_handle* H, const double* u1, const double* u2, const double* u3,
+                  const double* u4, double hist_scale, const double* g, double g_scale,
+                  double tol, double* u_out, int* iters_out, double* relres_out) {
+  if (!H || !u1 || !u2 || !u3 || !u4 || !u_out || !(tol >= 0.0) || !std::isfinite(hist_scale) ||
+      !std::isfinite(g_scale)) {
+    if (H) H->err = "bad argument to tpc_bdf4_step";
+    return TPC_EINVAL;
+  }
+  const long long n = H->d.lev[0].n;
+  cudaStream_t s = H->stream;
+  // the right-hand side goes to the residual buffer, which the solve copies before reuse
+  k_bdf4_rhs<<<grid_for(n), NTHREADS, 0, s>>>(H->r0, u1, u2, u3, u4, hist_scale, g, g_scale, n);
+  H->launches += 1;
+  TPC_CUDA(H, cudaGetLastError());
+  if (u_out != u1)  // initial guess: the previous level
+    TPC_CUDA(H, cudaMemcpyAsync(u_out, u1, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return solve_impl(H, H->r0, u_out, tol, 1, iters_out, relres_out);
+}
+
 int tpc_solve_batch(tpc_handle* const* hs, int count, const double* const* b_dev,
                     double* const* x_dev, double tol, int* iters_out, double* relres_out,
                     int* status_out) {

@@ -58,6 +58,37 @@ double coef_d(long long dist2, int r) {
 
 thread_local std::string g_host_err;
 
+// h = 2^-K (1 <= K <= 30) and the horizon ratio of section 2.2: r = floor(delta / h) >= 1, or
+// 1 when delta <= h.
+int grid_and_horizon(double delta, double h, int& K, int& r, std::string& err) {
+  if (!(h > 0.0) || !(h < 1.0) || !std::isfinite(delta) || !(delta > 0.0)) {
+    err = "need 0 < h < 1 and delta > 0";
+    return TPC_EINVAL;
+  }
+  K = (int)std::lround(std::log2(1.0 / h));
+  if (K < 1 || K > 30 || std::ldexp(1.0, -K) != h) {
+    err = "h must be 2^-K with 1 <= K <= 30";
+    return TPC_EINVAL;
+  }
+  r = 1;
+  if (delta > h) {
+    const double fr = std::floor(delta / h);
+    if (fr > 1e9) {
+      err = "delta/h too large";
+      return TPC_EINVAL;
+    }
+    r = (int)fr;
+  }
+  return TPC_OK;
+}
+
+// eta_h = 6 / (gamma h), gamma = gamma0, or 3 / delta^3 with delta = r h when gamma0 = 0.
+double eta_of(const tpc_params& p, int r, double h) {
+  const double d = r * h;
+  const double gamma = (p.gamma0 > 0.0) ? p.gamma0 : 3.0 / (d * d * d);
+  return 6.0 / (gamma * h);
+}
+
 LevelForm finest_form(int variant, int K, int r, double shift) {
   const long long Nint = 1LL << K;  // intervals
   LevelForm L;
@@ -216,16 +247,8 @@ int invert_dense(std::vector<double>& A, long long n, std::vector<double>& inv) 
 
 int build_host_hierarchy(const tpc_params& p, double delta, double h, int levels,
                          HostHierarchy& out, std::string& err) {
-  if (!(h > 0.0) || !(h < 1.0) || !std::isfinite(delta) || !(delta > 0.0)) {
-    err = "need 0 < h < 1 and delta > 0";
-    return TPC_EINVAL;
-  }
-  const double Kd = std::log2(1.0 / h);
-  const int K = (int)std::lround(Kd);
-  if (K < 1 || K > 30 || std::ldexp(1.0, -K) != h) {
-    err = "h must be 2^-K with 1 <= K <= 30";
-    return TPC_EINVAL;
-  }
+  int K = 0, r = 1;
+  if (const int rc = grid_and_horizon(delta, h, K, r, err)) return rc;
   if (p.variant != TPC_SPD && p.variant != TPC_NONSYM) {
     err = "variant must be TPC_SPD or TPC_NONSYM";
     return TPC_EINVAL;
@@ -259,17 +282,6 @@ int build_host_hierarchy(const tpc_params& p, double delta, double h, int levels
   if (kc > 7) {
     err = "the coarsest level kept by 'levels' must be <= 7 (dense solve of <= 255 unknowns)";
     return TPC_EINVAL;
-  }
-  // horizon ratio (section 2.2): r = floor(delta/h) >= 1, or 1 when delta <= h
-  const double ratio = delta / h;
-  int r = 1;
-  if (delta > h) {
-    const double fr = std::floor(ratio);
-    if (fr > 1e9) {
-      err = "delta/h too large";
-      return TPC_EINVAL;
-    }
-    r = (int)fr;
   }
   out.K = K;
   out.kc = kc;
@@ -386,6 +398,54 @@ int tpc_host_hierarchy(const tpc_params* p, double delta, double h, int levels,
   for (const auto& L : H.lev) {
     tpc::export_level(L, host_buf + o);
     o += tpc::export_count(L.N);
+  }
+  return TPC_OK;
+}
+
+int tpc_bdf4_coefficients(const tpc_params* p, double delta, double h, double tau,
+                          double* shift_out, double* hist_scale_out) {
+  if (!p || !shift_out || !hist_scale_out || !(tau > 0.0) || !std::isfinite(tau) ||
+      !(p->gamma0 >= 0.0) || !std::isfinite(p->gamma0)) {
+    tpc::g_host_err = "bad argument to tpc_bdf4_coefficients";
+    return TPC_EINVAL;
+  }
+  int K = 0, r = 1;
+  if (const int rc = tpc::grid_and_horizon(delta, h, K, r, tpc::g_host_err)) return rc;
+  const double eta = tpc::eta_of(*p, r, h);
+  *shift_out = 25.0 * eta / (12.0 * tau);
+  *hist_scale_out = eta / tau;
+  return TPC_OK;
+}
+
+int tpc_collocation_rhs(const tpc_params* p, double delta, double h, const double* f_colloc,
+                        const double* g_left, const double* g_right, double* rhs_out) {
+  if (!p || !rhs_out || (p->variant != TPC_SPD && p->variant != TPC_NONSYM) ||
+      !(p->gamma0 >= 0.0) || !std::isfinite(p->gamma0)) {
+    tpc::g_host_err = "bad argument to tpc_collocation_rhs";
+    return TPC_EINVAL;
+  }
+  int K = 0, r = 1;
+  if (const int rc = tpc::grid_and_horizon(delta, h, K, r, tpc::g_host_err)) return rc;
+  const long long Nint = 1LL << K, nn = Nint - 1, n = 2 * Nint - 1;
+  const double eta = tpc::eta_of(*p, r, h);
+  for (long long q = 0; q < n; ++q) rhs_out[q] = f_colloc ? eta * f_colloc[q] : 0.0;
+  const long long reach = 2LL * r + 1;  // largest twice-distance with a nonzero entry
+  // row p: twice-coordinate xp2 (nodes 2i, i = 1..Nint-1; midpoints 2i - 1, i = 1..Nint)
+  for (long long q = 0; q < n; ++q) {
+    const bool node = q < nn;
+    const long long xp2 = node ? 2 * (q + 1) : 2 * (q - nn + 1) - 1;
+    if (xp2 > reach && 2 * Nint - xp2 > reach) continue;  // no exterior point within reach
+    auto w = [&](long long dist2) {
+      if (node || p->variant == TPC_SPD) return tpc::coef_a(dist2, r);
+      return (dist2 & 1) ? tpc::coef_c(dist2, r) : tpc::coef_d(dist2, r);
+    };
+    double acc = 0.0;
+    for (long long j = 0; j <= 2LL * r; ++j) {
+      const long long dl = -j - xp2, dr = 2 * Nint + j - xp2;  // to x = -j h/2, 1 + j h/2
+      if (g_left && (dl < 0 ? -dl : dl) <= reach) acc += w(dl) * g_left[j];
+      if (g_right && (dr < 0 ? -dr : dr) <= reach) acc += w(dr) * g_right[j];
+    }
+    rhs_out[q] -= acc;
   }
   return TPC_OK;
 }

@@ -962,6 +962,17 @@ __global__ void k_axpy(T* u, const T* e, long long n) {
     u[i] += e[i];
 }
 
+// Right-hand side of one step of eq. (bdf4) for the shifted system (sigma I + A) U^k = b:
+// b = hs (4 u1 - 3 u2 + 4/3 u3 - 1/4 u4) + gs g  (u_j = U^{k-j}).
+static __global__ void k_bdf4_rhs(double* b, const double* u1, const double* u2, const double* u3,
+                           const double* u4, double hs, const double* g, double gs, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double hist = 4.0 * u1[i] - 3.0 * u2[i] + (4.0 / 3.0) * u3[i] - 0.25 * u4[i];
+    b[i] = hs * hist + (g ? gs * g[i] : 0.0);
+  }
+}
+
 template <typename T>
 __global__ void k_copy(const T* src, T* dst, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
