@@ -41,11 +41,14 @@ N_SMS = 152
 # level, from ncu (profiles/k_mid_pair_fp64_N2e22.md); unknown for other sizes
 MID_TRAFFIC = {}
 # Algorithmic bytes of the FP32 finest-level kernels per point of the FFT length m = 2N + 2
-# (residual epilogue, no prologue; x, f, y hold about m floats, q, zeta and p, xi about m/2 each):
-#   forward pass:           reads x (4m), q and zeta (4m); writes z (8m)               -> 16m
-#   contiguous-block kernel: reads z (8m) and 16 B of spectra per pair (8m); writes z -> 24m
-#   inverse pass:           reads z (8m), p and xi (4m), f (4m); writes y (4m)         -> 20m
-F32_BYTES_PER_POINT = (16, 24, 20)
+# (residual epilogue, no prologue; x, f, y hold about m floats; the Cross vectors q, zeta and
+# p, xi hold m/2 entries each of which only the first r are nonzero and read, a fraction r/N):
+#   forward pass:            reads x (4m), q and zeta (4m r/N); writes z (8m)   -> 12m + 4m r/N
+#   contiguous-block kernel: reads z (8m), 16 B of spectra per pair (8m); writes z  -> 24m
+#   inverse pass:            reads z (8m), p and xi (4m r/N), f (4m); writes y (4m) -> 16m + 4m r/N
+def f32_bytes_per_point(r, N):
+    frac = min(1.0, r / N)
+    return (12.0 + 4.0 * frac, 24.0, 16.0 + 4.0 * frac)
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP32 finest kernels, from ncu,
 # keyed by (K, kernel index); unknown for other sizes
 F32_TRAFFIC = {}
@@ -464,7 +467,7 @@ def run_ours(args, rank, world, local_rank):
     # dominant one is the slowest of the three
     names = ("k_fwd_strided<float>", "k_mid_pair<float>", "k_inv_strided<float>")
     dom = max(range(3), key=lambda i: ms3_32[i])
-    nbytes = [b * m for b in F32_BYTES_PER_POINT]
+    nbytes = [b * m for b in f32_bytes_per_point(cfg["r"], 2 ** args.K)]
     hbm = measured_hbm_gbs()
     ach32 = nbytes[dom] / (ms3_32[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": ach32, "peak": hbm["gbs"], "unit": "GB/s",
@@ -523,20 +526,22 @@ def run_profile_case(args):
 
 
 def run_profile_f32(args):
-    """A fixed launch sequence for profilers: mixed setup, then three FP32 finest products."""
+    """A fixed launch sequence for profilers: mixed setup, then the FP32 finest-level kernels
+    exactly as the bench's roofline times them (tpc_time_level_kernels_f32, residual epilogue):
+    forward pass x2, contiguous-block kernel x2, inverse pass x2 (the first of each a warm-up)."""
     import torch
 
     import paper_2202_11288_gb300 as tpc
     n = 2 ** (args.K + 1) - 1
     S = tpc.Solver(args.delta, 2.0 ** -args.K, precision=tpc.TPC_MIXED)
     x = torch.tensor(uniform_pm1(n, 5), dtype=torch.float32, device="cuda")
+    f = torch.tensor(uniform_pm1(n, 6), dtype=torch.float32, device="cuda")
     y = torch.empty_like(x)
-    for _ in range(3):
-        S.apply_f32(args.K, x, y)
+    ms = tpc.tpc_time_level_kernels_f32(S.handle, args.K, 1, x, f, y)
     torch.cuda.synchronize()
     assert torch.isfinite(y).all()
     S.close()
-    print(json.dumps({"profile_f32": f"N=2^{args.K}", "unknowns": n}))
+    print(json.dumps({"profile_f32": f"N=2^{args.K}", "unknowns": n, "ms": ms}))
 
 
 def run_profile_solve(args):

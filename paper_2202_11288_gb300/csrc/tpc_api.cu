@@ -41,8 +41,18 @@ template <typename T> struct DevLevel {
   T* xi = nullptr;
   T* zeta = nullptr;
   T o = 0, wA_pre = 0, wO_pre = 0, wD_pre = 0, wA_post = 0, wO_post = 0, wD_post = 0;
+  // support of the Cross vectors: q, zeta vanish from index nq on, p, xi from np on (the
+  // couplings to the middle unknown reach only about r points, scaled per level)
+  long long nq = 0, np = 0;
   c2<T>* twm = nullptr;
 };
+
+// Smallest s with v[i] == 0 for every i >= s (over the union of two vectors).
+inline long long support2(const std::vector<double>& a, const std::vector<double>& b) {
+  long long s = (long long)a.size();
+  while (s > 0 && a[s - 1] == 0.0 && b[s - 1] == 0.0) --s;
+  return s;
+}
 
 // Device hierarchy in one precision.
 template <typename T> struct Hier {
@@ -195,6 +205,8 @@ LevelArgs<T> level_args(const Hier<T>& G, const DevLevel<T>& L) {
   a.q = L.q;
   a.xi = L.xi;
   a.zeta = L.zeta;
+  a.nq = L.nq;
+  a.np = L.np;
   a.o = L.o;
   a.twm = L.twm;
   a.twL = G.twL;
@@ -447,6 +459,8 @@ int alloc_levels(tpc_handle* H, Hier<T>& G) {
     TPC_TRY(upload<T>(H, L.q, F.q));
     TPC_TRY(upload<T>(H, L.xi, F.xi));
     TPC_TRY(upload<T>(H, L.zeta, F.zeta));
+    L.nq = support2(F.q, F.zeta);
+    L.np = support2(F.p, F.xi);
     if (L.logR1 && sizeof(T) == sizeof(double)) {  // FP32 computes these (inter_tw)
       std::vector<double> twm;
       twiddles(L.m, L.m, twm);  // W_m^j, j < m

@@ -76,6 +76,7 @@ template <typename T> struct LevelArgs {
   const T* xi;
   const T* zeta;
   T o;
+  long long nq, np;      // q, zeta are zero from index nq on; p, xi from index np on
   T wA, wO, wD;          // omega / diagonal, per segment (damped Jacobi, eq. 7)
   const c2<T>* twm;      // strided pipelines only: W_m^j, j < m (FP64); two-level (FP32)
   const c2<T>* twL;      // W_{4096}^j, j < 4096 (FP32 copies the octant j <= 512 to shared)
@@ -282,8 +283,10 @@ template <typename T>
 __device__ __forceinline__ EpiRaw<T> epi_load(const LevelArgs<T>& a, long long i, int epi) {
   EpiRaw<T> r{0, 0, 0, 0, 0, 0};
   const long long iw = a.N + 1 + i;
-  r.p = a.p[i];
-  r.xi = a.xi[i];
+  if (i < a.np) {
+    r.p = a.p[i];
+    r.xi = a.xi[i];
+  }
   if (epi != EPI_APPLY) {
     r.fv = a.f[i];
     r.fw = a.f[iw];
@@ -407,8 +410,12 @@ __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_fwd_s
       if (P < a.N) {
         cp_async4(&lo->x, src + P);
         cp_async4(&lo->y, src + a.N + 1 + P);
-        cp_async4(&hi->x, a.q + P);
-        cp_async4(&hi->y, a.zeta + P);
+        if (P < a.nq) {
+          cp_async4(&hi->x, a.q + P);
+          cp_async4(&hi->y, a.zeta + P);
+        } else {
+          *hi = mk<T>(0, 0);
+        }
       } else {
         *lo = mk<T>(0, 0);
         *hi = mk<T>(0, 0);
@@ -465,8 +472,8 @@ __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_fwd_s
         if (ok[u]) {
           rv[u] = operand_load<T>(a, P, pro);
           rw[u] = operand_load<T>(a, a.N + 1 + P, pro);
-          qv[u] = a.q[P];
-          zv[u] = a.zeta[P];
+          qv[u] = (P < a.nq) ? a.q[P] : (T)0;
+          zv[u] = (P < a.nq) ? a.zeta[P] : (T)0;
         }
       }
 #pragma unroll
@@ -558,8 +565,8 @@ __device__ __forceinline__ void mid_core(const LevelArgs<T>& a, const c2<T>* tw,
         if (i < a.N) {
           rv[u] = operand_load<T>(a, i, a.pro);
           rw[u] = operand_load<T>(a, a.N + 1 + i, a.pro);
-          qv[u] = a.q[i];
-          zv[u] = a.zeta[i];
+          qv[u] = (i < a.nq) ? a.q[i] : (T)0;
+          zv[u] = (i < a.nq) ? a.zeta[i] : (T)0;
         }
       }
 #pragma unroll
@@ -784,6 +791,21 @@ __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_inv_s
   const T w_o = a.x[a.N];
   const int half = 1 << (logR1 - 1);
   const int nout = half << logC;
+  // FP32: the right-hand side pair (f_v, f_w) of each output arrives by asynchronous copies
+  // into the slot of row t + R1/2 (the rows the embedding discards, free after the transform)
+  constexpr bool ASYNC_F = sizeof(T) == 4 && EPI != EPI_APPLY;
+  if constexpr (ASYNC_F) {
+    for (int e = threadIdx.x; e < nout; e += blockDim.x) {
+      const int t = e >> logC, cc = e & (C - 1);
+      const long long P = c0 + cc + ((long long)t << logL);
+      if (P < a.N) {
+        c2<T>* hi = s + pad16(e + nout);
+        cp_async4(&hi->x, a.f + P);
+        cp_async4(&hi->y, a.f + a.N + 1 + P);
+      }
+    }
+    cp_async_wait_all();
+  }
   for (int e0 = threadIdx.x; e0 < nout; e0 += UNROLL * blockDim.x) {
     EpiRaw<T> er[UNROLL];
 #pragma unroll
@@ -791,7 +813,20 @@ __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_inv_s
       const int e = e0 + u * blockDim.x;
       const int t = e >> logC, cc = e & (C - 1);
       const long long P = c0 + cc + ((long long)t << logL);
-      if (e < nout && P < a.N) er[u] = epi_load<T>(a, P, epi);
+      if (e < nout && P < a.N) {
+        if constexpr (ASYNC_F) {
+          er[u] = epi_load<T>(a, P, EPI_APPLY);  // p, xi only
+          const c2<T> fp = s[pad16(e + nout)];
+          er[u].fv = fp.x;
+          er[u].fw = fp.y;
+          if (EPI == EPI_JACOBI) {
+            er[u].xv = a.x[P];
+            er[u].xw = a.x[a.N + 1 + P];
+          }
+        } else {
+          er[u] = epi_load<T>(a, P, epi);
+        }
+      }
     }
 #pragma unroll
     for (int u = 0; u < UNROLL; ++u) {

@@ -190,6 +190,8 @@ extern "C" int tpc_apply_noalloc(long long N, const double* tA, const double* tB
   a.q = q;
   a.xi = xi;
   a.zeta = zeta;
+  a.nq = N;  // full support (the caller's vectors are not scanned)
+  a.np = N;
   a.o = o;
   a.twm = twm;
   a.twL = twL;
