@@ -65,6 +65,9 @@ typedef struct tpc_params {
   int precision;      /* TPC_FP64, or TPC_MIXED: FP32 V-cycles inside FP64 refinement      */
   int max_iters;      /* outer iterations of tpc_solve (default 100)                       */
   int inner_cycles;   /* TPC_MIXED: FP32 V-cycles per FP64 residual (default 6)            */
+  int autotune;       /* 1 (default): tpc_setup times the tile widths of the strided FFT
+                         passes of every level and keeps the fastest (results are the same
+                         for every width); 0: the fixed rule                                */
 } tpc_params;
 
 typedef struct tpc_handle tpc_handle;

@@ -41,7 +41,8 @@ class TpcParams(ctypes.Structure):
                 ("shift", ctypes.c_double), ("m1", ctypes.c_int), ("m2", ctypes.c_int),
                 ("omega_pre", ctypes.c_double), ("omega_post", ctypes.c_double),
                 ("coarsest_level", ctypes.c_int), ("precision", ctypes.c_int),
-                ("max_iters", ctypes.c_int), ("inner_cycles", ctypes.c_int)]
+                ("max_iters", ctypes.c_int), ("inner_cycles", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
 
 
 class TpcServerConfig(ctypes.Structure):

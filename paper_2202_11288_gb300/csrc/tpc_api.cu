@@ -7,6 +7,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -473,7 +475,8 @@ int alloc_levels(tpc_handle* H, Hier<T>& G) {
     if (H->prm.variant == TPC_NONSYM) TPC_TRY(dalloc(H, &L.sC, L.m));
   }
   TPC_TRY(dalloc(H, &G.z, max_m));
-  TPC_TRY(dalloc(H, &G.partials, max_parts));
+  (void)max_parts;  // the autotuner may choose down to one column per block
+  TPC_TRY(dalloc(H, &G.partials, (size_t)1 << LOG_LMAX));
   const long long nc = 2 * HH.lev.back().N + 1;
   TPC_TRY(dalloc(H, &G.coarse_inv, (size_t)(nc * nc)));
   TPC_TRY(upload<T>(H, G.coarse_inv, HH.coarse_inv));
@@ -546,6 +549,83 @@ int build_bottom(tpc_handle* H, Hier<T>& G) {
   return TPC_OK;
 }
 
+// Column-group autotuner for the strided passes of one hierarchy: for every level it times the
+// forward and inverse strided passes (no prologue, residual epilogue, on the level's own work
+// vectors, zeroed) for each tile width 2^logC that fits (tile <= 2^LOG_TILE_MAX entries) and
+// keeps the fastest. The width changes which block transforms which column, not the
+// transforms; only the order in which the per-block partial sums of the Cross dot q.v +
+// zeta.w_bar are added follows the number of blocks. So that every handle of a process computes
+// bit for bit the same products (a solve alone and in a batch or the server agree exactly), the
+// choice is made once per (precision, level size) and kept for the process.
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, int> g_tuned_logC;  // (sizeof(T), log2 m) -> logC
+
+template <typename T>
+int autotune_levels(tpc_handle* H, Hier<T>& G, bool only_finest) {
+  cudaStream_t s = H->stream;
+  cudaEvent_t ev[2];
+  TPC_CUDA(H, cudaEventCreate(&ev[0]));
+  TPC_CUDA(H, cudaEventCreate(&ev[1]));
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  int rc = TPC_OK;
+  for (size_t li = 0; li < G.lev.size() && rc == TPC_OK; ++li) {
+    if (only_finest && li > 0) break;
+    DevLevel<T>& L = G.lev[li];
+    if (L.logR1 == 0 || !L.sA) continue;
+    const std::pair<int, int> key((int)sizeof(T), L.logm);
+    const auto hit = g_tuned_logC.find(key);
+    if (hit != g_tuned_logC.end()) {
+      L.logC = hit->second;
+      L.fwd_blocks = 1 << (L.logL - L.logC);
+      L.smem_strided =
+          sizeof(c2<T>) * (size_t)(tw_slots<T>() + padded_size(1 << (L.logR1 + L.logC)));
+      continue;
+    }
+    for (T* v : {G.e[li], G.f[li], G.t[li]})
+      if (cudaMemsetAsync(v, 0, (size_t)L.n * sizeof(T), s) != cudaSuccess) rc = TPC_ECUDA;
+    const int keep = L.logC;
+    float t[5] = {-1.0f, -1.0f, -1.0f, -1.0f, -1.0f};
+    for (int c = 0; c <= 4 && L.logR1 + c <= LOG_TILE_MAX && c <= L.logL && rc == TPC_OK; ++c) {
+      L.logC = c;
+      L.fwd_blocks = 1 << (L.logL - c);
+      L.smem_strided =
+          sizeof(c2<T>) * (size_t)(tw_slots<T>() + padded_size(1 << (L.logR1 + L.logC)));
+      LevelArgs<T> a = level_args<T>(G, L);
+      a.x = G.e[li];
+      a.f = G.f[li];
+      a.y = G.t[li];
+      a.pro = PRO_NONE;
+      a.epi = EPI_RESID;
+      for (int rep = 0; rep < 4; ++rep) {  // one warm-up, three timed
+        if (rep == 1) cudaEventRecord(ev[0], s);
+        launch_fwd_strided<T>(a, L.fwd_blocks, L.smem_strided, s);
+        launch_inv_strided<T>(a, L.fwd_blocks, L.smem_strided, s);
+      }
+      cudaEventRecord(ev[1], s);
+      if (cudaEventSynchronize(ev[1]) != cudaSuccess || cudaGetLastError() != cudaSuccess ||
+          cudaEventElapsedTime(&t[c], ev[0], ev[1]) != cudaSuccess) {
+        rc = TPC_ECUDA;
+        break;
+      }
+      H->launches += 8;
+    }
+    // the fastest width, unless the rule's own width is within 3 % of it (timing noise)
+    int best = keep;
+    for (int c = 0; c < 5; ++c)
+      if (t[c] >= 0.0f && (t[best] < 0.0f || t[c] < t[best])) best = c;
+    if (t[keep] >= 0.0f && t[keep] <= 1.03f * t[best]) best = keep;
+    if (rc == TPC_OK) g_tuned_logC[key] = best;
+    L.logC = best;
+    L.fwd_blocks = 1 << (L.logL - best);
+    L.smem_strided =
+        sizeof(c2<T>) * (size_t)(tw_slots<T>() + padded_size(1 << (L.logR1 + L.logC)));
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (rc != TPC_OK) return cuda_fail(H, cudaGetLastError(), "autotune");
+  return TPC_OK;
+}
+
 int setup_device(tpc_handle* H) {
   const HostHierarchy& HH = H->host;
   const int nlev = (int)HH.lev.size();
@@ -600,6 +680,14 @@ int setup_device(tpc_handle* H) {
         H->launches += 1;
       }
       TPC_CUDA(H, cudaGetLastError());
+    }
+  }
+  if (H->prm.autotune) {
+    if (mixed) {
+      TPC_TRY(autotune_levels<float>(H, H->s, false));
+      TPC_TRY(autotune_levels<double>(H, H->d, true));
+    } else {
+      TPC_TRY(autotune_levels<double>(H, H->d, false));
     }
   }
   const long long nK = H->d.lev[0].n;

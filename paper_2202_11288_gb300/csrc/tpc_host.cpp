@@ -265,6 +265,10 @@ int build_host_hierarchy(const tpc_params& p, double delta, double h, int levels
     err = "damping weights must lie in (0, 2)";
     return TPC_EINVAL;
   }
+  if (p.autotune != 0 && p.autotune != 1) {
+    err = "autotune must be 0 or 1";
+    return TPC_EINVAL;
+  }
   if (!std::isfinite(p.shift)) {
     err = "shift must be finite";
     return TPC_EINVAL;
@@ -372,6 +376,7 @@ void tpc_default_params(tpc_params* p) {
   p->precision = TPC_FP64;
   p->max_iters = 100;
   p->inner_cycles = 6;
+  p->autotune = 1;
 }
 
 int tpc_host_hierarchy(const tpc_params* p, double delta, double h, int levels,
