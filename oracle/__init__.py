@@ -20,12 +20,16 @@ Contents
 ``timestep`` -- section 5: the time-dependent problem advanced by the BDF4 scheme of eq.
              (bdf4) with the shifted system (sigma I + A) U^k = ..., for the exact solution
              u = e^t (1 + x)^6 of Tables 2 and 3.
+``weakly``  -- section 2.1: the weakly singular nonlocal model of eq. (3system) (diagonal minus
+             the 2x2 Toeplitz block matrix), assembled from exact element integrals, and its
+             BDF4 time stepping for Table 1.
 ``large``  -- the same finest-level operator for sizes where a dense matrix does not fit:
              selected dense rows, and the product computed with numpy's FFT as the
              convolution step (section 3.2, eq. ccs3.4).
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py`` (printed
 coefficients vs quadrature, Example 3.1, Toeplitz closure, SPD and the two-grid bound of
-Theorem 4.1, LU agreement, order of accuracy, the sixteen BDF4 errors of Tables 2 and 3).
+Theorem 4.1, LU agreement, order of accuracy, the sixteen BDF4 errors of Tables 2 and 3, the
+printed coefficient formulas of section 2.1 and the twelve BDF4 errors of Table 1).
 No function is "parity unpinned".
 """
