@@ -49,13 +49,19 @@ enum {
   TPC_EDIVERGED = -6  /* the residual became non-finite */
 };
 
-enum { TPC_SPD = 0, TPC_NONSYM = 1 };          /* eq. (system1) / eq. (nonsym system) */
+/* eq. (system1) / eq. (nonsym system) of the peridynamic model (section 2.2), and the weakly
+ * singular nonlocal model of section 2.1, eq. (3system): A_h = diag(D_1, D_2) - [M Q; P N] for
+ * L u = int_0^1 (u(x) - u(y)) |x - y|^{-gamma} dy on (0, 1) with gamma = kernel_a in [0, 1) (no
+ * horizon: delta is ignored). Its entries are the exact element integrals of the quadratic
+ * basis (the printed p_0 and boundary weights eta_{i/2}, i >= 2, are read as garbled); the
+ * diagonal D is not Toeplitz and coarsens to a tridiagonal band, applied beside the FFT product. */
+enum { TPC_SPD = 0, TPC_NONSYM = 1, TPC_WEAKLY = 2 };
 enum { TPC_FP64 = 0, TPC_MIXED = 1 };          /* precision of the inner V-cycle */
 
 typedef struct tpc_params {
-  int variant;        /* TPC_SPD or TPC_NONSYM                                            */
+  int variant;        /* TPC_SPD, TPC_NONSYM or TPC_WEAKLY                                */
   int kernel;         /* 0 = constant kernel gamma_delta (section 2.2); others: ENOTSUP    */
-  double kernel_a;    /* reserved for fractional kernels (not implemented)                 */
+  double kernel_a;    /* TPC_WEAKLY: the exponent gamma in [0, 1) of |x - y|^{-gamma}      */
   double gamma0;      /* kernel constant; only scales the right-hand side, not the matrix  */
   double shift;       /* sigma added to the diagonal of the finest matrix (sigma I + A)    */
   int m1, m2;         /* pre / post smoothing sweeps of Algorithm 2 (default 1, 1)         */
@@ -163,13 +169,19 @@ int tpc_export_level(const tpc_handle* H, int level, double* host_buf, size_t ca
 int tpc_host_hierarchy(const tpc_params* p, double delta, double h, int levels,
                        double* host_buf, size_t cap, size_t* need);
 
+/* Dense matrix of one level of the host hierarchy (generator-plus-Cross form plus the band of
+ * TPC_WEAKLY), row major, n_level x n_level with n_level <= 8191: for tests against a dense
+ * reference. out == NULL: only *need is set. Host only. Returns TPC_OK or a negative code. */
+int tpc_host_dense_level(const tpc_params* p, double delta, double h, int levels, int level,
+                         double* out, size_t cap, size_t* need);
+
 /* ---------------------------------------------------------------------------------------
  * Time stepping (section 5): u_t = L_delta u + f on (0, 1), u = g on the interaction domain,
  * advanced by the BDF4 scheme of eq. (bdf4),
  *   (25/12 I - tau L_delta) U^k = 4 U^{k-1} - 3 U^{k-2} + 4/3 U^{k-3} - 1/4 U^{k-4} + tau F^k.
  * The collocation system is A U = eta_h (-L_delta u)(x_p) - (exterior couplings of g) with
  * eta_h = 6 / (gamma h) (gamma = gamma0, or the paper's 3 / delta^3 with delta = r h when
- * gamma0 = 0), so a step is the shifted solve
+ * gamma0 = 0; TPC_WEAKLY: eta_{h,gamma} of eq. (3system)), so a step is the shifted solve
  *   (sigma I + A) U^k = (eta_h / tau) (4 U^{k-1} - 3 U^{k-2} + 4/3 U^{k-3} - 1/4 U^{k-4}) + b^k,
  *   sigma = 25 eta_h / (12 tau),  b^k = eta_h F^k(x_p) - (exterior couplings of g^k).
  * --------------------------------------------------------------------------------------- */
@@ -186,7 +198,10 @@ int tpc_bdf4_coefficients(const tpc_params* p, double delta, double h, double ta
  * then midpoints h/2..1-h/2), or NULL for f = 0. g_left[j] = g(-j h/2), g_right[j] =
  * g(1 + j h/2) for j = 0..2r (r = floor(delta/h), at least 1), or NULL for zero exterior
  * values. rhs_out: n doubles. Host memory, host work O(n + r^2). Returns TPC_OK or TPC_EINVAL.
- * (SPD system: the midpoint rows use the integer-row stencil, as eq. (system1) does.) */
+ * (SPD system: the midpoint rows use the integer-row stencil, as eq. (system1) does.)
+ * TPC_WEAKLY (no interaction domain): rhs = eta_{h,gamma} f + K0 g_left[0] + KN g_right[0] with
+ * eta_{h,gamma} = (3-gamma)(2-gamma)(1-gamma)/h^{1-gamma} and K0, KN the couplings of the
+ * boundary basis functions (u(0) = g_left[0], u(1) = g_right[0]; other entries unused). */
 int tpc_collocation_rhs(const tpc_params* p, double delta, double h, const double* f_colloc,
                         const double* g_left, const double* g_right, double* rhs_out);
 

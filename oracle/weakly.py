@@ -38,41 +38,39 @@ def _antideriv(coeffs, gamma, s):
 _GL_X, _GL_W = np.polynomial.legendre.leggauss(20)
 
 
-def _int_poly_weight(c, lo, hi, gamma):
-    """int_lo^hi (c0 + c1 s + c2 s^2) |s|^{-gamma} ds for lo < hi (units of h).
+def _element_integral(a, y0, y1, gamma):
+    """int_{y0}^{y1} phi(y) |y|^{-gamma} dy for phi = a0 + a1 u + a2 u^2, u = y - y0.
 
-    Near the singularity (an end within 4 of s = 0) the closed-form antiderivatives are exact
-    and well conditioned; farther away they cancel (terms of size |s|^{3-gamma} against a result
-    of size |s|^{-gamma}), and the integrand is smooth on the element, so 20-point
-    Gauss-Legendre quadrature (exact to rounding for this smooth weight) is used instead."""
-    if lo >= 4.0 or hi <= -4.0:
-        ys = 0.5 * (hi - lo) * _GL_X + 0.5 * (hi + lo)
-        vals = (c[0] + c[1] * ys + c[2] * ys * ys) * np.abs(ys) ** (-gamma)
-        return float(0.5 * (hi - lo) * np.dot(_GL_W, vals))
+    Near the singularity (an end within 4 of y = 0) the closed-form antiderivatives of the
+    polynomial in y are exact and well conditioned; farther away they cancel (terms of size
+    |y|^{3-gamma} against a result of size |y|^{-gamma}), while the integrand is smooth on the
+    element, so 20-point Gauss-Legendre quadrature is used with phi evaluated in u."""
+    if y0 >= 4.0 or y1 <= -4.0:
+        u = 0.5 * (y1 - y0) * (_GL_X + 1.0)
+        vals = (a[0] + u * (a[1] + u * a[2])) * np.abs(y0 + u) ** (-gamma)
+        return float(0.5 * (y1 - y0) * np.dot(_GL_W, vals))
+    c = (a[0] - a[1] * y0 + a[2] * y0 * y0, a[1] - 2 * a[2] * y0, a[2])
     tot = 0.0
-    if hi > 0.0:
-        tot += _antideriv(c, gamma, hi) - _antideriv(c, gamma, max(lo, 0.0))
-    if lo < 0.0:  # s = -t
+    if y1 > 0.0:
+        tot += _antideriv(c, gamma, y1) - _antideriv(c, gamma, max(y0, 0.0))
+    if y0 < 0.0:  # y = -t
         cm = (c[0], -c[1], c[2])
-        tot += _antideriv(cm, gamma, -lo) - _antideriv(cm, gamma, -min(hi, 0.0))
+        tot += _antideriv(cm, gamma, -y0) - _antideriv(cm, gamma, -min(y1, 0.0))
     return tot
 
 
 def _basis_pieces(q2: int, N: int):
     """Pieces of the basis function at twice-coordinate q2 (units of h/2) on [0, N]:
-    (y0, y1, A, B, C) with phi(y) = A + B y + C y^2 on [y0, y1] (y in units of h)."""
+    (y0, y1, (a0, a1, a2)) with phi = a0 + a1 u + a2 u^2, u = y - y0 (y in units of h)."""
     c = q2 / 2.0
-    if q2 % 2 == 0:  # node: t(2t - 1) with t = y - (c - 1) on the left, t = (c + 1) - y right
+    if q2 % 2 == 0:  # node: t (2t - 1), t = distance to the far end of each element
         out = []
         if c - 1 >= 0:
-            a = -(c - 1)
-            out.append((c - 1, c, 2 * a * a - a, 4 * a - 1, 2.0))
+            out.append((c - 1, c, (0.0, -1.0, 2.0)))      # 2u^2 - u
         if c + 1 <= N:
-            a = c + 1
-            out.append((c, c + 1, 2 * a * a - a, -4 * a + 1, 2.0))
+            out.append((c, c + 1, (1.0, -3.0, 2.0)))      # (1 - u)(1 - 2u)
         return out
-    # midpoint: 4 (y - (c - 1/2)) ((c + 1/2) - y)
-    return [(c - 0.5, c + 0.5, -4.0 * (c * c - 0.25), 8.0 * c, -4.0)]
+    return [(c - 0.5, c + 0.5, (0.0, 4.0, -4.0))]         # midpoint: 4 u (1 - u)
 
 
 def coupling(p2: int, q2: int, N: int, gamma: float) -> float:
@@ -80,15 +78,8 @@ def coupling(p2: int, q2: int, N: int, gamma: float) -> float:
     eta_{h,gamma} times the integral, at twice-coordinates p2 (collocation point) and q2."""
     xp = p2 / 2.0
     tot = 0.0
-    for y0, y1, A, B, C in _basis_pieces(q2, N):
-        # the piece as a polynomial in s = y - xp, built around the element's own left end
-        # (local coordinate u = y - y0 keeps the coefficients small): phi = a0 + a1 u + a2 u^2
-        a0 = A + B * y0 + C * y0 * y0
-        a1 = B + 2 * C * y0
-        a2 = C
-        d = xp - y0  # y - y0 = s + d
-        c = (a0 + a1 * d + a2 * d * d, a1 + 2 * a2 * d, a2)
-        tot += _int_poly_weight(c, y0 - xp, y1 - xp, gamma)
+    for y0, y1, a in _basis_pieces(q2, N):
+        tot += _element_integral(a, y0 - xp, y1 - xp, gamma)
     return (3 - gamma) * (2 - gamma) * (1 - gamma) * tot
 
 

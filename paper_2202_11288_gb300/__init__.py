@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libtpcamg.so")
 
 TPC_OK, TPC_ENOTCONV = 0, 1
 TPC_EINVAL, TPC_ENOMEM, TPC_ECUDA, TPC_ESINGULAR, TPC_ENOTSUP, TPC_EDIVERGED = -1, -2, -3, -4, -5, -6
-TPC_SPD, TPC_NONSYM = 0, 1
+TPC_SPD, TPC_NONSYM, TPC_WEAKLY = 0, 1, 2
 TPC_FP64, TPC_MIXED = 0, 1
 
 EXPORTED = ["tpc_default_params", "tpc_setup", "tpc_solve", "tpc_solve_batch", "tpc_solve_host",
@@ -30,6 +30,7 @@ EXPORTED = ["tpc_default_params", "tpc_setup", "tpc_solve", "tpc_solve_batch", "
             "tpc_export_level", "tpc_host_hierarchy", "tpc_time_level_kernels",
             "tpc_time_level_kernels_f32", "tpc_kernel_launches", "tpc_apply_noalloc",
             "tpc_bdf4_coefficients", "tpc_collocation_rhs", "tpc_bdf4_step",
+            "tpc_host_dense_level",
             "tpc_destroy", "tpc_last_error",
             "tpc_server_default_config", "tpc_server_create", "tpc_server_submit",
             "tpc_server_poll", "tpc_server_outstanding", "tpc_server_destroy"]
@@ -107,6 +108,8 @@ def lib() -> ctypes.CDLL:
     L.tpc_export_level.restype = I
     L.tpc_host_hierarchy.argtypes = [pp, D, D, I, P, SZ, ctypes.POINTER(SZ)]
     L.tpc_host_hierarchy.restype = I
+    L.tpc_host_dense_level.argtypes = [pp, D, D, I, I, P, SZ, ctypes.POINTER(SZ)]
+    L.tpc_host_dense_level.restype = I
     L.tpc_bdf4_coefficients.argtypes = [pp, D, D, D, ctypes.POINTER(D), ctypes.POINTER(D)]
     L.tpc_bdf4_coefficients.restype = I
     L.tpc_collocation_rhs.argtypes = [pp, D, D, P, P, P, P]
@@ -218,6 +221,21 @@ def tpc_solve(H, b, x, tol: float = 1e-10, use_x0: bool = False):
     rc = _check(lib().tpc_solve(H, _ptr(b), _ptr(x), tol, int(use_x0), ctypes.byref(it),
                                 ctypes.byref(rel)), H, allow=(TPC_OK, TPC_ENOTCONV))
     return rc, it.value, rel.value
+
+
+def tpc_host_dense_level(delta: float, h: float, level: int, levels: int = 0,
+                         params: TpcParams | None = None) -> np.ndarray:
+    """Dense matrix of one level of the host hierarchy (small levels only; no GPU)."""
+    p = params if params is not None else tpc_default_params()
+    need = ctypes.c_size_t(0)
+    _check(lib().tpc_host_dense_level(ctypes.byref(p), delta, h, levels, level, None, 0,
+                                      ctypes.byref(need)))
+    out = np.empty(need.value, dtype=np.float64)
+    _check(lib().tpc_host_dense_level(ctypes.byref(p), delta, h, levels, level,
+                                      out.ctypes.data_as(ctypes.c_void_p), need.value,
+                                      ctypes.byref(need)))
+    n = int(round(need.value ** 0.5))
+    return out.reshape(n, n)
 
 
 def tpc_bdf4_coefficients(delta: float, h: float, tau: float, params: TpcParams | None = None):

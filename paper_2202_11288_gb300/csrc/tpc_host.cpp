@@ -84,6 +84,10 @@ int grid_and_horizon(double delta, double h, int& K, int& r, std::string& err) {
 
 // eta_h = 6 / (gamma h), gamma = gamma0, or 3 / delta^3 with delta = r h when gamma0 = 0.
 double eta_of(const tpc_params& p, int r, double h) {
+  if (p.variant == TPC_WEAKLY) {  // eta_{h,gamma} = (3-g)(2-g)(1-g) / h^{1-g} (eq. (3system))
+    const double g = p.kernel_a;
+    return (3.0 - g) * (2.0 - g) * (1.0 - g) / std::pow(h, 1.0 - g);
+  }
   const double d = r * h;
   const double gamma = (p.gamma0 > 0.0) ? p.gamma0 : 3.0 / (d * d * d);
   return 6.0 / (gamma * h);
@@ -133,6 +137,142 @@ LevelForm finest_form(int variant, int K, int r, double shift) {
   L.tA[N - 1] += shift;
   L.tD[N - 1] += shift;
   L.o += shift;
+  return L;
+}
+
+// ---------------------------------------------------------------------------------------
+// Weakly singular model (section 2.1, eq. (3system)). Entries are (3-g)(2-g)(1-g) / h^{1-g}
+// times int phi_q(y) |x_p - y|^{-g} dy; in units of h the factor h^{1-g} cancels, leaving
+// (3-g)(2-g)(1-g) times the integral of the unit-spaced basis against |s|^{-g}.
+// ---------------------------------------------------------------------------------------
+
+// 20-point Gauss-Legendre nodes and weights on [-1, 1], by Newton's method on P_20.
+struct GaussLegendre20 {
+  double x[20], w[20];
+  GaussLegendre20() {
+    const int n = 20;
+    for (int i = 0; i < n; ++i) {
+      double z = std::cos(3.14159265358979323846 * (i + 0.75) / (n + 0.5)), dp = 1.0;
+      for (int it = 0; it < 100; ++it) {
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+          const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+          p0 = p1;
+          p1 = p2;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        const double dz = p1 / dp;
+        z -= dz;
+        if (std::fabs(dz) < 1e-16) break;
+      }
+      x[i] = z;
+      w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+  }
+};
+
+// int over [y0, y1] of phi(y) |y|^{-g} dy with phi = a0 + a1 u + a2 u^2, u = y - y0 (the
+// element's own coordinate, u in [0, y1 - y0]). Within 4 of the singularity y = 0: exact
+// antiderivatives of the polynomial in y times |y|^{-g} (small arguments, well conditioned).
+// Farther: the integrand is smooth; Gauss-Legendre with phi evaluated in u (no cancellation).
+double element_integral(double a0, double a1, double a2, double y0, double y1, double g) {
+  static const GaussLegendre20 gl;
+  if (y0 >= 4.0 || y1 <= -4.0) {
+    const double h2 = 0.5 * (y1 - y0);
+    double acc = 0.0;
+    for (int i = 0; i < 20; ++i) {
+      const double u = h2 * (gl.x[i] + 1.0), y = y0 + u;
+      acc += gl.w[i] * (a0 + u * (a1 + u * a2)) * std::pow(std::fabs(y), -g);
+    }
+    return h2 * acc;
+  }
+  const double c[3] = {a0 - a1 * y0 + a2 * y0 * y0, a1 - 2.0 * a2 * y0, a2};  // in powers of y
+  auto F = [&](const double* cc, double t) {
+    double v = 0.0;
+    for (int k = 0; k < 3; ++k) v += cc[k] * std::pow(t, k + 1 - g) / (k + 1 - g);
+    return v;
+  };
+  double tot = 0.0;
+  if (y1 > 0.0) tot += F(c, y1) - F(c, std::fmax(y0, 0.0));
+  if (y0 < 0.0) {
+    const double cm[3] = {c[0], -c[1], c[2]};  // y = -t
+    tot += F(cm, -y0) - F(cm, -std::fmin(y1, 0.0));
+  }
+  return tot;
+}
+
+// (3-g)(2-g)(1-g) int phi(y) |y|^{-g} dy for the basis function of the given type centred at
+// y = -dist2 / 2 (units of h): the coupling of a collocation point to a basis function at
+// distance dist2 / 2 on the left (dist2 = twice (x_p - x_q)). Node basis: t (2t - 1) on each of
+// its two elements (t = distance to the far end of the element); midpoint basis: 4 t (1 - t).
+double ws_coupling(bool q_node, long long dist2, double g) {
+  const double c = -0.5 * (double)dist2;  // centre of the basis function relative to x_p
+  double tot;
+  if (q_node)
+    tot = element_integral(0.0, -1.0, 2.0, c - 1.0, c, g)     // 2 u^2 - u
+          + element_integral(1.0, -3.0, 2.0, c, c + 1.0, g);  // (1 - u)(1 - 2u)
+  else
+    tot = element_integral(0.0, 4.0, -4.0, c - 0.5, c + 0.5, g);  // 4 u (1 - u)
+  return (3.0 - g) * (2.0 - g) * (1.0 - g) * tot;
+}
+
+// Couplings of the two boundary basis functions (nodes x = 0 and x = 1, one element each) to
+// the collocation point at twice-coordinate xp2: the columns K0, KN of the right-hand side.
+double ws_boundary(bool left, long long xp2, long long Nint, double g) {
+  const double xp = 0.5 * (double)xp2;
+  const double v = left ? element_integral(1.0, -3.0, 2.0, -xp, 1.0 - xp, g)
+                        : element_integral(0.0, -1.0, 2.0, (double)(Nint - 1) - xp,
+                                           (double)Nint - xp, g);
+  return (3.0 - g) * (2.0 - g) * (1.0 - g) * v;
+}
+
+// Finest level of eq. (3system): Toeplitz part -[M Q; P N] in the generator + Cross form of
+// finest_form (same block layout: nodes are the first segment, midpoints the second), and the
+// diagonal diag(D_1, D_2), d(x) = (3-g)(2-g)((x/h)^{1-g} + (1 - x)/h)^{1-g}), as the band.
+LevelForm finest_form_weakly(int K, double g, double shift) {
+  const long long Nint = 1LL << K;
+  LevelForm L;
+  L.k = K;
+  L.N = Nint - 1;
+  const long long N = L.N;
+  auto fA = [&](long long d) { return -ws_coupling(true, 2 * d, g); };       // node, node
+  auto fB = [&](long long d) { return -ws_coupling(false, 2 * d + 1, g); };  // node, mid
+  auto fC = [&](long long d) { return -ws_coupling(true, 2 * d - 1, g); };   // mid, node
+  auto fD = [&](long long d) { return -ws_coupling(false, 2 * d, g); };      // mid, mid
+  const size_t G = (size_t)(2 * N - 1);
+  L.tA.assign(G, 0.0);
+  L.tB.assign(G, 0.0);
+  L.tC.assign(G, 0.0);
+  L.tD.assign(G, 0.0);
+  for (long long d = -(N - 1); d <= N - 1; ++d) {
+    L.tA[d + N - 1] = fA(d);
+    L.tB[d + N - 1] = fB(d - 1);
+    L.tC[d + N - 1] = fC(d + 1);
+    L.tD[d + N - 1] = fD(d);
+  }
+  L.p.assign(N, 0.0);
+  L.q.assign(N, 0.0);
+  L.xi.assign(N, 0.0);
+  L.zeta.assign(N, 0.0);
+  for (long long i = 1; i <= N; ++i) {
+    L.p[i - 1] = fB(i - 1);
+    L.q[i - 1] = fC(1 - i);
+    L.zeta[i - 1] = fD(-i);
+    L.xi[i - 1] = fD(i);
+  }
+  L.o = fD(0);
+  L.tA[N - 1] += shift;
+  L.tD[N - 1] += shift;
+  L.o += shift;
+  const long long n = 2 * N + 1;
+  L.bl.assign(n, 0.0);
+  L.bu.assign(n, 0.0);
+  L.bd.assign(n, 0.0);
+  const double cdg = (3.0 - g) * (2.0 - g), e = 1.0 - g, X = (double)Nint;
+  for (long long i = 0; i < n; ++i) {
+    const double x = (i < N) ? (double)(i + 1) : (double)(i - N) + 0.5;  // units of h
+    L.bd[i] = cdg * (std::pow(x, e) + std::pow(X - x, e));
+  }
   return L;
 }
 
@@ -194,19 +334,50 @@ LevelForm coarsen(const LevelForm& F) {
   Cc.o = (tA(0) + 2.0 * p(N) + tB(N - 1) + 2.0 * q(N) + 4.0 * F.o + 2.0 * zeta(1) +
           tC(1 - N) + 2.0 * xi(1) + tD(0)) /
          8.0;
+  if (F.has_band()) {
+    // R B P of the tridiagonal part, R = 1/4 [1 2 1] on the concatenated vector (0-based fine
+    // indices 2I, 2I+1, 2I+2 for coarse I), P = 2 R^T: (1/8) sum w_a w_b B(2I+a, 2J+b), again
+    // tridiagonal.
+    const long long nf = 2 * N + 1, nc = 2 * Nc + 1;
+    auto band = [&](long long k, long long l) {
+      if (k < 0 || l < 0 || k >= nf || l >= nf) return 0.0;
+      if (l == k - 1) return F.bl[k];
+      if (l == k) return F.bd[k];
+      if (l == k + 1) return F.bu[k];
+      return 0.0;
+    };
+    Cc.bl.assign(nc, 0.0);
+    Cc.bd.assign(nc, 0.0);
+    Cc.bu.assign(nc, 0.0);
+    for (long long I = 0; I < nc; ++I) {
+      for (long long J = I - 1; J <= I + 1; ++J) {
+        if (J < 0 || J >= nc) continue;
+        double acc = 0.0;
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) acc += w[a] * w[b] * band(2 * I + a, 2 * J + b);
+        (J == I - 1 ? Cc.bl : J == I ? Cc.bd : Cc.bu)[I] = acc / 8.0;
+      }
+    }
+  }
   return Cc;
 }
 
 // Dense entry (i, j), 1-based, of a level in generator-plus-Cross form.
 double dense_entry(const LevelForm& L, long long i, long long j) {
+  double band = 0.0;
+  if (L.has_band()) {
+    if (j == i - 1) band = L.bl[i - 1];
+    if (j == i) band = L.bd[i - 1];
+    if (j == i + 1) band = L.bu[i - 1];
+  }
   const long long N = L.N;
   const bool iv = i <= N, im = i == N + 1, jv = j <= N, jm = j == N + 1;
-  if (im && jm) return L.o;
-  if (im) return jv ? L.q[j - 1] : L.zeta[j - N - 2];
-  if (jm) return iv ? L.p[i - 1] : L.xi[i - N - 2];
+  if (im && jm) return L.o + band;
+  if (im) return (jv ? L.q[j - 1] : L.zeta[j - N - 2]) + band;
+  if (jm) return (iv ? L.p[i - 1] : L.xi[i - N - 2]) + band;
   const long long ii = iv ? i : i - N - 1, jj = jv ? j : j - N - 1;
   const std::vector<double>& t = iv ? (jv ? L.tA : L.tB) : (jv ? L.tC : L.tD);
-  return t[ii - jj + N - 1];
+  return t[ii - jj + N - 1] + band;
 }
 
 int invert_dense(std::vector<double>& A, long long n, std::vector<double>& inv) {
@@ -249,8 +420,12 @@ int build_host_hierarchy(const tpc_params& p, double delta, double h, int levels
                          HostHierarchy& out, std::string& err) {
   int K = 0, r = 1;
   if (const int rc = grid_and_horizon(delta, h, K, r, err)) return rc;
-  if (p.variant != TPC_SPD && p.variant != TPC_NONSYM) {
-    err = "variant must be TPC_SPD or TPC_NONSYM";
+  if (p.variant != TPC_SPD && p.variant != TPC_NONSYM && p.variant != TPC_WEAKLY) {
+    err = "variant must be TPC_SPD, TPC_NONSYM or TPC_WEAKLY";
+    return TPC_EINVAL;
+  }
+  if (p.variant == TPC_WEAKLY && !(p.kernel_a >= 0.0 && p.kernel_a < 1.0)) {
+    err = "TPC_WEAKLY needs the exponent kernel_a in [0, 1)";
     return TPC_EINVAL;
   }
   if (p.kernel != 0) {
@@ -292,7 +467,8 @@ int build_host_hierarchy(const tpc_params& p, double delta, double h, int levels
   out.r = r;
   out.lev.clear();
   out.lev.reserve(K - kc + 1);
-  out.lev.push_back(finest_form(p.variant, K, r, p.shift));
+  out.lev.push_back(p.variant == TPC_WEAKLY ? finest_form_weakly(K, p.kernel_a, p.shift)
+                                             : finest_form(p.variant, K, r, p.shift));
   for (int k = K; k > kc; --k) out.lev.push_back(coarsen(out.lev.back()));
   const LevelForm& Lc = out.lev.back();
   const long long n = 2 * Lc.N + 1;
@@ -407,6 +583,38 @@ int tpc_host_hierarchy(const tpc_params* p, double delta, double h, int levels,
   return TPC_OK;
 }
 
+int tpc_host_dense_level(const tpc_params* p, double delta, double h, int levels, int level,
+                         double* out, size_t cap, size_t* need) {
+  if (!p || !need) {
+    tpc::g_host_err = "NULL argument";
+    return TPC_EINVAL;
+  }
+  tpc::HostHierarchy H;
+  std::string err;
+  const int rc = tpc::build_host_hierarchy(*p, delta, h, levels, H, err);
+  if (rc != TPC_OK) {
+    tpc::g_host_err = err;
+    return rc;
+  }
+  const int li = H.K - level;
+  if (li < 0 || li >= (int)H.lev.size()) {
+    tpc::g_host_err = "level outside the hierarchy";
+    return TPC_EINVAL;
+  }
+  const tpc::LevelForm& L = H.lev[li];
+  const long long n = 2 * L.N + 1;
+  if (n > 8191) {
+    tpc::g_host_err = "tpc_host_dense_level: level too large for a dense matrix (n > 8191)";
+    return TPC_EINVAL;
+  }
+  *need = (size_t)(n * n);
+  if (!out) return TPC_OK;
+  if (cap < *need) return TPC_EINVAL;
+  for (long long i = 1; i <= n; ++i)
+    for (long long j = 1; j <= n; ++j) out[(i - 1) * n + (j - 1)] = tpc::dense_entry(L, i, j);
+  return TPC_OK;
+}
+
 int tpc_bdf4_coefficients(const tpc_params* p, double delta, double h, double tau,
                           double* shift_out, double* hist_scale_out) {
   if (!p || !shift_out || !hist_scale_out || !(tau > 0.0) || !std::isfinite(tau) ||
@@ -424,8 +632,10 @@ int tpc_bdf4_coefficients(const tpc_params* p, double delta, double h, double ta
 
 int tpc_collocation_rhs(const tpc_params* p, double delta, double h, const double* f_colloc,
                         const double* g_left, const double* g_right, double* rhs_out) {
-  if (!p || !rhs_out || (p->variant != TPC_SPD && p->variant != TPC_NONSYM) ||
-      !(p->gamma0 >= 0.0) || !std::isfinite(p->gamma0)) {
+  if (!p || !rhs_out ||
+      (p->variant != TPC_SPD && p->variant != TPC_NONSYM && p->variant != TPC_WEAKLY) ||
+      !(p->gamma0 >= 0.0) || !std::isfinite(p->gamma0) ||
+      (p->variant == TPC_WEAKLY && !(p->kernel_a >= 0.0 && p->kernel_a < 1.0))) {
     tpc::g_host_err = "bad argument to tpc_collocation_rhs";
     return TPC_EINVAL;
   }
@@ -434,6 +644,16 @@ int tpc_collocation_rhs(const tpc_params* p, double delta, double h, const doubl
   const long long Nint = 1LL << K, nn = Nint - 1, n = 2 * Nint - 1;
   const double eta = tpc::eta_of(*p, r, h);
   for (long long q = 0; q < n; ++q) rhs_out[q] = f_colloc ? eta * f_colloc[q] : 0.0;
+  if (p->variant == TPC_WEAKLY) {
+    // A_h U = eta F + K (eq. (3system)): the boundary columns times u(0) = g_left[0] and
+    // u(1) = g_right[0], added (A_h = D - T, and the boundary part of T moves to the right)
+    for (long long q = 0; q < n; ++q) {
+      const long long xp2 = (q < nn) ? 2 * (q + 1) : 2 * (q - nn + 1) - 1;
+      if (g_left) rhs_out[q] += tpc::ws_boundary(true, xp2, Nint, p->kernel_a) * g_left[0];
+      if (g_right) rhs_out[q] += tpc::ws_boundary(false, xp2, Nint, p->kernel_a) * g_right[0];
+    }
+    return TPC_OK;
+  }
   const long long reach = 2LL * r + 1;  // largest twice-distance with a nonzero entry
   // row p: twice-coordinate xp2 (nodes 2i, i = 1..Nint-1; midpoints 2i - 1, i = 1..Nint)
   for (long long q = 0; q < n; ++q) {

@@ -18,6 +18,10 @@ struct LevelForm {
   std::vector<double> tA, tB, tC, tD;
   std::vector<double> p, q, xi, zeta;
   double o = 0.0;
+  // Non-Toeplitz tridiagonal part (weakly singular model of section 2.1 only, else empty):
+  // entries (i, i-1), (i, i), (i, i+1) of the concatenated 0-based index i < 2N + 1.
+  std::vector<double> bl, bd, bu;
+  bool has_band() const { return !bd.empty(); }
   double gen(const std::vector<double>& t, long long d) const { return t[d + N - 1]; }
 };
 
