@@ -46,6 +46,13 @@ template <typename T> struct DevLevel {
   // support of the Cross vectors: q, zeta vanish from index nq on, p, xi from np on (the
   // couplings to the middle unknown reach only about r points, scaled per level)
   long long nq = 0, np = 0;
+  // weakly singular model only: tridiagonal band (entries (i, i-1), (i, i), (i, i+1)) and the
+  // per-entry damped Jacobi weights omega / a_ii (the diagonal is not constant per segment)
+  T* bl = nullptr;
+  T* bd = nullptr;
+  T* bu = nullptr;
+  T* wpre = nullptr;
+  T* wpost = nullptr;
   c2<T>* twm = nullptr;
 };
 
@@ -209,6 +216,11 @@ LevelArgs<T> level_args(const Hier<T>& G, const DevLevel<T>& L) {
   a.zeta = L.zeta;
   a.nq = L.nq;
   a.np = L.np;
+  a.bl = L.bl;
+  a.bd = L.bd;
+  a.bu = L.bu;
+  a.pvec = L.wpre;
+  a.wvec = L.wpre;
   a.o = L.o;
   a.twm = L.twm;
   a.twL = G.twL;
@@ -239,6 +251,7 @@ void launch_matvec(tpc_handle* H, const Hier<T>& G, const DevLevel<T>& L, const 
   a.wA = post ? L.wA_post : L.wA_pre;
   a.wO = post ? L.wO_post : L.wO_pre;
   a.wD = post ? L.wD_post : L.wD_pre;
+  a.wvec = post ? L.wpost : L.wpre;
   a.pro = pro.mode;
   a.pA = L.wA_pre;
   a.pO = L.wO_pre;
@@ -262,7 +275,7 @@ void launch_matvec(tpc_handle* H, const Hier<T>& G, const DevLevel<T>& L, const 
 template <typename T>
 void matvec(tpc_handle* H, const Hier<T>& G, int li, const T* x, const T* f, T* y, int epi,
             bool post, const Prologue<T>& pro = Prologue<T>()) {
-  if (H->prm.variant == TPC_NONSYM)
+  if (H->prm.variant != TPC_SPD)
     launch_matvec<T, true>(H, G, G.lev[li], x, f, y, epi, post, pro);
   else
     launch_matvec<T, false>(H, G, G.lev[li], x, f, y, epi, post, pro);
@@ -284,7 +297,7 @@ T* enqueue_vcycle(tpc_handle* H, Hier<T>& G, int li, const T* f_top, const T* rf
   T* t = G.t[li];
   const T* f = rfine ? G.f[li] : f_top;
   if (G.bottom && li == G.bottom_li && rfine) {
-    if (H->prm.variant == TPC_NONSYM)
+    if (H->prm.variant != TPC_SPD)
       k_vcycle_bottom<T, true><<<1, fft_threads<T>(), G.bottom_smem, s>>>(G.bottom);
     else
       k_vcycle_bottom<T, false><<<1, fft_threads<T>(), G.bottom_smem, s>>>(G.bottom);
@@ -463,6 +476,26 @@ int alloc_levels(tpc_handle* H, Hier<T>& G) {
     TPC_TRY(upload<T>(H, L.zeta, F.zeta));
     L.nq = support2(F.q, F.zeta);
     L.np = support2(F.p, F.xi);
+    if (F.has_band()) {
+      const long long n = L.n;
+      TPC_TRY(dalloc(H, &L.bl, n));
+      TPC_TRY(dalloc(H, &L.bd, n));
+      TPC_TRY(dalloc(H, &L.bu, n));
+      TPC_TRY(upload<T>(H, L.bl, F.bl));
+      TPC_TRY(upload<T>(H, L.bd, F.bd));
+      TPC_TRY(upload<T>(H, L.bu, F.bu));
+      std::vector<double> wp((size_t)n), wq((size_t)n);
+      for (long long i = 0; i < n; ++i) {
+        const double t = (i < F.N) ? F.tA[F.N - 1] : (i == F.N ? F.o : F.tD[F.N - 1]);
+        const double aii = t + F.bd[i];
+        wp[i] = H->prm.omega_pre / aii;
+        wq[i] = H->prm.omega_post / aii;
+      }
+      TPC_TRY(dalloc(H, &L.wpre, n));
+      TPC_TRY(dalloc(H, &L.wpost, n));
+      TPC_TRY(upload<T>(H, L.wpre, wp));
+      TPC_TRY(upload<T>(H, L.wpost, wq));
+    }
     if (L.logR1 && sizeof(T) == sizeof(double)) {  // FP32 computes these (inter_tw)
       std::vector<double> twm;
       twiddles(L.m, L.m, twm);  // W_m^j, j < m
@@ -472,7 +505,7 @@ int alloc_levels(tpc_handle* H, Hier<T>& G) {
     TPC_TRY(dalloc(H, &L.sA, L.m));
     TPC_TRY(dalloc(H, &L.sD, L.m));
     TPC_TRY(dalloc(H, &L.sB, L.m));
-    if (H->prm.variant == TPC_NONSYM) TPC_TRY(dalloc(H, &L.sC, L.m));
+    if (H->prm.variant != TPC_SPD) TPC_TRY(dalloc(H, &L.sC, L.m));
   }
   TPC_TRY(dalloc(H, &G.z, max_m));
   (void)max_parts;  // the autotuner may choose down to one column per block
@@ -534,6 +567,7 @@ int build_bottom(tpc_handle* H, Hier<T>& G) {
     a.wA = L.wA_post;
     a.wO = L.wO_post;
     a.wD = L.wD_post;
+    a.wvec = L.wpost;
     bp.post[j] = a;
   }
   bp.cinv = G.coarse_inv;
@@ -950,7 +984,7 @@ int time_level(tpc_handle* H, const Hier<T>& G, int level, int reps, const T* x_
     return TPC_EINVAL;
   }
   const DevLevel<T>& L = G.lev[li];
-  const bool ns = H->prm.variant == TPC_NONSYM;
+  const bool ns = H->prm.variant != TPC_SPD;
   LevelArgs<T> a = level_args<T>(G, L);
   a.x = x_dev;
   a.f = f_dev;

@@ -77,6 +77,13 @@ template <typename T> struct LevelArgs {
   const T* zeta;
   T o;
   long long nq, np;      // q, zeta are zero from index nq on; p, xi from index np on
+  // weakly singular model (else null): tridiagonal band of the concatenated index and the
+  // per-entry Jacobi weights (pvec: pre-smoothing, for the prologue; wvec: this product's)
+  const T* bl;
+  const T* bd;
+  const T* bu;
+  const T* pvec;
+  const T* wvec;
   T wA, wO, wD;          // omega / diagonal, per segment (damped Jacobi, eq. 7)
   const c2<T>* twm;      // strided pipelines only: W_m^j, j < m (FP64); two-level (FP32)
   const c2<T>* twL;      // W_{4096}^j, j < 4096 (FP32 copies the octant j <= 512 to shared)
@@ -215,6 +222,7 @@ template <typename T>
 __device__ __forceinline__ T operand_finish(const LevelArgs<T>& a, long long j, const Raw<T>& r,
                                             T w, int pro) {
   if (pro == PRO_NONE) return r.a0;
+  if ((pro == PRO_SMOOTH || pro == PRO_RESTRICT) && a.pvec) w = a.pvec[j];
   if (pro == PRO_SMOOTH) {
     const T v = w * r.a0;
     a.xout[j] = v;
@@ -278,11 +286,30 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
 // the callers), then arithmetic and stores.
 template <typename T> struct EpiRaw {
   T p, xi, fv, fw, xv, xw;
+  T bv, bw;  // band products (B x)_i, (B x)_{iw} (weakly singular model, else 0)
+  T wv, ww;  // per-entry Jacobi weights (weakly singular model)
 };
+// (B x)_j of the tridiagonal band at concatenated index j (0 <= j < n).
+template <typename T>
+__device__ __forceinline__ T band_at(const LevelArgs<T>& a, long long j) {
+  const long long n = 2 * a.N + 1;
+  T s = a.bd[j] * a.x[j];
+  if (j > 0) s = fma(a.bl[j], a.x[j - 1], s);
+  if (j + 1 < n) s = fma(a.bu[j], a.x[j + 1], s);
+  return s;
+}
 template <typename T>
 __device__ __forceinline__ EpiRaw<T> epi_load(const LevelArgs<T>& a, long long i, int epi) {
-  EpiRaw<T> r{0, 0, 0, 0, 0, 0};
+  EpiRaw<T> r{0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   const long long iw = a.N + 1 + i;
+  if (a.bd) {
+    r.bv = band_at<T>(a, i);
+    r.bw = band_at<T>(a, iw);
+    if (epi == EPI_JACOBI) {
+      r.wv = a.wvec[i];
+      r.ww = a.wvec[iw];
+    }
+  }
   if (i < a.np) {
     r.p = a.p[i];
     r.xi = a.xi[i];
@@ -300,8 +327,8 @@ __device__ __forceinline__ EpiRaw<T> epi_load(const LevelArgs<T>& a, long long i
 template <typename T>
 __device__ __forceinline__ void epi_store(const LevelArgs<T>& a, long long i, const EpiRaw<T>& r,
                                           T ax_v, T ax_w, T w_o, int epi) {
-  const T yv = fma(r.p, w_o, ax_v);
-  const T yw = fma(r.xi, w_o, ax_w);
+  const T yv = fma(r.p, w_o, ax_v) + r.bv;
+  const T yw = fma(r.xi, w_o, ax_w) + r.bw;
   const long long iw = a.N + 1 + i;
   if (epi == EPI_APPLY) {
     a.y[i] = yv;
@@ -310,21 +337,21 @@ __device__ __forceinline__ void epi_store(const LevelArgs<T>& a, long long i, co
     a.y[i] = r.fv - yv;
     a.y[iw] = r.fw - yw;
   } else {
-    a.y[i] = fma(a.wA, r.fv - yv, r.xv);
-    a.y[iw] = fma(a.wD, r.fw - yw, r.xw);
+    a.y[i] = fma(a.bd ? r.wv : a.wA, r.fv - yv, r.xv);
+    a.y[iw] = fma(a.bd ? r.ww : a.wD, r.fw - yw, r.xw);
   }
 }
 
 template <typename T>
 __device__ __forceinline__ void epi_middle(const LevelArgs<T>& a, T dot, T w_o, int epi) {
-  const T ym = fma(a.o, w_o, dot);
   const long long im = a.N;
+  const T ym = fma(a.o, w_o, dot) + (a.bd ? band_at<T>(a, im) : (T)0);
   if (epi == EPI_APPLY)
     a.y[im] = ym;
   else if (epi == EPI_RESID)
     a.y[im] = a.f[im] - ym;
   else
-    a.y[im] = fma(a.wO, a.f[im] - ym, a.x[im]);
+    a.y[im] = fma(a.bd ? a.wvec[im] : a.wO, a.f[im] - ym, a.x[im]);
 }
 
 // Spectral 2x2 block product for the frequency pair held at positions (lower, upper).
@@ -822,6 +849,10 @@ __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_inv_s
           if (EPI == EPI_JACOBI) {
             er[u].xv = a.x[P];
             er[u].xw = a.x[a.N + 1 + P];
+            if (a.bd) {
+              er[u].wv = a.wvec[P];
+              er[u].ww = a.wvec[a.N + 1 + P];
+            }
           }
         } else {
           er[u] = epi_load<T>(a, P, epi);
