@@ -39,7 +39,7 @@ FP64_FLOP_PER_CLK_PER_SM = 4      # 2 DFMA per clock per SM (FMA-loop probe: 1.1
 N_SMS = 152
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_mid_pair<double> launch at the finest
 # level, from ncu (profiles/k_mid_pair_fp64_N2e22.md); unknown for other sizes
-MID_TRAFFIC = {}
+MID_TRAFFIC = {22: 357.7e6}
 # Algorithmic bytes of the FP32 finest-level kernels per point of the FFT length m = 2N + 2
 # (residual epilogue, no prologue; x, f, y hold about m floats; the Cross vectors q, zeta and
 # p, xi hold m/2 entries each of which only the first r are nonzero and read, a fraction r/N):
@@ -49,9 +49,9 @@ MID_TRAFFIC = {}
 def f32_bytes_per_point(r, N):
     frac = min(1.0, r / N)
     return (12.0 + 4.0 * frac, 24.0, 16.0 + 4.0 * frac)
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP32 finest kernels, from ncu,
-# keyed by (K, kernel index); unknown for other sizes
-F32_TRAFFIC = {}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP32 finest kernels, from ncu
+# (profiles/fp32_transform_kernels_N2e22.md), keyed by (K, kernel index); unknown for other sizes
+F32_TRAFFIC = {(22, 0): 53.9e6, (22, 1): 153.9e6, (22, 2): 115.7e6}
 
 
 def measured_hbm_gbs():
@@ -514,7 +514,7 @@ def run_profile_case(args):
 
     import paper_2202_11288_gb300 as tpc
     n = 2 ** (args.K + 1) - 1
-    S = tpc.Solver(args.delta, 2.0 ** -args.K)
+    S = tpc.Solver(args.delta, 2.0 ** -args.K, autotune=0)  # no tuning launches in the list
     x = torch.tensor(uniform_pm1(n, 5), device="cuda")
     y = torch.empty_like(x)
     for _ in range(3):
@@ -533,7 +533,7 @@ def run_profile_f32(args):
 
     import paper_2202_11288_gb300 as tpc
     n = 2 ** (args.K + 1) - 1
-    S = tpc.Solver(args.delta, 2.0 ** -args.K, precision=tpc.TPC_MIXED)
+    S = tpc.Solver(args.delta, 2.0 ** -args.K, precision=tpc.TPC_MIXED, autotune=0)
     x = torch.tensor(uniform_pm1(n, 5), dtype=torch.float32, device="cuda")
     f = torch.tensor(uniform_pm1(n, 6), dtype=torch.float32, device="cuda")
     y = torch.empty_like(x)
@@ -551,7 +551,8 @@ def run_profile_solve(args):
     import paper_2202_11288_gb300 as tpc
     n = 2 ** (args.K + 1) - 1
     prec = tpc.TPC_MIXED if args.profile_solve == "mixed" else tpc.TPC_FP64
-    S = tpc.Solver(args.delta, 2.0 ** -args.K, precision=prec, inner_cycles=args.inner)
+    S = tpc.Solver(args.delta, 2.0 ** -args.K, precision=prec, inner_cycles=args.inner,
+                   autotune=0)
     b = torch.tensor(uniform_pm1(n, 0), device="cuda")
     x = torch.zeros_like(b)
     rc, it, rel = S.solve(b, x, tol=args.tol)
