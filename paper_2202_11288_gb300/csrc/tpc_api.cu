@@ -268,7 +268,7 @@ void launch_matvec(tpc_handle* H, const Hier<T>& G, const DevLevel<T>& L, const 
   }
   H->launches += 3;
   launch_fwd_strided<T>(a, L.fwd_blocks, L.smem_strided, s);
-  k_mid_pair<T, NS><<<L.mid_blocks, fft_threads<T>(), L.smem_mid, s>>>(a);
+  launch_mid_pair<T, NS>(a, L.mid_blocks, L.smem_mid, s);
   launch_inv_strided<T>(a, L.fwd_blocks, L.smem_strided, s);
 }
 
@@ -296,13 +296,15 @@ T* enqueue_vcycle(tpc_handle* H, Hier<T>& G, int li, const T* f_top, const T* rf
   T* e = G.e[li];
   T* t = G.t[li];
   const T* f = rfine ? G.f[li] : f_top;
-  if (G.bottom && li == G.bottom_li && rfine) {
-    if (H->prm.variant != TPC_SPD)
-      k_vcycle_bottom<T, true><<<1, fft_threads<T>(), G.bottom_smem, s>>>(G.bottom);
-    else
-      k_vcycle_bottom<T, false><<<1, fft_threads<T>(), G.bottom_smem, s>>>(G.bottom);
-    H->launches += 1;
-    return t;  // the last post-smoothing product of level li writes G.t[li]
+  if constexpr (sizeof(T) == 4) {  // the single-block bottom exists in FP32 only
+    if (G.bottom && li == G.bottom_li && rfine) {
+      if (H->prm.variant != TPC_SPD)
+        k_vcycle_bottom<T, true><<<1, fft_threads<T>(), G.bottom_smem, s>>>(G.bottom);
+      else
+        k_vcycle_bottom<T, false><<<1, fft_threads<T>(), G.bottom_smem, s>>>(G.bottom);
+      H->launches += 1;
+      return t;  // the last post-smoothing product of level li writes G.t[li]
+    }
   }
   if (L.k == H->kc) {
     if (rfine) {
@@ -386,13 +388,14 @@ cudaError_t set_smem_attrs() {
   const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e;
   if ((e = strided_smem_attrs<T>(big)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_fwd_strided<T, IN_REAL, PRO_NONE>, A, big)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_mid_pair<T, NS>, A, big)) != cudaSuccess) return e;
+  if ((e = mid_pair_smem_attrs<T, NS>(big)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_mid_whole<T, NS>, A, big)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_mid_fwd<T>, A, big)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_mid_fwd_real<T>, A, big)) != cudaSuccess) return e;
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (sizeof(T) == 8) {  // the generator spectra are transformed in FP64 only
+    if ((e = cudaFuncSetAttribute(k_fwd_strided<T, IN_REAL, PRO_NONE>, A, big)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(k_mid_fwd<T>, A, big)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_mid_fwd_real<T>, A, big)) != cudaSuccess) return e;
+  } else {  // the single-block V-cycle bottom runs in FP32 only
     if ((e = cudaFuncSetAttribute(k_vcycle_bottom<T, NS>, A, big)) != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -1008,8 +1011,8 @@ int time_level(tpc_handle* H, const Hier<T>& G, int level, int reps, const T* x_
         if (ns) k_mid_whole<T, true><<<1, nt, L.smem_mid, s>>>(a);
         else k_mid_whole<T, false><<<1, nt, L.smem_mid, s>>>(a);
       } else {
-        if (ns) k_mid_pair<T, true><<<L.mid_blocks, nt, L.smem_mid, s>>>(a);
-        else k_mid_pair<T, false><<<L.mid_blocks, nt, L.smem_mid, s>>>(a);
+        if (ns) launch_mid_pair<T, true>(a, L.mid_blocks, L.smem_mid, s);
+        else launch_mid_pair<T, false>(a, L.mid_blocks, L.smem_mid, s);
       }
       H->launches += 1;
     }

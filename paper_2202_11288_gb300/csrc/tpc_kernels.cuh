@@ -574,12 +574,14 @@ __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_fwd_s
 // ------------------------------------------------------------------------------------
 // Body of the contiguous-block kernels on blocks (b, b2) with the step twiddles tw, the padded
 // data area s and the reduction scratch red in shared memory.
-template <typename T, int MODE, bool NS>
+// LOGL_CT, NSEQ_CT: when nonzero, log2 L and the number of blocks (1 or 2) as compile-time
+// constants, so that every step's strides, task counts and radix are folded into the code.
+template <typename T, int MODE, bool NS, int LOGL_CT = 0, int NSEQ_CT = 0>
 __device__ __forceinline__ void mid_core(const LevelArgs<T>& a, const c2<T>* tw, c2<T>* s,
                                          T* red, long long b, long long b2) {
-  const int logL = a.logL;
+  const int logL = LOGL_CT ? LOGL_CT : a.logL;
   const int L = 1 << logL;
-  const int nseq = (b != b2) ? 2 : 1;
+  const int nseq = NSEQ_CT ? NSEQ_CT : ((b != b2) ? 2 : 1);
   const int total = nseq << logL;
   T dot = 0;
   if constexpr (MODE == MID_WHOLE) {
@@ -708,7 +710,7 @@ __device__ __forceinline__ void mid_core(const LevelArgs<T>& a, const c2<T>* tw,
   }
 }
 
-template <typename T, int MODE, bool NS>
+template <typename T, int MODE, bool NS, int LOGL_CT = 0>
 __device__ __forceinline__ void mid_body(const LevelArgs<T>& a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2<T>* tab = reinterpret_cast<c2<T>*>(smem_raw);
@@ -729,13 +731,19 @@ __device__ __forceinline__ void mid_body(const LevelArgs<T>& a) {
       b2 = 3 * (2LL << g) - 1 - b;
     }
   }
-  mid_core<T, MODE, NS>(a, tw, s, red, b, b2);
+  if constexpr (LOGL_CT > 0) {
+    if (b != b2) mid_core<T, MODE, NS, LOGL_CT, 2>(a, tw, s, red, b, b2);
+    else mid_core<T, MODE, NS, LOGL_CT, 1>(a, tw, s, red, b, b2);
+  } else {
+    mid_core<T, MODE, NS>(a, tw, s, red, b, b2);
+  }
 }
 
 // One kernel name per mode (so profilers can select them).
-template <typename T, bool NS>
+// LOGL_CT: 0 for any L, or log2 L fixed at compile time (the launch picks the instance).
+template <typename T, bool NS, int LOGL_CT = 0>
 __global__ void __launch_bounds__(fft_threads<T>(), mid_min_blocks<T>()) k_mid_pair(LevelArgs<T> a) {
-  mid_body<T, MID_PAIR, NS>(a);
+  mid_body<T, MID_PAIR, NS, LOGL_CT>(a);
 }
 template <typename T, bool NS>
 __global__ void __launch_bounds__(fft_threads<T>(), mid_min_blocks<T>()) k_mid_whole(LevelArgs<T> a) {
@@ -1108,6 +1116,28 @@ inline void launch_inv_strided(const LevelArgs<T>& a, int blocks, size_t smem, c
     default: k_inv_strided<T, EPI_APPLY><<<blocks, nt, smem, s>>>(a); break;
   }
 }
+// The contiguous-block kernel: the instance with L fixed at compile time for the FP32 levels
+// with L = 2^10 .. 2^12 (the largest ones), the general one otherwise.
+template <typename T, bool NS>
+inline void launch_mid_pair(const LevelArgs<T>& a, int blocks, size_t smem, cudaStream_t s) {
+  const int nt = fft_threads<T>();
+  if (sizeof(T) == 4 && a.logL == 12) k_mid_pair<T, NS, 12><<<blocks, nt, smem, s>>>(a);
+  else if (sizeof(T) == 4 && a.logL == 11) k_mid_pair<T, NS, 11><<<blocks, nt, smem, s>>>(a);
+  else if (sizeof(T) == 4 && a.logL == 10) k_mid_pair<T, NS, 10><<<blocks, nt, smem, s>>>(a);
+  else k_mid_pair<T, NS><<<blocks, nt, smem, s>>>(a);
+}
+template <typename T, bool NS>
+inline cudaError_t mid_pair_smem_attrs(int bytes) {
+  const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e;
+  if constexpr (sizeof(T) == 4) {
+    if ((e = cudaFuncSetAttribute(k_mid_pair<T, NS, 12>, A, bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_mid_pair<T, NS, 11>, A, bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_mid_pair<T, NS, 10>, A, bytes)) != cudaSuccess) return e;
+  }
+  return cudaFuncSetAttribute(k_mid_pair<T, NS>, A, bytes);
+}
+
 // Raise the dynamic shared-memory limit of every strided-pass instance.
 template <typename T>
 inline cudaError_t strided_smem_attrs(int bytes) {
