@@ -175,15 +175,6 @@ template <typename T>
 __device__ __forceinline__ T restrict_at(const T* __restrict__ r, long long I) {
   return (T)0.25 * r[2 * I] + (T)0.5 * r[2 * I + 1] + (T)0.25 * r[2 * I + 2];
 }
-// Prolongation I_{k-1}^k = 2 (I_k^{k-1})^T at fine index j (nc coarse entries).
-template <typename T>
-__device__ __forceinline__ T prolong_at(const T* __restrict__ ec, long long j, long long nc) {
-  if (j & 1) return ec[(j - 1) / 2];
-  const long long I = j / 2;
-  const T lo = (I >= 1) ? ec[I - 1] : (T)0;
-  const T hi = (I < nc) ? ec[I] : (T)0;
-  return (T)0.5 * (lo + hi);
-}
 // Operand entry j of the product (concatenated index), formed by the prologue; w is the
 // pre-smoothing weight of j's segment. Split into the loads (issued in batches, so that many
 // loads are in flight per thread) and the arithmetic and stores that follow them.
@@ -967,27 +958,6 @@ __global__ void k_extract_cplx(const c2<T>* z, c2<T>* out, long long m, T scale)
 // ------------------------------------------------------------------------------------
 // V-cycle pieces (Algorithm 2)
 // ------------------------------------------------------------------------------------
-// First pre-smoothing sweep from u = 0: u = omega D^{-1} f.
-template <typename T>
-__global__ void k_smooth_init(const T* f, T* e, long long N, T wA, T wO, T wD) {
-  const long long n = 2 * N + 1;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const T w = (i < N) ? wA : ((i == N) ? wO : wD);
-    e[i] = w * f[i];
-  }
-}
-
-// Restriction I_k^{k-1}: fc[I] = (r[2I] + 2 r[2I+1] + r[2I+2]) / 4 (0-based, section 3.1).
-template <typename T>
-__global__ void k_restrict(const T* r, T* fc, long long nc) {
-  for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < nc;
-       I += (long long)gridDim.x * blockDim.x) {
-    const T a = r[2 * I], b = r[2 * I + 1], c = r[2 * I + 2];
-    fc[I] = (T)0.25 * a + (T)0.5 * b + (T)0.25 * c;
-  }
-}
-
 // Correction with P = 2 (I_k^{k-1})^T: e[2I+1] += ec[I], e[2I], e[2I+2] += ec[I] / 2.
 template <typename T>
 __global__ void k_prolong_add(T* e, const T* ec, long long nf) {
