@@ -68,7 +68,7 @@ def measured_hbm_gbs():
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--K", type=int, default=22)
@@ -195,7 +195,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -277,7 +277,7 @@ def time_batch(tpc, torch, args, rank):
         rc, its, rels, sts = tpc.tpc_solve_batch(handles, bs, xs, tol=args.tol)
         assert rc == tpc.TPC_OK, rc
     torch.cuda.synchronize()
-    steps = max(1, args.steps)
+    steps = min(5, max(1, args.steps))  # the batch is a secondary measurement: a few steps
     t0 = time.perf_counter()
     for _ in range(steps):
         rc, its, rels, sts = tpc.tpc_solve_batch(handles, bs, xs, tol=args.tol)
