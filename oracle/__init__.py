@@ -23,6 +23,9 @@ Contents
 ``weakly``  -- section 2.1: the weakly singular nonlocal model of eq. (3system) (diagonal minus
              the 2x2 Toeplitz block matrix), assembled from exact element integrals, and its
              BDF4 time stepping for Table 1.
+``fractional`` -- a fractional kernel |s|^{-(1+2a)} with a horizon (not in the paper): exact
+             element integrals of the same collocation. PARITY UNPINNED by the paper (pinned
+             only by mathematics: a = -1/2 is the printed matrix, exactness on quadratics).
 ``large``  -- the same finest-level operator for sizes where a dense matrix does not fit:
              selected dense rows, and the product computed with numpy's FFT as the
              convolution step (section 3.2, eq. ccs3.4).
@@ -31,5 +34,5 @@ Parity status: every function here is pinned by ``tests/test_oracle_*.py`` (prin
 coefficients vs quadrature, Example 3.1, Toeplitz closure, SPD and the two-grid bound of
 Theorem 4.1, LU agreement, order of accuracy, the sixteen BDF4 errors of Tables 2 and 3, the
 printed coefficient formulas of section 2.1 and the twelve BDF4 errors of Table 1).
-No function is "parity unpinned".
+``fractional`` is the one part whose parity the paper cannot pin.
 """

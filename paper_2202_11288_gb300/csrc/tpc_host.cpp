@@ -216,6 +216,153 @@ double ws_coupling(bool q_node, long long dist2, double g) {
   return (3.0 - g) * (2.0 - g) * (1.0 - g) * tot;
 }
 
+// ---------------------------------------------------------------------------------------
+// Fractional kernel with a horizon, gamma(|s|) = gamma0 |s|^{-(1+2a)} for |s| < delta (the
+// constant kernel is a = -1/2). Not defined by the paper; entries are the collocation of
+// -L_delta u written as exact element integrals, scaled (like section 2.2's eta_h) so that they
+// are numbers independent of h: 6 int_{|s|<r} |s|^{-(1+2a)} [phi_q(x_p) - phi_q(x_p + s)] ds in
+// units of h. Implemented for -1/2 <= a < 1/2, where every integral converges (a >= 1/2 needs
+// Hadamard finite parts near the diagonal).
+// ---------------------------------------------------------------------------------------
+
+// int_{y0}^{y1} (a0 + a1 u + a2 u^2) |y|^{-g} dy with u = y - y0 and 0 not inside (y0, y1); the
+// polynomial must vanish at y = 0 when y = 0 is an end and g >= 1. Near y = 0: antiderivatives
+// in powers of y; farther: Gauss-Legendre in u.
+double frac_piece(double a0, double a1, double a2, double y0, double y1, double g) {
+  static const GaussLegendre20 gl;
+  if (y1 <= y0) return 0.0;
+  if (y0 >= 4.0 || y1 <= -4.0) {
+    const double h2 = 0.5 * (y1 - y0);
+    double acc = 0.0;
+    for (int i = 0; i < 20; ++i) {
+      const double u = h2 * (gl.x[i] + 1.0), y = y0 + u;
+      acc += gl.w[i] * (a0 + u * (a1 + u * a2)) * std::pow(std::fabs(y), -g);
+    }
+    return h2 * acc;
+  }
+  const bool neg = y1 <= 0.0;  // integrate over t = |y| >= 0
+  double c[3] = {a0 - a1 * y0 + a2 * y0 * y0, a1 - 2.0 * a2 * y0, a2};  // powers of y
+  if (neg) c[1] = -c[1];                                                 // y = -t
+  const double t0 = neg ? -y1 : y0, t1 = neg ? -y0 : y1;
+  auto F = [&](double t) {
+    double v = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      if (c[k] == 0.0) continue;
+      const double e = k + 1 - g;
+      if (t == 0.0) continue;  // e > 0 for every nonzero term that reaches t = 0
+      v += c[k] * (e == 0.0 ? std::log(t) : std::pow(t, e) / e);
+    }
+    return v;
+  };
+  return F(t1) - F(t0);
+}
+
+// Same, splitting at y = 0 when it lies inside the piece (the basis then vanishes there).
+double frac_int(double a0, double a1, double a2, double y0, double y1, double g) {
+  if (y0 < 0.0 && y1 > 0.0) {
+    // the polynomial in the second half's own coordinate u' = y (u = y - y0)
+    const double b0 = a0 - a1 * y0 + a2 * y0 * y0, b1 = a1 - 2.0 * a2 * y0;
+    return frac_piece(a0, a1, a2, y0, 0.0, g) + frac_piece(b0, b1, a2, 0.0, y1, g);
+  }
+  return frac_piece(a0, a1, a2, y0, y1, g);
+}
+
+// 6 int_{|s|<r} |s|^{-g} [phi_q(x_p) - phi_q(x_p + s)] ds (units of h), g = 1 + 2a, for the
+// column at twice-distance dist2 = 2 (x_p - x_q) from a row of the given type. Column basis:
+// node type for nodes and midpoint type for midpoints, swapped in the midpoint rows of the SPD
+// system (its midpoint rows are collocated on the mesh shifted by h/2, section 2.2.2).
+double frac_coef(int variant, bool row_node, long long dist2, int r, double a) {
+  const double g = 1.0 + 2.0 * a;
+  const bool col_node = row_node ? (dist2 % 2 == 0) : (dist2 % 2 != 0);
+  const bool node_type = (variant == TPC_SPD && !row_node) ? !col_node : col_node;
+  const double c = -0.5 * (double)dist2, R = (double)r;
+  // pieces (y0, y1, a0, a1, a2) of the basis, phi = a0 + a1 u + a2 u^2, u = y - y0
+  double pc[2][5];
+  int np = 0;
+  if (node_type) {
+    pc[np][0] = c - 1.0; pc[np][1] = c; pc[np][2] = 0.0; pc[np][3] = -1.0; pc[np][4] = 2.0; ++np;
+    pc[np][0] = c; pc[np][1] = c + 1.0; pc[np][2] = 1.0; pc[np][3] = -3.0; pc[np][4] = 2.0; ++np;
+  } else {
+    pc[np][0] = c - 0.5; pc[np][1] = c + 0.5; pc[np][2] = 0.0; pc[np][3] = 4.0; pc[np][4] = -4.0;
+    ++np;
+  }
+  double v = 0.0;
+  if (dist2 == 0) {
+    // diagonal: int over the support of (1 - phi) |s|^{-g}, plus int of |s|^{-g} beyond it
+    const double sup = node_type ? 1.0 : 0.5;
+    for (int i = 0; i < np; ++i) {
+      const double y0 = std::fmax(pc[i][0], -R), y1 = std::fmin(pc[i][1], R);
+      if (y1 <= y0) continue;
+      // 1 - phi in the clipped piece's coordinate u'' = y - y0 (shift from the piece's own)
+      const double d = y0 - pc[i][0];
+      const double b0 = 1.0 - (pc[i][2] + pc[i][3] * d + pc[i][4] * d * d);
+      const double b1 = -(pc[i][3] + 2.0 * pc[i][4] * d), b2 = -pc[i][4];
+      v += frac_int(b0, b1, b2, y0, y1, g);
+    }
+    if (R > sup) {
+      const double e = 1.0 - g;
+      v += 2.0 * (e == 0.0 ? std::log(R / sup) : (std::pow(R, e) - std::pow(sup, e)) / e);
+    }
+    return 6.0 * v;
+  }
+  for (int i = 0; i < np; ++i) {
+    const double y0 = std::fmax(pc[i][0], -R), y1 = std::fmin(pc[i][1], R);
+    if (y1 <= y0) continue;
+    const double d = y0 - pc[i][0];
+    v += frac_int(pc[i][2] + pc[i][3] * d + pc[i][4] * d * d, pc[i][3] + 2.0 * pc[i][4] * d,
+                  pc[i][4], y0, y1, g);
+  }
+  return -6.0 * v;
+}
+
+// Finest level for the fractional kernel: finest_form's block layout with frac_coef entries.
+LevelForm finest_form_frac(int variant, int K, int r, double a, double shift) {
+  const long long Nint = 1LL << K;
+  LevelForm L;
+  L.k = K;
+  L.N = Nint - 1;
+  const long long N = L.N;
+  // the entries vanish beyond twice-distance 2r + 2; tabulate them once per row type
+  const long long reach = 2LL * r + 3;
+  std::vector<double> nodeRow(2 * reach + 1), midRow(2 * reach + 1);
+  for (long long d2 = -reach; d2 <= reach; ++d2) {
+    nodeRow[d2 + reach] = frac_coef(variant, true, d2, r, a);
+    midRow[d2 + reach] = frac_coef(variant, false, d2, r, a);
+  }
+  auto nr = [&](long long d2) { return (d2 < -reach || d2 > reach) ? 0.0 : nodeRow[d2 + reach]; };
+  auto mr = [&](long long d2) { return (d2 < -reach || d2 > reach) ? 0.0 : midRow[d2 + reach]; };
+  auto fA = [&](long long d) { return nr(2 * d); };
+  auto fB = [&](long long d) { return nr(2 * d + 1); };
+  auto fC = [&](long long d) { return mr(2 * d - 1); };
+  auto fD = [&](long long d) { return mr(2 * d); };
+  const size_t G = (size_t)(2 * N - 1);
+  L.tA.assign(G, 0.0);
+  L.tB.assign(G, 0.0);
+  L.tC.assign(G, 0.0);
+  L.tD.assign(G, 0.0);
+  for (long long d = -(N - 1); d <= N - 1; ++d) {
+    L.tA[d + N - 1] = fA(d);
+    L.tB[d + N - 1] = fB(d - 1);
+    L.tC[d + N - 1] = fC(d + 1);
+    L.tD[d + N - 1] = fD(d);
+  }
+  L.p.assign(N, 0.0);
+  L.q.assign(N, 0.0);
+  L.xi.assign(N, 0.0);
+  L.zeta.assign(N, 0.0);
+  for (long long i = 1; i <= N; ++i) {
+    L.p[i - 1] = fB(i - 1);
+    L.q[i - 1] = fC(1 - i);
+    L.zeta[i - 1] = fD(-i);
+    L.xi[i - 1] = fD(i);
+  }
+  L.o = fD(0);
+  L.tA[N - 1] += shift;
+  L.tD[N - 1] += shift;
+  L.o += shift;
+  return L;
+}
+
 // Couplings of the two boundary basis functions (nodes x = 0 and x = 1, one element each) to
 // the collocation point at twice-coordinate xp2: the columns K0, KN of the right-hand side.
 double ws_boundary(bool left, long long xp2, long long Nint, double g) {
@@ -428,9 +575,17 @@ int build_host_hierarchy(const tpc_params& p, double delta, double h, int levels
     err = "TPC_WEAKLY needs the exponent kernel_a in [0, 1)";
     return TPC_EINVAL;
   }
-  if (p.kernel != 0) {
-    err = "only the constant kernel (kernel = 0) is implemented";
-    return TPC_ENOTSUP;
+  if (p.kernel != 0 && p.kernel != 1) {
+    err = "kernel must be 0 (constant) or 1 (fractional |s|^-(1+2a), a = kernel_a)";
+    return TPC_EINVAL;
+  }
+  if (p.kernel == 1 && p.variant != TPC_WEAKLY) {
+    if (!(p.kernel_a >= -0.5 && p.kernel_a < 0.5)) {
+      err = p.kernel_a >= 0.5
+                ? "fractional kernel with a >= 1/2 needs finite-part integrals: not implemented"
+                : "fractional kernel needs -1/2 <= kernel_a < 1/2";
+      return p.kernel_a >= 0.5 ? TPC_ENOTSUP : TPC_EINVAL;
+    }
   }
   if (p.m1 < 1 || p.m2 < 0 || p.m1 > 8 || p.m2 > 8) {
     err = "need 1 <= m1 <= 8 and 0 <= m2 <= 8";
@@ -467,8 +622,12 @@ int build_host_hierarchy(const tpc_params& p, double delta, double h, int levels
   out.r = r;
   out.lev.clear();
   out.lev.reserve(K - kc + 1);
-  out.lev.push_back(p.variant == TPC_WEAKLY ? finest_form_weakly(K, p.kernel_a, p.shift)
-                                             : finest_form(p.variant, K, r, p.shift));
+  if (p.variant == TPC_WEAKLY)
+    out.lev.push_back(finest_form_weakly(K, p.kernel_a, p.shift));
+  else if (p.kernel == 1)
+    out.lev.push_back(finest_form_frac(p.variant, K, r, p.kernel_a, p.shift));
+  else
+    out.lev.push_back(finest_form(p.variant, K, r, p.shift));
   for (int k = K; k > kc; --k) out.lev.push_back(coarsen(out.lev.back()));
   const LevelForm& Lc = out.lev.back();
   const long long n = 2 * Lc.N + 1;
@@ -622,6 +781,10 @@ int tpc_bdf4_coefficients(const tpc_params* p, double delta, double h, double ta
     tpc::g_host_err = "bad argument to tpc_bdf4_coefficients";
     return TPC_EINVAL;
   }
+  if (p->kernel != 0 && p->variant != TPC_WEAKLY) {
+    tpc::g_host_err = "tpc_bdf4_coefficients: the fractional kernel is not supported";
+    return TPC_ENOTSUP;
+  }
   int K = 0, r = 1;
   if (const int rc = tpc::grid_and_horizon(delta, h, K, r, tpc::g_host_err)) return rc;
   const double eta = tpc::eta_of(*p, r, h);
@@ -638,6 +801,10 @@ int tpc_collocation_rhs(const tpc_params* p, double delta, double h, const doubl
       (p->variant == TPC_WEAKLY && !(p->kernel_a >= 0.0 && p->kernel_a < 1.0))) {
     tpc::g_host_err = "bad argument to tpc_collocation_rhs";
     return TPC_EINVAL;
+  }
+  if (p->kernel != 0 && p->variant != TPC_WEAKLY) {
+    tpc::g_host_err = "tpc_collocation_rhs: the fractional kernel is not supported";
+    return TPC_ENOTSUP;
   }
   int K = 0, r = 1;
   if (const int rc = tpc::grid_and_horizon(delta, h, K, r, tpc::g_host_err)) return rc;
