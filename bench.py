@@ -51,7 +51,7 @@ def f32_bytes_per_point(r, N):
     return (12.0 + 4.0 * frac, 24.0, 16.0 + 4.0 * frac)
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP32 finest kernels, from ncu
 # (profiles/fp32_transform_kernels_N2e22.md), keyed by (K, kernel index); unknown for other sizes
-F32_TRAFFIC = {(22, 0): 53.9e6, (22, 1): 153.9e6, (22, 2): 115.7e6}
+F32_TRAFFIC = {(22, 0): 53.6e6, (22, 1): 154.2e6, (22, 2): 115.7e6}
 
 
 def measured_hbm_gbs():
@@ -253,7 +253,8 @@ def time_solves(tpc, torch, S, stream, rhs, x, args, clocks=None):
 def batch_workload(count, seed=0):
     """Uneven 1-D instances: N = 2^K with K uniform in 9..17 (1023 .. 262143 unknowns), delta
     uniform in [0.02, 0.25] (redrawn until r >= 1), SPD / nonsymmetric alternating, constant
-    kernel, uniform[-1,1) right-hand sides."""
+    kernel (the V-cycle needs tens to hundreds of cycles with the fractional kernel), uniform[-1,1)
+    right-hand sides. Entries: (K, delta, variant, kernel, a)."""
     rng = np.random.default_rng(seed)
     specs = []
     for i in range(count):
@@ -262,14 +263,15 @@ def batch_workload(count, seed=0):
             delta = float(rng.uniform(0.02, 0.25))
             if delta * (1 << K) >= 1.0:
                 break
-        specs.append((K, delta, i % 2))
+        specs.append((K, delta, i % 2, 0, 0.0))
     return specs
 
 
 def time_batch(tpc, torch, args, rank):
     """One step = one tpc_solve_batch call over all instances (mixed precision)."""
     specs = batch_workload(args.batch)
-    solvers = [tpc.Solver(d, 2.0 ** -K, variant=v, precision=tpc.TPC_MIXED) for K, d, v in specs]
+    solvers = [tpc.Solver(d, 2.0 ** -K, variant=v, kernel=kk, kernel_a=a,
+                          precision=tpc.TPC_MIXED) for K, d, v, kk, a in specs]
     bs = [torch.tensor(uniform_pm1(S.n, 5000 + i), device="cuda") for i, S in enumerate(solvers)]
     xs = [torch.zeros_like(b) for b in bs]
     handles = [S.handle for S in solvers]
@@ -290,13 +292,15 @@ def time_batch(tpc, torch, args, rank):
     return {"instances": len(specs), "solves_per_s": len(specs) / sec, "dof_per_s": dof / sec,
             "ms_per_batch": 1000.0 * sec, "unknowns_total": dof,
             "workload": "N=2^K, K uniform in 9..17, delta uniform in [0.02,0.25], SPD/nonsym, "
-                        "mixed precision, tol 1e-10, one tpc_solve_batch per step (host clock)"}
+                        "constant kernel, mixed precision, tol 1e-10, one tpc_solve_batch per "
+                        "step (host clock)"}
 
 
 def serve_keys():
     """Problems of the serving measurement: N = 2^K, K in 9..21 (1023 .. 4,194,303 unknowns,
-    log-uniform when K is uniform), delta in {0.05, 0.1, 0.2}, SPD or nonsymmetric."""
-    return [(v, d, K) for K in range(9, 22) for d in (0.05, 0.1, 0.2) for v in (0, 1)]
+    log-uniform when K is uniform), delta in {0.05, 0.1, 0.2}, SPD or nonsymmetric, constant
+    kernel: (variant, delta, K, kernel, a)."""
+    return [(v, d, K, 0, 0.0) for K in range(9, 22) for d in (0.05, 0.1, 0.2) for v in (0, 1)]
 
 
 def time_serving(tpc, torch, args):
@@ -313,15 +317,16 @@ def time_serving(tpc, torch, args):
 
     srv = tpc.Server(hbm_budget_bytes=150 << 30, max_inflight=32, precision=tpc.TPC_MIXED)
     out = {"workload": "Poisson arrivals; N=2^K, K uniform in 9..21 (1023..4,194,303 unknowns), "
-                       "delta in {0.05,0.1,0.2}, SPD/nonsym, mixed precision, tol 1e-10, host "
-                       "buffers (pinned); hierarchies resident (HBM budget 150 GB, 32 slots)",
+                       "delta in {0.05,0.1,0.2}, SPD/nonsym, constant kernel, mixed precision, "
+                       "tol 1e-10, host buffers (pinned); hierarchies resident (HBM budget "
+                       "150 GB, 32 slots)",
            "rates": []}
     try:
         owner = {}
         t0 = time.perf_counter()
-        for v, d, K in keys:                           # prewarm: build every hierarchy once
+        for v, d, K, kk, a in keys:                    # prewarm: build every hierarchy once
             x = xbuf(K)
-            owner[srv.submit(v, d, 2.0 ** -K, rhs[K], x, args.tol)] = (K, x)
+            owner[srv.submit(v, d, 2.0 ** -K, rhs[K], x, args.tol, kk, a)] = (K, x)
         got = 0
         while got < len(keys):
             for r in srv.poll(256, wait_ms=20):
@@ -348,9 +353,9 @@ def time_serving(tpc, torch, args):
                     if dt <= 0:
                         break
                     time.sleep(min(dt, 0.0005))
-                v, d, K = keys[picks[i]]
+                v, d, K, kk, a = keys[picks[i]]
                 x = xbuf(K)
-                owner[srv.submit(v, d, 2.0 ** -K, rhs[K], x, args.tol)] = (K, x)
+                owner[srv.submit(v, d, 2.0 ** -K, rhs[K], x, args.tol, kk, a)] = (K, x)
             while owner:
                 for r in srv.poll(256, wait_ms=20):
                     K, x = owner.pop(r["ticket"])

@@ -266,12 +266,14 @@ typedef struct tpc_server_config {
                               duplicate set-up); requests of other keys pass a waiting one  */
 } tpc_server_config;
 typedef struct tpc_request {
-  int variant;             /* TPC_SPD or TPC_NONSYM                                          */
+  int variant;             /* TPC_SPD, TPC_NONSYM or TPC_WEAKLY                              */
   double delta, h;         /* horizon and mesh size (h = 2^-K), as for tpc_setup             */
   long long n;             /* 2/h - 1 unknowns: the length of b_host and x_host              */
   const double* b_host;    /* right-hand side, host memory (pinned for speed), read once     */
   double* x_host;          /* solution, host memory; valid when the result is polled         */
   double tol;              /* relative residual target                                       */
+  int kernel;              /* as tpc_params.kernel (0 constant, 1 fractional)                */
+  double kernel_a;         /* as tpc_params.kernel_a                                         */
 } tpc_request;
 typedef struct tpc_server_result {
   long long ticket;        /* as returned by tpc_server_submit                               */

@@ -54,7 +54,7 @@ class TpcServerConfig(ctypes.Structure):
 class TpcRequest(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("delta", ctypes.c_double), ("h", ctypes.c_double),
                 ("n", ctypes.c_longlong), ("b_host", ctypes.c_void_p), ("x_host", ctypes.c_void_p),
-                ("tol", ctypes.c_double)]
+                ("tol", ctypes.c_double), ("kernel", ctypes.c_int), ("kernel_a", ctypes.c_double)]
 
 
 class TpcServerResult(ctypes.Structure):
@@ -433,12 +433,13 @@ class Server:
         _check(lib().tpc_server_create(ctypes.byref(cfg), ctypes.byref(p), ctypes.byref(self.handle)))
         self._keep = {}
 
-    def submit(self, variant: int, delta: float, h: float, b, x, tol: float = 1e-10) -> int:
+    def submit(self, variant: int, delta: float, h: float, b, x, tol: float = 1e-10,
+               kernel: int = 0, kernel_a: float = 0.0) -> int:
         """b, x: contiguous float64 host arrays (numpy, or pinned torch CPU tensors)."""
         n = b.numel() if hasattr(b, "numel") else b.size
         bp = b.data_ptr() if hasattr(b, "data_ptr") else b.ctypes.data
         xp = x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
-        r = TpcRequest(variant, delta, h, n, bp, xp, tol)
+        r = TpcRequest(variant, delta, h, n, bp, xp, tol, kernel, kernel_a)
         t = ctypes.c_longlong(0)
         _check(lib().tpc_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)))
         self._keep[t.value] = (b, x)

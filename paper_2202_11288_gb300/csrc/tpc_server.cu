@@ -3,7 +3,7 @@
 // A worker thread owns every handle. Requests (problem description + host buffers) are queued
 // by tpc_server_submit; the worker admits them while a slot (max_inflight) and device memory
 // (the HBM budget) are free, keeps level hierarchies resident keyed by the problem (variant,
-// horizon, mesh size, precision) and reuses an idle one when the key repeats (a request whose
+// kernel, horizon, mesh size, precision) and reuses an idle one when the key repeats (a request whose
 // key's hierarchies are all busy waits for one, unless the key may have another; later
 // requests of other keys go ahead), evicting idle hierarchies least-recently-used first when
 // the budget requires. Every admitted solve runs on
@@ -40,8 +40,8 @@ struct Request {
 };
 
 struct Entry {
-  int variant = 0, precision = 0;
-  double delta = 0.0, h = 0.0;
+  int variant = 0, precision = 0, kernel = 0;
+  double delta = 0.0, h = 0.0, kernel_a = 0.0;
   tpc_handle* H = nullptr;
   size_t bytes = 0;
   bool busy = false;
@@ -80,7 +80,8 @@ struct tpc_server {
 namespace {
 
 bool same_key(const Entry& e, const tpc_request& r, int precision) {
-  return e.variant == r.variant && e.precision == precision && e.delta == r.delta && e.h == r.h;
+  return e.variant == r.variant && e.precision == precision && e.delta == r.delta && e.h == r.h &&
+         e.kernel == r.kernel && e.kernel_a == r.kernel_a;
 }
 
 // Device bytes a hierarchy of this key needs: the size of a resident one with the same mesh
@@ -151,6 +152,8 @@ bool admit(tpc_server* S, Request& req) {
     }
     tpc_params p = S->prm;
     p.variant = req.r.variant;
+    p.kernel = req.r.kernel;
+    p.kernel_a = req.r.kernel_a;
     tpc_handle* H = nullptr;
     const int rc = tpc_setup(&p, req.r.delta, req.r.h, 0, nullptr, &H);
     if (rc != TPC_OK) {
@@ -162,6 +165,8 @@ bool admit(tpc_server* S, Request& req) {
     ent->precision = prec;
     ent->delta = req.r.delta;
     ent->h = req.r.h;
+    ent->kernel = req.r.kernel;
+    ent->kernel_a = req.r.kernel_a;
     ent->H = H;
     ent->bytes = tpc::handle_device_bytes(H);
     S->used_bytes += ent->bytes;

@@ -16,8 +16,11 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-KEYS = [(tpc.TPC_SPD, 0.05, 10), (tpc.TPC_NONSYM, 0.1, 11), (tpc.TPC_SPD, 0.2, 9),
-        (tpc.TPC_SPD, 0.125, 12), (tpc.TPC_NONSYM, 0.3, 10)]
+# (variant, delta, K, kernel, a); the last key differs from the first only in its kernel, so a
+# hierarchy must not be shared across kernels
+KEYS = [(tpc.TPC_SPD, 0.05, 10, 0, 0.0), (tpc.TPC_NONSYM, 0.1, 11, 0, 0.0),
+        (tpc.TPC_SPD, 0.2, 9, 0, 0.0), (tpc.TPC_SPD, 0.125, 12, 0, 0.0),
+        (tpc.TPC_NONSYM, 0.3, 10, 0, 0.0), (tpc.TPC_SPD, 0.05, 10, 1, 0.25)]
 
 
 def _wait_all(srv, count, timeout_s=120.0):
@@ -31,16 +34,17 @@ def _wait_all(srv, count, timeout_s=120.0):
 def test_server_results_equal_alone_with_eviction():
     rng = np.random.default_rng(3)
     reqs = []
-    for i in range(20):
-        v, d, K = KEYS[int(rng.integers(len(KEYS)))]
+    for i in range(24):
+        v, d, K, kk, a = KEYS[i % len(KEYS)] if i < len(KEYS) else KEYS[int(rng.integers(len(KEYS)))]
         n = (1 << (K + 1)) - 1
         b = torch.tensor(uniform_pm1(n, 700 + i)).pin_memory()
         x = torch.zeros(n, dtype=torch.float64).pin_memory()
-        reqs.append((v, d, K, b, x))
-    # a budget below the five hierarchies' total (about 5 MB), so the LRU eviction runs
+        reqs.append((v, d, K, kk, a, b, x))
+    # a budget below the six hierarchies' total (about 6 MB), so the LRU eviction runs
     srv = tpc.Server(hbm_budget_bytes=4 << 20, max_inflight=4, precision=tpc.TPC_MIXED)
     try:
-        tickets = {srv.submit(v, d, 2.0 ** -K, b, x): i for i, (v, d, K, b, x) in enumerate(reqs)}
+        tickets = {srv.submit(v, d, 2.0 ** -K, b, x, 1e-10, kk, a): i
+                   for i, (v, d, K, kk, a, b, x) in enumerate(reqs)}
         res = _wait_all(srv, len(reqs))
         assert len(res) == len(reqs)
         assert srv.outstanding() == 0
@@ -48,10 +52,10 @@ def test_server_results_equal_alone_with_eviction():
         srv.close()
     for r in res:
         i = tickets[r["ticket"]]
-        v, d, K, b, x = reqs[i]
+        v, d, K, kk, a, b, x = reqs[i]
         assert r["status"] == tpc.TPC_OK and r["relres"] < 1e-10
         assert r["latency_s"] >= r["queue_s"] >= 0.0
-        S = tpc.Solver(d, 2.0 ** -K, variant=v, precision=tpc.TPC_MIXED)
+        S = tpc.Solver(d, 2.0 ** -K, variant=v, kernel=kk, kernel_a=a, precision=tpc.TPC_MIXED)
         try:
             xa = np.zeros(b.numel())
             rc, it, rel = S.solve_host(b.numpy(), xa, tol=1e-10)
