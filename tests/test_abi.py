@@ -35,3 +35,15 @@ def test_device_calls_fail_cleanly_without_a_gpu():
     assert ei.value.code == tpc.TPC_ECUDA
     assert tpc.lib().tpc_level_size(None, 7) == 0
     tpc.lib().tpc_destroy(None)
+
+
+def test_server_and_batch_fail_cleanly_without_a_gpu():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(tpc.TpcError) as ei:
+        tpc.Server(hbm_budget_bytes=1 << 20)
+    assert ei.value.code == tpc.TPC_ECUDA
+    rc, its, rels, sts = tpc.tpc_solve_batch([], [], [])  # an empty batch needs no device
+    assert rc == tpc.TPC_OK and its == [] and sts == []
+    tpc.lib().tpc_server_destroy(None)
