@@ -78,7 +78,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=512,
                     help="instances of the batched-uneven measurement (0 = skip it)")
-    ap.add_argument("--serve-rates", default="50,200,1000,2000",
+    ap.add_argument("--serve-rates", default="50,100,200,500,1000,2000",
                     help="Poisson arrival rates (req/s) of the serving measurement ('' = skip)")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="arrival window per rate of the serving measurement")
