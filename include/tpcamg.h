@@ -61,10 +61,11 @@ enum { TPC_FP64 = 0, TPC_MIXED = 1 };          /* precision of the inner V-cycle
 typedef struct tpc_params {
   int variant;        /* TPC_SPD, TPC_NONSYM or TPC_WEAKLY                                */
   int kernel;         /* 0 = constant kernel gamma_delta (section 2.2); 1 = fractional
-                         kernel |s|^{-(1+2a)} inside the horizon, a = kernel_a in [-1/2, 1/2)
+                         kernel |s|^{-(1+2a)} inside the horizon, a = kernel_a in [-1/2, 1)
                          (not defined by the paper: entries are the exact element integrals
-                         of the same collocation; a = -1/2 is the constant kernel; a >= 1/2
-                         needs finite parts: ENOTSUP); set-up, products and solves only   */
+                         of the same collocation, Hadamard finite parts for a >= 1/2, where
+                         the system is indefinite and the V-cycle diverges; a = -1/2 is the
+                         constant kernel; a >= 1: ENOTSUP); set-up, products and solves   */
   double kernel_a;    /* kernel = 1: a. TPC_WEAKLY: the exponent gamma in [0, 1)          */
   double gamma0;      /* kernel constant; only scales the right-hand side, not the matrix  */
   double shift;       /* sigma added to the diagonal of the finest matrix (sigma I + A)    */

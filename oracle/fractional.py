@@ -12,9 +12,13 @@ quadratic basis, each entry written as an exact integral,
 (units of h, r = floor(delta / h)); the factor 6 and the units make a = -1/2 (the constant
 kernel) reproduce the printed coefficients of section 2.2, and the SPD system collocates its
 midpoint rows on the mesh shifted by h/2 as eq. (system1) does. Integrals are evaluated exactly
-with sympy (rational exponent), for -1/2 <= a < 1/2, where all of them converge; a >= 1/2 would
-need finite parts. PARITY UNPINNED by the paper: the pins are mathematical (a = -1/2 gives the
-printed matrix; the stencil is exact on 1, x, x^2; symmetry of the SPD system).
+with sympy (rational exponent), term by term over the powers of s, for -1/2 <= a < 1. For
+a < 1/2 every integral converges. For 1/2 <= a < 1 the linear term of the basis next to the
+singularity gives int_0 s^{-2a} ds, which diverges; the entry is then its Hadamard finite
+part, the analytic continuation in a: int_0^c s^{e-1} ds = c^e / e also for e < 0, and
+log c (units of h) for e = 0 (a = 1/2). PARITY UNPINNED by the paper: the pins are
+mathematical (a = -1/2 gives the printed matrix; the stencil is exact on 1, x, x^2, which
+holds for the finite parts too since continuation in a is linear; symmetry of the SPD system).
 """
 from __future__ import annotations
 
@@ -38,17 +42,31 @@ def _basis(node_type: bool, c: sp.Rational):
     return [(c - half, c + half, 4 * (_S - (c - half)) * ((c + half) - _S))]
 
 
+def _int_power(k, g, lo, hi):
+    """int_lo^hi t^{k-g} dt for 0 <= lo < hi; at t = 0 with k - g <= -1 the Hadamard finite
+    part (the antiderivative t^e / e or log t is taken as 0 there)."""
+    e = k + 1 - g
+
+    def F(t):
+        if t == 0:
+            return sp.Integer(0)
+        return sp.log(t) if e == 0 else t ** e / e
+
+    return F(hi) - F(lo)
+
+
 def _int_weighted(expr, lo, hi, g):
-    """Exact int_lo^hi expr(s) |s|^{-g} ds, split at s = 0."""
+    """Exact int_lo^hi expr(s) |s|^{-g} ds (a finite part where it diverges at s = 0), split
+    at s = 0 into integrals over t = |s| >= 0 of the polynomial's powers."""
     tot = sp.Integer(0)
     if hi > 0:
-        a = max(lo, 0)
-        tot += sp.integrate(sp.expand(expr) * _S ** (-g), (_S, a, hi))
+        poly = sp.Poly(sp.expand(expr), _S)
+        for (k,), c in poly.terms():
+            tot += c * _int_power(k, g, max(lo, 0), hi)
     if lo < 0:
-        b = min(hi, 0)
-        # s = -t, t in [-b, -lo]
-        t = sp.Symbol("t", positive=True)
-        tot += sp.integrate(sp.expand(expr.subs(_S, -t)) * t ** (-g), (t, -b, -lo))
+        poly = sp.Poly(sp.expand(expr.subs(_S, -_S)), _S)  # s = -t
+        for (k,), c in poly.terms():
+            tot += c * _int_power(k, g, max(-hi, 0), -lo)
     return tot
 
 

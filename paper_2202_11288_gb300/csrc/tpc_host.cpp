@@ -221,13 +221,17 @@ double ws_coupling(bool q_node, long long dist2, double g) {
 // constant kernel is a = -1/2). Not defined by the paper; entries are the collocation of
 // -L_delta u written as exact element integrals, scaled (like section 2.2's eta_h) so that they
 // are numbers independent of h: 6 int_{|s|<r} |s|^{-(1+2a)} [phi_q(x_p) - phi_q(x_p + s)] ds in
-// units of h. Implemented for -1/2 <= a < 1/2, where every integral converges (a >= 1/2 needs
-// Hadamard finite parts near the diagonal).
+// units of h. Implemented for -1/2 <= a < 1. For a < 1/2 every integral converges; for
+// 1/2 <= a < 1 the linear term of the basis next to s = 0 makes int_0 s^{-2a} ds diverge, and
+// the entry is its Hadamard finite part, the analytic continuation in a (int_0^c t^{e-1} dt =
+// c^e / e for e < 0, log c in units of h for e = 0). Exactness on quadratics holds for these
+// too; the SPD system is then no longer positive definite.
 // ---------------------------------------------------------------------------------------
 
 // int_{y0}^{y1} (a0 + a1 u + a2 u^2) |y|^{-g} dy with u = y - y0 and 0 not inside (y0, y1); the
 // polynomial must vanish at y = 0 when y = 0 is an end and g >= 1. Near y = 0: antiderivatives
-// in powers of y; farther: Gauss-Legendre in u.
+// in powers of y (at t = 0 they are taken as 0: the true value where the power is positive,
+// the finite part where it is not); farther: Gauss-Legendre in u.
 double frac_piece(double a0, double a1, double a2, double y0, double y1, double g) {
   static const GaussLegendre20 gl;
   if (y1 <= y0) return 0.0;
@@ -249,7 +253,7 @@ double frac_piece(double a0, double a1, double a2, double y0, double y1, double 
     for (int k = 0; k < 3; ++k) {
       if (c[k] == 0.0) continue;
       const double e = k + 1 - g;
-      if (t == 0.0) continue;  // e > 0 for every nonzero term that reaches t = 0
+      if (t == 0.0) continue;  // t^e / e -> 0 (e > 0), or the finite part (e <= 0)
       v += c[k] * (e == 0.0 ? std::log(t) : std::pow(t, e) / e);
     }
     return v;
@@ -580,11 +584,11 @@ int build_host_hierarchy(const tpc_params& p, double delta, double h, int levels
     return TPC_EINVAL;
   }
   if (p.kernel == 1 && p.variant != TPC_WEAKLY) {
-    if (!(p.kernel_a >= -0.5 && p.kernel_a < 0.5)) {
-      err = p.kernel_a >= 0.5
-                ? "fractional kernel with a >= 1/2 needs finite-part integrals: not implemented"
-                : "fractional kernel needs -1/2 <= kernel_a < 1/2";
-      return p.kernel_a >= 0.5 ? TPC_ENOTSUP : TPC_EINVAL;
+    if (!(p.kernel_a >= -0.5 && p.kernel_a < 1.0)) {
+      err = p.kernel_a >= 1.0
+                ? "fractional kernel with a >= 1: the stencil is not exact on x^2 (diverges)"
+                : "fractional kernel needs -1/2 <= kernel_a < 1";
+      return p.kernel_a >= 1.0 ? TPC_ENOTSUP : TPC_EINVAL;
     }
   }
   if (p.m1 < 1 || p.m2 < 0 || p.m1 > 8 || p.m2 > 8) {

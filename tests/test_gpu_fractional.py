@@ -1,7 +1,9 @@
 """GPU path with the fractional kernel (kernel = 1; a reading of this build, see
 oracle/fractional.py) against the oracle: products at every level, V-cycle iterates, and a
-mixed-precision solve. The kernels are those of the constant kernel (same banded
-Toeplitz-plus-Cross structure, other coefficients); tolerances as in tests/test_gpu_parity.py."""
+mixed-precision solve; for a >= 1/2 (finite-part entries, indefinite system) the iterates of
+the diverging V-cycle and its reported non-convergence. The kernels are those of the constant
+kernel (same banded Toeplitz-plus-Cross structure, other coefficients); tolerances as in
+tests/test_gpu_parity.py."""
 import numpy as np
 import pytest
 import sympy as sp
@@ -20,7 +22,8 @@ def dev(x, dtype=torch.float64):
 
 
 @pytest.mark.parametrize("variant", [SPD, NONSYM])
-@pytest.mark.parametrize("a", [sp.Integer(0), sp.Rational(1, 4)])
+@pytest.mark.parametrize("a", [sp.Integer(0), sp.Rational(1, 4), sp.Rational(1, 2),
+                               sp.Rational(3, 4)])
 def test_products_every_level(variant, a):
     K, r = 7, 16
     N = 1 << K
@@ -46,8 +49,10 @@ def test_products_every_level(variant, a):
 
 
 @pytest.mark.parametrize("variant", [SPD, NONSYM])
-def test_vcycle_iterates_match_oracle(variant):
-    K, r, a = 7, 16, sp.Rational(1, 4)
+@pytest.mark.parametrize("a", [sp.Rational(1, 4), sp.Rational(1, 2), sp.Rational(3, 4)])
+def test_vcycle_iterates_match_oracle(variant, a):
+    """Iterates after 1 and 3 cycles (for a = 1/2 the residual grows about sevenfold a cycle)."""
+    K, r = 7, 16
     N = 1 << K
     H = amg.Hierarchy(fractional.assemble(variant, N, r, a), kc=3)
     b = uniform_pm1(2 * N - 1, 9)
@@ -79,5 +84,20 @@ def test_mixed_solve_converges():
         S.apply(K, x, y)
         torch.cuda.synchronize()
         assert (torch.linalg.norm(b - y) / torch.linalg.norm(b)).item() < 1.05e-10
+    finally:
+        S.close()
+
+
+def test_finite_part_solve_reports_non_convergence():
+    """a = 1/2, N = 2^7, delta = 1/8: the V-cycle diverges (indefinite system); the solver stops
+    at max_iters with TPC_ENOTCONV and a relative residual above 1."""
+    K, r = 7, 16
+    N = 1 << K
+    S = tpc.Solver(r / N, 1.0 / N, kernel=1, kernel_a=0.5, max_iters=20)
+    try:
+        b = dev(uniform_pm1(S.n, 4))
+        x = torch.zeros_like(b)
+        rc, it, rel = S.solve(b, x, tol=1e-10)
+        assert rc == tpc.TPC_ENOTCONV and it == 20 and rel > 1.0
     finally:
         S.close()

@@ -10,7 +10,8 @@ from oracle.model import NONSYM, SPD
 
 
 @pytest.mark.parametrize("variant", [SPD, NONSYM])
-@pytest.mark.parametrize("a", [sp.Integer(0), sp.Rational(1, 4), sp.Rational(2, 5)])
+@pytest.mark.parametrize("a", [sp.Integer(0), sp.Rational(1, 4), sp.Rational(2, 5),
+                               sp.Rational(1, 2), sp.Rational(3, 4), sp.Rational(9, 10)])
 def test_levels_match_oracle(variant, a):
     K, r = 5, 3
     N = 1 << K
@@ -25,7 +26,7 @@ def test_levels_match_oracle(variant, a):
 def test_fractional_exponent_limits():
     with pytest.raises(tpc.TpcError) as ei:
         tpc.tpc_host_dense_level(0.25, 1 / 16, 4,
-                                 params=tpc.tpc_default_params(kernel=1, kernel_a=0.5))
+                                 params=tpc.tpc_default_params(kernel=1, kernel_a=1.0))
     assert ei.value.code == tpc.TPC_ENOTSUP
     with pytest.raises(tpc.TpcError):
         tpc.tpc_host_dense_level(0.25, 1 / 16, 4,

@@ -56,7 +56,7 @@ def test_levels_argument_sets_the_coarsest_level():
     ({"coarsest_level": 0}, 0.1, 2.0 ** -6, 0, tpc.TPC_EINVAL),
     ({}, 0.1, 2.0 ** -6, 5, tpc.TPC_EINVAL),           # more levels than K - kc + 1
     ({"variant": 5}, 0.1, 2.0 ** -6, 0, tpc.TPC_EINVAL),
-    ({"kernel": 1, "kernel_a": 0.5}, 0.1, 2.0 ** -6, 0, tpc.TPC_ENOTSUP),
+    ({"kernel": 1, "kernel_a": 1.0}, 0.1, 2.0 ** -6, 0, tpc.TPC_ENOTSUP),
     ({"kernel": 2}, 0.1, 2.0 ** -6, 0, tpc.TPC_EINVAL),
     ({"omega_pre": 2.5}, 0.1, 2.0 ** -6, 0, tpc.TPC_EINVAL),
     ({"m1": 0}, 0.1, 2.0 ** -6, 0, tpc.TPC_EINVAL),
