@@ -164,6 +164,54 @@ __device__ __forceinline__ const c2<T>* step_table(c2<T>* tab, const c2<T>* __re
   }
 }
 
+// FP32: the same copy as asynchronous copies issued together with a tile's, no barrier; the
+// caller waits for its copies (cp.async.wait_all) and passes a barrier before the first step.
+template <typename T>
+__device__ __forceinline__ const c2<T>* step_table_issue(c2<T>* tab, const c2<T>* __restrict__ g) {
+  if constexpr (sizeof(T) == 8) {
+    return g;
+  } else {
+    for (int j = threadIdx.x; j <= 512; j += blockDim.x) {
+      const unsigned d = (unsigned)__cvta_generic_to_shared(tab + j);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d),
+                   "l"(__cvta_generic_to_global(g + j))
+                   : "memory");
+    }
+    return tab;
+  }
+}
+// FP32: a thread's share of the table (entries threadIdx.x + k * blockDim.x), read early into
+// registers while the slots still hold something else, stored by step_table_store.
+constexpr int TW_PER_THREAD = (513 + 255) / 256;  // blockDim.x >= 256
+template <typename T> struct TabRegs { c2<T> v[TW_PER_THREAD]; };
+template <typename T>
+__device__ __forceinline__ TabRegs<T> step_table_load(const c2<T>* __restrict__ g) {
+  TabRegs<T> r{};
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int k = 0; k < TW_PER_THREAD; ++k) {
+      const int j = threadIdx.x + k * blockDim.x;
+      if (j <= 512) r.v[k] = g[j];
+    }
+  }
+  return r;
+}
+// Stores the loaded share (no barrier: the caller passes one before the first step).
+template <typename T>
+__device__ __forceinline__ const c2<T>* step_table_store(c2<T>* tab, const c2<T>* __restrict__ g,
+                                                         const TabRegs<T>& r) {
+  if constexpr (sizeof(T) == 8) {
+    return g;
+  } else {
+#pragma unroll
+    for (int k = 0; k < TW_PER_THREAD; ++k) {
+      const int j = threadIdx.x + k * blockDim.x;
+      if (j <= 512) tab[j] = r.v[k];
+    }
+    return tab;
+  }
+}
+
 template <int R> __device__ __forceinline__ int brev_r(int t) {
   return (int)(__brev((unsigned)t) >> (32 - (R == 16 ? 4 : R == 8 ? 3 : R == 4 ? 2 : 1)));
 }

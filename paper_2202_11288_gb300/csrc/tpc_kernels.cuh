@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_fwd_s
   c2<T>* s = tab + tw_slots<T>();
   __shared__ T red[FFT_THREADS / 32];
   const int logR1 = a.logR1, logC = a.logC, logL = a.logL;
-  const c2<T>* tw = step_table<T>(tab, a.twL);
+  const c2<T>* tw = step_table_issue<T>(tab, a.twL);  // in flight with the tile's copies
   const int C = 1 << logC;
   const int tile = 1 << (logR1 + logC);
   const long long c0 = (long long)blockIdx.x << logC;
@@ -527,6 +527,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_fwd_s
     }
   }
   (void)half;
+  if constexpr (sizeof(T) == 4) cp_async_wait_all();  // the step table
   __syncthreads();
   smem_dif<T, true>(s, logR1, logC, C, 1, tw, LOG_LMAX);
   if (sizeof(T) == 4 && tile >= 2 * (int)blockDim.x &&
@@ -635,6 +636,7 @@ __device__ __forceinline__ void mid_core(const LevelArgs<T>& a, const c2<T>* tw,
     if (threadIdx.x == 0 && a.pro != PRO_NONE) (void)operand<T>(a, a.N, a.pO, a.pro);  // middle w_o
     dot_total = block_sum<T>(dot, red);
   }
+  if constexpr (sizeof(T) == 4) cp_async_wait_all();  // the step table
   __syncthreads();
   smem_dif<T, false>(s, logL, nseq - 1, 1, L, tw, LOG_LMAX);
   if constexpr (MODE == MID_FWD || MODE == MID_FWD_REAL) {
@@ -707,7 +709,7 @@ __device__ __forceinline__ void mid_body(const LevelArgs<T>& a) {
   c2<T>* tab = reinterpret_cast<c2<T>*>(smem_raw);
   c2<T>* s = tab + tw_slots<T>();
   __shared__ T red[FFT_THREADS / 32];
-  const c2<T>* tw = step_table<T>(tab, a.twL);
+  const c2<T>* tw = step_table_issue<T>(tab, a.twL);  // in flight with the tile's copies
   long long b, b2;
   if (MODE == MID_FWD || MODE == MID_FWD_REAL || MODE == MID_WHOLE) {
     b = b2 = blockIdx.x;
@@ -765,6 +767,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_inv_s
   const long long c0 = (long long)blockIdx.x << logC;
   const bool fact = sizeof(T) == 4 && tile >= 2 * (int)blockDim.x &&
                     (long long)tile * C <= (long long)TW_TAB * blockDim.x;
+  const TabRegs<T> tr = step_table_load<T>(a.twL);  // in flight with the tile's copies
   InterTw32 it{};
   const float2* t2 = reinterpret_cast<const float2*>(tab);
   if (fact) {
@@ -811,8 +814,9 @@ __global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_inv_s
       }
     }
   }
-  __syncthreads();
-  const c2<T>* tw = step_table<T>(tab, a.twL);
+  __syncthreads();  // the factored twiddles' slots are free
+  const c2<T>* tw = step_table_store<T>(tab, a.twL, tr);
+  if constexpr (sizeof(T) == 4) __syncthreads();
   smem_dit<T, true>(s, logR1, logC, C, 1, tw, LOG_LMAX);
   const T w_o = a.x[a.N];
   const int half = 1 << (logR1 - 1);
