@@ -75,7 +75,8 @@ typedef struct tpc_params {
   int coarsest_level; /* kc, 1 <= kc <= K (default 3)                                      */
   int precision;      /* TPC_FP64, or TPC_MIXED: FP32 V-cycles inside FP64 refinement      */
   int max_iters;      /* outer iterations of tpc_solve (default 100)                       */
-  int inner_cycles;   /* TPC_MIXED: FP32 V-cycles per FP64 residual (default 6)            */
+  int inner_cycles;   /* TPC_MIXED: at most this many FP32 V-cycles per FP64 residual
+                         (default 6; see tpc_solve)                                        */
   int autotune;       /* 1 (default): tpc_setup times the tile widths of the strided FFT
                          passes of every level and keeps the fastest (results are the same
                          for every width); 0: the fixed rule                                */
@@ -100,9 +101,12 @@ int tpc_setup(const tpc_params* p, double delta, double h, int levels, void* cud
               tpc_handle** out);
 
 /* Solve A_K x = b to ||b - A x||_2 / ||b - A x0||_2 < tol (section 5 stopping rule) with
- * repeated V-cycles (Algorithm 2). With precision TPC_MIXED each outer iteration runs
- * inner_cycles FP32 V-cycle iterations on the FP64 residual (scaled to unit RMS) and adds the
- * correction in FP64; the residual and the stopping test are always FP64. b_dev, x_dev: device pointers to n_K doubles (caller
+ * repeated V-cycles (Algorithm 2). With precision TPC_MIXED each outer iteration runs FP32
+ * V-cycle iterations on the FP64 residual (scaled to unit RMS) and adds the correction in
+ * FP64; the residual and the stopping test are always FP64. The first outer iteration runs
+ * inner_cycles of them, each later one the fewest (at most inner_cycles) that reach tol / 4
+ * at the reduction per cycle observed in the iteration before (a deterministic function of
+ * the FP64 residual norms). b_dev, x_dev: device pointers to n_K doubles (caller
  * owned; they may not alias). use_x0 != 0 starts from the values in x_dev, else from 0.
  * iters_out / relres_out (host pointers, may be NULL) receive the number of outer
  * iterations and the final relative residual. Blocks the host until the result is in

@@ -98,9 +98,11 @@ struct tpc_handle {
   double* sumsq_host = nullptr;       // pinned
   double* hb = nullptr;               // device staging for tpc_solve_host (b, x)
   double* hx = nullptr;
-  cudaGraphExec_t iter_exec = nullptr;
+  // one outer iteration as a CUDA graph per count of inner FP32 cycles (the index; FP64: 1
+  // only), all captured at set-up
+  cudaGraphExec_t iter_exec[33] = {};
+  long long iter_nodes[33] = {};      // kernel nodes of iter_exec[c]
   cudaEvent_t ev = nullptr;           // marks the latest ||r||^2 read-back
-  long long iter_nodes = 0;           // kernel nodes of iter_exec
   long long launches = 0;             // kernels launched so far (see tpc_kernel_launches)
   std::string err;
   std::vector<void*> dev_allocs;
@@ -353,9 +355,9 @@ void enqueue_sumsq(tpc_handle* H, const double* r, long long n) {
 
 // One outer iteration.
 //   FP64:  u += B_K r; r = b - A u; ||r||^2.
-//   mixed: f = s r in FP32 (s = sqrt(n) / ||r||); inner_cycles FP32 iterations
+//   mixed: f = s r in FP32 (s = sqrt(n) / ||r||); `cycles` FP32 iterations
 //          e <- e + B_K (f - A e) from e = 0; u += e / s; then the FP64 residual and norm.
-void enqueue_iteration(tpc_handle* H) {
+void enqueue_iteration(tpc_handle* H, int cycles) {
   const long long n = H->d.lev[0].n;
   const int g = grid_for(n);
   if (H->prm.precision == TPC_MIXED) {
@@ -365,7 +367,7 @@ void enqueue_iteration(tpc_handle* H) {
     const float* ec = enqueue_vcycle<float>(H, S, 0, S.f[0], nullptr);
     k_copy<float><<<g, NTHREADS, 0, H->stream>>>(ec, H->acc32, n);
     H->launches += 1;
-    for (int c = 1; c < H->prm.inner_cycles; ++c) {
+    for (int c = 1; c < cycles; ++c) {
       matvec<float>(H, S, 0, H->acc32, S.f[0], H->res32, EPI_RESID, false);
       ec = enqueue_vcycle<float>(H, S, 0, H->res32, nullptr);
       k_axpy<float><<<g, NTHREADS, 0, H->stream>>>(H->acc32, ec, n);
@@ -380,6 +382,32 @@ void enqueue_iteration(tpc_handle* H) {
   }
   matvec<double>(H, H->d, 0, H->u, H->b, H->r0, EPI_RESID, false);
   enqueue_sumsq(H, H->r0, n);
+}
+
+int full_cycles(const tpc_handle* H) {
+  return H->prm.precision == TPC_MIXED ? H->prm.inner_cycles : 1;
+}
+
+// Captures and instantiates the iteration graph with `cycles` inner cycles unless it exists.
+int iter_graph(tpc_handle* H, int cycles) {
+  if (cycles < 1 || cycles > 32) return TPC_EINVAL;
+  if (H->iter_exec[cycles]) return TPC_OK;
+  cudaGraph_t graph = nullptr;
+  TPC_CUDA(H, cudaStreamBeginCapture(H->stream, cudaStreamCaptureModeThreadLocal));
+  const long long before = H->launches;
+  enqueue_iteration(H, cycles);
+  const long long nodes = H->launches - before;
+  H->launches = before;
+  cudaError_t ce = cudaStreamEndCapture(H->stream, &graph);
+  if (ce != cudaSuccess) return cuda_fail(H, ce, "cudaStreamEndCapture");
+  ce = cudaGraphInstantiate(&H->iter_exec[cycles], graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) {
+    H->iter_exec[cycles] = nullptr;
+    return cuda_fail(H, ce, "cudaGraphInstantiate");
+  }
+  H->iter_nodes[cycles] = nodes;
+  return TPC_OK;
 }
 
 template <typename T, bool NS>
@@ -740,24 +768,15 @@ int setup_device(tpc_handle* H) {
   TPC_CUDA(H, cudaMallocHost(&H->sumsq_host, sizeof(double)));
   TPC_CUDA(H, cudaEventCreateWithFlags(&H->ev, cudaEventDisableTiming));
   TPC_CUDA(H, cudaStreamSynchronize(H->stream));
-  // one outer iteration as a CUDA graph
-  cudaGraph_t graph = nullptr;
-  TPC_CUDA(H, cudaStreamBeginCapture(H->stream, cudaStreamCaptureModeThreadLocal));
-  const long long before = H->launches;
-  enqueue_iteration(H);
-  H->iter_nodes = H->launches - before;
-  H->launches = before;
-  cudaError_t ce = cudaStreamEndCapture(H->stream, &graph);
-  if (ce != cudaSuccess) return cuda_fail(H, ce, "cudaStreamEndCapture");
-  ce = cudaGraphInstantiate(&H->iter_exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (ce != cudaSuccess) return cuda_fail(H, ce, "cudaGraphInstantiate");
+  // every count the solve may choose, so that solves allocate nothing
+  for (int c = 1; c <= full_cycles(H); ++c) TPC_TRY(iter_graph(H, c));
   return TPC_OK;
 }
 
 void release(tpc_handle* H) {
   if (!H) return;
-  if (H->iter_exec) cudaGraphExecDestroy(H->iter_exec);
+  for (cudaGraphExec_t g : H->iter_exec)
+    if (g) cudaGraphExecDestroy(g);
   if (H->stream) cudaStreamSynchronize(H->stream);
   if (H->ev) cudaEventDestroy(H->ev);
   for (void* p : H->dev_allocs) cudaFreeAsync(p, H->stream);
@@ -783,9 +802,28 @@ struct SolveState {
   tpc_handle* H = nullptr;
   double* x_dev = nullptr;
   double tol = 0.0, r0 = 0.0, rel = 0.0;
+  double rel_prev = 0.0;  // relative residual before the latest iteration
+  int cycles = 0;         // inner cycles of the latest iteration
   int it = 0, status = TPC_OK;
   bool started = false, done = false;
 };
+
+// Inner FP32 cycles of the next mixed-precision iteration: the full count first; then the
+// fewest that reach tol / 4 if the residual keeps falling at the rate per cycle observed in
+// the previous iteration (the FP64 residuals measure it; a rate slowed by FP32 rounding only
+// asks for more cycles). Fewer cycles in the last iteration save whole V-cycles; a miss costs
+// one more iteration. FP64 solves run one V-cycle per iteration.
+int next_cycles(const SolveState& st) {
+  const int full = full_cycles(st.H);
+  if (st.H->prm.precision != TPC_MIXED || st.it == 0 || st.cycles < 1) return full;
+  const double red = st.rel / st.rel_prev;
+  if (!(red > 0.0 && red < 1.0)) return full;
+  const double rho = std::pow(red, 1.0 / st.cycles);
+  const double need = st.tol / (4.0 * st.rel);
+  if (!(rho > 0.0 && rho < 1.0) || !(need > 0.0 && need < 1.0)) return full;
+  const double c = std::ceil(std::log(need) / std::log(rho));
+  return c < 1.0 ? 1 : (c > full ? full : (int)c);
+}
 
 int solve_begin(SolveState& st, const double* b_dev, double* x_dev, double tol, int use_x0) {
   tpc_handle* H = st.H;
@@ -847,8 +885,12 @@ int solve_step(SolveState& st) {
     st.done = true;
     return TPC_OK;
   }
-  TPC_CUDA(H, cudaGraphLaunch(H->iter_exec, s));
-  H->launches += H->iter_nodes;
+  const int c = next_cycles(st);
+  if (!H->iter_exec[c]) return TPC_EINVAL;  // every count 1..full is captured at set-up
+  st.rel_prev = st.rel;
+  st.cycles = c;
+  TPC_CUDA(H, cudaGraphLaunch(H->iter_exec[c], s));
+  H->launches += H->iter_nodes[c];
   TPC_CUDA(H, cudaMemcpyAsync(H->sumsq_host, H->sumsq, sizeof(double), cudaMemcpyDeviceToHost, s));
   TPC_CUDA(H, cudaEventRecord(H->ev, s));
   return TPC_OK;
