@@ -49,6 +49,16 @@ template <typename T> constexpr int fft_threads() { return sizeof(T) == 8 ? 512 
 template <typename T> constexpr int fft_min_blocks() {
   return sizeof(T) == 8 ? 1 : TPC_F32_MIN_BLOCKS;
 }
+// FP32 strided passes of levels up to m = 2^LOG_M_HIGH_OCC: instances held to three resident
+// blocks per SM (at most 85 registers a thread, none spilled) instead of two. Alone a level
+// runs as fast either way (these levels are latency-bound); beside other solves (batches,
+// the server) the third slot per SM lets more of their blocks run at once. The largest
+// levels keep two (their radix-16 steps slow down under the register cap).
+#ifndef TPC_LOG_M_HIGH_OCC
+#define TPC_LOG_M_HIGH_OCC 18
+#endif
+constexpr int LOG_M_HIGH_OCC = TPC_LOG_M_HIGH_OCC;
+constexpr int F32_HIGH_OCC_BLOCKS = 3;
 // contiguous-block kernels
 template <typename T> constexpr int mid_min_blocks() {
   return sizeof(T) == 8 ? 1 : TPC_F32_MID_MIN_BLOCKS;
@@ -397,8 +407,8 @@ __device__ __forceinline__ void block0_pair(int q, int& p, int& pp) {
 // columns (stride L), each followed by the twiddle W_m^{c k}. One CTA: 2^logC columns.
 // ------------------------------------------------------------------------------------
 // PRO: the prologue, fixed at compile time (the launch selects the instance from a.pro).
-template <typename T, int IN, int PRO>
-__global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_fwd_strided(LevelArgs<T> a) {
+template <typename T, int IN, int PRO, int MINB = fft_min_blocks<T>()>
+__global__ void __launch_bounds__(fft_threads<T>(), MINB) k_fwd_strided(LevelArgs<T> a) {
   constexpr int pro = PRO;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2<T>* tab = reinterpret_cast<c2<T>*>(smem_raw);
@@ -755,8 +765,8 @@ __global__ void __launch_bounds__(fft_threads<T>(), mid_min_blocks<T>()) k_mid_f
 // Inverse strided pass: twiddle conj(W_m^{c k}), R1-point DIT per column, epilogue.
 // ------------------------------------------------------------------------------------
 // EPI: the epilogue, fixed at compile time (the launch selects the instance from a.epi).
-template <typename T, int EPI>
-__global__ void __launch_bounds__(fft_threads<T>(), fft_min_blocks<T>()) k_inv_strided(LevelArgs<T> a) {
+template <typename T, int EPI, int MINB = fft_min_blocks<T>()>
+__global__ void __launch_bounds__(fft_threads<T>(), MINB) k_inv_strided(LevelArgs<T> a) {
   constexpr int epi = EPI;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2<T>* tab = reinterpret_cast<c2<T>*>(smem_raw);
@@ -1070,25 +1080,45 @@ static __global__ void k_sumsq_final(const double* part, int np, double* out) {
 }
 
 // Launches of the strided passes with the prologue / epilogue instance chosen from the
-// arguments' runtime mode.
-template <typename T>
-inline void launch_fwd_strided(const LevelArgs<T>& a, int blocks, size_t smem, cudaStream_t s) {
+// arguments' runtime mode, and (FP32) the occupancy instance from the level size.
+template <typename T, int MB>
+inline void launch_fwd_strided_mb(const LevelArgs<T>& a, int blocks, size_t smem, cudaStream_t s) {
   const int nt = fft_threads<T>();
   switch (a.pro) {
-    case PRO_SMOOTH: k_fwd_strided<T, IN_PACK, PRO_SMOOTH><<<blocks, nt, smem, s>>>(a); break;
-    case PRO_RESTRICT: k_fwd_strided<T, IN_PACK, PRO_RESTRICT><<<blocks, nt, smem, s>>>(a); break;
-    case PRO_PROLONG: k_fwd_strided<T, IN_PACK, PRO_PROLONG><<<blocks, nt, smem, s>>>(a); break;
-    default: k_fwd_strided<T, IN_PACK, PRO_NONE><<<blocks, nt, smem, s>>>(a); break;
+    case PRO_SMOOTH: k_fwd_strided<T, IN_PACK, PRO_SMOOTH, MB><<<blocks, nt, smem, s>>>(a); break;
+    case PRO_RESTRICT: k_fwd_strided<T, IN_PACK, PRO_RESTRICT, MB><<<blocks, nt, smem, s>>>(a); break;
+    case PRO_PROLONG: k_fwd_strided<T, IN_PACK, PRO_PROLONG, MB><<<blocks, nt, smem, s>>>(a); break;
+    default: k_fwd_strided<T, IN_PACK, PRO_NONE, MB><<<blocks, nt, smem, s>>>(a); break;
+  }
+}
+template <typename T>
+inline void launch_fwd_strided(const LevelArgs<T>& a, int blocks, size_t smem, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (a.logm <= LOG_M_HIGH_OCC) {
+      launch_fwd_strided_mb<T, F32_HIGH_OCC_BLOCKS>(a, blocks, smem, s);
+      return;
+    }
+  }
+  launch_fwd_strided_mb<T, fft_min_blocks<T>()>(a, blocks, smem, s);
+}
+template <typename T, int MB>
+inline void launch_inv_strided_mb(const LevelArgs<T>& a, int blocks, size_t smem, cudaStream_t s) {
+  const int nt = fft_threads<T>();
+  switch (a.epi) {
+    case EPI_RESID: k_inv_strided<T, EPI_RESID, MB><<<blocks, nt, smem, s>>>(a); break;
+    case EPI_JACOBI: k_inv_strided<T, EPI_JACOBI, MB><<<blocks, nt, smem, s>>>(a); break;
+    default: k_inv_strided<T, EPI_APPLY, MB><<<blocks, nt, smem, s>>>(a); break;
   }
 }
 template <typename T>
 inline void launch_inv_strided(const LevelArgs<T>& a, int blocks, size_t smem, cudaStream_t s) {
-  const int nt = fft_threads<T>();
-  switch (a.epi) {
-    case EPI_RESID: k_inv_strided<T, EPI_RESID><<<blocks, nt, smem, s>>>(a); break;
-    case EPI_JACOBI: k_inv_strided<T, EPI_JACOBI><<<blocks, nt, smem, s>>>(a); break;
-    default: k_inv_strided<T, EPI_APPLY><<<blocks, nt, smem, s>>>(a); break;
+  if constexpr (sizeof(T) == 4) {
+    if (a.logm <= LOG_M_HIGH_OCC) {
+      launch_inv_strided_mb<T, F32_HIGH_OCC_BLOCKS>(a, blocks, smem, s);
+      return;
+    }
   }
+  launch_inv_strided_mb<T, fft_min_blocks<T>()>(a, blocks, smem, s);
 }
 // The contiguous-block kernel: the instance with L fixed at compile time for the FP32 levels
 // with L = 2^10 .. 2^12 (the largest ones), the general one otherwise.
@@ -1113,17 +1143,25 @@ inline cudaError_t mid_pair_smem_attrs(int bytes) {
 }
 
 // Raise the dynamic shared-memory limit of every strided-pass instance.
-template <typename T>
-inline cudaError_t strided_smem_attrs(int bytes) {
+template <typename T, int MB>
+inline cudaError_t strided_smem_attrs_mb(int bytes) {
   const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_fwd_strided<T, IN_PACK, PRO_NONE>, A, bytes)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_fwd_strided<T, IN_PACK, PRO_SMOOTH>, A, bytes)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_fwd_strided<T, IN_PACK, PRO_RESTRICT>, A, bytes)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_fwd_strided<T, IN_PACK, PRO_PROLONG>, A, bytes)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_inv_strided<T, EPI_APPLY>, A, bytes)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_inv_strided<T, EPI_RESID>, A, bytes)) != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_inv_strided<T, EPI_JACOBI>, A, bytes);
+  if ((e = cudaFuncSetAttribute(k_fwd_strided<T, IN_PACK, PRO_NONE, MB>, A, bytes)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_fwd_strided<T, IN_PACK, PRO_SMOOTH, MB>, A, bytes)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_fwd_strided<T, IN_PACK, PRO_RESTRICT, MB>, A, bytes)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_fwd_strided<T, IN_PACK, PRO_PROLONG, MB>, A, bytes)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_inv_strided<T, EPI_APPLY, MB>, A, bytes)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_inv_strided<T, EPI_RESID, MB>, A, bytes)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_inv_strided<T, EPI_JACOBI, MB>, A, bytes);
+}
+template <typename T>
+inline cudaError_t strided_smem_attrs(int bytes) {
+  if constexpr (sizeof(T) == 4) {
+    const cudaError_t e = strided_smem_attrs_mb<T, F32_HIGH_OCC_BLOCKS>(bytes);
+    if (e != cudaSuccess) return e;
+  }
+  return strided_smem_attrs_mb<T, fft_min_blocks<T>()>(bytes);
 }
 
 }  // namespace tpc
