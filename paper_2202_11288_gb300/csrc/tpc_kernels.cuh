@@ -578,9 +578,12 @@ __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_fwd_strided(LevelArg
 // data area s and the reduction scratch red in shared memory.
 // LOGL_CT, NSEQ_CT: when nonzero, log2 L and the number of blocks (1 or 2) as compile-time
 // constants, so that every step's strides, task counts and radix are folded into the code.
-template <typename T, int MODE, bool NS, int LOGL_CT = 0, int NSEQ_CT = 0>
+template <typename T, int MODE, bool NS, int LOGL_CT = 0, int NSEQ_CT = 0, int PRO_CT = -1,
+          int EPI_CT = -1>
 __device__ __forceinline__ void mid_core(const LevelArgs<T>& a, const c2<T>* tw, c2<T>* s,
                                          T* red, long long b, long long b2) {
+  const int pro = PRO_CT >= 0 ? PRO_CT : a.pro;
+  const int epi = EPI_CT >= 0 ? EPI_CT : a.epi;
   const int logL = LOGL_CT ? LOGL_CT : a.logL;
   const int L = 1 << logL;
   const int nseq = NSEQ_CT ? NSEQ_CT : ((b != b2) ? 2 : 1);
@@ -594,8 +597,8 @@ __device__ __forceinline__ void mid_core(const LevelArgs<T>& a, const c2<T>* tw,
       for (int u = 0; u < UNROLL; ++u) {
         const int i = e0 + u * blockDim.x;
         if (i < a.N) {
-          rv[u] = operand_load<T>(a, i, a.pro);
-          rw[u] = operand_load<T>(a, a.N + 1 + i, a.pro);
+          rv[u] = operand_load<T>(a, i, pro);
+          rw[u] = operand_load<T>(a, a.N + 1 + i, pro);
           qv[u] = (i < a.nq) ? a.q[i] : (T)0;
           zv[u] = (i < a.nq) ? a.zeta[i] : (T)0;
         }
@@ -606,8 +609,8 @@ __device__ __forceinline__ void mid_core(const LevelArgs<T>& a, const c2<T>* tw,
         if (i >= total) continue;
         c2<T> v = mk<T>(0, 0);
         if (i < a.N) {
-          const T xv = operand_finish<T>(a, i, rv[u], a.pA, a.pro);
-          const T xw = operand_finish<T>(a, a.N + 1 + i, rw[u], a.pD, a.pro);
+          const T xv = operand_finish<T>(a, i, rv[u], a.pA, pro);
+          const T xw = operand_finish<T>(a, a.N + 1 + i, rw[u], a.pD, pro);
           v = mk<T>(xv, xw);
           dot = fma(qv[u], xv, fma(zv[u], xw, dot));
         }
@@ -643,7 +646,7 @@ __device__ __forceinline__ void mid_core(const LevelArgs<T>& a, const c2<T>* tw,
   }
   T dot_total = 0;
   if (MODE == MID_WHOLE) {
-    if (threadIdx.x == 0 && a.pro != PRO_NONE) (void)operand<T>(a, a.N, a.pO, a.pro);  // middle w_o
+    if (threadIdx.x == 0 && pro != PRO_NONE) (void)operand<T>(a, a.N, a.pO, pro);  // middle w_o
     dot_total = block_sum<T>(dot, red);
   }
   if constexpr (sizeof(T) == 4) cp_async_wait_all();  // the step table
@@ -693,18 +696,18 @@ __device__ __forceinline__ void mid_core(const LevelArgs<T>& a, const c2<T>* tw,
 #pragma unroll
       for (int u = 0; u < UNROLL; ++u) {
         const int i = i0 + u * blockDim.x;
-        if (i < a.N) er[u] = epi_load<T>(a, i, a.epi);
+        if (i < a.N) er[u] = epi_load<T>(a, i, epi);
       }
 #pragma unroll
       for (int u = 0; u < UNROLL; ++u) {
         const int i = i0 + u * blockDim.x;
         if (i < a.N) {
           const c2<T> y = s[pad16(i)];
-          epi_store<T>(a, i, er[u], y.x, y.y, w_o, a.epi);
+          epi_store<T>(a, i, er[u], y.x, y.y, w_o, epi);
         }
       }
     }
-    if (threadIdx.x == 0) epi_middle<T>(a, dot_total, w_o, a.epi);
+    if (threadIdx.x == 0) epi_middle<T>(a, dot_total, w_o, epi);
   } else {
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
       const int sq = e >> logL, i = e & (L - 1);
@@ -897,7 +900,8 @@ __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_inv_strided(LevelArg
 // Descent, level i: u = omega D^{-1} (restriction of the finer residual), r = f - A u
 // (PRO_RESTRICT + EPI_RESID); coarsest: f = restriction, e = A^{-1} f; ascent: u + P e_c then
 // one damped Jacobi sweep (PRO_PROLONG + EPI_JACOBI). Same arithmetic, buffers and order as
-// the per-level launches, without one launch per product.
+// the per-level launches, without one launch per product; the two modes are compile-time
+// constants of the two loops.
 // ------------------------------------------------------------------------------------
 constexpr int BOTTOM_MAX_LEVELS = 12;
 template <typename T> struct BottomPlan {
@@ -930,7 +934,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), 1) k_vcycle_bottom(const Bot
   const c2<T>* tw = step_table<T>(tab, bp->pre[0].twL);
   for (int i = 0; i < nlev; ++i) {
     copy_args<T>(&la, &bp->pre[i]);
-    mid_core<T, MID_WHOLE, NS>(la, tw, s, red, 0, 0);
+    mid_core<T, MID_WHOLE, NS, 0, 0, PRO_RESTRICT, EPI_RESID>(la, tw, s, red, 0, 0);
     __syncthreads();
   }
   {
@@ -950,7 +954,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), 1) k_vcycle_bottom(const Bot
   }
   for (int i = nlev - 1; i >= 0; --i) {
     copy_args<T>(&la, &bp->post[i]);
-    mid_core<T, MID_WHOLE, NS>(la, tw, s, red, 0, 0);
+    mid_core<T, MID_WHOLE, NS, 0, 0, PRO_PROLONG, EPI_JACOBI>(la, tw, s, red, 0, 0);
     __syncthreads();
   }
 }
