@@ -203,7 +203,7 @@ void plan_level(DevLevel<T>& L) {
 template <typename T>
 LevelArgs<T> level_args(const Hier<T>& G, const DevLevel<T>& L) {
   LevelArgs<T> a{};
-  a.N = L.N;
+  a.N = (int)L.N;  // levels have m <= 2^23
   a.logm = L.logm;
   a.logR1 = L.logR1;
   a.logL = L.logL;
@@ -216,8 +216,8 @@ LevelArgs<T> level_args(const Hier<T>& G, const DevLevel<T>& L) {
   a.q = L.q;
   a.xi = L.xi;
   a.zeta = L.zeta;
-  a.nq = L.nq;
-  a.np = L.np;
+  a.nq = (int)L.nq;
+  a.np = (int)L.np;
   a.bl = L.bl;
   a.bd = L.bd;
   a.bu = L.bu;

@@ -74,8 +74,11 @@ enum Pro { PRO_NONE = 0, PRO_SMOOTH = 1, PRO_RESTRICT = 2, PRO_PROLONG = 3 };
 enum MidMode { MID_PAIR = 0, MID_WHOLE = 1, MID_FWD = 2, MID_FWD_REAL = 3 };
 enum InMode { IN_PACK = 0, IN_REAL = 1 };
 
+// Element indices inside a level's product are 32-bit: m <= 2^23 (the strided passes take
+// R1 <= 2^11 rows of L <= 2^12 columns), so every index of z, the vectors and the tables is
+// below 2^24.
 template <typename T> struct LevelArgs {
-  long long N;           // N_k
+  int N;                 // N_k
   int logm, logR1, logL, logC;
   const T* sA;           // spectra at bit-reversed positions, already divided by 2m
   const T* sD;
@@ -86,7 +89,7 @@ template <typename T> struct LevelArgs {
   const T* xi;
   const T* zeta;
   T o;
-  long long nq, np;      // q, zeta are zero from index nq on; p, xi from index np on
+  int nq, np;            // q, zeta are zero from index nq on; p, xi from index np on
   // weakly singular model (else null): tridiagonal band of the concatenated index and the
   // per-entry Jacobi weights (pvec: pre-smoothing, for the prologue; wvec: this product's)
   const T* bl;
@@ -172,17 +175,17 @@ __device__ __forceinline__ float2 inter_tw32(const InterTw32& it, const float2* 
 }
 
 template <typename T>
-__device__ __forceinline__ c2<T> inter_tw(const c2<T>* __restrict__ twm, long long e, int logm) {
+__device__ __forceinline__ c2<T> inter_tw(const c2<T>* __restrict__ twm, int e, int logm) {
   if constexpr (sizeof(T) == 8) {
     return __ldg(twm + e);
   } else {
-    return w_f32((int)e, logm);  // e < m <= 2^24
+    return w_f32(e, logm);  // e < m <= 2^23
   }
 }
 
 // Restriction I_k^{k-1} (section 3.1) at coarse index I: (r[2I] + 2 r[2I+1] + r[2I+2]) / 4.
 template <typename T>
-__device__ __forceinline__ T restrict_at(const T* __restrict__ r, long long I) {
+__device__ __forceinline__ T restrict_at(const T* __restrict__ r, int I) {
   return (T)0.25 * r[2 * I] + (T)0.5 * r[2 * I + 1] + (T)0.25 * r[2 * I + 2];
 }
 // Operand entry j of the product (concatenated index), formed by the prologue; w is the
@@ -193,17 +196,17 @@ template <typename T> struct Raw {
 };
 // The coarse-correction values of PRO_PROLONG at fine index j (a1, a2 of Raw).
 template <typename T>
-__device__ __forceinline__ void prolong_load(const LevelArgs<T>& a, long long j, Raw<T>& r) {
+__device__ __forceinline__ void prolong_load(const LevelArgs<T>& a, int j, Raw<T>& r) {
   if (j & 1) {
     r.a1 = a.ec[(j - 1) / 2];
   } else {
-    const long long I = j / 2;
+    const int I = j / 2;
     r.a1 = (I >= 1) ? a.ec[I - 1] : (T)0;
     r.a2 = (I < a.N) ? a.ec[I] : (T)0;  // coarse size n_{k-1} = N_k
   }
 }
 template <typename T>
-__device__ __forceinline__ Raw<T> operand_load(const LevelArgs<T>& a, long long j, int pro) {
+__device__ __forceinline__ Raw<T> operand_load(const LevelArgs<T>& a, int j, int pro) {
   Raw<T> r{0, 0, 0};
   if (pro == PRO_NONE) {
     r.a0 = a.x[j];
@@ -220,7 +223,7 @@ __device__ __forceinline__ Raw<T> operand_load(const LevelArgs<T>& a, long long 
   return r;
 }
 template <typename T>
-__device__ __forceinline__ T operand_finish(const LevelArgs<T>& a, long long j, const Raw<T>& r,
+__device__ __forceinline__ T operand_finish(const LevelArgs<T>& a, int j, const Raw<T>& r,
                                             T w, int pro) {
   if (pro == PRO_NONE) return r.a0;
   if ((pro == PRO_SMOOTH || pro == PRO_RESTRICT) && a.pvec) w = a.pvec[j];
@@ -241,7 +244,7 @@ __device__ __forceinline__ T operand_finish(const LevelArgs<T>& a, long long j, 
   return v;
 }
 template <typename T>
-__device__ __forceinline__ T operand(const LevelArgs<T>& a, long long j, T w, int pro) {
+__device__ __forceinline__ T operand(const LevelArgs<T>& a, int j, T w, int pro) {
   return operand_finish<T>(a, j, operand_load<T>(a, j, pro), w, pro);
 }
 
@@ -292,17 +295,17 @@ template <typename T> struct EpiRaw {
 };
 // (B x)_j of the tridiagonal band at concatenated index j (0 <= j < n).
 template <typename T>
-__device__ __forceinline__ T band_at(const LevelArgs<T>& a, long long j) {
-  const long long n = 2 * a.N + 1;
+__device__ __forceinline__ T band_at(const LevelArgs<T>& a, int j) {
+  const int n = 2 * a.N + 1;
   T s = a.bd[j] * a.x[j];
   if (j > 0) s = fma(a.bl[j], a.x[j - 1], s);
   if (j + 1 < n) s = fma(a.bu[j], a.x[j + 1], s);
   return s;
 }
 template <typename T>
-__device__ __forceinline__ EpiRaw<T> epi_load(const LevelArgs<T>& a, long long i, int epi) {
+__device__ __forceinline__ EpiRaw<T> epi_load(const LevelArgs<T>& a, int i, int epi) {
   EpiRaw<T> r{0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  const long long iw = a.N + 1 + i;
+  const int iw = a.N + 1 + i;
   if (a.bd) {
     r.bv = band_at<T>(a, i);
     r.bw = band_at<T>(a, iw);
@@ -326,11 +329,11 @@ __device__ __forceinline__ EpiRaw<T> epi_load(const LevelArgs<T>& a, long long i
   return r;
 }
 template <typename T>
-__device__ __forceinline__ void epi_store(const LevelArgs<T>& a, long long i, const EpiRaw<T>& r,
+__device__ __forceinline__ void epi_store(const LevelArgs<T>& a, int i, const EpiRaw<T>& r,
                                           T ax_v, T ax_w, T w_o, int epi) {
   const T yv = fma(r.p, w_o, ax_v) + r.bv;
   const T yw = fma(r.xi, w_o, ax_w) + r.bw;
-  const long long iw = a.N + 1 + i;
+  const int iw = a.N + 1 + i;
   if (epi == EPI_APPLY) {
     a.y[i] = yv;
     a.y[iw] = yw;
@@ -345,7 +348,7 @@ __device__ __forceinline__ void epi_store(const LevelArgs<T>& a, long long i, co
 
 template <typename T>
 __device__ __forceinline__ void epi_middle(const LevelArgs<T>& a, T dot, T w_o, int epi) {
-  const long long im = a.N;
+  const int im = a.N;
   const T ym = fma(a.o, w_o, dot) + (a.bd ? band_at<T>(a, im) : (T)0);
   if (epi == EPI_APPLY)
     a.y[im] = ym;
@@ -362,7 +365,7 @@ template <typename T> struct Spec {
   c2<T> sb, sc;
 };
 template <typename T, bool NS>
-__device__ __forceinline__ Spec<T> spec_load(const LevelArgs<T>& a, long long P) {
+__device__ __forceinline__ Spec<T> spec_load(const LevelArgs<T>& a, int P) {
   Spec<T> r;
   r.sa = a.sA[P];
   r.sd = a.sD[P];
@@ -418,7 +421,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_fwd_strided(LevelArg
   const c2<T>* tw = step_table_issue<T>(tab, a.twL);  // in flight with the tile's copies
   const int C = 1 << logC;
   const int tile = 1 << (logR1 + logC);
-  const long long c0 = (long long)blockIdx.x << logC;
+  const int c0 = (int)blockIdx.x << logC;
   const int half = 1 << (logR1 - 1);
   T dot = 0;
   // FP32 (bound by memory latency): the raw operand values and the Cross rows q, zeta arrive by
@@ -432,7 +435,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_fwd_strided(LevelArg
     const T* src = (PRO == PRO_SMOOTH) ? a.f : a.x;
     for (int e = threadIdx.x; e < ht; e += blockDim.x) {
       const int t = e >> logC, cc = e & (C - 1);
-      const long long P = c0 + cc + ((long long)t << logL);
+      const int P = c0 + cc + (t << logL);
       c2<T>* lo = s + pad16(e);
       c2<T>* hi = s + pad16(e + ht);
       if (P < a.N) {
@@ -457,7 +460,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_fwd_strided(LevelArg
         for (int u = 0; u < UNROLL; ++u) {
           const int e = e0 + u * blockDim.x;
           const int t = e >> logC, cc = e & (C - 1);
-          const long long P = c0 + cc + ((long long)t << logL);
+          const int P = c0 + cc + (t << logL);
           if (e < ht && P < a.N) {
             prolong_load<T>(a, P, rv[u]);
             prolong_load<T>(a, a.N + 1 + P, rw[u]);
@@ -469,7 +472,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_fwd_strided(LevelArg
         const int e = e0 + u * blockDim.x;
         if (e >= ht) continue;
         const int t = e >> logC, cc = e & (C - 1);
-        const long long P = c0 + cc + ((long long)t << logL);
+        const int P = c0 + cc + (t << logL);
         c2<T>* lo = s + pad16(e);
         c2<T>* hi = s + pad16(e + ht);
         if (P < a.N) {
@@ -495,7 +498,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_fwd_strided(LevelArg
       for (int u = 0; u < UNROLL; ++u) {
         const int e = e0 + u * blockDim.x;
         const int t = e >> logC, cc = e & (C - 1);
-        const long long P = c0 + cc + ((long long)t << logL);
+        const int P = c0 + cc + (t << logL);
         ok[u] = (e < (tile >> 1)) && P < a.N;
         if (ok[u]) {
           rv[u] = operand_load<T>(a, P, pro);
@@ -509,7 +512,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_fwd_strided(LevelArg
         const int e = e0 + u * blockDim.x;
         if (e >= (tile >> 1)) continue;
         const int t = e >> logC, cc = e & (C - 1);
-        const long long P = c0 + cc + ((long long)t << logL);
+        const int P = c0 + cc + (t << logL);
         c2<T> v = mk<T>(0, 0);
         if (ok[u]) {
           const T xv = operand_finish<T>(a, P, rv[u], a.pA, pro);
@@ -527,7 +530,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_fwd_strided(LevelArg
       for (int u = 0; u < UNROLL; ++u) {
         const int e = e0 + u * blockDim.x;
         const int t = e >> logC, cc = e & (C - 1);
-        if (e < tile) rv[u] = a.real_in[c0 + cc + ((long long)t << logL)];
+        if (e < tile) rv[u] = a.real_in[c0 + cc + (t << logL)];
       }
 #pragma unroll
       for (int u = 0; u < UNROLL; ++u) {
@@ -549,16 +552,16 @@ __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_fwd_strided(LevelArg
     int j = 0;
     for (int e = threadIdx.x; e < tile; e += blockDim.x, ++j) {
       const int t = e >> logC, cc = e & (C - 1);
-      const long long P = c0 + cc + ((long long)t << logL);
+      const int P = c0 + cc + (t << logL);
       const float2 w = inter_tw32(it, t2, j);
       a.z[P] = cmul<T>(s[pad16(e)], mk<T>((T)w.x, (T)w.y));
     }
   } else {
     for (int e = threadIdx.x; e < tile; e += blockDim.x) {
       const int t = e >> logC, cc = e & (C - 1);
-      const long long c = c0 + cc;
-      const long long P = c + ((long long)t << logL);
-      const long long kb = (long long)brev_bits((unsigned)t, logR1);
+      const int c = c0 + cc;
+      const int P = c + (t << logL);
+      const int kb = (int)brev_bits((unsigned)t, logR1);
       a.z[P] = cmul<T>(s[pad16(e)], inter_tw<T>(a.twm, c * kb, a.logm));
     }
   }
@@ -581,7 +584,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_fwd_strided(LevelArg
 template <typename T, int MODE, bool NS, int LOGL_CT = 0, int NSEQ_CT = 0, int PRO_CT = -1,
           int EPI_CT = -1>
 __device__ __forceinline__ void mid_core(const LevelArgs<T>& a, const c2<T>* tw, c2<T>* s,
-                                         T* red, long long b, long long b2) {
+                                         T* red, int b, int b2) {
   const int pro = PRO_CT >= 0 ? PRO_CT : a.pro;
   const int epi = EPI_CT >= 0 ? EPI_CT : a.epi;
   const int logL = LOGL_CT ? LOGL_CT : a.logL;
@@ -621,7 +624,7 @@ __device__ __forceinline__ void mid_core(const LevelArgs<T>& a, const c2<T>* tw,
     // FP32: asynchronous copies, all of a thread's copies in flight at once
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
       const int sq = e >> logL, i = e & (L - 1);
-      cp_async8(s + pad16(e), a.z + (sq ? b2 : b) * (long long)L + i);
+      cp_async8(s + pad16(e), a.z + (sq ? b2 : b) * L + i);
     }
     cp_async_wait_all();
   } else {
@@ -631,7 +634,7 @@ __device__ __forceinline__ void mid_core(const LevelArgs<T>& a, const c2<T>* tw,
       for (int u = 0; u < 2 * UNROLL; ++u) {
         const int e = e0 + u * blockDim.x;
         const int sq = e >> logL, i = e & (L - 1);
-        const long long P = (sq ? b2 : b) * (long long)L + i;
+        const int P = (sq ? b2 : b) * L + i;
         if (e < total) {
           if constexpr (MODE == MID_FWD_REAL) v[u] = mk<T>(a.real_in[P], 0);
           else v[u] = a.z[P];
@@ -653,7 +656,7 @@ __device__ __forceinline__ void mid_core(const LevelArgs<T>& a, const c2<T>* tw,
   __syncthreads();
   smem_dif<T, false>(s, logL, nseq - 1, 1, L, tw, LOG_LMAX);
   if constexpr (MODE == MID_FWD || MODE == MID_FWD_REAL) {
-    for (int e = threadIdx.x; e < L; e += blockDim.x) a.z[b * (long long)L + e] = s[pad16(e)];
+    for (int e = threadIdx.x; e < L; e += blockDim.x) a.z[b * L + e] = s[pad16(e)];
     return;
   }
   // spectral product: ntask frequency pairs; task i -> (lower, upper) shared-memory slots and
@@ -667,7 +670,7 @@ __device__ __forceinline__ void mid_core(const LevelArgs<T>& a, const c2<T>* tw,
       if (i < ntask) {
         int p = i, pp;
         if (b == 0) block0_pair(i, p, pp);
-        sp[u] = spec_load<T, NS>(a, b * (long long)L + p);
+        sp[u] = spec_load<T, NS>(a, b * L + p);
       }
     }
 #pragma unroll
@@ -711,7 +714,7 @@ __device__ __forceinline__ void mid_core(const LevelArgs<T>& a, const c2<T>* tw,
   } else {
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
       const int sq = e >> logL, i = e & (L - 1);
-      a.z[(sq ? b2 : b) * (long long)L + i] = s[pad16(e)];
+      a.z[(sq ? b2 : b) * L + i] = s[pad16(e)];
     }
   }
 }
@@ -723,7 +726,7 @@ __device__ __forceinline__ void mid_body(const LevelArgs<T>& a) {
   c2<T>* s = tab + tw_slots<T>();
   __shared__ T red[FFT_THREADS / 32];
   const c2<T>* tw = step_table_issue<T>(tab, a.twL);  // in flight with the tile's copies
-  long long b, b2;
+  int b, b2;
   if (MODE == MID_FWD || MODE == MID_FWD_REAL || MODE == MID_WHOLE) {
     b = b2 = blockIdx.x;
   } else {
@@ -731,10 +734,10 @@ __device__ __forceinline__ void mid_body(const LevelArgs<T>& a) {
     if (cta < 2) {
       b = b2 = cta;
     } else {
-      const long long j = cta - 1;
-      const int g = 63 - __clzll(j);
-      b = j + (1LL << g);
-      b2 = 3 * (2LL << g) - 1 - b;
+      const int j = cta - 1;
+      const int g = 31 - __clz(j);
+      b = j + (1 << g);
+      b2 = 3 * (2 << g) - 1 - b;
     }
   }
   if constexpr (LOGL_CT > 0) {
@@ -777,7 +780,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_inv_strided(LevelArg
   const int logR1 = a.logR1, logC = a.logC, logL = a.logL;
   const int C = 1 << logC;
   const int tile = 1 << (logR1 + logC);
-  const long long c0 = (long long)blockIdx.x << logC;
+  const int c0 = (int)blockIdx.x << logC;
   const bool fact = sizeof(T) == 4 && tile >= 2 * (int)blockDim.x &&
                     (long long)tile * C <= (long long)TW_TAB * blockDim.x;
   const TabRegs<T> tr = step_table_load<T>(a.twL);  // in flight with the tile's copies
@@ -792,7 +795,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_inv_strided(LevelArg
     // asynchronous copies of the tile, then the twiddle in place (each thread its own slots)
     for (int e = threadIdx.x; e < tile; e += blockDim.x) {
       const int t = e >> logC, cc = e & (C - 1);
-      cp_async8(s + pad16(e), a.z + c0 + cc + ((long long)t << logL));
+      cp_async8(s + pad16(e), a.z + c0 + cc + (t << logL));
     }
     cp_async_wait_all();
     int j = 0;
@@ -803,7 +806,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_inv_strided(LevelArg
         w = mk<T>((T)wf.x, (T)wf.y);
       } else {
         const int t = e >> logC, cc = e & (C - 1);
-        const long long kb = (long long)brev_bits((unsigned)t, logR1);
+        const int kb = (int)brev_bits((unsigned)t, logR1);
         w = inter_tw<T>(a.twm, (c0 + cc) * kb, a.logm);
       }
       s[pad16(e)] = cmulc<T>(s[pad16(e)], w);
@@ -815,14 +818,14 @@ __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_inv_strided(LevelArg
       for (int u = 0; u < 2 * UNROLL; ++u) {
         const int e = e0 + u * blockDim.x;
         const int t = e >> logC, cc = e & (C - 1);
-        if (e < tile) v[u] = a.z[c0 + cc + ((long long)t << logL)];
+        if (e < tile) v[u] = a.z[c0 + cc + (t << logL)];
       }
 #pragma unroll
       for (int u = 0; u < 2 * UNROLL; ++u) {
         const int e = e0 + u * blockDim.x;
         if (e >= tile) continue;
         const int t = e >> logC, cc = e & (C - 1);
-        const long long kb = (long long)brev_bits((unsigned)t, logR1);
+        const int kb = (int)brev_bits((unsigned)t, logR1);
         s[pad16(e)] = cmulc<T>(v[u], inter_tw<T>(a.twm, (c0 + cc) * kb, a.logm));
       }
     }
@@ -840,7 +843,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_inv_strided(LevelArg
   if constexpr (ASYNC_F) {
     for (int e = threadIdx.x; e < nout; e += blockDim.x) {
       const int t = e >> logC, cc = e & (C - 1);
-      const long long P = c0 + cc + ((long long)t << logL);
+      const int P = c0 + cc + (t << logL);
       if (P < a.N) {
         c2<T>* hi = s + pad16(e + nout);
         cp_async4(&hi->x, a.f + P);
@@ -855,7 +858,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_inv_strided(LevelArg
     for (int u = 0; u < UNROLL; ++u) {
       const int e = e0 + u * blockDim.x;
       const int t = e >> logC, cc = e & (C - 1);
-      const long long P = c0 + cc + ((long long)t << logL);
+      const int P = c0 + cc + (t << logL);
       if (e < nout && P < a.N) {
         if constexpr (ASYNC_F) {
           er[u] = epi_load<T>(a, P, EPI_APPLY);  // p, xi only
@@ -879,7 +882,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_inv_strided(LevelArg
     for (int u = 0; u < UNROLL; ++u) {
       const int e = e0 + u * blockDim.x;
       const int t = e >> logC, cc = e & (C - 1);
-      const long long P = c0 + cc + ((long long)t << logL);
+      const int P = c0 + cc + (t << logL);
       if (e < nout && P < a.N) {
         const c2<T> y = s[pad16(e)];
         epi_store<T>(a, P, er[u], y.x, y.y, w_o, epi);

@@ -177,7 +177,7 @@ extern "C" int tpc_apply_noalloc(long long N, const double* tA, const double* tB
   double* parts = reinterpret_cast<double*>(base + OFF_PART);
 
   LevelArgs<double> a{};
-  a.N = N;
+  a.N = (int)N;  // N <= 32767 (checked above)
   a.logm = logm;
   a.logR1 = logR1;
   a.logL = logL;
@@ -190,8 +190,8 @@ extern "C" int tpc_apply_noalloc(long long N, const double* tA, const double* tB
   a.q = q;
   a.xi = xi;
   a.zeta = zeta;
-  a.nq = N;  // full support (the caller's vectors are not scanned)
-  a.np = N;
+  a.nq = (int)N;  // full support (the caller's vectors are not scanned)
+  a.np = (int)N;
   a.o = o;
   a.twm = twm;
   a.twL = twL;
