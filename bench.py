@@ -51,7 +51,7 @@ def f32_bytes_per_point(r, N):
     return (12.0 + 4.0 * frac, 24.0, 16.0 + 4.0 * frac)
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP32 finest kernels, from ncu
 # (profiles/fp32_transform_kernels_N2e22.md), keyed by (K, kernel index); unknown for other sizes
-F32_TRAFFIC = {(22, 0): 54.6e6, (22, 1): 154.4e6, (22, 2): 115.1e6}
+F32_TRAFFIC = {(22, 0): 54.3e6, (22, 1): 154.3e6, (22, 2): 115.9e6}
 
 
 def measured_hbm_gbs():
