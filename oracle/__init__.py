@@ -24,8 +24,9 @@ Contents
              the 2x2 Toeplitz block matrix), assembled from exact element integrals, and its
              BDF4 time stepping for Table 1.
 ``fractional`` -- a fractional kernel |s|^{-(1+2a)} with a horizon (not in the paper): exact
-             element integrals of the same collocation. PARITY UNPINNED by the paper (pinned
-             only by mathematics: a = -1/2 is the printed matrix, exactness on quadratics).
+             element integrals of the same collocation, Hadamard finite parts for a >= 1/2.
+             PARITY UNPINNED by the paper (pinned only by mathematics: a = -1/2 is the printed
+             matrix, exactness on quadratics, Hadamard's definition by quadrature).
 ``large``  -- the same finest-level operator for sizes where a dense matrix does not fit:
              selected dense rows, and the product computed with numpy's FFT as the
              convolution step (section 3.2, eq. ccs3.4).
