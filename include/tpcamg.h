@@ -80,6 +80,10 @@ typedef struct tpc_params {
   int autotune;       /* 1 (default): tpc_setup times the tile widths of the strided FFT
                          passes of every level and keeps the fastest (results are the same
                          for every width); 0: the fixed rule                                */
+  int poison;         /* checking aid, 0 (default) or 1: every device buffer of the handle
+                         is filled with all-ones bytes (NaN in FP32 and FP64) when it is
+                         allocated, so that a value read before it is written shows up as
+                         NaN in the results; results are otherwise identical              */
 } tpc_params;
 
 typedef struct tpc_handle tpc_handle;

@@ -43,7 +43,7 @@ class TpcParams(ctypes.Structure):
                 ("omega_pre", ctypes.c_double), ("omega_post", ctypes.c_double),
                 ("coarsest_level", ctypes.c_int), ("precision", ctypes.c_int),
                 ("max_iters", ctypes.c_int), ("inner_cycles", ctypes.c_int),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("poison", ctypes.c_int)]
 
 
 class TpcServerConfig(ctypes.Structure):

@@ -4,6 +4,7 @@
 // tpc_vcycle) and FP32 (precision = TPC_MIXED: the inner V-cycles). The FP32 spectra are the
 // FP64 spectra rounded once.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -111,6 +112,15 @@ struct tpc_handle {
 
 namespace {
 
+// NVTX ranges (header-only NVTX3: no cost unless a profiler is attached) mark set-up phases,
+// solves and outer iterations on the host timeline.
+struct NvtxScope {
+  explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+  ~NvtxScope() { nvtxRangePop(); }
+  NvtxScope(const NvtxScope&) = delete;
+  NvtxScope& operator=(const NvtxScope&) = delete;
+};
+
 int cuda_fail(tpc_handle* H, cudaError_t e, const char* what) {
   std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
   if (H) H->err = msg;
@@ -145,6 +155,10 @@ int dalloc(tpc_handle* H, P** ptr, size_t count) {
   H->dev_allocs.push_back(v);
   H->dev_bytes += count * sizeof(P) + 16;
   *ptr = reinterpret_cast<P*>(v);
+  if (H->prm.poison) {  // all bits set: NaN in FP32 and FP64
+    e = cudaMemsetAsync(v, 0xFF, count * sizeof(P) + 16, H->stream);
+    if (e != cudaSuccess) return cuda_fail(H, e, "cudaMemsetAsync (poison)");
+  }
   return TPC_OK;
 }
 
@@ -692,6 +706,7 @@ int autotune_levels(tpc_handle* H, Hier<T>& G, bool only_finest) {
 }
 
 int setup_device(tpc_handle* H) {
+  NvtxScope range("tpc_setup: device levels, spectra, autotune, graphs");
   const HostHierarchy& HH = H->host;
   const int nlev = (int)HH.lev.size();
   const bool mixed = H->prm.precision == TPC_MIXED;
@@ -748,6 +763,7 @@ int setup_device(tpc_handle* H) {
     }
   }
   if (H->prm.autotune) {
+    NvtxScope tune("tpc_setup: autotune");
     if (mixed) {
       TPC_TRY(autotune_levels<float>(H, H->s, false));
       TPC_TRY(autotune_levels<double>(H, H->d, true));
@@ -769,6 +785,7 @@ int setup_device(tpc_handle* H) {
   TPC_CUDA(H, cudaEventCreateWithFlags(&H->ev, cudaEventDisableTiming));
   TPC_CUDA(H, cudaStreamSynchronize(H->stream));
   // every count the solve may choose, so that solves allocate nothing
+  NvtxScope graphs("tpc_setup: iteration graphs");
   for (int c = 1; c <= full_cycles(H); ++c) TPC_TRY(iter_graph(H, c));
   return TPC_OK;
 }
@@ -806,6 +823,7 @@ struct SolveState {
   int cycles = 0;         // inner cycles of the latest iteration
   int it = 0, status = TPC_OK;
   bool started = false, done = false;
+  nvtxRangeId_t iter_range = 0;  // NVTX range of the iteration in flight (0: none)
 };
 
 // Inner FP32 cycles of the next mixed-precision iteration: the full count first; then the
@@ -854,6 +872,10 @@ int solve_begin(SolveState& st, const double* b_dev, double* x_dev, double tol, 
 // Call when H->ev has completed. Decides and, if the solve goes on, enqueues one iteration.
 int solve_step(SolveState& st) {
   tpc_handle* H = st.H;
+  if (st.iter_range) {
+    nvtxRangeEnd(st.iter_range);
+    st.iter_range = 0;
+  }
   cudaStream_t s = H->stream;
   const double ss = *H->sumsq_host;
   if (!st.started) {
@@ -889,6 +911,14 @@ int solve_step(SolveState& st) {
   if (!H->iter_exec[c]) return TPC_EINVAL;  // every count 1..full is captured at set-up
   st.rel_prev = st.rel;
   st.cycles = c;
+  nvtxEventAttributes_t ea{};
+  ea.version = NVTX_VERSION;
+  ea.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+  ea.messageType = NVTX_MESSAGE_TYPE_ASCII;
+  ea.message.ascii = "tpc outer iteration (payload: inner cycles)";
+  ea.payloadType = NVTX_PAYLOAD_TYPE_INT32;
+  ea.payload.iValue = c;
+  st.iter_range = nvtxRangeStartEx(&ea);
   TPC_CUDA(H, cudaGraphLaunch(H->iter_exec[c], s));
   H->launches += H->iter_nodes[c];
   TPC_CUDA(H, cudaMemcpyAsync(H->sumsq_host, H->sumsq, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -898,6 +928,10 @@ int solve_step(SolveState& st) {
 
 int solve_finish(SolveState& st) {
   tpc_handle* H = st.H;
+  if (st.iter_range) {
+    nvtxRangeEnd(st.iter_range);
+    st.iter_range = 0;
+  }
   const size_t bytes = (size_t)H->d.lev[0].n * sizeof(double);
   if (st.status != TPC_EINVAL)
     TPC_CUDA(H, cudaMemcpyAsync(st.x_dev, H->u, bytes, cudaMemcpyDeviceToDevice, H->stream));
@@ -906,6 +940,7 @@ int solve_finish(SolveState& st) {
 
 int solve_impl(tpc_handle* H, const double* b_dev, double* x_dev, double tol, int use_x0,
                int* iters_out, double* relres_out) {
+  NvtxScope range("tpc_solve");
   SolveState st;
   st.H = H;
   TPC_TRY(solve_begin(st, b_dev, x_dev, tol, use_x0));
@@ -1095,7 +1130,11 @@ int tpc_setup(const tpc_params* p, double delta, double h, int levels, void* cud
   H->prm = *p;
   if (H->prm.max_iters < 0) H->prm.max_iters = 0;
   std::string err;
-  int rc = build_host_hierarchy(*p, delta, h, levels, H->host, err);
+  int rc;
+  {
+    NvtxScope range("tpc_setup: host hierarchy");
+    rc = build_host_hierarchy(*p, delta, h, levels, H->host, err);
+  }
   if (rc != TPC_OK) {
     set_host_error(err);
     delete H;
@@ -1181,6 +1220,7 @@ int tpc_solve_batch(tpc_handle* const* hs, int count, const double* const* b_dev
     set_host_error("tpc_solve_batch: a handle appears twice (each instance needs its own)");
     return TPC_EINVAL;
   }
+  NvtxScope range("tpc_solve_batch");
   std::vector<SolveState> st(count);
   for (int i = 0; i < count; ++i) {
     st[i].H = hs[i];
@@ -1221,6 +1261,7 @@ int tpc_solve_batch(tpc_handle* const* hs, int count, const double* const* b_dev
 
 int tpc_solve_host(tpc_handle* H, const double* b_host, double* x_host, double tol, int use_x0,
                    int* iters_out, double* relres_out) {
+  NvtxScope range("tpc_solve_host");
   if (!H || !b_host || !x_host || !(tol >= 0.0)) {
     if (H) H->err = "bad argument to tpc_solve_host";
     return TPC_EINVAL;

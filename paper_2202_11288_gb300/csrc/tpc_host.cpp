@@ -599,6 +599,10 @@ int build_host_hierarchy(const tpc_params& p, double delta, double h, int levels
     err = "damping weights must lie in (0, 2)";
     return TPC_EINVAL;
   }
+  if (p.poison != 0 && p.poison != 1) {
+    err = "poison must be 0 or 1";
+    return TPC_EINVAL;
+  }
   if (p.autotune != 0 && p.autotune != 1) {
     err = "autotune must be 0 or 1";
     return TPC_EINVAL;
@@ -716,6 +720,7 @@ void tpc_default_params(tpc_params* p) {
   p->max_iters = 100;
   p->inner_cycles = 6;
   p->autotune = 1;
+  p->poison = 0;
 }
 
 int tpc_host_hierarchy(const tpc_params* p, double delta, double h, int levels,

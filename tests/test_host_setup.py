@@ -75,3 +75,10 @@ def test_horizon_ratio_rule():
         assert model.horizon_ratio(delta, h) == r
         lev = tpc.tpc_host_hierarchy(delta, h, 0)[0]
         assert lev["A"][lev["N"] - 1] == 12 * r - 2
+
+
+def test_poison_flag_is_validated():
+    assert tpc.tpc_default_params().poison == 0
+    with pytest.raises(tpc.TpcError) as ei:
+        tpc.tpc_host_dense_level(0.25, 1 / 16, 4, params=tpc.tpc_default_params(poison=2))
+    assert ei.value.code == tpc.TPC_EINVAL
