@@ -39,7 +39,7 @@ FP64_FLOP_PER_CLK_PER_SM = 4      # 2 DFMA per clock per SM (FMA-loop probe: 1.1
 N_SMS = 152
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_mid_pair<double> launch at the finest
 # level, from ncu (profiles/k_mid_pair_fp64_N2e22.md); unknown for other sizes
-MID_TRAFFIC = {22: 357.7e6}
+MID_TRAFFIC = {22: 356.8e6}
 # Algorithmic bytes of the FP32 finest-level kernels per point of the FFT length m = 2N + 2
 # (residual epilogue, no prologue; x, f, y hold about m floats; the Cross vectors q, zeta and
 # p, xi hold m/2 entries each of which only the first r are nonzero and read, a fraction r/N):
