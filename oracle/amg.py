@@ -33,16 +33,39 @@ def prolongation(n_fine: int) -> np.ndarray:
     return 2.0 * restriction(n_fine).T
 
 
-def galerkin(A: np.ndarray) -> np.ndarray:
-    """A_{k-1} = I_k^{k-1} A_k I_{k-1}^k (eq. 5 / eq. block Galerkin)."""
-    n = A.shape[0]
-    return restriction(n) @ A @ prolongation(n)
+def position_order(n: int) -> np.ndarray:
+    """Concatenated indices [v; w] of a level with n = 2N + 1 unknowns, listed by position:
+    node v_i sits at x = i h (i = 1..N), midpoint w_j at x = (j - 1/2) h (j = 1..N+1)."""
+    N = (n - 1) // 2
+    x = np.concatenate([np.arange(1, N + 1), np.arange(1, N + 2) - 0.5])
+    return np.argsort(x, kind="stable")
+
+
+def restriction_geometric(n_fine: int) -> np.ndarray:
+    """Not the paper's transfer: the same 1/4 [1 2 1] rows applied to the unknowns listed by
+    position (spacing h/2), the coarse unknowns being the fine nodes x = I h, which are the
+    nodes and midpoints of the coarse mesh. Returned in the concatenated orderings of both
+    levels: R[pc, pf] with the rows / columns permuted by position_order."""
+    n_c = (n_fine - 1) // 2
+    pf, pc = position_order(n_fine), position_order(n_c)
+    R = np.zeros((n_c, n_fine))
+    R[np.ix_(pc, pf)] = restriction(n_fine)
+    return R
+
+
+TRANSFERS = {"paper": restriction, "geometric": restriction_geometric}
+
+
+def galerkin(A: np.ndarray, transfer: str = "paper") -> np.ndarray:
+    """A_{k-1} = I_k^{k-1} A_k I_{k-1}^k (eq. 5 / eq. block Galerkin), I_{k-1}^k = 2 (I_k^{k-1})^T."""
+    R = TRANSFERS[transfer](A.shape[0])
+    return R @ A @ (2.0 * R.T)
 
 
 class Hierarchy:
     """Dense level matrices A_K..A_kc plus the LU factors of the coarsest one."""
 
-    def __init__(self, A_fine: np.ndarray, kc: int = 3):
+    def __init__(self, A_fine: np.ndarray, kc: int = 3, transfer: str = "paper"):
         n = A_fine.shape[0]
         K = int(round(np.log2(n + 1))) - 1
         if (1 << (K + 1)) - 1 != n:
@@ -50,9 +73,10 @@ class Hierarchy:
         if not (1 <= kc <= K):
             raise ValueError("coarsest level out of range")
         self.K, self.kc = K, kc
+        self.transfer = transfer
         self.A = {K: A_fine}
         for k in range(K, kc, -1):
-            self.A[k - 1] = galerkin(self.A[k])
+            self.A[k - 1] = galerkin(self.A[k], transfer)
         self.lu = sla.lu_factor(self.A[kc])
 
     def n(self, k: int) -> int:
@@ -78,9 +102,9 @@ def vcycle(H: Hierarchy, k: int, b: np.ndarray, m1: int = 1, m2: int = 1,
     for _ in range(m1):
         u = u + omega_pre * (b - A @ u) / d
     r = b - A @ u
-    n = A.shape[0]
-    e = vcycle(H, k - 1, restriction(n) @ r, m1, m2, omega_pre, omega_post)
-    u = u + prolongation(n) @ e
+    R = TRANSFERS[getattr(H, "transfer", "paper")](A.shape[0])
+    e = vcycle(H, k - 1, R @ r, m1, m2, omega_pre, omega_post)
+    u = u + 2.0 * R.T @ e
     for _ in range(m2):
         u = u + omega_post * (b - A @ u) / d
     return u
