@@ -57,6 +57,7 @@ enum {
  * diagonal D is not Toeplitz and coarsens to a tridiagonal band, applied beside the FFT product. */
 enum { TPC_SPD = 0, TPC_NONSYM = 1, TPC_WEAKLY = 2 };
 enum { TPC_FP64 = 0, TPC_MIXED = 1 };          /* precision of the inner V-cycle */
+enum { TPC_TRANSFER_PAPER = 0, TPC_TRANSFER_GEOMETRIC = 1 };  /* tpc_params.transfer */
 
 typedef struct tpc_params {
   int variant;        /* TPC_SPD, TPC_NONSYM or TPC_WEAKLY                                */
@@ -84,6 +85,12 @@ typedef struct tpc_params {
                          is filled with all-ones bytes (NaN in FP32 and FP64) when it is
                          allocated, so that a value read before it is written shows up as
                          NaN in the results; results are otherwise identical              */
+  int transfer;       /* TPC_TRANSFER_PAPER (default): the 1/4 [1 2 1] restriction on the
+                         concatenated vector [v; w] (section 3.1) and P = 2 R^T;
+                         TPC_TRANSFER_GEOMETRIC (not in the paper): the same rows on the
+                         unknowns listed by position, whose coarse unknowns are the fine
+                         nodes; the V-cycle then converges at the constant kernel's rate
+                         for the fractional kernel too. Not for TPC_WEAKLY (ENOTSUP)      */
 } tpc_params;
 
 typedef struct tpc_handle tpc_handle;

@@ -22,6 +22,7 @@ TPC_OK, TPC_ENOTCONV = 0, 1
 TPC_EINVAL, TPC_ENOMEM, TPC_ECUDA, TPC_ESINGULAR, TPC_ENOTSUP, TPC_EDIVERGED = -1, -2, -3, -4, -5, -6
 TPC_SPD, TPC_NONSYM, TPC_WEAKLY = 0, 1, 2
 TPC_FP64, TPC_MIXED = 0, 1
+TPC_TRANSFER_PAPER, TPC_TRANSFER_GEOMETRIC = 0, 1
 
 EXPORTED = ["tpc_default_params", "tpc_setup", "tpc_solve", "tpc_solve_batch", "tpc_solve_host",
             "tpc_apply",
@@ -43,7 +44,8 @@ class TpcParams(ctypes.Structure):
                 ("omega_pre", ctypes.c_double), ("omega_post", ctypes.c_double),
                 ("coarsest_level", ctypes.c_int), ("precision", ctypes.c_int),
                 ("max_iters", ctypes.c_int), ("inner_cycles", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("poison", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("poison", ctypes.c_int),
+                ("transfer", ctypes.c_int)]
 
 
 class TpcServerConfig(ctypes.Structure):

@@ -75,6 +75,7 @@ template <typename T> struct Hier {
   BottomPlan<T>* bottom = nullptr;  // single-block V-cycle bottom (FP32, V(1,1)), or null
   int bottom_li = -1;               // level index where it takes over
   size_t bottom_smem = 0;
+  int geo = 0;                      // transfer (tpc_params.transfer)
 };
 
 }  // namespace tpc
@@ -243,6 +244,7 @@ LevelArgs<T> level_args(const Hier<T>& G, const DevLevel<T>& L) {
   a.z = G.z;
   a.partials = G.partials;
   a.nparts = L.fwd_blocks;
+  a.geo = G.geo;
   return a;
 }
 
@@ -324,10 +326,10 @@ T* enqueue_vcycle(tpc_handle* H, Hier<T>& G, int li, const T* f_top, const T* rf
   }
   if (L.k == H->kc) {
     if (rfine) {
-      k_coarse_solve<T><<<1, 256, 0, s>>>(G.coarse_inv, G.f[li], rfine, e, (int)L.n);
+      k_coarse_solve<T><<<1, 256, 0, s>>>(G.coarse_inv, G.f[li], rfine, e, (int)L.n, G.geo);
     } else {
       k_coarse_solve<T><<<1, 256, 0, s>>>(G.coarse_inv, const_cast<T*>(f_top), nullptr, e,
-                                         (int)L.n);
+                                         (int)L.n, G.geo);
     }
     H->launches += 1;
     return e;
@@ -345,7 +347,7 @@ T* enqueue_vcycle(tpc_handle* H, Hier<T>& G, int li, const T* f_top, const T* rf
   matvec<T>(H, G, li, e, f, t, EPI_RESID, false, first);
   const T* ec = enqueue_vcycle<T>(H, G, li + 1, nullptr, t);
   if (H->prm.m2 == 0) {
-    k_prolong_add<T><<<grid_for(L.n), NTHREADS, 0, s>>>(e, ec, L.n);
+    k_prolong_add<T><<<grid_for(L.n), NTHREADS, 0, s>>>(e, ec, L.n, G.geo);
     H->launches += 1;
     return e;
   }
@@ -479,6 +481,7 @@ int alloc_levels(tpc_handle* H, Hier<T>& G) {
   const HostHierarchy& HH = H->host;
   const int nlev = (int)HH.lev.size();
   G.lev.resize(nlev);
+  G.geo = H->prm.transfer == TPC_TRANSFER_GEOMETRIC ? 1 : 0;
   std::vector<double> tw;
   twiddles(1LL << LOG_LMAX, 1LL << LOG_LMAX, tw);  // W_4096^j, j < 4096
   TPC_TRY(dalloc(H, &G.twL, (size_t)1 << LOG_LMAX));
@@ -616,6 +619,7 @@ int build_bottom(tpc_handle* H, Hier<T>& G) {
     bp.post[j] = a;
   }
   bp.cinv = G.coarse_inv;
+  bp.geo = G.geo;
   bp.rc = G.t[ic - 1];
   bp.fc = G.f[ic];
   bp.ec = G.e[ic];

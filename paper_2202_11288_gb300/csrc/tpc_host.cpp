@@ -319,22 +319,16 @@ double frac_coef(int variant, bool row_node, long long dist2, int r, double a) {
   return -6.0 * v;
 }
 
-// Finest level for the fractional kernel: finest_form's block layout with frac_coef entries.
-LevelForm finest_form_frac(int variant, int K, int r, double a, double shift) {
-  const long long Nint = 1LL << K;
+// A level of order 2N + 1, N = 2^k - 1, whose entries depend only on the row type and the
+// twice-distance d2 = 2 (x_p - x_q) / h: nr(d2) for node rows, mr(d2) for midpoint rows (the
+// matrix is 2-periodic Toeplitz with the unknowns listed by position), written in finest_form's
+// block layout (nodes first, then midpoints; the Cross continues the Toeplitz blocks).
+template <typename FN, typename FM>
+LevelForm form_from_rows(int k, FN nr, FM mr, double shift) {
   LevelForm L;
-  L.k = K;
-  L.N = Nint - 1;
+  L.k = k;
+  L.N = (1LL << k) - 1;
   const long long N = L.N;
-  // the entries vanish beyond twice-distance 2r + 2; tabulate them once per row type
-  const long long reach = 2LL * r + 3;
-  std::vector<double> nodeRow(2 * reach + 1), midRow(2 * reach + 1);
-  for (long long d2 = -reach; d2 <= reach; ++d2) {
-    nodeRow[d2 + reach] = frac_coef(variant, true, d2, r, a);
-    midRow[d2 + reach] = frac_coef(variant, false, d2, r, a);
-  }
-  auto nr = [&](long long d2) { return (d2 < -reach || d2 > reach) ? 0.0 : nodeRow[d2 + reach]; };
-  auto mr = [&](long long d2) { return (d2 < -reach || d2 > reach) ? 0.0 : midRow[d2 + reach]; };
   auto fA = [&](long long d) { return nr(2 * d); };
   auto fB = [&](long long d) { return nr(2 * d + 1); };
   auto fC = [&](long long d) { return mr(2 * d - 1); };
@@ -365,6 +359,20 @@ LevelForm finest_form_frac(int variant, int K, int r, double a, double shift) {
   L.tD[N - 1] += shift;
   L.o += shift;
   return L;
+}
+
+// Finest level for the fractional kernel: finest_form's block layout with frac_coef entries.
+LevelForm finest_form_frac(int variant, int K, int r, double a, double shift) {
+  // the entries vanish beyond twice-distance 2r + 2; tabulate them once per row type
+  const long long reach = 2LL * r + 3;
+  std::vector<double> nodeRow(2 * reach + 1), midRow(2 * reach + 1);
+  for (long long d2 = -reach; d2 <= reach; ++d2) {
+    nodeRow[d2 + reach] = frac_coef(variant, true, d2, r, a);
+    midRow[d2 + reach] = frac_coef(variant, false, d2, r, a);
+  }
+  auto nr = [&](long long d2) { return (d2 < -reach || d2 > reach) ? 0.0 : nodeRow[d2 + reach]; };
+  auto mr = [&](long long d2) { return (d2 < -reach || d2 > reach) ? 0.0 : midRow[d2 + reach]; };
+  return form_from_rows(K, nr, mr, shift);
 }
 
 // Couplings of the two boundary basis functions (nodes x = 0 and x = 1, one element each) to
@@ -531,6 +539,35 @@ double dense_entry(const LevelForm& L, long long i, long long j) {
   return t[ii - jj + N - 1] + band;
 }
 
+// Galerkin coarsening with the geometric transfer (an option of this build, not the paper's):
+// the full weighting 1/4 [1 2 1] acts on the unknowns listed by position (spacing h/2), and the
+// coarse unknowns are the fine nodes x = t h, t = 1..N_f, i.e. the coarse mesh's nodes (t even)
+// and midpoints (t odd). Every level here is 2-periodic Toeplitz in position order (Toeplitz
+// blocks, the Cross continuing them, the shift on the diagonal), so the coarse matrix
+// (1/8) sum_{a,b} w_a w_b A(2t + a, 2t' + b) depends on t - t' only: one value c(t - t') per
+// offset, taken from nine fine entries at one (t, t') pair, and the coarse level is
+// form_from_rows with nr = mr = c.
+LevelForm coarsen_geometric(const LevelForm& F) {
+  const long long Nf = F.N;
+  const long long nc = Nf;  // coarse order 2 N_c + 1 with N_c = (N_f - 1) / 2
+  // 1-based concatenated index of the fine unknown at position s h / 2, s = 1..2 N_f + 1
+  auto conc = [&](long long s) { return (s % 2 == 0) ? s / 2 : Nf + (s + 1) / 2; };
+  const double w[3] = {1.0, 2.0, 1.0};
+  std::vector<double> c((size_t)(2 * nc - 1));
+  for (long long D = -(nc - 1); D <= nc - 1; ++D) {
+    const long long t = D >= 0 ? D + 1 : 1, tp = t - D;
+    double acc = 0.0;
+    for (int a = -1; a <= 1; ++a)
+      for (int b = -1; b <= 1; ++b)
+        acc += w[a + 1] * w[b + 1] * dense_entry(F, conc(2 * t + a), conc(2 * tp + b));
+    c[(size_t)(D + nc - 1)] = acc / 8.0;
+  }
+  auto cc = [&](long long d2) {
+    return (d2 < -(nc - 1) || d2 > nc - 1) ? 0.0 : c[(size_t)(d2 + nc - 1)];
+  };
+  return form_from_rows(F.k - 1, cc, cc, 0.0);
+}
+
 int invert_dense(std::vector<double>& A, long long n, std::vector<double>& inv) {
   std::vector<long long> piv(n);
   double amax = 0.0;
@@ -603,6 +640,15 @@ int build_host_hierarchy(const tpc_params& p, double delta, double h, int levels
     err = "poison must be 0 or 1";
     return TPC_EINVAL;
   }
+  if (p.transfer != TPC_TRANSFER_PAPER && p.transfer != TPC_TRANSFER_GEOMETRIC) {
+    err = "transfer must be TPC_TRANSFER_PAPER or TPC_TRANSFER_GEOMETRIC";
+    return TPC_EINVAL;
+  }
+  if (p.transfer == TPC_TRANSFER_GEOMETRIC && p.variant == TPC_WEAKLY) {
+    err = "the geometric transfer needs levels that are Toeplitz in position order; the weakly "
+          "singular model's diagonal is not";
+    return TPC_ENOTSUP;
+  }
   if (p.autotune != 0 && p.autotune != 1) {
     err = "autotune must be 0 or 1";
     return TPC_EINVAL;
@@ -636,7 +682,9 @@ int build_host_hierarchy(const tpc_params& p, double delta, double h, int levels
     out.lev.push_back(finest_form_frac(p.variant, K, r, p.kernel_a, p.shift));
   else
     out.lev.push_back(finest_form(p.variant, K, r, p.shift));
-  for (int k = K; k > kc; --k) out.lev.push_back(coarsen(out.lev.back()));
+  for (int k = K; k > kc; --k)
+    out.lev.push_back(p.transfer == TPC_TRANSFER_GEOMETRIC ? coarsen_geometric(out.lev.back())
+                                                            : coarsen(out.lev.back()));
   const LevelForm& Lc = out.lev.back();
   const long long n = 2 * Lc.N + 1;
   std::vector<double> A((size_t)(n * n));
@@ -721,6 +769,7 @@ void tpc_default_params(tpc_params* p) {
   p->inner_cycles = 6;
   p->autotune = 1;
   p->poison = 0;
+  p->transfer = TPC_TRANSFER_PAPER;
 }
 
 int tpc_host_hierarchy(const tpc_params* p, double delta, double h, int levels,

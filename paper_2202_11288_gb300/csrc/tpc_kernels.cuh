@@ -115,6 +115,7 @@ template <typename T> struct LevelArgs {
   c2<T>* z;              // complex work array (m)
   T* partials;           // per-CTA partial dots of the forward strided pass
   int nparts;
+  int geo;               // transfer: 0 the paper's (concatenated vector), 1 geometric
 };
 
 // Twiddle W_m^e of the strided passes, e < m. FP64 (whose kernels are bound by the FP64 pipe)
@@ -183,10 +184,35 @@ __device__ __forceinline__ c2<T> inter_tw(const c2<T>* __restrict__ twm, int e, 
   }
 }
 
-// Restriction I_k^{k-1} (section 3.1) at coarse index I: (r[2I] + 2 r[2I+1] + r[2I+2]) / 4.
+// Fine indices (concatenated, 0-based) of the three restricted values of coarse index I, with
+// weights 1/4, 1/2, 1/4. The paper's transfer (section 3.1): 2I, 2I+1, 2I+2. The geometric
+// one (an option, not the paper's): the coarse unknown at position t h (t = 2(I+1) for a node
+// I < Nc, t = 2(I-Nc)+1 for a midpoint) takes the fine midpoint, node and midpoint at
+// (t - 1/2) h, t h, (t + 1/2) h, i.e. w_t, v_t, w_{t+1} (Nf = 2 Nc + 1 fine nodes).
+__device__ __forceinline__ void restrict_idx(int I, int Nc, int geo, int& i0, int& i1, int& i2) {
+  if (!geo) {
+    i0 = 2 * I;
+    i1 = 2 * I + 1;
+    i2 = 2 * I + 2;
+    return;
+  }
+  const int t = (I < Nc) ? 2 * (I + 1) : 2 * (I - Nc) + 1;
+  const int Nf = 2 * Nc + 1;
+  i0 = Nf + t - 1;
+  i1 = t - 1;
+  i2 = Nf + t;
+}
+// Restriction at coarse index I of a level with Nc nodes.
 template <typename T>
-__device__ __forceinline__ T restrict_at(const T* __restrict__ r, int I) {
-  return (T)0.25 * r[2 * I] + (T)0.5 * r[2 * I + 1] + (T)0.25 * r[2 * I + 2];
+__device__ __forceinline__ T restrict_at(const T* __restrict__ r, int I, int Nc, int geo) {
+  int i0, i1, i2;
+  restrict_idx(I, Nc, geo, i0, i1, i2);
+  return (T)0.25 * r[i0] + (T)0.5 * r[i1] + (T)0.25 * r[i2];
+}
+// Coarse index (concatenated, 0-based) of the coarse unknown at position t h (geometric
+// transfer), t = 1..Nf: a coarse node for even t, a coarse midpoint for odd t.
+__device__ __forceinline__ int coarse_of_position(int t, int Nc) {
+  return (t & 1) ? Nc + (t - 1) / 2 : t / 2 - 1;
 }
 // Operand entry j of the product (concatenated index), formed by the prologue; w is the
 // pre-smoothing weight of j's segment. Split into the loads (issued in batches, so that many
@@ -197,6 +223,27 @@ template <typename T> struct Raw {
 // The coarse-correction values of PRO_PROLONG at fine index j (a1, a2 of Raw).
 template <typename T>
 __device__ __forceinline__ void prolong_load(const LevelArgs<T>& a, int j, Raw<T>& r) {
+  if (a.geo) {
+    // P = 2 R^T of the geometric transfer: node v_t (j = t - 1) takes the coarse value at
+    // t h; midpoint w_u (j = N + u - 1) half of those at (u - 1) h and u h (0 outside 1..N).
+    // Laid out for operand_finish, which adds a1 at odd j and (a1 + a2) / 2 at even j.
+    const int N = a.N, Nc = (N - 1) / 2;
+    if (j < N) {
+      r.a1 = a.ec[coarse_of_position(j + 1, Nc)];
+      r.a2 = r.a1;
+    } else {
+      const int u = j - N + 1;
+      const T lo = (u >= 2) ? a.ec[coarse_of_position(u - 1, Nc)] : (T)0;
+      const T hi = (u <= N) ? a.ec[coarse_of_position(u, Nc)] : (T)0;
+      if (j & 1) {
+        r.a1 = (T)0.5 * (lo + hi);
+      } else {
+        r.a1 = lo;
+        r.a2 = hi;
+      }
+    }
+    return;
+  }
   if (j & 1) {
     r.a1 = a.ec[(j - 1) / 2];
   } else {
@@ -213,9 +260,11 @@ __device__ __forceinline__ Raw<T> operand_load(const LevelArgs<T>& a, int j, int
   } else if (pro == PRO_SMOOTH) {
     r.a0 = a.f[j];
   } else if (pro == PRO_RESTRICT) {
-    r.a0 = a.rfine[2 * j];
-    r.a1 = a.rfine[2 * j + 1];
-    r.a2 = a.rfine[2 * j + 2];
+    int i0, i1, i2;
+    restrict_idx(j, a.N, a.geo, i0, i1, i2);
+    r.a0 = a.rfine[i0];
+    r.a1 = a.rfine[i1];
+    r.a2 = a.rfine[i2];
   } else {
     r.a0 = a.x[j];
     prolong_load<T>(a, j, r);
@@ -913,6 +962,7 @@ template <typename T> struct BottomPlan {
   LevelArgs<T> pre[BOTTOM_MAX_LEVELS];
   LevelArgs<T> post[BOTTOM_MAX_LEVELS];
   const T* cinv;                         // coarsest inverse (nc x nc)
+  int geo;                               // transfer (see LevelArgs)
   const T* rc;                           // residual of the level above the coarsest
   T* fc;                                 // coarsest right-hand side
   T* ec;                                 // coarsest solution
@@ -945,7 +995,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), 1) k_vcycle_bottom(const Bot
     T* fs = reinterpret_cast<T*>(s);
     const int nc = bp->nc;
     for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-      fs[i] = restrict_at<T>(bp->rc, i);
+      fs[i] = restrict_at<T>(bp->rc, i, (nc - 1) / 2, bp->geo);
       bp->fc[i] = fs[i];
     }
     __syncthreads();
@@ -982,12 +1032,22 @@ __global__ void k_extract_cplx(const c2<T>* z, c2<T>* out, long long m, T scale)
 // ------------------------------------------------------------------------------------
 // Correction with P = 2 (I_k^{k-1})^T: e[2I+1] += ec[I], e[2I], e[2I+2] += ec[I] / 2.
 template <typename T>
-__global__ void k_prolong_add(T* e, const T* ec, long long nf) {
+__global__ void k_prolong_add(T* e, const T* ec, long long nf, int geo) {
   const long long nc = (nf - 1) / 2;
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nf;
        j += (long long)gridDim.x * blockDim.x) {
     T add;
-    if (j & 1) {
+    if (geo) {  // geometric transfer: see prolong_load
+      const int N = (int)nc, Nc = (N - 1) / 2;
+      if (j < N) {
+        add = ec[coarse_of_position((int)j + 1, Nc)];
+      } else {
+        const int u = (int)j - N + 1;
+        const T lo = (u >= 2) ? ec[coarse_of_position(u - 1, Nc)] : (T)0;
+        const T hi = (u <= N) ? ec[coarse_of_position(u, Nc)] : (T)0;
+        add = (T)0.5 * (lo + hi);
+      }
+    } else if (j & 1) {
       add = ec[(j - 1) / 2];
     } else {
       const long long I = j / 2;
@@ -1003,11 +1063,11 @@ __global__ void k_prolong_add(T* e, const T* ec, long long nf) {
 // rfine != nullptr the right-hand side is first restricted from the finer residual (and
 // stored in f).
 template <typename T>
-__global__ void k_coarse_solve(const T* inv, T* f, const T* rfine, T* e, int n) {
+__global__ void k_coarse_solve(const T* inv, T* f, const T* rfine, T* e, int n, int geo) {
   __shared__ T fs[256];
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     if (rfine) {
-      fs[i] = restrict_at<T>(rfine, i);
+      fs[i] = restrict_at<T>(rfine, i, (n - 1) / 2, geo);
       f[i] = fs[i];
     } else {
       fs[i] = f[i];
