@@ -97,3 +97,41 @@ def test_fractional_solves_converge_at_the_constant_kernels_rate(variant):
             assert (torch.linalg.norm(b - y) / torch.linalg.norm(b)).item() < 1.05e-10
         finally:
             S.close()
+
+
+def test_server_mix_with_the_geometric_transfer_equals_lone_solves():
+    """A server whose handles use the geometric transfer, fed constant- and fractional-kernel
+    requests (a budget small enough to evict): every result equals, bit for bit and with the
+    same iteration count, the lone solve of the same request."""
+    import time
+    keys = [(SPD, 0.05, 10, 1, 0.25), (NONSYM, 0.1, 11, 1, 0.3), (SPD, 0.2, 9, 0, 0.0),
+            (NONSYM, 0.05, 12, 1, 0.1)]
+    reqs = []
+    for i in range(12):
+        v, d, K, kk, a = keys[i % len(keys)]
+        n = (1 << (K + 1)) - 1
+        b = torch.tensor(uniform_pm1(n, 300 + i)).pin_memory()
+        reqs.append((v, d, K, kk, a, b, torch.zeros(n, dtype=torch.float64).pin_memory()))
+    srv = tpc.Server(hbm_budget_bytes=4 << 20, max_inflight=3, precision=tpc.TPC_MIXED,
+                     transfer=GEO)
+    try:
+        tickets = {srv.submit(v, d, 2.0 ** -K, b, x, 1e-10, kk, a): i
+                   for i, (v, d, K, kk, a, b, x) in enumerate(reqs)}
+        got, t0 = [], time.time()
+        while len(got) < len(reqs) and time.time() - t0 < 120:
+            got += srv.poll(64, wait_ms=50)
+        assert len(got) == len(reqs)
+    finally:
+        srv.close()
+    for r in got:
+        v, d, K, kk, a, b, x = reqs[tickets[r["ticket"]]]
+        assert r["status"] == tpc.TPC_OK and r["relres"] < 1e-10
+        S = tpc.Solver(d, 2.0 ** -K, variant=v, kernel=kk, kernel_a=a, transfer=GEO,
+                       precision=tpc.TPC_MIXED)
+        try:
+            xa = np.zeros(b.numel())
+            rc, it, rel = S.solve_host(b.numpy(), xa, tol=1e-10)
+        finally:
+            S.close()
+        assert it == r["iters"] and rel == r["relres"]
+        assert np.array_equal(xa, x.numpy())
