@@ -16,7 +16,9 @@ Contents
              R A P, eq. (block Galerkin)), damped Jacobi (eq. 7), the block V-cycle of
              Algorithm 2 with a dense LU at the coarsest level, the outer iteration and the
              stopping rule of section 5; the Cross splitting of eq. (split01) read off a
-             dense level matrix; the two-grid factor of Theorem 4.1.
+             dense level matrix; the two-grid factor of Theorem 4.1. Also, as an option
+             that is not the paper's, the geometric transfer (the same restriction rows on
+             the unknowns listed by position), pinned by tests/test_oracle_geometric.py.
 ``timestep`` -- section 5: the time-dependent problem advanced by the BDF4 scheme of eq.
              (bdf4) with the shifted system (sigma I + A) U^k = ..., for the exact solution
              u = e^t (1 + x)^6 of Tables 2 and 3.
