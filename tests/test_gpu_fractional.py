@@ -101,3 +101,33 @@ def test_finite_part_solve_reports_non_convergence():
         assert rc == tpc.TPC_ENOTCONV and it == 20 and rel > 1.0
     finally:
         S.close()
+
+
+def test_non_finite_residual_and_right_hand_side_are_reported():
+    """a = 1/2 grows the residual about sevenfold a cycle: given enough iterations it overflows
+    and the solve stops with TPC_EDIVERGED; a right-hand side with a NaN is refused with
+    TPC_EINVAL. The handle and the context stay usable afterwards."""
+    K, r = 7, 16
+    N = 1 << K
+    S = tpc.Solver(r / N, 1.0 / N, kernel=1, kernel_a=0.5, max_iters=2000)
+    try:
+        b = dev(uniform_pm1(S.n, 4))
+        x = torch.zeros_like(b)
+        with pytest.raises(tpc.TpcError) as ei:
+            S.solve(b, x, tol=1e-10)
+        assert ei.value.code == tpc.TPC_EDIVERGED
+        bad = b.clone()
+        bad[3] = float("nan")
+        with pytest.raises(tpc.TpcError) as ei:
+            S.solve(bad, x, tol=1e-10)
+        assert ei.value.code == tpc.TPC_EINVAL
+    finally:
+        S.close()
+    C = tpc.Solver(r / N, 1.0 / N)
+    try:
+        b = dev(uniform_pm1(C.n, 5))
+        x = torch.zeros_like(b)
+        rc, it, rel = C.solve(b, x, tol=1e-10)
+        assert rc == tpc.TPC_OK and rel < 1e-10
+    finally:
+        C.close()
