@@ -177,14 +177,14 @@ def is_toeplitz(T: np.ndarray, tol: float = 0.0) -> bool:
 # Two-grid factor of Theorem 4.1
 # ----------------------------------------------------------------------------------------
 
-def two_grid_factor(A: np.ndarray, omega: float) -> float:
+def two_grid_factor(A: np.ndarray, omega: float, transfer: str = "paper") -> float:
     """||S_K T_K||_A with T_K = I - P A_c^{-1} R A and S_K = I - omega D^{-1} A (section 3.1).
 
     The A-norm of a matrix M is ||L^T M L^{-T}||_2 where A = L L^T (A must be SPD).
     """
     n = A.shape[0]
-    R = restriction(n)
-    P = prolongation(n)
+    R = TRANSFERS[transfer](n)
+    P = 2.0 * R.T
     Ac = R @ A @ P
     T = np.eye(n) - P @ np.linalg.solve(Ac, R @ A)
     S = np.eye(n) - omega * (A / np.diag(A)[:, None])

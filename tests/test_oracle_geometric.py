@@ -75,3 +75,18 @@ def test_fractional_kernel_converges_fast(variant):
     it = amg.solve(amg.Hierarchy(A, kc=3, transfer="geometric"), b, tol=1e-10,
                    max_iters=100)[1]
     assert it <= 15
+
+
+@pytest.mark.parametrize("a", [sp.Rational(-1, 2), sp.Integer(0), sp.Rational(1, 4)])
+def test_two_grid_factor_below_one(a):
+    """SPD system, N = 64, r = 6, omega = 2/3: ||S T||_A < 1 with the geometric transfer; for the
+    fractional kernels it is far below the paper transfer's factor (the cause of the slow
+    V-cycle), for the constant kernel both are below Theorem 4.1's sqrt(47/48)."""
+    A = fractional.assemble(SPD, 64, 6, a)
+    fg = amg.two_grid_factor(A, 2.0 / 3.0, "geometric")
+    fp = amg.two_grid_factor(A, 2.0 / 3.0)
+    assert 0.0 < fg < 1.0
+    if a == sp.Rational(-1, 2):
+        assert fg <= np.sqrt(47.0 / 48.0) and fp <= np.sqrt(47.0 / 48.0)
+    else:
+        assert fg < fp
