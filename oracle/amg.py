@@ -45,7 +45,8 @@ def restriction_geometric(n_fine: int) -> np.ndarray:
     """Not the paper's transfer: the same 1/4 [1 2 1] rows applied to the unknowns listed by
     position (spacing h/2), the coarse unknowns being the fine nodes x = I h, which are the
     nodes and midpoints of the coarse mesh. Returned in the concatenated orderings of both
-    levels: R[pc, pf] with the rows / columns permuted by position_order."""
+    levels: R[pc, pf] with the rows / columns permuted by position_order. PARITY UNPINNED by
+    the paper (pinned by mathematics only: tests/test_oracle_geometric.py)."""
     n_c = (n_fine - 1) // 2
     pf, pc = position_order(n_fine), position_order(n_c)
     R = np.zeros((n_c, n_fine))
