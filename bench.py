@@ -37,21 +37,62 @@ METRIC = ("solves/s to rel-res 1e-10 (1D SPD peridynamic system; mixed FP32 V-cy
 UNIT = "solves/s"
 FP64_FLOP_PER_CLK_PER_SM = 4      # 2 DFMA per clock per SM (FMA-loop probe: 1.19 TFLOP/s at 1995 MHz)
 N_SMS = 152
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_mid_pair<double> launch at the finest
-# level, from ncu (profiles/k_mid_pair_fp64_N2e22.md); unknown for other sizes
-MID_TRAFFIC = {22: 356.8e6}
-# Algorithmic bytes of the FP32 finest-level kernels per point of the FFT length m = 2N + 2
-# (residual epilogue, no prologue; x, f, y hold about m floats; the Cross vectors q, zeta and
-# p, xi hold m/2 entries each of which only the first r are nonzero and read, a fraction r/N):
-#   forward pass:            reads x (4m), q and zeta (4m r/N); writes z (8m)   -> 12m + 4m r/N
-#   contiguous-block kernel: reads z (8m), 16 B of spectra per pair (8m); writes z  -> 24m
-#   inverse pass:            reads z (8m), p and xi (4m r/N), f (4m); writes y (4m) -> 16m + 4m r/N
-def f32_bytes_per_point(r, N):
-    frac = min(1.0, r / N)
-    return (12.0 + 4.0 * frac, 24.0, 16.0 + 4.0 * frac)
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP32 finest kernels, from ncu
-# (profiles/fp32_transform_kernels_N2e22.md), keyed by (K, kernel index); unknown for other sizes
-F32_TRAFFIC = {(22, 0): 54.3e6, (22, 1): 154.3e6, (22, 2): 115.9e6}
+
+
+# Algorithmic bytes of one Toeplitz-plus-Cross product on a level with N_k nodes, ideal
+# single-pass I/O (n = N_k): read the operand u (2n words), the spectra (SPD: real A^ and D^
+# over n + 1 frequencies plus complex B^, i.e. 4 (n + 1) words; nonsymmetric: four complex
+# spectra, 8 (n + 1) words), write y (2n words) and read the right-hand side of the fused
+# epilogue (2n words). Words are 4 B (FP32) or 8 B (FP64): 40 n / 80 n B for the SPD system.
+# Multi-pass transforms move more (the work array z between passes): that is measured
+# traffic, not algorithmic bytes.
+def product_bytes(n, word, nonsym=False):
+    return word * (2 * n + (8 if nonsym else 4) * (n + 1) + 2 * n + 2 * n)
+
+
+# The same bytes split over the three kernels of a strided-pipeline product: the forward pass
+# reads u, the contiguous-block kernel reads the spectra, the inverse pass writes y and reads
+# the right-hand side.
+def product_bytes_split(n, word, nonsym=False):
+    return (word * 2 * n, word * (8 if nonsym else 4) * (n + 1), word * 4 * n)
+
+
+def solve_bytes(K, kc, vcycles, outer, mixed, nonsym=False):
+    """Algorithmic bytes of one solve: V(1,1) cycles run two products per level above the
+    coarsest (the residual after the first sweep, the post-smoothing sweep); a mixed solve
+    adds one FP32 finest residual per inner cycle after the first of each outer iteration and
+    one FP64 finest residual per outer iteration; an FP64 solve one FP64 finest residual per
+    V-cycle."""
+    word = 4 if mixed else 8
+    per_cycle = sum(2 * product_bytes((1 << k) - 1, word, nonsym) for k in range(kc + 1, K + 1))
+    nK = (1 << K) - 1
+    total = vcycles * per_cycle + outer * product_bytes(nK, 8, nonsym)
+    if mixed:
+        total += (vcycles - outer) * product_bytes(nK, 4, nonsym)
+    return total
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture, valid only for
+# the kernel sources it was taken with (SHA-256 of the two device headers below, first 16 hex
+# digits) and for the level it was taken at; any other build reports traffic as null.
+KERNEL_SOURCES = ("paper_2202_11288_gb300/csrc/tpc_kernels.cuh",
+                  "paper_2202_11288_gb300/csrc/tpc_fft.cuh")
+TRAFFIC = {"digest": None, "K": 22, "f32": None, "f64_mid": None}
+
+
+def kernel_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(key, K):
+    if TRAFFIC.get("digest") != kernel_digest() or TRAFFIC.get("K") != K:
+        return None
+    return TRAFFIC.get(key)
 
 
 def measured_hbm_gbs():
@@ -106,28 +147,32 @@ def workload(K, delta):
 # --------------------------------------------------------------------------------------
 
 def oracle_hierarchy(K_sample, delta):
-    from oracle import amg, model
+    from oracle import amg, large, model
     N = 1 << K_sample
-    return amg.Hierarchy(model.assemble(model.SPD, N, model.horizon_ratio(delta, 1.0 / N)), kc=3)
+    r = model.horizon_ratio(delta, 1.0 / N)
+    return amg.Hierarchy(large.rows(model.SPD, N, r, np.arange(2 * N - 1)), kc=3)
 
 
-def oracle_sample(K_sample, delta, tol, reps, budget_s=20.0, H=None):
-    """Time the dense oracle's solve at N = 2^K_sample; returns (solves/s measured, detail)."""
+def oracle_sample(K_sample, delta, tol, reps, budget_s=20.0, H=None, seed0=0):
+    """Time the dense oracle's solve at N = 2^K_sample (set-up not timed); returns
+    (solves/s measured, detail, solution of the first right-hand side)."""
     from oracle import amg
     N = 1 << K_sample
     if H is None:
         H = oracle_hierarchy(K_sample, delta)
-    times, its = [], []
+    times, its, first = [], [], None
     t_start = time.perf_counter()
     for i in range(reps):
-        b = uniform_pm1(2 * N - 1, i)
+        b = uniform_pm1(2 * N - 1, seed0 + i)
         t0 = time.perf_counter()
-        _, it, rel, _ = amg.solve(H, b, tol=tol)
+        u, it, rel, _ = amg.solve(H, b, tol=tol)
         times.append(time.perf_counter() - t0)
         its.append(it)
+        if first is None:
+            first = u
         if time.perf_counter() - t_start > budget_s:
             break
-    return len(times) / sum(times), {"solves": len(times), "seconds": sum(times), "iters": its}
+    return len(times) / sum(times), {"solves": len(times), "seconds": sum(times), "iters": its}, first
 
 
 def cpu_cores():
@@ -143,24 +188,44 @@ def extrapolate(value_sample, K_sample, K):
     return value_sample / ratio
 
 
-def cpu_baseline(args, K_sample=11):
-    v, det = oracle_sample(K_sample, args.delta, args.tol, reps=8)
-    return {"value": extrapolate(v, K_sample, args.K), "unit": UNIT, "cores": cpu_cores(),
-            "kind": "oracle",
-            "sample": f"dense FP64 oracle solve at N=2^{K_sample} ({2 ** (K_sample + 1) - 1} "
-                      f"unknowns): {det['solves']} solves in {det['seconds']:.2f} s "
-                      f"({v:.3f} solves/s, iters {det['iters'][0]}); value extrapolated to "
-                      f"N=2^{args.K} by the n^2 cost of its dense products"}
+ORACLE_K_SMALL, ORACLE_K_LARGE = 7, 12
+
+
+def cpu_baseline(args, gpu_solutions=None):
+    """The oracle timed on the host cores at two sizes: N = 128 (delta = 0.125, the small
+    configuration) and N = 2^12 (the headline's delta), solves after set-up. The value is the
+    N = 2^12 rate extrapolated to the headline size by the n^2 cost of dense products (an
+    extrapolation: the dense oracle does not fit at N = 2^22). gpu_solutions(K, b), when given,
+    returns {name: GPU solution} for the N = 2^12 right-hand side; their distance to the
+    oracle's solution of it is reported."""
+    v7, d7, _ = oracle_sample(ORACLE_K_SMALL, 0.125, args.tol, reps=8, budget_s=5.0)
+    K = ORACLE_K_LARGE
+    v12, d12, u12 = oracle_sample(K, args.delta, args.tol, reps=8, budget_s=15.0, seed0=4242)
+    out = {"value": extrapolate(v12, K, args.K), "unit": UNIT, "cores": cpu_cores(),
+           "kind": "oracle",
+           "sample": f"dense FP64 oracle solves (set-up not timed): N=2^{ORACLE_K_SMALL}, "
+                     f"delta=0.125: {d7['solves']} solves in {d7['seconds']:.3f} s "
+                     f"({v7:.1f} solves/s); N=2^{K} ({2 ** (K + 1) - 1} unknowns), "
+                     f"delta={args.delta}: {d12['solves']} solves in {d12['seconds']:.2f} s "
+                     f"({v12:.3f} solves/s, {d12['iters'][0]} V-cycles); value = the N=2^{K} "
+                     f"rate EXTRAPOLATED to N=2^{args.K} by the n^2 cost of dense products",
+           "measured": {f"N=2^{ORACLE_K_SMALL}": v7, f"N=2^{K}": v12}}
+    errs = {}
+    if gpu_solutions is not None:
+        b = uniform_pm1(2 ** (K + 1) - 1, 4242)
+        for name, xg in gpu_solutions(K, b).items():
+            errs[f"{name}_vs_oracle_N2e{K}"] = float(np.linalg.norm(xg - u12) / np.linalg.norm(u12))
+    return out, errs
 
 
 def run_reference(args, rank):
     if rank != 0:
         return
-    K_sample = 11
+    K_sample = ORACLE_K_LARGE
     H = oracle_hierarchy(K_sample, args.delta)
     per = []
     for s in range(args.warmup + args.steps):
-        v, det = oracle_sample(K_sample, args.delta, args.tol, reps=1, H=H)
+        v, det, _ = oracle_sample(K_sample, args.delta, args.tol, reps=1, H=H, seed0=s)
         if s >= args.warmup:
             per.append(1.0 / v)
     sec = float(np.mean(per))
@@ -172,7 +237,8 @@ def run_reference(args, rank):
             "config": workload(args.K, args.delta),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                              "sample": f"each step one dense oracle solve at N=2^{K_sample} "
-                                       f"({sec:.3f} s); extrapolated to N=2^{args.K} by n^2"},
+                                       f"({sec:.3f} s, set-up not timed); value EXTRAPOLATED "
+                                       f"to N=2^{args.K} by the n^2 cost of dense products"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -405,6 +471,23 @@ def time_serving(tpc, torch, args):
     return out
 
 
+def gpu_solutions(tpc, torch, args, K, b):
+    """GPU solutions (mixed and FP64, tol as the headline) of one right-hand side at N = 2^K."""
+    out = {}
+    for name, prec in (("mixed", tpc.TPC_MIXED), ("fp64", tpc.TPC_FP64)):
+        S = tpc.Solver(args.delta, 2.0 ** -K, precision=prec)
+        try:
+            bd = torch.tensor(b, device="cuda")
+            xd = torch.zeros_like(bd)
+            rc, it, rel = S.solve(bd, xd, tol=args.tol)
+            assert rc == tpc.TPC_OK and rel < args.tol
+            torch.cuda.synchronize()
+            out[name] = xd.cpu().numpy()
+        finally:
+            S.close()
+    return out
+
+
 def replica_throughput(local_ms, steps, world, dist=None, device=None):
     """Whole-job throughput of N replicas: every rank times `steps` of its own solves; the
     job's time is the maximum over ranks (all_reduce MAX), and the value counts the solves of
@@ -450,6 +533,11 @@ def run_ours(args, rank, world, local_rank):
     ms64, it64, l64, _ = time_solves(tpc, torch, S64, stream, rhs, x, args)
     barrier()
     ms64 = max_over_ranks(ms64)
+    cyc64 = tpc.tpc_last_solve_cycles(S64.handle)
+    # FP64 solution of rhs[0], the reference of the mixed solutions' error
+    x64 = torch.zeros_like(x)
+    rc, it, rel = S64.solve(rhs[0], x64, tol=args.tol)
+    assert rc == tpc.TPC_OK and rel < args.tol
     # dominant FP64 kernel: the contiguous-block kernel of the finest level (forward transform
     # stages, spectral product, inverse transform stages), timed with CUDA events
     y = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -465,8 +553,13 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     ms_max = max_over_ranks(ms)
     value = world * args.steps / (ms_max / 1000.0)
-    # check the last result against an FP64 residual computed by the FP64 product
-    x_last = x.clone()
+    cyc_mixed = tpc.tpc_last_solve_cycles(S.handle)
+    # per-result error of the mixed solution against the FP64 solution of the same system
+    xm = torch.zeros_like(x)
+    rc, it_m, rel_m = S.solve(rhs[0], xm, tol=args.tol)
+    assert rc == tpc.TPC_OK and rel_m < args.tol
+    err_vs_fp64 = (torch.linalg.norm(xm - x64) / torch.linalg.norm(x64)).item()
+    del xm, x64
 
     # end to end through the host-buffer entry point (pinned host memory)
     b_host = torch.tensor(uniform_pm1(n, 77 + rank), dtype=torch.float64).pin_memory()
@@ -484,36 +577,69 @@ def run_ours(args, rank, world, local_rank):
     y32 = torch.empty_like(x32)
     ms3_32 = tpc.tpc_time_level_kernels_f32(S.handle, args.K, 5, x32, f32, y32)
     S.close()
-    del x_last, x32, f32, y32
+    del x32, f32, y32
 
+    NK = (1 << args.K) - 1
+    hbm = measured_hbm_gbs()
+    digest = kernel_digest()
+    # headline path: one FP32 product of the finest level = forward strided pass +
+    # contiguous-block kernel + inverse strided pass (residual epilogue), each timed alone
+    names = ("k_fwd_strided<float>", "k_mid_pair<float>", "k_inv_strided<float>")
+    t_prod = sum(ms3_32) * 1e-3
+    b_prod = product_bytes(NK, 4)
+    split = product_bytes_split(NK, 4)
+    ach32 = b_prod / t_prod / 1e9
+    tr32 = traffic_for("f32", args.K)
+    roofline = {"bound": "hbm", "achieved": ach32, "peak": hbm["gbs"], "unit": "GB/s",
+                "frac": ach32 / hbm["gbs"],
+                "traffic": (sum(tr32) if tr32 else None),
+                "kernel": "FP32 finest-level product (k_fwd_strided + k_mid_pair + "
+                          "k_inv_strided, residual epilogue), N_K = 2^%d - 1" % args.K,
+                "algorithmic_bytes_per_launch": b_prod,
+                "algorithmic_bytes_rule": "40 n B per FP32 SPD product, n = N_K (read u 8n, "
+                                          "spectra 16n, write y 8n, right-hand side 8n)",
+                "peak_source": hbm["source"] + " (of measured)",
+                "ms_per_launch": dict(zip(("fwd_strided", "mid", "inv_strided"), ms3_32)),
+                "achieved_per_kernel": {names[i]: split[i] / (ms3_32[i] * 1e-3) / 1e9
+                                        for i in range(3)},
+                "traffic_per_kernel": (dict(zip(names, tr32)) if tr32 else None),
+                "kernel_digest": digest}
+    # FP64 residual product: bound by the FP64 pipe on GB300
     m = 2 ** (args.K + 1)
     logL = min(12, (args.K + 2) // 2)
     flops_mid = m * (2 * 5 * logL + 14)       # DIF + DIT radix-2 stages, spectral product
     achieved = flops_mid / (ms3[1] * 1e-3) / 1e12
     sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
     peak = N_SMS * FP64_FLOP_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
+    b64 = product_bytes(NK, 8)
     roofline_fp64 = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": MID_TRAFFIC.get(args.K),
+                     "frac": achieved / peak, "traffic": traffic_for("f64_mid", args.K),
                      "kernel": "k_mid_pair<double> (finest level; the FP64 residual product)",
                      "peak_source": "FP64: 152 SMs x 4 flop/clk x max SM clock (unit counts "
                                     "and clocks; FMA-loop probe 1.19 TFLOP/s)",
                      "ms_per_launch": {"fwd_strided": ms3[0], "mid": ms3[1],
-                                       "inv_strided": ms3[2]}}
-    # headline path: the FP32 finest-level kernels, each launched once per FP32 product; the
-    # dominant one is the slowest of the three
-    names = ("k_fwd_strided<float>", "k_mid_pair<float>", "k_inv_strided<float>")
-    dom = max(range(3), key=lambda i: ms3_32[i])
-    nbytes = [b * m for b in f32_bytes_per_point(cfg["r"], 2 ** args.K)]
-    hbm = measured_hbm_gbs()
-    ach32 = nbytes[dom] / (ms3_32[dom] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": ach32, "peak": hbm["gbs"], "unit": "GB/s",
-                "frac": ach32 / hbm["gbs"], "traffic": F32_TRAFFIC.get((args.K, dom)),
-                "kernel": names[dom] + " (finest level of the FP32 V-cycles)",
-                "algorithmic_bytes_per_launch": nbytes[dom],
-                "peak_source": hbm["source"],
-                "ms_per_launch": dict(zip(("fwd_strided", "mid", "inv_strided"), ms3_32)),
-                "achieved_all": {names[i]: nbytes[i] / (ms3_32[i] * 1e-3) / 1e9
-                                 for i in range(3)}}
+                                       "inv_strided": ms3[2]},
+                     "product_hbm": {"algorithmic_bytes": b64,
+                                     "achieved_gbs": b64 / (sum(ms3) * 1e-3) / 1e9,
+                                     "frac_of_hbm": b64 / (sum(ms3) * 1e-3) / 1e9 / hbm["gbs"]}}
+    # whole solves: the algorithmic bytes of every product the solve runs over its time
+    kc = 3
+    sb_mixed = solve_bytes(args.K, kc, cyc_mixed, iters[-1], True)
+    sb_fp64 = solve_bytes(args.K, kc, cyc64, it64[-1], False)
+    solve_level = {
+        "mixed": {"algorithmic_bytes": sb_mixed, "vcycles_fp32": cyc_mixed,
+                  "outer_iters": iters[-1],
+                  "achieved_gbs": sb_mixed / (ms_max / args.steps * 1e-3) / 1e9,
+                  "frac_of_hbm": sb_mixed / (ms_max / args.steps * 1e-3) / 1e9 / hbm["gbs"]},
+        "fp64": {"algorithmic_bytes": sb_fp64, "vcycles": cyc64,
+                 "achieved_gbs": sb_fp64 / (ms64 / args.steps * 1e-3) / 1e9,
+                 "frac_of_hbm": sb_fp64 / (ms64 / args.steps * 1e-3) / 1e9 / hbm["gbs"]},
+        "rule": "sum over the solve's products of the per-product algorithmic bytes (40 n_k B "
+                "FP32, 80 n_k B FP64, SPD): 2 per level above the coarsest per V-cycle, plus "
+                "the finest residuals; element-wise kernels not counted"}
+    errors = {"mixed_vs_fp64_gpu_N2e%d" % args.K: err_vs_fp64,
+              "note": "||x_mixed - x_fp64|| / ||x_fp64|| for the same right-hand side, both "
+                      "at relative residual < %g" % args.tol}
     # the fractional-kernel, batched and served measurements run on one GPU (a single-rank job)
     frac = time_fractional(tpc, torch, args, stream) if world == 1 else None
     batch = time_batch(tpc, torch, args, rank) if (args.batch > 0 and world == 1) else None
@@ -532,6 +658,7 @@ def run_ours(args, rank, world, local_rank):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                         "d2h_bytes_per_step": 8 * n},
                 "roofline": roofline, "roofline_fp64": roofline_fp64, "clocks": clk,
+                "solve_level_hbm": solve_level, "result_errors": errors,
                 "gpu_launches": int(launches)}
         line["speedup_mixed_vs_fp64"] = line["value"] / line["fp64"]["value"]
         if frac:
@@ -541,7 +668,9 @@ def run_ours(args, rank, world, local_rank):
         if serving:
             line["serving"] = serving
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(args)
+            line["cpu_baseline"], oerr = cpu_baseline(args, lambda K, b: gpu_solutions(
+                tpc, torch, args, K, b))
+            errors.update(oerr)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -245,6 +245,11 @@ int tpc_time_level_kernels_f32(tpc_handle* H, int level, int reps, const float* 
  * of the graph). */
 long long tpc_kernel_launches(const tpc_handle* H);
 
+/* V-cycles (Algorithm 2) run by the handle's latest solve: FP32 V-cycles summed over the outer
+ * iterations for TPC_MIXED, one per outer iteration for TPC_FP64. Used to count the work of a
+ * solve (its products per level) for measurements. -1 for a NULL handle. */
+int tpc_last_solve_cycles(const tpc_handle* H);
+
 /* y = A x for ONE level given in generator-plus-Cross form, for callers that cannot allocate
  * device memory (work recorded while a CUDA graph is captured with allocation disallowed, a
  * plugin whose host application owns every device allocation, a path that must not let
@@ -258,9 +263,10 @@ long long tpc_kernel_launches(const tpc_handle* H);
  * doubles, not aliasing. Work is ordered on cuda_stream (NULL = default stream) and the call
  * does not block. All calls share the static array and it keeps the last call's contents:
  * calls that overlap on the GPU race, so order them on one stream. The first call on a device
- * sets that device up (static array address, kernel limits, twiddle table) and synchronises
- * it; make it before any stream capture. Returns TPC_OK, TPC_EINVAL or TPC_ECUDA (message in
- * tpc_last_error(NULL)). */
+ * sets that device up (static array address, kernel limits) and synchronises it; make it
+ * before any stream capture. Levels of TPC_SPD and TPC_NONSYM handles only: the tridiagonal
+ * band of a TPC_WEAKLY level is not in this layout and is not applied. Returns TPC_OK,
+ * TPC_EINVAL or TPC_ECUDA (message in tpc_last_error(NULL)). */
 int tpc_apply_noalloc(long long N, const double* tA, const double* tB, const double* tC,
                       const double* tD, const double* p, const double* q, const double* xi,
                       const double* zeta, double o, const double* x_dev, double* y_dev,

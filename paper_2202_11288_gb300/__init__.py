@@ -29,7 +29,8 @@ EXPORTED = ["tpc_default_params", "tpc_setup", "tpc_solve", "tpc_solve_batch", "
             "tpc_apply_f32",
             "tpc_vcycle", "tpc_level_size", "tpc_finest_level", "tpc_coarsest_level",
             "tpc_export_level", "tpc_host_hierarchy", "tpc_time_level_kernels",
-            "tpc_time_level_kernels_f32", "tpc_kernel_launches", "tpc_apply_noalloc",
+            "tpc_time_level_kernels_f32", "tpc_kernel_launches", "tpc_last_solve_cycles",
+            "tpc_apply_noalloc",
             "tpc_bdf4_coefficients", "tpc_collocation_rhs", "tpc_bdf4_step",
             "tpc_host_dense_level",
             "tpc_destroy", "tpc_last_error",
@@ -124,6 +125,8 @@ def lib() -> ctypes.CDLL:
     L.tpc_time_level_kernels_f32.restype = I
     L.tpc_kernel_launches.argtypes = [P]
     L.tpc_kernel_launches.restype = LL
+    L.tpc_last_solve_cycles.argtypes = [P]
+    L.tpc_last_solve_cycles.restype = I
     L.tpc_apply_noalloc.argtypes = [LL, P, P, P, P, P, P, P, P, D, P, P, P]
     L.tpc_apply_noalloc.restype = I
     L.tpc_server_default_config.argtypes = [ctypes.POINTER(TpcServerConfig)]
@@ -351,6 +354,10 @@ def tpc_time_level_kernels_f32(H, level: int, reps: int, x, f, y):
 
 def tpc_kernel_launches(H) -> int:
     return int(lib().tpc_kernel_launches(H))
+
+
+def tpc_last_solve_cycles(H) -> int:
+    return int(lib().tpc_last_solve_cycles(H))
 
 
 def tpc_apply_noalloc(N: int, tA, tB, tC, tD, p, q, xi, zeta, o: float, x, y,

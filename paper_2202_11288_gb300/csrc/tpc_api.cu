@@ -106,6 +106,7 @@ struct tpc_handle {
   long long iter_nodes[33] = {};      // kernel nodes of iter_exec[c]
   cudaEvent_t ev = nullptr;           // marks the latest ||r||^2 read-back
   long long launches = 0;             // kernels launched so far (see tpc_kernel_launches)
+  int last_cycles = 0;                // V-cycles of the latest solve (tpc_last_solve_cycles)
   std::string err;
   std::vector<void*> dev_allocs;
   size_t dev_bytes = 0;               // device memory held by the handle
@@ -858,6 +859,7 @@ int solve_begin(SolveState& st, const double* b_dev, double* x_dev, double tol, 
   st.status = TPC_OK;
   st.started = false;
   st.done = false;
+  H->last_cycles = 0;
   TPC_CUDA(H, cudaMemcpyAsync(H->b, b_dev, bytes, cudaMemcpyDeviceToDevice, s));
   if (use_x0) {
     TPC_CUDA(H, cudaMemcpyAsync(H->u, x_dev, bytes, cudaMemcpyDeviceToDevice, s));
@@ -925,6 +927,7 @@ int solve_step(SolveState& st) {
   st.iter_range = nvtxRangeStartEx(&ea);
   TPC_CUDA(H, cudaGraphLaunch(H->iter_exec[c], s));
   H->launches += H->iter_nodes[c];
+  H->last_cycles += c;
   TPC_CUDA(H, cudaMemcpyAsync(H->sumsq_host, H->sumsq, sizeof(double), cudaMemcpyDeviceToHost, s));
   TPC_CUDA(H, cudaEventRecord(H->ev, s));
   return TPC_OK;
@@ -1339,6 +1342,8 @@ int tpc_time_level_kernels_f32(tpc_handle* H, int level, int reps, const float* 
 }
 
 long long tpc_kernel_launches(const tpc_handle* H) { return H ? H->launches : 0; }
+
+int tpc_last_solve_cycles(const tpc_handle* H) { return H ? H->last_cycles : -1; }
 
 void tpc_destroy(tpc_handle* H) { release(H); }
 

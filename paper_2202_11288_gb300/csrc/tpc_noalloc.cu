@@ -19,11 +19,18 @@
 //     on the GPU (different streams, or different host threads) race and corrupt each other;
 //     calls must be ordered (same stream, or synchronised);
 //   * the first call on a device does a one-time set-up on that device (the array's device
-//     address via cudaGetSymbolAddress, shared-memory limits of the kernels, the 4096-point
-//     twiddle table); make that first call before any stream capture.
+//     address via cudaGetSymbolAddress, shared-memory limits of the kernels) and synchronises
+//     it; make that first call before any stream capture. Every call looks the address up
+//     again and repeats the set-up if it changed (the device was reset and the module loaded
+//     anew), and writes the 4096-point twiddle table on its own stream, so nothing of an
+//     earlier context is trusted.
+//   * only Toeplitz-plus-Cross levels (TPC_SPD, TPC_NONSYM): the tridiagonal band of the
+//     weakly singular model (section 2.1) is not part of the generator-plus-Cross layout and
+//     is not applied.
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "tpc_internal.h"
@@ -57,7 +64,9 @@ constexpr size_t NOALLOC_BYTES = OFF_PART + NA_MAX_PARTS * 8;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
+// Per device: the address the last set-up found (nullptr: not set up), guarded by g_mu.
 unsigned char* g_dev_ptr[NOALLOC_MAX_DEV] = {nullptr};
+std::mutex g_mu;
 
 // W_n^j = exp(-2 pi i j / n), j < count (n a power of two), from sincospi.
 __global__ void k_na_twiddles(double2* out, long long n, long long count) {
@@ -85,16 +94,20 @@ int fail(int code, const char* msg) {
   return code;
 }
 
+// The static array's device address on the current device (looked up on every call, which
+// allocates nothing), and the kernels' shared-memory limits, set once per address.
 int setup_device(int dev, unsigned char** base) {
-  if (g_dev_ptr[dev]) {
-    *base = g_dev_ptr[dev];
-    return TPC_OK;
-  }
   void* p = nullptr;
   cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess || !p) {
     (void)cudaGetLastError();
     return fail(TPC_ECUDA, "tpc_apply_noalloc: cudaGetSymbolAddress failed");
+  }
+  unsigned char* b = static_cast<unsigned char*>(p);
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_dev_ptr[dev] == b) {
+    *base = b;
+    return TPC_OK;
   }
   const int big = 150 * 1024;
   const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
@@ -108,12 +121,8 @@ int setup_device(int dev, unsigned char** base) {
     (void)cudaGetLastError();
     return fail(TPC_ECUDA, "tpc_apply_noalloc: cudaFuncSetAttribute failed");
   }
-  unsigned char* b = static_cast<unsigned char*>(p);
-  const long long nl = 1LL << LOG_LMAX;
-  k_na_twiddles<<<(unsigned)((nl + 255) / 256), 256>>>(reinterpret_cast<double2*>(b + OFF_TWL),
-                                                      nl, nl);
   e = cudaDeviceSynchronize();
-  if (e != cudaSuccess) return fail(TPC_ECUDA, "tpc_apply_noalloc: set-up kernel failed");
+  if (e != cudaSuccess) return fail(TPC_ECUDA, "tpc_apply_noalloc: device set-up failed");
   g_dev_ptr[dev] = b;
   *base = b;
   return TPC_OK;
@@ -199,6 +208,8 @@ extern "C" int tpc_apply_noalloc(long long N, const double* tA, const double* tB
   a.partials = parts;
   a.nparts = fwd_blocks;
   const unsigned gm = (unsigned)((m + 255) / 256);
+  const long long nl = 1LL << LOG_LMAX;
+  k_na_twiddles<<<(unsigned)((nl + 255) / 256), 256, 0, s>>>(twL, nl, nl);
   if (logR1) k_na_twiddles<<<gm, 256, 0, s>>>(twm, m, m);
 
   // spectra of the four Toeplitz blocks, divided by 2m, in bit-reversed order
