@@ -17,6 +17,7 @@
 
 #include "tpc_internal.h"
 #include "tpc_kernels.cuh"
+#include "tpc_f32.cuh"
 
 namespace tpc {
 void set_host_error(const std::string& s);
@@ -55,6 +56,9 @@ template <typename T> struct DevLevel {
   T* wpre = nullptr;
   T* wpost = nullptr;
   c2<T>* twm = nullptr;
+  // FP32 levels with m = 2^20 .. 2^23 (no band): the register-resident kernels of tpc_f32.cuh
+  // with four columns per strided tile
+  bool f32reg = false;
 };
 
 // Smallest s with v[i] == 0 for every i >= s (over the union of two vectors).
@@ -71,6 +75,7 @@ template <typename T> struct Hier {
   c2<T>* z = nullptr;            // complex work array (m_K)
   T* partials = nullptr;
   c2<T>* twL = nullptr;          // W_4096^j, j < 4096 (FP32 kernels copy j <= 512)
+  c2<T>* tws = nullptr;          // FP32: step twiddle tables (f32p::STEP_TW_ENTRIES)
   T* coarse_inv = nullptr;
   BottomPlan<T>* bottom = nullptr;  // single-block V-cycle bottom (FP32, V(1,1)), or null
   int bottom_li = -1;               // level index where it takes over
@@ -242,6 +247,7 @@ LevelArgs<T> level_args(const Hier<T>& G, const DevLevel<T>& L) {
   a.o = L.o;
   a.twm = L.twm;
   a.twL = G.twL;
+  a.tws = G.tws;
   a.z = G.z;
   a.partials = G.partials;
   a.nparts = L.fwd_blocks;
@@ -286,6 +292,14 @@ void launch_matvec(tpc_handle* H, const Hier<T>& G, const DevLevel<T>& L, const 
     return;
   }
   H->launches += 3;
+  if constexpr (sizeof(T) == 4) {
+    if (L.f32reg) {
+      f32p::launch_fwd(a, L.fwd_blocks, s);
+      f32p::launch_mid<NS>(a, L.mid_blocks, s);
+      f32p::launch_inv(a, L.fwd_blocks, s);
+      return;
+    }
+  }
   launch_fwd_strided<T>(a, L.fwd_blocks, L.smem_strided, s);
   launch_mid_pair<T, NS>(a, L.mid_blocks, L.smem_mid, s);
   launch_inv_strided<T>(a, L.fwd_blocks, L.smem_strided, s);
@@ -440,8 +454,9 @@ cudaError_t set_smem_attrs() {
       return e;
     if ((e = cudaFuncSetAttribute(k_mid_fwd<T>, A, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_mid_fwd_real<T>, A, big)) != cudaSuccess) return e;
-  } else {  // the single-block V-cycle bottom runs in FP32 only
+  } else {  // the single-block V-cycle bottom and the register-resident kernels: FP32 only
     if ((e = cudaFuncSetAttribute(k_vcycle_bottom<T, NS>, A, big)) != cudaSuccess) return e;
+    if ((e = f32p::set_attrs()) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -476,6 +491,26 @@ int forward_real(tpc_handle* H, const Hier<double>& G, const DevLevel<double>& L
   return TPC_OK;
 }
 
+// Step twiddles of the register-resident FP32 kernels: for S = 2^s, s = 5..12, the entries
+// W_S^{c bitrev_16(t)} (t < 16, c < S / 16) at complex offset (S - 32) + t (S / 16) + c.
+void step_twiddle_tables(std::vector<double>& out) {
+  out.assign(2 * (size_t)f32p::STEP_TW_ENTRIES, 0.0);
+  std::vector<double> w;
+  for (int ls = 5; ls <= 12; ++ls) {
+    const long long S = 1LL << ls, cols = S / 16;
+    twiddles(S, S, w);
+    for (int t = 0; t < 16; ++t) {
+      const long long bt = (long long)(((t & 1) << 3) | ((t & 2) << 1) | ((t & 4) >> 1) | ((t & 8) >> 3));
+      for (long long c = 0; c < cols; ++c) {
+        const long long e = (c * bt) % S;
+        const size_t o = (size_t)(f32p::steptw_off(ls) + t * cols + c);
+        out[2 * o] = w[2 * e];
+        out[2 * o + 1] = w[2 * e + 1];
+      }
+    }
+  }
+}
+
 // Level data (plan, Cross, diagonal weights, twiddles, vectors) of hierarchy G.
 template <typename T>
 int alloc_levels(tpc_handle* H, Hier<T>& G) {
@@ -487,6 +522,12 @@ int alloc_levels(tpc_handle* H, Hier<T>& G) {
   twiddles(1LL << LOG_LMAX, 1LL << LOG_LMAX, tw);  // W_4096^j, j < 4096
   TPC_TRY(dalloc(H, &G.twL, (size_t)1 << LOG_LMAX));
   TPC_TRY(upload<T>(H, reinterpret_cast<T*>(G.twL), tw));
+  if (sizeof(T) == 4) {
+    std::vector<double> st;
+    step_twiddle_tables(st);
+    TPC_TRY(dalloc(H, &G.tws, (size_t)f32p::STEP_TW_ENTRIES));
+    TPC_TRY(upload<T>(H, reinterpret_cast<T*>(G.tws), st));
+  }
   long long max_m = 0;
   int max_parts = 1;
   for (int i = 0; i < nlev; ++i) {
@@ -497,6 +538,13 @@ int alloc_levels(tpc_handle* H, Hier<T>& G) {
     L.n = 2 * F.N + 1;
     L.m = 2 * F.N + 2;
     plan_level(L);
+    if (sizeof(T) == 4 && f32p::eligible(L.logm, L.logR1, L.logL, F.has_band())) {
+      L.f32reg = true;
+      L.logC = f32p::LOG_CT;
+      L.fwd_blocks = 1 << (L.logL - f32p::LOG_CT);
+      L.smem_strided = f32p::strided_smem(L.logR1);
+      L.smem_mid = f32p::mid_smem(L.logL);
+    }
     if (L.logR1 > LOG_R1_MAX) {
       H->err = "level too large for this build (m > 2^23)";
       return TPC_ENOTSUP;
@@ -655,7 +703,7 @@ int autotune_levels(tpc_handle* H, Hier<T>& G, bool only_finest) {
   for (size_t li = 0; li < G.lev.size() && rc == TPC_OK; ++li) {
     if (only_finest && li > 0) break;
     DevLevel<T>& L = G.lev[li];
-    if (L.logR1 == 0 || !L.sA) continue;
+    if (L.logR1 == 0 || !L.sA || L.f32reg) continue;
     const std::pair<int, int> key((int)sizeof(T), L.logm);
     const auto hit = g_tuned_logC.find(key);
     if (hit != g_tuned_logC.end()) {
@@ -1087,7 +1135,18 @@ int time_level(tpc_handle* H, const Hier<T>& G, int level, int reps, const T* x_
     if (L.logR1 == 0 && which != 1) continue;
     for (int rep = 0; rep <= reps; ++rep) {
       if (rep == 1) cudaEventRecord(ev[0], s);
-      if (which == 0) {
+      bool done = false;
+      if constexpr (sizeof(T) == 4) {
+        if (L.f32reg) {
+          if (which == 0) f32p::launch_fwd(a, L.fwd_blocks, s);
+          else if (which == 2) f32p::launch_inv(a, L.fwd_blocks, s);
+          else if (ns) f32p::launch_mid<true>(a, L.mid_blocks, s);
+          else f32p::launch_mid<false>(a, L.mid_blocks, s);
+          done = true;
+        }
+      }
+      if (done) {
+      } else if (which == 0) {
         launch_fwd_strided<T>(a, L.fwd_blocks, L.smem_strided, s);
       } else if (which == 2) {
         launch_inv_strided<T>(a, L.fwd_blocks, L.smem_strided, s);

@@ -100,6 +100,7 @@ template <typename T> struct LevelArgs {
   T wA, wO, wD;          // omega / diagonal, per segment (damped Jacobi, eq. 7)
   const c2<T>* twm;      // strided pipelines only: W_m^j, j < m (FP64); two-level (FP32)
   const c2<T>* twL;      // W_{4096}^j, j < 4096 (FP32 copies the octant j <= 512 to shared)
+  const c2<T>* tws;      // FP32: step twiddle tables of the register-resident kernels (tpc_f32.cuh)
   // per call
   int pro;               // Pro
   T pA, pO, pD;          // pre-smoothing omega / diagonal per segment (PRO_SMOOTH, PRO_RESTRICT)
