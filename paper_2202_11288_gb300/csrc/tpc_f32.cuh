@@ -25,6 +25,14 @@ namespace tpc {
 namespace f32p {
 
 constexpr int NT_STRIDED = 256;  // threads of the strided passes
+// Resident blocks per SM the strided passes are compiled for, and whether a row moves as one
+// 32-byte access (1) or as two 16-byte ones (0).
+#ifndef TPC_F32_STRIDED_MINB
+#define TPC_F32_STRIDED_MINB 2
+#endif
+#ifndef TPC_F32_ROW_V8
+#define TPC_F32_ROW_V8 1
+#endif
 constexpr int CT = 4;            // columns per strided tile
 constexpr int LOG_CT = 2;
 
@@ -38,9 +46,42 @@ __host__ __device__ constexpr int steptw_off(int logS) { return (1 << logS) - 32
 __device__ __forceinline__ int pidx(int i) { return i + 2 * (i >> 4); }
 __host__ __device__ constexpr int pblock(int n) { return n + 2 * (n >> 4); }
 
-// Column pitch of a strided tile (float2 units): R1 rows padded as above, plus 4 so that the
-// four columns of a row fall on different shared-memory banks (pitch = 4 mod 16).
-__host__ __device__ constexpr int col_pitch(int R1) { return pblock(R1) + 4; }
+// Strided tile (float2 units): row-major, the four columns of a row side by side, 16 bytes of
+// padding after every group of RS rows (RS = R1 / 256, the radix of the last step). The radix-16
+// steps then touch 256 contiguous bytes per warp access and the last step's 16-byte accesses
+// (one group per lane) fall on distinct banks.
+template <int LRS>
+__device__ __forceinline__ int tidx(int row, int cc) { return 4 * row + cc + 2 * (row >> LRS); }
+// R1 / RS = 256 groups, so a tile holds 4 R1 + 512 float2.
+__host__ __device__ constexpr int tile_size(int R1) { return 4 * R1 + 512; }
+
+// 32-byte row of four complex values (one full sector) to / from global memory in one access;
+// the address must be 32-byte aligned.
+__device__ __forceinline__ void st_row(float2* dst, float2 a, float2 b, float2 c, float2 d) {
+#if !TPC_F32_ROW_V8
+  reinterpret_cast<float4*>(dst)[0] = make_float4(a.x, a.y, b.x, b.y);
+  reinterpret_cast<float4*>(dst)[1] = make_float4(c.x, c.y, d.x, d.y);
+  return;
+#endif
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(dst), "f"(a.x),
+               "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y), "f"(d.x), "f"(d.y)
+               : "memory");
+}
+__device__ __forceinline__ void ld_row(const float2* src, float2& a, float2& b, float2& c,
+                                       float2& d) {
+#if !TPC_F32_ROW_V8
+  const float4 t0 = reinterpret_cast<const float4*>(src)[0], t1 = reinterpret_cast<const float4*>(src)[1];
+  a = make_float2(t0.x, t0.y);
+  b = make_float2(t0.z, t0.w);
+  c = make_float2(t1.x, t1.y);
+  d = make_float2(t1.z, t1.w);
+  return;
+#endif
+  asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(a.x), "=f"(a.y), "=f"(b.x), "=f"(b.y), "=f"(c.x), "=f"(c.y), "=f"(d.x),
+                 "=f"(d.y)
+               : "l"(src));
+}
 
 // R-point DIF / DIT register networks (tpc_fft.cuh), R in {4, 8, 16}.
 template <int R>
@@ -122,17 +163,17 @@ __device__ __forceinline__ void mac_reg(float sa, float sd, float2 sb, float2 sc
 // W_m^{c bitrev_R1(t)}, result to z. The prologue forms the operand while it is loaded.
 // ------------------------------------------------------------------------------------------
 template <int LR1, int PRO>
-__global__ void __launch_bounds__(NT_STRIDED, 2) k32_fwd(LevelArgs<float> a) {
+__global__ void __launch_bounds__(NT_STRIDED, TPC_F32_STRIDED_MINB) k32_fwd(LevelArgs<float> a) {
   constexpr int R1 = 1 << LR1;
   constexpr int RS = R1 >> 8;                   // radix of the last step (4 or 8)
   constexpr int LRS = LR1 - 8;
-  constexpr int CP = col_pitch(R1);
   constexpr int ST1 = R1 / 16;                  // stride of the first step
   constexpr int TASKS = CT * R1 / 16;           // tasks of the radix-16 steps per tile
   static_assert(TASKS % NT_STRIDED == 0, "tile / threads");
+  static_assert(tile_size(R1) == 4 * R1 + 2 * (R1 / RS), "tile size");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* s = reinterpret_cast<float2*>(smem_raw);
-  float2* wc = s + CT * CP;                     // W_{L RS}^{(c0 + cc) k}, [cc][k]
+  float2* wc = s + tile_size(R1);               // W_{L RS}^{(c0 + cc) k}, [cc][k]
   __shared__ float red[NT_STRIDED / 32];
   const int tid = threadIdx.x;
   const int L = 1 << a.logL;
@@ -149,41 +190,45 @@ __global__ void __launch_bounds__(NT_STRIDED, 2) k32_fwd(LevelArgs<float> a) {
   for (int q = tid; q < TASKS; q += NT_STRIDED) {
     const int cc = q & (CT - 1), c1 = q >> LOG_CT;
     float2 v[16];
-    Raw<float> rv[8], rw[8];
-    float qv[8], zv[8];
+    // operand loads issued four rows at a time (fewer live registers), then formed
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int P = c0 + cc + (c1 + ST1 * j) * L;
-      rv[j] = Raw<float>{0, 0, 0};
-      rw[j] = Raw<float>{0, 0, 0};
-      qv[j] = 0.0f;
-      zv[j] = 0.0f;
-      if (P < N) {
-        rv[j] = operand_load<float>(a, P, PRO);
-        rw[j] = operand_load<float>(a, N + 1 + P, PRO);
-        if (P < a.nq) {
-          qv[j] = __ldg(a.q + P);
-          zv[j] = __ldg(a.zeta + P);
+    for (int h = 0; h < 8; h += 4) {
+      Raw<float> rv[4], rw[4];
+      float qv[4], zv[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int P = c0 + cc + (c1 + ST1 * (h + j)) * L;
+        rv[j] = Raw<float>{0, 0, 0};
+        rw[j] = Raw<float>{0, 0, 0};
+        qv[j] = 0.0f;
+        zv[j] = 0.0f;
+        if (P < N) {
+          rv[j] = operand_load<float>(a, P, PRO);
+          rw[j] = operand_load<float>(a, N + 1 + P, PRO);
+          if (P < a.nq) {
+            qv[j] = __ldg(a.q + P);
+            zv[j] = __ldg(a.zeta + P);
+          }
         }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int P = c0 + cc + (c1 + ST1 * (h + j)) * L;
+        float xv = 0.0f, xw = 0.0f;
+        if (P < N) {
+          xv = operand_finish<float>(a, P, rv[j], a.pA, PRO);
+          xw = operand_finish<float>(a, N + 1 + P, rw[j], a.pD, PRO);
+          dot = fmaf(qv[j], xv, fmaf(zv[j], xw, dot));
+        }
+        v[h + j] = make_float2(xv, xw);
       }
     }
     float2 w[16];
     load_tw<LR1>(a.tws, c1, w);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int P = c0 + cc + (c1 + ST1 * j) * L;
-      float xv = 0.0f, xw = 0.0f;
-      if (P < N) {
-        xv = operand_finish<float>(a, P, rv[j], a.pA, PRO);
-        xw = operand_finish<float>(a, N + 1 + P, rw[j], a.pD, PRO);
-        dot = fmaf(qv[j], xv, fmaf(zv[j], xw, dot));
-      }
-      v[j] = make_float2(xv, xw);
-    }
     dif16_zero_upper(v);
     apply_tw(v, w);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) s[cc * CP + pidx(c1 + ST1 * j)] = v[j];
+    for (int j = 0; j < 16; ++j) s[tidx<LRS>(c1 + ST1 * j, cc)] = v[j];
   }
   __syncthreads();
   // step 2: radix 16 on sub-blocks of 16 RS rows, stride RS
@@ -193,15 +238,14 @@ __global__ void __launch_bounds__(NT_STRIDED, 2) k32_fwd(LevelArgs<float> a) {
     const int cc = (q >> LRS) & (CT - 1);
     const int sb = q >> (LRS + LOG_CT);
     float2 v[16], w[16];
-    const int base = cc * CP;
     const int r0 = sb * 16 * RS + c2;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = s[base + pidx(r0 + RS * j)];
+    for (int j = 0; j < 16; ++j) v[j] = s[tidx<LRS>(r0 + RS * j, cc)];
     load_tw<LRS + 4>(a.tws, c2, w);
     dif<16>(v);
     apply_tw(v, w);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) s[base + pidx(r0 + RS * j)] = v[j];
+    for (int j = 0; j < 16; ++j) s[tidx<LRS>(r0 + RS * j, cc)] = v[j];
   }
   __syncthreads();
   // step 3: radix RS on groups of RS consecutive rows, all four columns per thread; inter-pass
@@ -210,14 +254,15 @@ __global__ void __launch_bounds__(NT_STRIDED, 2) k32_fwd(LevelArgs<float> a) {
   {
     const int g = tid;  // 256 groups
     float2 v[CT][RS];
+    {
+      const float4* src = reinterpret_cast<const float4*>(s + tidx<LRS>(RS * g, 0));
 #pragma unroll
-    for (int cc = 0; cc < CT; ++cc) {
-      const float4* src = reinterpret_cast<const float4*>(s + cc * CP + pidx(RS * g));
-#pragma unroll
-      for (int k = 0; k < RS / 2; ++k) {
-        const float4 t4 = src[k];
-        v[cc][2 * k] = make_float2(t4.x, t4.y);
-        v[cc][2 * k + 1] = make_float2(t4.z, t4.w);
+      for (int k = 0; k < RS; ++k) {
+        const float4 t0 = src[2 * k], t1 = src[2 * k + 1];
+        v[0][k] = make_float2(t0.x, t0.y);
+        v[1][k] = make_float2(t0.z, t0.w);
+        v[2][k] = make_float2(t1.x, t1.y);
+        v[3][k] = make_float2(t1.z, t1.w);
       }
     }
     const int bg = (int)(__brev((unsigned)g) >> 24);
@@ -232,11 +277,7 @@ __global__ void __launch_bounds__(NT_STRIDED, 2) k32_fwd(LevelArgs<float> a) {
       }
     }
 #pragma unroll
-    for (int k = 0; k < RS; ++k) {
-      float4* dst = reinterpret_cast<float4*>(a.z + c0 + (RS * g + k) * L);
-      dst[0] = make_float4(v[0][k].x, v[0][k].y, v[1][k].x, v[1][k].y);
-      dst[1] = make_float4(v[2][k].x, v[2][k].y, v[3][k].x, v[3][k].y);
-    }
+    for (int k = 0; k < RS; ++k) st_row(a.z + c0 + (RS * g + k) * L, v[0][k], v[1][k], v[2][k], v[3][k]);
   }
   const float tot = block_sum<float>(dot, red);
   if (tid == 0) {
@@ -466,16 +507,15 @@ __global__ void __launch_bounds__(1 << (LL - 4), 1 << (13 - LL)) k32_mid(LevelAr
 // columns, epilogue on the rows t < R1/2 (the first N outputs of each half).
 // ------------------------------------------------------------------------------------------
 template <int LR1, int EPI>
-__global__ void __launch_bounds__(NT_STRIDED, 2) k32_inv(LevelArgs<float> a) {
+__global__ void __launch_bounds__(NT_STRIDED, TPC_F32_STRIDED_MINB) k32_inv(LevelArgs<float> a) {
   constexpr int R1 = 1 << LR1;
   constexpr int RS = R1 >> 8;
   constexpr int LRS = LR1 - 8;
-  constexpr int CP = col_pitch(R1);
   constexpr int ST1 = R1 / 16;
   constexpr int TASKS = CT * R1 / 16;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* s = reinterpret_cast<float2*>(smem_raw);
-  float2* wc = s + CT * CP;
+  float2* wc = s + tile_size(R1);
   const int tid = threadIdx.x;
   const int L = 1 << a.logL;
   const int c0 = blockIdx.x * CT;
@@ -489,14 +529,8 @@ __global__ void __launch_bounds__(NT_STRIDED, 2) k32_inv(LevelArgs<float> a) {
     const int g = tid;
     float2 v[CT][RS];
 #pragma unroll
-    for (int k = 0; k < RS; ++k) {
-      const float4* src = reinterpret_cast<const float4*>(a.z + c0 + (RS * g + k) * L);
-      const float4 t0 = src[0], t1 = src[1];
-      v[0][k] = make_float2(t0.x, t0.y);
-      v[1][k] = make_float2(t0.z, t0.w);
-      v[2][k] = make_float2(t1.x, t1.y);
-      v[3][k] = make_float2(t1.z, t1.w);
-    }
+    for (int k = 0; k < RS; ++k)
+      ld_row(a.z + c0 + (RS * g + k) * L, v[0][k], v[1][k], v[2][k], v[3][k]);
     __syncthreads();  // the W_{L RS} table
     const int bg = (int)(__brev((unsigned)g) >> 24);
 #pragma unroll
@@ -508,11 +542,12 @@ __global__ void __launch_bounds__(NT_STRIDED, 2) k32_inv(LevelArgs<float> a) {
         v[cc][k] = cmulc<float>(v[cc][k], tw);
       }
       dit<RS>(v[cc]);
-      float4* dst = reinterpret_cast<float4*>(s + cc * CP + pidx(RS * g));
+    }
+    float4* dst = reinterpret_cast<float4*>(s + tidx<LRS>(RS * g, 0));
 #pragma unroll
-      for (int k = 0; k < RS / 2; ++k)
-        dst[k] = make_float4(v[cc][2 * k].x, v[cc][2 * k].y, v[cc][2 * k + 1].x,
-                             v[cc][2 * k + 1].y);
+    for (int k = 0; k < RS; ++k) {
+      dst[2 * k] = make_float4(v[0][k].x, v[0][k].y, v[1][k].x, v[1][k].y);
+      dst[2 * k + 1] = make_float4(v[2][k].x, v[2][k].y, v[3][k].x, v[3][k].y);
     }
   }
   __syncthreads();
@@ -523,15 +558,14 @@ __global__ void __launch_bounds__(NT_STRIDED, 2) k32_inv(LevelArgs<float> a) {
     const int cc = (q >> LRS) & (CT - 1);
     const int sb = q >> (LRS + LOG_CT);
     float2 v[16], w[16];
-    const int base = cc * CP;
     const int r0 = sb * 16 * RS + c2;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = s[base + pidx(r0 + RS * j)];
+    for (int j = 0; j < 16; ++j) v[j] = s[tidx<LRS>(r0 + RS * j, cc)];
     load_tw<LRS + 4>(a.tws, c2, w);
     apply_twc(v, w);
     dit<16>(v);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) s[base + pidx(r0 + RS * j)] = v[j];
+    for (int j = 0; j < 16; ++j) s[tidx<LRS>(r0 + RS * j, cc)] = v[j];
   }
   __syncthreads();
   // last DIT step (radix 16, stride R1/16), rows c1 + (R1/16) j for j < 8, and the epilogue
@@ -543,48 +577,51 @@ __global__ void __launch_bounds__(NT_STRIDED, 2) k32_inv(LevelArgs<float> a) {
     {
       float2 w[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = s[cc * CP + pidx(c1 + ST1 * j)];
+      for (int j = 0; j < 16; ++j) v[j] = s[tidx<LRS>(c1 + ST1 * j, cc)];
       load_tw<LR1>(a.tws, c1, w);
       apply_twc(v, w);
     }
-    // the epilogue's operands (no band on these levels): Cross column p, xi below its
-    // support, right-hand side f (residual, Jacobi), current iterate x (Jacobi)
-    float pv[8], xiv[8], fv[8], fw[8], xv[8], xw[8];
+    dit16_lower_half(v);
+    // the epilogue (no band on these levels), four rows at a time: Cross column p, xi below
+    // its support, right-hand side f (residual, Jacobi), current iterate x (Jacobi)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int P = c0 + cc + (c1 + ST1 * j) * L;
-      pv[j] = xiv[j] = fv[j] = fw[j] = xv[j] = xw[j] = 0.0f;
-      if (P < N) {
-        if (P < a.np) {
-          pv[j] = __ldg(a.p + P);
-          xiv[j] = __ldg(a.xi + P);
-        }
-        if (EPI != EPI_APPLY) {
-          fv[j] = __ldg(a.f + P);
-          fw[j] = __ldg(a.f + N + 1 + P);
-        }
-        if (EPI == EPI_JACOBI) {
-          xv[j] = a.x[P];
-          xw[j] = a.x[N + 1 + P];
+    for (int h = 0; h < 8; h += 4) {
+      float pv[4], xiv[4], fv[4], fw[4], xv[4], xw[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int P = c0 + cc + (c1 + ST1 * (h + j)) * L;
+        pv[j] = xiv[j] = fv[j] = fw[j] = xv[j] = xw[j] = 0.0f;
+        if (P < N) {
+          if (P < a.np) {
+            pv[j] = __ldg(a.p + P);
+            xiv[j] = __ldg(a.xi + P);
+          }
+          if (EPI != EPI_APPLY) {
+            fv[j] = __ldg(a.f + P);
+            fw[j] = __ldg(a.f + N + 1 + P);
+          }
+          if (EPI == EPI_JACOBI) {
+            xv[j] = a.x[P];
+            xw[j] = a.x[N + 1 + P];
+          }
         }
       }
-    }
-    dit16_lower_half(v);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int P = c0 + cc + (c1 + ST1 * j) * L;
-      if (P < N) {
-        const float yv = fmaf(pv[j], w_o, v[j].x);
-        const float yw = fmaf(xiv[j], w_o, v[j].y);
-        if (EPI == EPI_APPLY) {
-          a.y[P] = yv;
-          a.y[N + 1 + P] = yw;
-        } else if (EPI == EPI_RESID) {
-          a.y[P] = fv[j] - yv;
-          a.y[N + 1 + P] = fw[j] - yw;
-        } else {
-          a.y[P] = fmaf(a.wA, fv[j] - yv, xv[j]);
-          a.y[N + 1 + P] = fmaf(a.wD, fw[j] - yw, xw[j]);
+      for (int j = 0; j < 4; ++j) {
+        const int P = c0 + cc + (c1 + ST1 * (h + j)) * L;
+        if (P < N) {
+          const float yv = fmaf(pv[j], w_o, v[h + j].x);
+          const float yw = fmaf(xiv[j], w_o, v[h + j].y);
+          if (EPI == EPI_APPLY) {
+            a.y[P] = yv;
+            a.y[N + 1 + P] = yw;
+          } else if (EPI == EPI_RESID) {
+            a.y[P] = fv[j] - yv;
+            a.y[N + 1 + P] = fw[j] - yw;
+          } else {
+            a.y[P] = fmaf(a.wA, fv[j] - yv, xv[j]);
+            a.y[N + 1 + P] = fmaf(a.wD, fw[j] - yw, xw[j]);
+          }
         }
       }
     }
@@ -600,7 +637,7 @@ __global__ void __launch_bounds__(NT_STRIDED, 2) k32_inv(LevelArgs<float> a) {
 // Dynamic shared memory of the kernels.
 inline size_t strided_smem(int logR1) {
   const int R1 = 1 << logR1;
-  return sizeof(float2) * (size_t)(CT * col_pitch(R1) + CT * (R1 >> 8));
+  return sizeof(float2) * (size_t)(tile_size(R1) + CT * (R1 >> 8));
 }
 inline size_t mid_smem(int logL) { return sizeof(float2) * (size_t)(2 * pblock(1 << logL)); }
 
