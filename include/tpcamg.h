@@ -91,6 +91,11 @@ typedef struct tpc_params {
                          unknowns listed by position, whose coarse unknowns are the fine
                          nodes; the V-cycle then converges at the constant kernel's rate
                          for the fractional kernel too. Not for TPC_WEAKLY (ENOTSUP)      */
+  int box_residual;   /* 1 (default): when the finest level's Toeplitz generators are piecewise
+                         constant (the constant kernel, eq. (2.9) / eq. (2.11), any shift),
+                         the outer FP64 residual b - A u is formed from prefix sums of u, one
+                         term per run of equal generator values, instead of two FFTs; 0: the
+                         FFT product always. The V-cycles are not affected                 */
 } tpc_params;
 
 typedef struct tpc_handle tpc_handle;
@@ -244,6 +249,17 @@ int tpc_time_level_kernels_f32(tpc_handle* H, int level, int reps, const float* 
 /* Number of kernels this handle has launched so far (graph launches count every kernel node
  * of the graph). */
 long long tpc_kernel_launches(const tpc_handle* H);
+
+/* r = b - A_K x on the finest level, the outer residual of tpc_solve (section 5), formed the
+ * way the solver forms it: from prefix sums of x over the runs of equal generator values when
+ * the handle uses box_residual (see tpc_params), else with the FFT product of eq. (3.4).
+ * x_dev, b_dev, r_dev: device arrays of n_K doubles; r_dev must alias neither input.
+ * Stream-ordered on the handle's stream, does not block. TPC_OK or TPC_EINVAL. */
+int tpc_residual(tpc_handle* H, const double* x_dev, const double* b_dev, double* r_dev);
+
+/* 1 if the handle forms its outer residual from prefix sums (box_residual in effect), 0 if it
+ * uses the FFT product; -1 for a NULL handle. */
+int tpc_uses_box_residual(const tpc_handle* H);
 
 /* V-cycles (Algorithm 2) run by the handle's latest solve: FP32 V-cycles summed over the outer
  * iterations for TPC_MIXED, one per outer iteration for TPC_FP64. Used to count the work of a

@@ -30,6 +30,7 @@ EXPORTED = ["tpc_default_params", "tpc_setup", "tpc_solve", "tpc_solve_batch", "
             "tpc_vcycle", "tpc_level_size", "tpc_finest_level", "tpc_coarsest_level",
             "tpc_export_level", "tpc_host_hierarchy", "tpc_time_level_kernels",
             "tpc_time_level_kernels_f32", "tpc_kernel_launches", "tpc_last_solve_cycles",
+            "tpc_residual", "tpc_uses_box_residual",
             "tpc_apply_noalloc",
             "tpc_bdf4_coefficients", "tpc_collocation_rhs", "tpc_bdf4_step",
             "tpc_host_dense_level",
@@ -46,7 +47,7 @@ class TpcParams(ctypes.Structure):
                 ("coarsest_level", ctypes.c_int), ("precision", ctypes.c_int),
                 ("max_iters", ctypes.c_int), ("inner_cycles", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("poison", ctypes.c_int),
-                ("transfer", ctypes.c_int)]
+                ("transfer", ctypes.c_int), ("box_residual", ctypes.c_int)]
 
 
 class TpcServerConfig(ctypes.Structure):
@@ -127,6 +128,10 @@ def lib() -> ctypes.CDLL:
     L.tpc_kernel_launches.restype = LL
     L.tpc_last_solve_cycles.argtypes = [P]
     L.tpc_last_solve_cycles.restype = I
+    L.tpc_residual.argtypes = [P, P, P, P]
+    L.tpc_residual.restype = I
+    L.tpc_uses_box_residual.argtypes = [P]
+    L.tpc_uses_box_residual.restype = I
     L.tpc_apply_noalloc.argtypes = [LL, P, P, P, P, P, P, P, P, D, P, P, P]
     L.tpc_apply_noalloc.restype = I
     L.tpc_server_default_config.argtypes = [ctypes.POINTER(TpcServerConfig)]
@@ -356,6 +361,14 @@ def tpc_kernel_launches(H) -> int:
     return int(lib().tpc_kernel_launches(H))
 
 
+def tpc_residual(H, x, b, r) -> None:
+    _check(lib().tpc_residual(H, _ptr(x), _ptr(b), _ptr(r)), H)
+
+
+def tpc_uses_box_residual(H) -> int:
+    return int(lib().tpc_uses_box_residual(H))
+
+
 def tpc_last_solve_cycles(H) -> int:
     return int(lib().tpc_last_solve_cycles(H))
 
@@ -403,6 +416,9 @@ class Solver:
 
     def vcycle(self, r, e) -> None:
         tpc_vcycle(self.handle, r, e)
+
+    def residual(self, x, b, r) -> None:
+        tpc_residual(self.handle, x, b, r)
 
     def level_size(self, level: int) -> int:
         return tpc_level_size(self.handle, level)

@@ -18,6 +18,7 @@
 #include "tpc_internal.h"
 #include "tpc_kernels.cuh"
 #include "tpc_f32.cuh"
+#include "tpc_box.cuh"
 
 namespace tpc {
 void set_host_error(const std::string& s);
@@ -112,6 +113,10 @@ struct tpc_handle {
   cudaEvent_t ev = nullptr;           // marks the latest ||r||^2 read-back
   long long launches = 0;             // kernels launched so far (see tpc_kernel_launches)
   int last_cycles = 0;                // V-cycles of the latest solve (tpc_last_solve_cycles)
+  // finest residual from prefix sums (tpc_params.box_residual, piecewise-constant generators):
+  // the arguments with the work arrays filled in (operand, right-hand side, result per call)
+  bool box_on = false;
+  box::BoxArgs box_args{};
   std::string err;
   std::vector<void*> dev_allocs;
   size_t dev_bytes = 0;               // device memory held by the handle
@@ -378,6 +383,78 @@ T* enqueue_vcycle(tpc_handle* H, Hier<T>& G, int li, const T* f_top, const T* rf
   return e;
 }
 
+// r = b - A_K x on the finest level (the outer residual): from prefix sums when the handle
+// uses the box form, else the FFT product with its residual epilogue.
+void enqueue_finest_residual(tpc_handle* H, const double* x, const double* b, double* r) {
+  if (!H->box_on) {
+    matvec<double>(H, H->d, 0, x, b, r, EPI_RESID, false);
+    return;
+  }
+  box::BoxArgs a = H->box_args;
+  a.x = x;
+  a.b = b;
+  a.r = r;
+  cudaStream_t s = H->stream;
+  box::k_box_local<<<2 * a.nblk, box::NT, 0, s>>>(a);
+  box::k_box_offsets<<<1, 1024, 0, s>>>(a);
+  const int gx = (int)std::min<long long>((a.N + box::NT - 1) / box::NT, 4 * 152);
+  box::k_box_resid<<<dim3(gx, 2), box::NT, 0, s>>>(a);
+  H->launches += 3;
+}
+
+// Runs of equal nonzero values of a generator t[d + N - 1] (d = -(N-1)..N-1); -1 if there are
+// more than maxr.
+int generator_runs(const std::vector<double>& t, long long N, box::Run* out, int maxr) {
+  int n = 0;
+  long long d = -(N - 1);
+  while (d <= N - 1) {
+    const double v = t[(size_t)(d + N - 1)];
+    long long e = d;
+    while (e + 1 <= N - 1 && t[(size_t)(e + 1 + N - 1)] == v) ++e;
+    if (v != 0.0) {
+      if (n == maxr) return -1;
+      out[n].lo = (int)d;
+      out[n].hi = (int)e;
+      out[n].val = v;
+      ++n;
+    }
+    d = e + 1;
+  }
+  return n;
+}
+
+// Sets up the box form of the finest residual when the finest generators have few runs.
+int setup_box(tpc_handle* H) {
+  H->box_on = false;
+  if (!H->prm.box_residual) return TPC_OK;
+  const LevelForm& F = H->host.lev[0];
+  const DevLevel<double>& L = H->d.lev[0];
+  if (F.has_band() || !L.p) return TPC_OK;
+  box::BoxArgs a{};
+  const std::vector<double>* gens[4] = {&F.tA, &F.tB, &F.tC, &F.tD};
+  for (int g = 0; g < 4; ++g) {
+    a.nrun[g] = generator_runs(*gens[g], F.N, a.run[g], box::MAXR);
+    if (a.nrun[g] < 0) return TPC_OK;  // not piecewise constant enough: FFT residual
+  }
+  a.N = (int)F.N;
+  a.nblk = (int)((F.N + 1 + box::BLK - 1) / box::BLK);
+  TPC_TRY(dalloc(H, &a.loc, 2 * (size_t)(F.N + 1)));
+  TPC_TRY(dalloc(H, &a.bsum, 2 * (size_t)a.nblk));
+  TPC_TRY(dalloc(H, &a.off, 2 * (size_t)a.nblk));
+  TPC_TRY(dalloc(H, &a.part, 2 * (size_t)a.nblk));
+  TPC_TRY(dalloc(H, &a.dot, 1));
+  a.p = L.p;
+  a.q = L.q;
+  a.xi = L.xi;
+  a.zeta = L.zeta;
+  a.o = L.o;
+  a.nq = (int)L.nq;
+  a.np = (int)L.np;
+  H->box_args = a;
+  H->box_on = true;
+  return TPC_OK;
+}
+
 void enqueue_sumsq(tpc_handle* H, const double* r, long long n) {
   H->launches += 2;
   k_sumsq_partial<double><<<NORM_BLOCKS, NTHREADS, 0, H->stream>>>(r, n, H->sumsq_part);
@@ -411,7 +488,7 @@ void enqueue_iteration(tpc_handle* H, int cycles) {
     k_axpy<double><<<g, NTHREADS, 0, H->stream>>>(H->u, e, n);
     H->launches += 1;
   }
-  matvec<double>(H, H->d, 0, H->u, H->b, H->r0, EPI_RESID, false);
+  enqueue_finest_residual(H, H->u, H->b, H->r0);
   enqueue_sumsq(H, H->r0, n);
 }
 
@@ -824,6 +901,7 @@ int setup_device(tpc_handle* H) {
       TPC_TRY(autotune_levels<double>(H, H->d, false));
     }
   }
+  TPC_TRY(setup_box(H));
   const long long nK = H->d.lev[0].n;
   TPC_TRY(dalloc(H, &H->u, nK));
   TPC_TRY(dalloc(H, &H->b, nK));
@@ -911,7 +989,7 @@ int solve_begin(SolveState& st, const double* b_dev, double* x_dev, double tol, 
   TPC_CUDA(H, cudaMemcpyAsync(H->b, b_dev, bytes, cudaMemcpyDeviceToDevice, s));
   if (use_x0) {
     TPC_CUDA(H, cudaMemcpyAsync(H->u, x_dev, bytes, cudaMemcpyDeviceToDevice, s));
-    matvec<double>(H, H->d, 0, H->u, H->b, H->r0, EPI_RESID, false);
+    enqueue_finest_residual(H, H->u, H->b, H->r0);
   } else {
     TPC_CUDA(H, cudaMemsetAsync(H->u, 0, bytes, s));
     TPC_CUDA(H, cudaMemcpyAsync(H->r0, H->b, bytes, cudaMemcpyDeviceToDevice, s));
@@ -1403,6 +1481,20 @@ int tpc_time_level_kernels_f32(tpc_handle* H, int level, int reps, const float* 
 long long tpc_kernel_launches(const tpc_handle* H) { return H ? H->launches : 0; }
 
 int tpc_last_solve_cycles(const tpc_handle* H) { return H ? H->last_cycles : -1; }
+
+int tpc_residual(tpc_handle* H, const double* x_dev, const double* b_dev, double* r_dev) {
+  if (!H) return TPC_EINVAL;
+  if (!x_dev || !b_dev || !r_dev || (const void*)r_dev == (const void*)x_dev ||
+      (const void*)r_dev == (const void*)b_dev) {
+    H->err = "bad argument to tpc_residual";
+    return TPC_EINVAL;
+  }
+  enqueue_finest_residual(H, x_dev, b_dev, r_dev);
+  TPC_CUDA(H, cudaGetLastError());
+  return TPC_OK;
+}
+
+int tpc_uses_box_residual(const tpc_handle* H) { return H ? (H->box_on ? 1 : 0) : -1; }
 
 void tpc_destroy(tpc_handle* H) { release(H); }
 

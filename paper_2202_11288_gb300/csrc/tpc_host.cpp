@@ -653,6 +653,10 @@ int build_host_hierarchy(const tpc_params& p, double delta, double h, int levels
     err = "autotune must be 0 or 1";
     return TPC_EINVAL;
   }
+  if (p.box_residual != 0 && p.box_residual != 1) {
+    err = "box_residual must be 0 or 1";
+    return TPC_EINVAL;
+  }
   if (!std::isfinite(p.shift)) {
     err = "shift must be finite";
     return TPC_EINVAL;
@@ -770,6 +774,7 @@ void tpc_default_params(tpc_params* p) {
   p->autotune = 1;
   p->poison = 0;
   p->transfer = TPC_TRANSFER_PAPER;
+  p->box_residual = 1;
 }
 
 int tpc_host_hierarchy(const tpc_params* p, double delta, double h, int levels,
