@@ -288,6 +288,52 @@ int tpc_apply_noalloc(long long N, const double* tA, const double* tB, const dou
                       const double* zeta, double o, const double* x_dev, double* y_dev,
                       void* cuda_stream);
 
+/* ---- 2-D Toeplitz-like-plus-Cross systems (not defined by the paper) ----
+ * The reading of this library: the constant kernel on the unit square with the square horizon
+ * [-delta, delta]^2 and tensor-product quadratic collocation, i.e. the 1-D unknowns of section
+ * 2.2 ([v; w] per axis, n = 2N - 1 of them) on each axis, U[i][j] at (x_i, y_j) stored row by
+ * row (n^2 doubles). Its matrix is A2 = A (x) I + I (x) A - (A (x) A) / (12 r), A the 1-D matrix
+ * of eq. (2.9) (TPC_NONSYM) or eq. (2.10) (TPC_SPD), r = floor(delta / h): each block is block
+ * Toeplitz with Toeplitz blocks plus Cross rows and columns. The V-cycle of Algorithm 2 uses the
+ * section 3.1 transfers on each axis (R (x) R, P (x) P), Galerkin levels (eq. (3.2), of the form
+ * A_k (x) Q_k + Q_k (x) A_k - A_k (x) A_k / (12 r)), damped Jacobi with the diagonal of each level
+ * and a dense solve at the coarsest level; products are FFT products (eq. (3.4)) along rows and
+ * columns. precision TPC_MIXED runs FP32 V-cycles inside FP64 refinement as tpc_solve does. */
+typedef struct tpc2d_handle tpc2d_handle;
+
+/* Set up on the caller's stream (NULL: a stream of the handle). Needs variant TPC_SPD or
+ * TPC_NONSYM, kernel 0, the paper's transfer (else TPC_ENOTSUP), h = 2^-K with K <= 11 and
+ * coarsest_level <= 3 (else TPC_EINVAL); other codes as tpc_setup. *out stays NULL on failure. */
+int tpc2d_setup(const tpc_params* p, double delta, double h, void* cuda_stream,
+                tpc2d_handle** out);
+
+/* Solve A2 x = b to ||b - A2 x||_2 / ||b||_2 < tol (FP64 residual). b_dev, x_dev: device arrays
+ * of n_K^2 doubles (x_dev also the initial guess when use_x0). Blocks until done. Returns TPC_OK,
+ * TPC_ENOTCONV (x holds the last iterate), TPC_EDIVERGED, or a negative error. */
+int tpc2d_solve(tpc2d_handle* H, const double* b_dev, double* x_dev, double tol, int use_x0,
+                int* iters_out, double* relres_out);
+
+/* y = A2_level x (FP64; levels above the coarsest), stream-ordered. n_level^2 doubles each. */
+int tpc2d_apply(tpc2d_handle* H, int level, const double* x_dev, double* y_dev);
+
+/* The same product in FP32 (TPC_MIXED handles). */
+int tpc2d_apply_f32(tpc2d_handle* H, int level, const float* x_dev, float* y_dev);
+
+/* e = B_K r: one V-cycle (FP64) from a zero initial guess, stream-ordered. */
+int tpc2d_vcycle(tpc2d_handle* H, const double* r_dev, double* e_dev);
+
+/* n_level^2 (0 for a bad level), finest and coarsest level numbers, V-cycles of the latest solve,
+ * kernels launched so far (graph launches are not counted), and the last error message. */
+long long tpc2d_level_size(const tpc2d_handle* H, int level);
+int tpc2d_finest_level(const tpc2d_handle* H);
+int tpc2d_coarsest_level(const tpc2d_handle* H);
+int tpc2d_last_solve_cycles(const tpc2d_handle* H);
+long long tpc2d_kernel_launches(const tpc2d_handle* H);
+const char* tpc2d_last_error(const tpc2d_handle* H);
+
+/* Frees everything; NULL-safe. */
+void tpc2d_destroy(tpc2d_handle* H);
+
 /* ---- Request server: continuous batching of independent solves (not in the paper) ----
  * A worker thread admits submitted requests while a slot (max_inflight) and device memory
  * (hbm_budget_bytes) are free, keeps level hierarchies resident keyed by (variant, delta, h,

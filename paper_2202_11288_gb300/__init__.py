@@ -35,6 +35,10 @@ EXPORTED = ["tpc_default_params", "tpc_setup", "tpc_solve", "tpc_solve_batch", "
             "tpc_bdf4_coefficients", "tpc_collocation_rhs", "tpc_bdf4_step",
             "tpc_host_dense_level",
             "tpc_destroy", "tpc_last_error",
+            "tpc2d_setup", "tpc2d_solve", "tpc2d_apply", "tpc2d_apply_f32", "tpc2d_vcycle",
+            "tpc2d_level_size", "tpc2d_finest_level", "tpc2d_coarsest_level",
+            "tpc2d_last_solve_cycles", "tpc2d_kernel_launches", "tpc2d_last_error",
+            "tpc2d_destroy",
             "tpc_server_default_config", "tpc_server_create", "tpc_server_submit",
             "tpc_server_poll", "tpc_server_outstanding", "tpc_server_destroy"]
 
@@ -148,6 +152,26 @@ def lib() -> ctypes.CDLL:
     L.tpc_server_destroy.restype = None
     L.tpc_destroy.argtypes = [P]
     L.tpc_destroy.restype = None
+    L.tpc2d_setup.argtypes = [pp, D, D, P, ctypes.POINTER(P)]
+    L.tpc2d_setup.restype = I
+    L.tpc2d_solve.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]
+    L.tpc2d_solve.restype = I
+    for nm in ("tpc2d_apply", "tpc2d_apply_f32"):
+        getattr(L, nm).argtypes = [P, I, P, P]
+        getattr(L, nm).restype = I
+    L.tpc2d_vcycle.argtypes = [P, P, P]
+    L.tpc2d_vcycle.restype = I
+    L.tpc2d_level_size.argtypes = [P, I]
+    L.tpc2d_level_size.restype = LL
+    for nm in ("tpc2d_finest_level", "tpc2d_coarsest_level", "tpc2d_last_solve_cycles"):
+        getattr(L, nm).argtypes = [P]
+        getattr(L, nm).restype = I
+    L.tpc2d_kernel_launches.argtypes = [P]
+    L.tpc2d_kernel_launches.restype = LL
+    L.tpc2d_last_error.argtypes = [P]
+    L.tpc2d_last_error.restype = ctypes.c_char_p
+    L.tpc2d_destroy.argtypes = [P]
+    L.tpc2d_destroy.restype = None
     L.tpc_last_error.argtypes = [P]
     L.tpc_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -429,6 +453,61 @@ class Solver:
     def close(self) -> None:
         if self.handle:
             tpc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Solver2D:
+    """Owns one 2-D handle (tpc2d_*): ``Solver2D(delta, h, variant=TPC_SPD, ...)`` then
+    ``solve(b, x)`` with b, x device tensors of n^2 doubles (row-major U[i][j])."""
+
+    def __init__(self, delta: float, h: float, stream=None, **params):
+        self.params = tpc_default_params(**params)
+        H = ctypes.c_void_p()
+        _check(lib().tpc2d_setup(ctypes.byref(self.params), delta, h, _stream_handle(stream),
+                                 ctypes.byref(H)))
+        self.handle = H
+        self.K = int(lib().tpc2d_finest_level(H))
+        self.kc = int(lib().tpc2d_coarsest_level(H))
+        self.nn = int(lib().tpc2d_level_size(H, self.K))
+        self.n = int(round(self.nn ** 0.5))
+
+    def _check(self, rc, allow=(TPC_OK,)):
+        if rc not in allow:
+            msg = lib().tpc2d_last_error(self.handle)
+            raise TpcError(rc, msg.decode() if msg else "")
+        return rc
+
+    def solve(self, b, x, tol: float = 1e-10, use_x0: bool = False):
+        it, rel = ctypes.c_int(0), ctypes.c_double(0.0)
+        rc = self._check(lib().tpc2d_solve(self.handle, _ptr(b), _ptr(x), tol, int(use_x0),
+                                           ctypes.byref(it), ctypes.byref(rel)),
+                         allow=(TPC_OK, TPC_ENOTCONV))
+        return rc, it.value, rel.value
+
+    def apply(self, level: int, x, y) -> None:
+        self._check(lib().tpc2d_apply(self.handle, level, _ptr(x), _ptr(y)))
+
+    def apply_f32(self, level: int, x, y) -> None:
+        self._check(lib().tpc2d_apply_f32(self.handle, level, _ptr(x), _ptr(y)))
+
+    def vcycle(self, r, e) -> None:
+        self._check(lib().tpc2d_vcycle(self.handle, _ptr(r), _ptr(e)))
+
+    def level_size(self, level: int) -> int:
+        return int(lib().tpc2d_level_size(self.handle, level))
+
+    def last_cycles(self) -> int:
+        return int(lib().tpc2d_last_solve_cycles(self.handle))
+
+    def close(self) -> None:
+        if self.handle:
+            lib().tpc2d_destroy(self.handle)
             self.handle = None
 
     def __del__(self):  # pragma: no cover

@@ -1504,3 +1504,6 @@ const char* tpc_last_error(const tpc_handle* H) {
 }
 
 }  // extern "C"
+
+// The 2-D system (tensor-product reading of section 2.2), built on the 1-D hierarchy above.
+#include "tpc_2d.cuh"

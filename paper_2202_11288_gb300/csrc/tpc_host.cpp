@@ -701,6 +701,30 @@ int build_host_hierarchy(const tpc_params& p, double delta, double h, int levels
   return TPC_OK;
 }
 
+// Inverse of the coarsest 2-D matrix A (x) Q + Q (x) A - (A (x) A) / d (row-major, n^2 x n^2,
+// n = 2 N + 1), A the level's dense matrix and Q = tridiag(q1, q0, q1).
+int coarse_inverse_2d(const LevelForm& Lc, double q0, double q1, double d,
+                      std::vector<double>& inv) {
+  const long long n = 2 * Lc.N + 1, nn = n * n;
+  std::vector<double> A((size_t)(n * n)), Q((size_t)(n * n), 0.0);
+  for (long long i = 0; i < n; ++i) {
+    for (long long j = 0; j < n; ++j) A[i * n + j] = dense_entry(Lc, i + 1, j + 1);
+    Q[i * n + i] = q0;
+    if (i > 0) Q[i * n + i - 1] = q1;
+    if (i + 1 < n) Q[i * n + i + 1] = q1;
+  }
+  std::vector<double> M((size_t)(nn * nn));
+  for (long long i = 0; i < n; ++i)
+    for (long long j = 0; j < n; ++j)
+      for (long long p = 0; p < n; ++p)
+        for (long long q = 0; q < n; ++q) {
+          const double a_ip = A[i * n + p], a_jq = A[j * n + q];
+          M[(i * n + j) * nn + (p * n + q)] =
+              a_ip * Q[j * n + q] + Q[i * n + p] * a_jq - a_ip * a_jq / d;
+        }
+  return invert_dense(M, nn, inv);
+}
+
 size_t export_count(long long N) { return (size_t)(2 + 4 * (2 * N - 1) + 4 * N); }
 
 void export_level(const LevelForm& L, double* dst) {

@@ -36,6 +36,11 @@ struct HostHierarchy {
 int build_host_hierarchy(const tpc_params& p, double delta, double h, int levels,
                          HostHierarchy& out, std::string& err);
 
+// Inverse of the coarsest level of the 2-D system, A (x) Q + Q (x) A - (A (x) A) / d with
+// A the level's dense matrix and Q = tridiag(q1, q0, q1) (row-major, (2N+1)^2 square).
+int coarse_inverse_2d(const LevelForm& Lc, double q0, double q1, double d,
+                      std::vector<double>& inv);
+
 // Export layout of one level (see tpc_export_level).
 size_t export_count(long long N);
 void export_level(const LevelForm& L, double* dst);

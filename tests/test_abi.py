@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     text = open(os.path.join(ROOT, "include", "tpcamg.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(tpc_[a-z0-9_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(tpc(?:2d)?_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_header_declares_the_binding_names():
