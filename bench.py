@@ -117,6 +117,7 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--inner", type=int, default=6, help="FP32 V-cycles per FP64 residual")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-twod", action="store_true", help="skip the 2-D measurement")
     ap.add_argument("--batch", type=int, default=512,
                     help="instances of the batched-uneven measurement (0 = skip it)")
     ap.add_argument("--serve-rates", default="50,100,200,500,1000,2000",
@@ -393,6 +394,38 @@ def time_fractional(tpc, torch, args, stream):
     return out
 
 
+def time_twod(tpc, torch, args, stream, K=11, delta=0.1):
+    """The 2-D configuration: the tensor-product reading of the constant kernel on the unit square
+    with a square horizon, n x n unknowns with n = 2^(K+1) - 1 (K = 11: 4095^2 = 16.8 M), delta
+    = 0.1, SPD and nonsymmetric, uniform[-1,1) right-hand sides, tol 1e-10; mixed (FP32 V-cycles,
+    FP64 refinement) and FP64; 3 solves after 1 warm-up, CUDA events on the solver's stream."""
+    out = {"workload": f"2-D constant kernel, square horizon, n = {2 ** (K + 1) - 1}^2 unknowns, "
+                       f"delta = {delta}, uniform[-1,1) RHS, tol {args.tol}; 3 solves after 1 "
+                       f"warm-up"}
+    for vname, variant in (("spd", tpc.TPC_SPD), ("nonsym", tpc.TPC_NONSYM)):
+        for pname, prec in (("mixed", tpc.TPC_MIXED), ("fp64", tpc.TPC_FP64)):
+            S = tpc.Solver2D(delta, 2.0 ** -K, stream=stream, variant=variant, precision=prec)
+            with torch.cuda.stream(stream):
+                b = torch.tensor(uniform_pm1(S.nn, 3030), device="cuda")
+                x = torch.zeros_like(b)
+            rc, it, rel = S.solve(b, x, tol=args.tol)
+            assert rc == tpc.TPC_OK and rel < args.tol, (rc, rel)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(3):
+                rc, it, rel = S.solve(b, x, tol=args.tol)
+                assert rc == tpc.TPC_OK and rel < args.tol, (rc, rel)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1) / 3
+            out[f"{vname}_{pname}"] = {"value": 1000.0 / ms, "unit": UNIT, "ms_per_solve": ms,
+                                       "dof_per_s": S.nn * 1000.0 / ms, "outer_iters": it,
+                                       "vcycles": S.last_cycles(), "relres": rel}
+            S.close()
+    return out
+
+
 def serve_keys():
     """Problems of the serving measurement: N = 2^K, K in 9..21 (1023 .. 4,194,303 unknowns,
     log-uniform when K is uniform), delta in {0.05, 0.1, 0.2}, SPD or nonsymmetric, constant
@@ -642,6 +675,7 @@ def run_ours(args, rank, world, local_rank):
                       "at relative residual < %g" % args.tol}
     # the fractional-kernel, batched and served measurements run on one GPU (a single-rank job)
     frac = time_fractional(tpc, torch, args, stream) if world == 1 else None
+    twod = time_twod(tpc, torch, args, stream) if (world == 1 and not args.no_twod) else None
     batch = time_batch(tpc, torch, args, rank) if (args.batch > 0 and world == 1) else None
     serving = (time_serving(tpc, torch, args)
                if (args.serve_rates.strip() and world == 1) else None)
@@ -663,6 +697,8 @@ def run_ours(args, rank, world, local_rank):
         line["speedup_mixed_vs_fp64"] = line["value"] / line["fp64"]["value"]
         if frac:
             line["fractional_a025"] = frac
+        if twod:
+            line["twod"] = twod
         if batch:
             line["batch_uneven"] = batch
         if serving:

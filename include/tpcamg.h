@@ -9,12 +9,12 @@
  * problem -L_delta u = f on (0,1), u = g on [-delta,0] U [1,1+delta], constant kernel,
  * piecewise-quadratic collocation with N = 1/h = 2^K intervals and horizon ratio
  * r = floor(delta/h) (r = 1 when delta <= h). Its matrix is the 2x2 block matrix
- * [A B; C D] of eq. (nonsym system) (variant 1) or the shifted-symmetric [A B; B^T A_hat]
- * of eq. (system1) (variant 0), of order n_K = 2N - 1.
+ * [A B; C D] of eq. (2.9) (variant 1) or the shifted-symmetric [A B; B^T A_hat]
+ * of eq. (2.10) (variant 0), of order n_K = 2N - 1.
  *
  * Vector layout everywhere (section 2.2.1, the grid function U_h): n = 2 N_k + 1 doubles,
  * first the N_k node values v, then the N_k + 1 midpoint values w. In the Cross splitting
- * of eq. (split01), w = [w_o; w_bar]: element N_k (0-based) is w_o.
+ * of eq. (3.7), w = [w_o; w_bar]: element N_k (0-based) is w_o.
  *
  * Levels (section 3.1): level k has N_k = 2^k - 1 and n_k = 2^(k+1) - 1 unknowns; the finest
  * level is K = log2(1/h); the coarsest level kc (default 3, 15 unknowns) is solved with a
@@ -49,8 +49,8 @@ enum {
   TPC_EDIVERGED = -6  /* the residual became non-finite */
 };
 
-/* eq. (system1) / eq. (nonsym system) of the peridynamic model (section 2.2), and the weakly
- * singular nonlocal model of section 2.1, eq. (3system): A_h = diag(D_1, D_2) - [M Q; P N] for
+/* eq. (2.10) / eq. (2.9) of the peridynamic model (section 2.2), and the weakly
+ * singular nonlocal model of section 2.1, eq. (2.3): A_h = diag(D_1, D_2) - [M Q; P N] for
  * L u = int_0^1 (u(x) - u(y)) |x - y|^{-gamma} dy on (0, 1) with gamma = kernel_a in [0, 1) (no
  * horizon: delta is ignored). Its entries are the exact element integrals of the quadratic
  * basis (the printed p_0 and boundary weights eta_{i/2}, i >= 2, are read as garbled); the
@@ -108,8 +108,8 @@ void tpc_default_params(tpc_params* p);
  * h must be 2^-K with K >= coarsest_level; levels = number of levels K - kc + 1 to use,
  * or 0 for all of them (the coarsest level is then kc). The finest generators come from
  * the printed coefficients of section 2.2; coarse levels from the Galerkin product
- * A_{k-1} = R A_k P (eq. block Galerkin) evaluated in generator-plus-Cross form
- * (Lemma 3.1, eq. split 02); the Toeplitz blocks' circulant-embedding spectra (eq. ccs3.4)
+ * A_{k-1} = R A_k P (eq. (3.6)) evaluated in generator-plus-Cross form
+ * (Lemma 3.1, eq. (3.8)); the Toeplitz blocks' circulant-embedding spectra (eq. (3.4))
  * are computed on the device. cuda_stream is a cudaStream_t (NULL = default stream).
  * On success *out owns all device memory of the hierarchy until tpc_destroy; on failure
  * *out is NULL and tpc_last_error(NULL) describes the error. */
@@ -131,7 +131,7 @@ int tpc_setup(const tpc_params* p, double delta, double h, int levels, void* cud
 int tpc_solve(tpc_handle* H, const double* b_dev, double* x_dev, double tol, int use_x0,
               int* iters_out, double* relres_out);
 
-/* One step of eq. (bdf4) on a handle set up with shift = sigma (tpc_bdf4_coefficients):
+/* One step of eq. (5.1) on a handle set up with shift = sigma (tpc_bdf4_coefficients):
  * forms b = hist_scale (4 u1 - 3 u2 + 4/3 u3 - 1/4 u4) + g_scale g on the device (u_j = U^{k-j};
  * g may be NULL for no source term) and solves (sigma I + A) u_out = b from the initial guess
  * u1, stopping as tpc_solve does (relative to the initial residual). Device pointers of n_K
@@ -161,7 +161,7 @@ int tpc_solve_batch(tpc_handle* const* hs, int count, const double* const* b_dev
 int tpc_solve_host(tpc_handle* H, const double* b_host, double* x_host, double tol,
                    int use_x0, int* iters_out, double* relres_out);
 
-/* y = A_level x in FP64 through the Toeplitz-plus-Cross product (eq. split01 and the
+/* y = A_level x in FP64 through the Toeplitz-plus-Cross product (eq. (3.7) and the
  * matrix-vector formula after it). level in [kc, K]; x_dev, y_dev: device pointers to
  * n_level doubles, not aliasing. Stream ordered, does not block. */
 int tpc_apply(tpc_handle* H, int level, const double* x_dev, double* y_dev);
@@ -183,7 +183,7 @@ int tpc_coarsest_level(const tpc_handle* H);
 /* Copy the generator-plus-Cross form of one level to host memory, as doubles:
  * [N_k, o, tA, tB, tC, tD, p, q, xi, zeta] where each t* has 2 N_k - 1 entries t[d],
  * d = i - j = -(N_k-1)..N_k-1 (T(i,j) = t_{i-j}), for the blocks A, B_bar, C_bar, D_bar of
- * eq. (split01), and p, q, xi, zeta have N_k entries. *need receives the count
+ * eq. (3.7), and p, q, xi, zeta have N_k entries. *need receives the count
  * 2 + 4(2 N_k - 1) + 4 N_k; nothing is written if cap < *need (returns TPC_EINVAL). */
 int tpc_export_level(const tpc_handle* H, int level, double* host_buf, size_t cap,
                      size_t* need);
@@ -202,11 +202,11 @@ int tpc_host_dense_level(const tpc_params* p, double delta, double h, int levels
 
 /* ---------------------------------------------------------------------------------------
  * Time stepping (section 5): u_t = L_delta u + f on (0, 1), u = g on the interaction domain,
- * advanced by the BDF4 scheme of eq. (bdf4),
+ * advanced by the BDF4 scheme of eq. (5.1),
  *   (25/12 I - tau L_delta) U^k = 4 U^{k-1} - 3 U^{k-2} + 4/3 U^{k-3} - 1/4 U^{k-4} + tau F^k.
  * The collocation system is A U = eta_h (-L_delta u)(x_p) - (exterior couplings of g) with
  * eta_h = 6 / (gamma h) (gamma = gamma0, or the paper's 3 / delta^3 with delta = r h when
- * gamma0 = 0; TPC_WEAKLY: eta_{h,gamma} of eq. (3system)), so a step is the shifted solve
+ * gamma0 = 0; TPC_WEAKLY: eta_{h,gamma} of eq. (2.3)), so a step is the shifted solve
  *   (sigma I + A) U^k = (eta_h / tau) (4 U^{k-1} - 3 U^{k-2} + 4/3 U^{k-3} - 1/4 U^{k-4}) + b^k,
  *   sigma = 25 eta_h / (12 tau),  b^k = eta_h F^k(x_p) - (exterior couplings of g^k).
  * --------------------------------------------------------------------------------------- */
@@ -216,14 +216,14 @@ int tpc_host_dense_level(const tpc_params* p, double delta, double h, int levels
 int tpc_bdf4_coefficients(const tpc_params* p, double delta, double h, double tau,
                           double* shift_out, double* hist_scale_out);
 
-/* Collocation right-hand side of section 2.2 (eq. ccs2.5 with the constrained exterior values
- * moved to the right, eqs. rightside1-2, each row with its own stencil):
+/* Collocation right-hand side of section 2.2 (eq. (2.5) with the constrained exterior values
+ * moved to the right, eqs. (2.7)-(2.8), each row with its own stencil):
  *   rhs[p] = eta_h f_colloc[p] - sum over exterior points q within the horizon of A(p, q) g(x_q).
  * f_colloc: n = 2/h - 1 values of f at the collocation points in unknown order (nodes h..1-h,
  * then midpoints h/2..1-h/2), or NULL for f = 0. g_left[j] = g(-j h/2), g_right[j] =
  * g(1 + j h/2) for j = 0..2r (r = floor(delta/h), at least 1), or NULL for zero exterior
  * values. rhs_out: n doubles. Host memory, host work O(n + r^2). Returns TPC_OK or TPC_EINVAL.
- * (SPD system: the midpoint rows use the integer-row stencil, as eq. (system1) does.)
+ * (SPD system: the midpoint rows use the integer-row stencil, as eq. (2.10) does.)
  * TPC_WEAKLY (no interaction domain): rhs = eta_{h,gamma} f + K0 g_left[0] + KN g_right[0] with
  * eta_{h,gamma} = (3-gamma)(2-gamma)(1-gamma)/h^{1-gamma} and K0, KN the couplings of the
  * boundary basis functions (u(0) = g_left[0], u(1) = g_right[0]; other entries unused). */

@@ -110,7 +110,7 @@ def vcycle(H: Hierarchy, k: int, b: np.ndarray, m1: int = 1, m2: int = 1,
            omega_pre: float = 2.0 / 3.0, omega_post: float = 2.0 / 3.0) -> np.ndarray:
     """Algorithm 2: returns B_k b with zero initial guess.
 
-    1. pre-smooth m1 times: u <- u + omega_pre D^{-1} (b - A u)  (damped Jacobi, eq. 7;
+    1. pre-smooth m1 times: u <- u + omega_pre D^{-1} (b - A u)  (damped Jacobi, eq. (3.3);
        the update form is the standard one, the smoother being I - omega D^{-1} A);
     2. coarse-grid solution e = B_{k-1} I_k^{k-1} (b - A u);
     3. correction u <- u + I_{k-1}^k e;
@@ -157,11 +157,11 @@ def solve(H: Hierarchy, b: np.ndarray, tol: float = 1e-10, max_iters: int = 100,
 
 
 # ----------------------------------------------------------------------------------------
-# Cross splitting (eq. split01) read off a dense level matrix
+# Cross splitting (eq. (3.7)) read off a dense level matrix
 # ----------------------------------------------------------------------------------------
 
 def split_cross(M: np.ndarray) -> dict:
-    """Split a level matrix (n = 2 N_k + 1) as in eq. (split01).
+    """Split a level matrix (n = 2 N_k + 1) as in eq. (3.7).
 
     Toeplitz blocks A (rows/cols 1..N), B_bar (rows 1..N, cols N+2..2N+1), C_bar, D_bar,
     returned as generators t[d] = T(i, j) for d = i - j in [-(N-1), N-1], stored at index

@@ -11,7 +11,7 @@ quadratic basis, each entry written as an exact integral,
 
 (units of h, r = floor(delta / h)); the factor 6 and the units make a = -1/2 (the constant
 kernel) reproduce the printed coefficients of section 2.2, and the SPD system collocates its
-midpoint rows on the mesh shifted by h/2 as eq. (system1) does. Integrals are evaluated exactly
+midpoint rows on the mesh shifted by h/2 as eq. (2.10) does. Integrals are evaluated exactly
 with sympy (rational exponent), term by term over the powers of s, for -1/2 <= a < 1. For
 a < 1/2 every integral converges. For 1/2 <= a < 1 the linear term of the basis next to the
 singularity gives int_0 s^{-2a} ds, which diverges; the entry is then its Hadamard finite

@@ -2,13 +2,13 @@
 
 Test infrastructure only (see the package docstring).
 
-The four blocks of eq. (nonsym system) / eq. (system1) are Toeplitz; each is described here
+The four blocks of eq. (2.9) / eq. (2.10) are Toeplitz; each is described here
 by its first column and first row exactly as printed in section 2.2 (Matlab toeplitz(c, r)
 semantics: entry (i, j) is c[i-j] for i >= j and r[j-i] otherwise). Two uses:
 
 * ``rows``: selected dense rows of the finest matrix, O(n) per row;
 * ``matvec``: the product A u with each Toeplitz block applied as a convolution computed by
-  scipy's FFT (the library FFT stands for the convolution step of section 3.2, eq. ccs3.4).
+  scipy's FFT (the library FFT stands for the convolution step of section 3.2, eq. (3.4)).
 """
 from __future__ import annotations
 

@@ -13,8 +13,8 @@ from fractions import Fraction
 
 import numpy as np
 
-SPD = 0      # shifted-symmetric system, section 2.2.2, eq. (system1)
-NONSYM = 1   # nonsymmetric indefinite system, section 2.2.1, eq. (nonsym system)
+SPD = 0      # shifted-symmetric system, section 2.2.2, eq. (2.10)
+NONSYM = 1   # nonsymmetric indefinite system, section 2.2.1, eq. (2.9)
 
 
 def horizon_ratio(delta: float, h: float) -> int:
@@ -32,7 +32,7 @@ def coefficients(r: int) -> dict:
     """The printed stencil coefficients for horizon ratio r.
 
     a_0 = 12r-2, a_m = -2 (1<=m<=r-1), a_r = -1, a_{m+1/2} = -4 (0<=m<=r-1)   (section 2.2.1
-    and eq. coeeq: system1); c_m = -2 (0<=m<=r-2), c_{r-1} = -9/4, c_r = 1/4;
+    and eq. (2.11)); c_m = -2 (0<=m<=r-2), c_{r-1} = -9/4, c_r = 1/4;
     d_0 = 12r-4, d_m = -4 (1<=m<=r-1), d_r = -2 (section 2.2.1).
 
     Returned as arrays: ``a_int[m]`` = a_m (m=0..r), ``a_half[m]`` = a_{m+1/2} (m=0..r-1),
@@ -72,7 +72,7 @@ def _fit(values, length: int) -> list:
 
 
 def assemble(variant: int, N: int, r: int) -> np.ndarray:
-    """Dense matrix of eq. (nonsym system) (variant NONSYM) or eq. (system1) (variant SPD).
+    """Dense matrix of eq. (2.9) (variant NONSYM) or eq. (2.10) (variant SPD).
 
     A = toeplitz(a_0..a_r, 0), (N-1)x(N-1);
     B = toeplitz([a_{1/2}..a_{r-1/2}, 0], [a_{1/2}, a_{1/2}, a_{3/2}..a_{r-1/2}, 0]), (N-1)xN;
@@ -210,9 +210,9 @@ def manufactured(variant: int, N: int, r: int):
 
     Row p: b_p = (6/h) [2 delta u(x_p) - int_{x_p-delta}^{x_p+delta} u(y) dy]
                  - sum over exterior points q of entry(p, q) u(x_q),
-    i.e. eta_h f(x_p) with f = -L_delta u (section 2.2, eq. ccs2.5; eta_h = 6/(gamma h) so
+    i.e. eta_h f(x_p) with f = -L_delta u (section 2.2, eq. (2.5); eta_h = 6/(gamma h) so
     the kernel constant cancels), minus the constrained values moved to the right-hand side
-    with the same row stencil (eqs. rightside1-2, read row by row). delta = r h.
+    with the same row stencil (eqs. (2.7)-(2.8), read row by row). delta = r h.
     Returns (b, u_exact) in the unknown ordering of the module docstring.
     """
     return manufactured_rhs(variant, N, r, _u_poly, _u_antiderivative)
@@ -234,7 +234,7 @@ def exterior_points(N: int, r: int):
 
 def exterior_rhs(variant: int, N: int, r: int, g_left, g_right) -> np.ndarray:
     """Minus the couplings of each row to the constrained exterior values (eqs.
-    rightside1-2, read row by row with the row's own stencil): -sum_q entry(p, q) g(x_q).
+    (2.7)-(2.8), read row by row with the row's own stencil): -sum_q entry(p, q) g(x_q).
     g_left[j], g_right[j]: values at the points of :func:`exterior_points`."""
     nodes, mids = grid_points(N)
     rows = [(x, True) for x in nodes] + [(x, False) for x in mids]

@@ -1,12 +1,12 @@
 """Time-dependent problem of section 5: u_t = L_delta u + f on (0, 1) x (0, T], u = g on the
-interaction domain, advanced by the BDF4 scheme of eq. (bdf4).
+interaction domain, advanced by the BDF4 scheme of eq. (5.1).
 
 Test infrastructure only (see the package docstring).
 
 The collocation system of section 2.2 is A U = eta_h (-L_delta u)(x_p) - (exterior
 couplings of g), with eta_h = 6/(gamma h) (the printed integer coefficients are eta_h times
 the collocation of -L_delta). With the discrete operator L_delta U = -(A U + B_ext g) / eta_h,
-eq. (bdf4), (25/12 I - tau L_delta) U^k = 4 U^{k-1} - 3 U^{k-2} + 4/3 U^{k-3} - 1/4 U^{k-4}
+eq. (5.1), (25/12 I - tau L_delta) U^k = 4 U^{k-1} - 3 U^{k-2} + 4/3 U^{k-3} - 1/4 U^{k-4}
 + tau F^k, multiplied by eta_h / tau reads
 
     (sigma I + A) U^k = (eta_h / tau) (4 U^{k-1} - 3 U^{k-2} + 4/3 U^{k-3} - 1/4 U^{k-4})
@@ -52,7 +52,7 @@ def source_vector(variant: int, N: int, r: int, gamma: float | None = None) -> n
 
 
 def bdf4(variant: int, N: int, r: int, T: float = 1.0, gamma: float | None = None):
-    """Runs eq. (bdf4) with tau = h from the exact starting values U^0..U^3 to t = T.
+    """Runs eq. (5.1) with tau = h from the exact starting values U^0..U^3 to t = T.
 
     Returns (error, U_T): the maximum-norm error at t = T and the final level."""
     h = 1.0 / N

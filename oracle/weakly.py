@@ -1,4 +1,4 @@
-"""The weakly singular nonlocal model of section 2.1 (eq. (3system)) and its time stepping.
+"""The weakly singular nonlocal model of section 2.1 (eq. (2.3)) and its time stepping.
 
 Test infrastructure only (see the package docstring).
 
@@ -6,7 +6,7 @@ Problem: u_t + L u = f on (0, 1), L u(x) = int_0^1 (u(x) - u(y)) |x - y|^{-gamma
 0 <= gamma < 1, u given at x = 0 and x = 1. (Section 2.1 writes u_t - L u with this L; the
 sign that gives a well-posed problem, and the one that reproduces Table 1, is u_t + L u.)
 Piecewise quadratic collocation at the nodes x_j = j h and midpoints x_{j-1/2} (the unknown
-ordering of eq. (3system): nodes 1..N-1, then midpoints 1/2..N-1/2), scaled by
+ordering of eq. (2.3): nodes 1..N-1, then midpoints 1/2..N-1/2), scaled by
 eta_{h,gamma} = (3-gamma)(2-gamma)(1-gamma) / h^{1-gamma}:
 
     A_h U = eta_{h,gamma} F + K,    A_h = diag(D_1, D_2) - [M Q; P N],
@@ -96,7 +96,7 @@ def diagonal(N: int, gamma: float) -> np.ndarray:
 
 
 def assemble(N: int, gamma: float) -> np.ndarray:
-    """Dense A_h = diag(D_1, D_2) - [M Q; P N] of eq. (3system)."""
+    """Dense A_h = diag(D_1, D_2) - [M Q; P N] of eq. (2.3)."""
     pts = points(N)
     T = np.array([[coupling(p, q, N, gamma) for q in pts] for p in pts])
     return np.diag(diagonal(N, gamma)) - T
@@ -130,7 +130,7 @@ def L_phi(x, gamma):
 
 
 def bdf4(N: int, gamma: float, T: float = 1.0):
-    """Eq. (bdf4) with tau = h for u = e^t (1 + x)^6 from the exact U^0..U^3: each step solves
+    """Eq. (5.1) with tau = h for u = e^t (1 + x)^6 from the exact U^0..U^3: each step solves
     (sigma I + A_h) U^k = (eta / tau) hist + e^{t_k} (eta (phi + L phi) + K0 phi(0) + KN phi(1)),
     sigma = 25 eta / (12 tau). Returns (max-norm error at T, U_T)."""
     tau = 1.0 / N

@@ -429,7 +429,7 @@ class Solver:
 
     def bdf4_step(self, u1, u2, u3, u4, hist_scale: float, g, g_scale: float, out,
                   tol: float = 1e-12):
-        """One step of eq. (bdf4) (the handle's shift must be sigma, tpc_bdf4_coefficients)."""
+        """One step of eq. (5.1) (the handle's shift must be sigma, tpc_bdf4_coefficients)."""
         return tpc_bdf4_step(self.handle, u1, u2, u3, u4, hist_scale, g, g_scale, tol, out)
 
     def apply(self, level: int, x, y) -> None:

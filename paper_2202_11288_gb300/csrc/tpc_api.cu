@@ -538,7 +538,7 @@ cudaError_t set_smem_attrs() {
   return cudaSuccess;
 }
 
-// Circulant first column of an N x N Toeplitz generator, embedded in length m (eq. ccs3.4):
+// Circulant first column of an N x N Toeplitz generator, embedded in length m (eq. (3.4)):
 // c[d] = t_d, c[m - d] = t_{-d} for 1 <= d <= N - 1, zero elsewhere.
 void circulant_column(const std::vector<double>& t, long long N, long long m,
                       std::vector<double>& c) {

@@ -5,7 +5,7 @@
 // computed decimation-in-frequency (natural order in, bit-reversed order out); the inverse is
 // decimation-in-time with conjugate twiddles (bit-reversed in, natural out) and no 1/m factor
 // (the 1/m is folded into the stored spectra). The product C x = ifft(fft(c) .* fft(x)) of a
-// circulant embedding (eq. ccs3.4) never needs the bit-reversal permutation: spectra are
+// circulant embedding (eq. (3.4)) never needs the bit-reversal permutation: spectra are
 // stored in the same bit-reversed order as the forward output.
 //
 // A DIF step of radix R on sub-blocks of length S treats each sub-block as R rows of S/R

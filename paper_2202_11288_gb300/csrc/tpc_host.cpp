@@ -2,10 +2,10 @@
 //
 // * Finest level: the printed coefficients of section 2.2 (a_m, a_{m+1/2}, c_m, d_m), read as
 //   functions of the distance between a collocation point and a grid point, give the
-//   generators of the four Toeplitz blocks of eq. (nonsym system) / eq. (system1). The Cross
-//   splitting of eq. (split01) then peels off the first midpoint unknown w_o:
+//   generators of the four Toeplitz blocks of eq. (2.9) / eq. (2.10). The Cross
+//   splitting of eq. (3.7) then peels off the first midpoint unknown w_o:
 //   B = [p B_bar], C = [q; C_bar], D = [o zeta; xi D_bar].
-// * Coarse levels: the Galerkin product A_{k-1} = R A_k P (eq. block Galerkin) with
+// * Coarse levels: the Galerkin product A_{k-1} = R A_k P (eq. (3.6)) with
 //   R = 1/4 [1 2 1] on the concatenated vector and P = 2 R^T (section 3.1). Every coarse entry
 //   is (1/8) sum_{a,b in {-1,0,1}} w_a w_b A_k(2I+a, 2J+b), w = (1,2,1). Inside a segment
 //   this is the Toeplitz rule of Lemma 3.1; rows/columns through the middle unknown give the
@@ -84,7 +84,7 @@ int grid_and_horizon(double delta, double h, int& K, int& r, std::string& err) {
 
 // eta_h = 6 / (gamma h), gamma = gamma0, or 3 / delta^3 with delta = r h when gamma0 = 0.
 double eta_of(const tpc_params& p, int r, double h) {
-  if (p.variant == TPC_WEAKLY) {  // eta_{h,gamma} = (3-g)(2-g)(1-g) / h^{1-g} (eq. (3system))
+  if (p.variant == TPC_WEAKLY) {  // eta_{h,gamma} = (3-g)(2-g)(1-g) / h^{1-g} (eq. (2.3))
     const double g = p.kernel_a;
     return (3.0 - g) * (2.0 - g) * (1.0 - g) / std::pow(h, 1.0 - g);
   }
@@ -141,7 +141,7 @@ LevelForm finest_form(int variant, int K, int r, double shift) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Weakly singular model (section 2.1, eq. (3system)). Entries are (3-g)(2-g)(1-g) / h^{1-g}
+// Weakly singular model (section 2.1, eq. (2.3)). Entries are (3-g)(2-g)(1-g) / h^{1-g}
 // times int phi_q(y) |x_p - y|^{-g} dy; in units of h the factor h^{1-g} cancels, leaving
 // (3-g)(2-g)(1-g) times the integral of the unit-spaced basis against |s|^{-g}.
 // ---------------------------------------------------------------------------------------
@@ -385,7 +385,7 @@ double ws_boundary(bool left, long long xp2, long long Nint, double g) {
   return (3.0 - g) * (2.0 - g) * (1.0 - g) * v;
 }
 
-// Finest level of eq. (3system): Toeplitz part -[M Q; P N] in the generator + Cross form of
+// Finest level of eq. (2.3): Toeplitz part -[M Q; P N] in the generator + Cross form of
 // finest_form (same block layout: nodes are the first segment, midpoints the second), and the
 // diagonal diag(D_1, D_2), d(x) = (3-g)(2-g)((x/h)^{1-g} + (1 - x)/h)^{1-g}), as the band.
 LevelForm finest_form_weakly(int K, double g, double shift) {
@@ -899,7 +899,7 @@ int tpc_collocation_rhs(const tpc_params* p, double delta, double h, const doubl
   const double eta = tpc::eta_of(*p, r, h);
   for (long long q = 0; q < n; ++q) rhs_out[q] = f_colloc ? eta * f_colloc[q] : 0.0;
   if (p->variant == TPC_WEAKLY) {
-    // A_h U = eta F + K (eq. (3system)): the boundary columns times u(0) = g_left[0] and
+    // A_h U = eta F + K (eq. (2.3)): the boundary columns times u(0) = g_left[0] and
     // u(1) = g_right[0], added (A_h = D - T, and the boundary part of T moves to the right)
     for (long long q = 0; q < n; ++q) {
       const long long xp2 = (q < nn) ? 2 * (q + 1) : 2 * (q - nn + 1) - 1;

@@ -8,7 +8,7 @@
 
 namespace tpc {
 
-// One level in generator-plus-Cross form (eq. split01).
+// One level in generator-plus-Cross form (eq. (3.7)).
 //   Toeplitz blocks A, B_bar, C_bar, D_bar (N x N) as generators t[d + N - 1] = T(i, j),
 //   d = i - j in [-(N-1), N-1]; Cross vectors p (column), q (row), xi (column), zeta (row),
 //   each N long, 0-based; o the middle diagonal entry.

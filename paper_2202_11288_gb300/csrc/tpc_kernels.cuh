@@ -1,11 +1,11 @@
 // Kernels of one Toeplitz-plus-Cross level and of the V-cycle (Algorithm 2).
 //
 // Level k (section 3.2.2): u = [v (N); w_o (1); w_bar (N)], N = N_k = 2^k - 1, m = 2N + 2.
-// y = A_k u is computed as (eq. split01 and the product formula after it)
+// y = A_k u is computed as (eq. (3.7) and the product formula after it)
 //   [A v + B_bar w_bar ; q.v + o w_o + zeta.w_bar ; C_bar v + D_bar w_bar]
 //   + [p w_o ; 0 ; xi w_o],
 // with the four Toeplitz products done through one circulant embedding of length m
-// (eq. ccs3.4): z = pad(v) + i pad(w_bar) is transformed once, the 2x2 block product
+// (eq. (3.4)): z = pad(v) + i pad(w_bar) is transformed once, the 2x2 block product
 // [Y1; Y2] = [A^ B^; C^ D^] [V^; W^] is formed per frequency pair (j, m-j) (V^, W^ are the
 // transforms of v and w_bar, unpacked from Z_j and conj(Z_{m-j})), and Y1 + i Y2 is
 // transformed back: the real part is A v + B_bar w_bar, the imaginary part C_bar v + D_bar w_bar.
@@ -97,7 +97,7 @@ template <typename T> struct LevelArgs {
   const T* bu;
   const T* pvec;
   const T* wvec;
-  T wA, wO, wD;          // omega / diagonal, per segment (damped Jacobi, eq. 7)
+  T wA, wO, wD;          // omega / diagonal, per segment (damped Jacobi, eq. (3.3))
   const c2<T>* twm;      // strided pipelines only: W_m^j, j < m (FP64); two-level (FP32)
   const c2<T>* twL;      // W_{4096}^j, j < 4096 (FP32 copies the octant j <= 512 to shared)
   const c2<T>* tws;      // FP32: step twiddle tables of the register-resident kernels (tpc_f32.cuh)
@@ -1089,7 +1089,7 @@ __global__ void k_axpy(T* u, const T* e, long long n) {
     u[i] += e[i];
 }
 
-// Right-hand side of one step of eq. (bdf4) for the shifted system (sigma I + A) U^k = b:
+// Right-hand side of one step of eq. (5.1) for the shifted system (sigma I + A) U^k = b:
 // b = hs (4 u1 - 3 u2 + 4/3 u3 - 1/4 u4) + gs g  (u_j = U^{k-j}).
 static __global__ void k_bdf4_rhs(double* b, const double* u1, const double* u2, const double* u3,
                            const double* u4, double hs, const double* g, double gs, long long n) {

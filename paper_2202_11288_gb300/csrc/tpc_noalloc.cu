@@ -79,7 +79,7 @@ __global__ void k_na_twiddles(double2* out, long long n, long long count) {
 }
 
 // Circulant first column of an N x N Toeplitz generator t (t[d + N - 1] = T(i, j), d = i - j),
-// embedded in length m (eq. ccs3.4); every entry is written (the zeros included).
+// embedded in length m (eq. (3.4)); every entry is written (the zeros included).
 __global__ void k_na_circulant(const double* t, long long N, long long m, double* c) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= m) return;
@@ -230,7 +230,7 @@ extern "C" int tpc_apply_noalloc(long long N, const double* tA, const double* tB
     if (blk == 3) k_extract_real<double><<<gm, 256, 0, s>>>(z, sD, m, scale);
   }
 
-  // the product y = A x (eq. split01 and the product formula after it)
+  // the product y = A x (eq. (3.7) and the product formula after it)
   a.real_in = nullptr;
   a.x = x_dev;
   a.y = y_dev;

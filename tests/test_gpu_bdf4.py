@@ -1,4 +1,4 @@
-"""Time stepping on the GPU (section 5, eq. (bdf4)): each step is tpc_bdf4_step on a handle
+"""Time stepping on the GPU (section 5, eq. (5.1)): each step is tpc_bdf4_step on a handle
 whose shift is sigma = 25 eta_h / (12 tau). The final errors are compared with the values the
 paper prints in Tables 2 and 3 and the final level with the oracle's dense time stepping.
 

@@ -1,4 +1,4 @@
-"""GPU path of the weakly singular model (section 2.1, eq. (3system)) against the oracle:
+"""GPU path of the weakly singular model (section 2.1, eq. (2.3)) against the oracle:
 products at every level (FFT for the Toeplitz part plus the tridiagonal band), V-cycle iterates,
 and the BDF4 time stepping of Table 1.
 

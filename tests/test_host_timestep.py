@@ -1,6 +1,6 @@
 """Host entry points of the time stepping (no GPU): the collocation right-hand side and the
-BDF4 coefficients against the oracle (section 5, eq. (bdf4); section 2.2 eqs. ccs2.5 and
-rightside1-2)."""
+BDF4 coefficients against the oracle (section 5, eq. (5.1); section 2.2 eqs. (2.5) and
+(2.7)-(2.8))."""
 import math
 
 import numpy as np

@@ -1,4 +1,4 @@
-"""Host setup of the weakly singular model (section 2.1, eq. (3system)) against the oracle, no
+"""Host setup of the weakly singular model (section 2.1, eq. (2.3)) against the oracle, no
 GPU: every level's dense matrix (finest: A_h; coarse: the dense Galerkin R A P of Algorithm 2),
 the right-hand side pieces and the BDF4 coefficients."""
 import math

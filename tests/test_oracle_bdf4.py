@@ -1,4 +1,4 @@
-"""The oracle's time stepping (eq. (bdf4), section 5) against the errors the paper prints in
+"""The oracle's time stepping (eq. (5.1), section 5) against the errors the paper prints in
 Tables 2 and 3 (tests/golden/bdf4_tables.txt). These pin, together, the printed coefficients
 of both systems, the exterior couplings moved to the right-hand side, the kernel constant
 gamma = 3 / delta^3 with delta = r h, and the BDF4 recurrence: all sixteen printed errors are

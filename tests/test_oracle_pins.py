@@ -74,7 +74,7 @@ def test_example_3_1_fails_for_per_block_restriction():
 @pytest.mark.parametrize("variant", [SPD, NONSYM])
 @pytest.mark.parametrize("K,r", [(6, 4), (6, 7), (7, 16)])
 def test_toeplitz_plus_cross_closure_and_lemma31(variant, K, r):
-    """At every level the four blocks of eq. (split01) are Toeplitz, and the Toeplitz part of
+    """At every level the four blocks of eq. (3.7) are Toeplitz, and the Toeplitz part of
     Lemma 3.1 (8 a'_i = a_{2i-2} + 4 a_{2i-1} + 6 a_{2i} + 4 a_{2i+1} + a_{2i+2}) holds."""
     N = 1 << K
     H = amg.Hierarchy(model.assemble(variant, N, r), kc=2)

@@ -1,4 +1,4 @@
-"""Oracle of the weakly singular nonlocal model (section 2.1, eq. (3system)) against what the
+"""Oracle of the weakly singular nonlocal model (section 2.1, eq. (2.3)) against what the
 paper prints: the coefficient formulas of M, N, P, Q and D (equal to the exact element
 integrals, except p_0 and the boundary weights eta_{i/2}, i >= 2, which are read as garbled),
 and the twelve BDF4 errors of Table 1 (tests/golden/bdf4_table1.txt)."""
