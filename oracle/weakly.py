@@ -14,8 +14,8 @@ eta_{h,gamma} = (3-gamma)(2-gamma)(1-gamma) / h^{1-gamma}:
 where the diagonal is eta times int_0^1 |x_p - y|^{-gamma} dy, every entry of [M Q; P N] is
 eta times int phi_q(y) |x_p - y|^{-gamma} dy, and K holds the same integrals of the two
 boundary basis functions times u(0), u(1). All of them are computed here as exact integrals
-of a quadratic times |s|^{-gamma} over each element (closed-form antiderivatives next to the
-singularity, 20-point Gauss-Legendre on the smooth far elements).
+of a quadratic times |s|^{-gamma} over each element: closed-form antiderivatives of the powers
+of |s| on every element, evaluated in 40-digit arithmetic (no quadrature rule).
 
 Readings of the printed formulas (pinned in tests/test_oracle_weakly.py): the printed d_{i/2},
 m_k, n_k, q_k and p_k (k >= 1) equal these integrals; the printed p_0 and eta_{i/2} (i >= 2) do
@@ -26,60 +26,65 @@ reproduced.
 from __future__ import annotations
 
 import math
+from functools import lru_cache
 
+import mpmath
 import numpy as np
+
+_DPS = 40  # decimal digits of the exact antiderivatives' evaluation
 
 
 def _antideriv(coeffs, gamma, s):
-    """Antiderivative at s >= 0 of sum_k coeffs[k] s^{k - gamma}."""
+    """Antiderivative at s >= 0 of sum_k coeffs[k] s^{k - gamma} (mpmath numbers; 0 at s = 0,
+    every exponent k + 1 - gamma being positive)."""
+    if s == 0:
+        return mpmath.mpf(0)
     return sum(c * s ** (k + 1 - gamma) / (k + 1 - gamma) for k, c in enumerate(coeffs))
-
-
-_GL_X, _GL_W = np.polynomial.legendre.leggauss(20)
 
 
 def _element_integral(a, y0, y1, gamma):
     """int_{y0}^{y1} phi(y) |y|^{-gamma} dy for phi = a0 + a1 u + a2 u^2, u = y - y0.
 
-    Near the singularity (an end within 4 of y = 0) the closed-form antiderivatives of the
-    polynomial in y are exact and well conditioned; farther away they cancel (terms of size
-    |y|^{3-gamma} against a result of size |y|^{-gamma}), while the integrand is smooth on the
-    element, so 20-point Gauss-Legendre quadrature is used with phi evaluated in u."""
-    if y0 >= 4.0 or y1 <= -4.0:
-        u = 0.5 * (y1 - y0) * (_GL_X + 1.0)
-        vals = (a[0] + u * (a[1] + u * a[2])) * np.abs(y0 + u) ** (-gamma)
-        return float(0.5 * (y1 - y0) * np.dot(_GL_W, vals))
-    c = (a[0] - a[1] * y0 + a[2] * y0 * y0, a[1] - 2 * a[2] * y0, a[2])
-    tot = 0.0
-    if y1 > 0.0:
-        tot += _antideriv(c, gamma, y1) - _antideriv(c, gamma, max(y0, 0.0))
-    if y0 < 0.0:  # y = -t
-        cm = (c[0], -c[1], c[2])
-        tot += _antideriv(cm, gamma, -y0) - _antideriv(cm, gamma, -min(y1, 0.0))
-    return tot
+    Exact: phi is rewritten in powers of y, split at y = 0 into powers of |y|, and integrated with
+    the closed-form antiderivatives, evaluated in 40-digit arithmetic. Far from the singularity
+    the terms (size |y|^{3-gamma}) cancel down to the result (size |y|^{-gamma}); at 40 digits
+    that costs at most log10(|y|^3) digits, so the result is exact to double precision at every
+    distance, with no quadrature rule involved."""
+    with mpmath.workdps(_DPS):
+        g = mpmath.mpf(gamma)
+        y0m, y1m = mpmath.mpf(y0), mpmath.mpf(y1)
+        a0, a1, a2 = (mpmath.mpf(v) for v in a)
+        c = (a0 - a1 * y0m + a2 * y0m * y0m, a1 - 2 * a2 * y0m, a2)
+        tot = mpmath.mpf(0)
+        if y1m > 0:
+            tot += _antideriv(c, g, y1m) - _antideriv(c, g, max(y0m, mpmath.mpf(0)))
+        if y0m < 0:  # y = -t
+            cm = (c[0], -c[1], c[2])
+            tot += _antideriv(cm, g, -y0m) - _antideriv(cm, g, -min(y1m, mpmath.mpf(0)))
+        return float(tot)
 
 
-def _basis_pieces(q2: int, N: int):
-    """Pieces of the basis function at twice-coordinate q2 (units of h/2) on [0, N]:
-    (y0, y1, (a0, a1, a2)) with phi = a0 + a1 u + a2 u^2, u = y - y0 (y in units of h)."""
-    c = q2 / 2.0
-    if q2 % 2 == 0:  # node: t (2t - 1), t = distance to the far end of each element
-        out = []
-        if c - 1 >= 0:
-            out.append((c - 1, c, (0.0, -1.0, 2.0)))      # 2u^2 - u
-        if c + 1 <= N:
-            out.append((c, c + 1, (1.0, -3.0, 2.0)))      # (1 - u)(1 - 2u)
-        return out
-    return [(c - 0.5, c + 0.5, (0.0, 4.0, -4.0))]         # midpoint: 4 u (1 - u)
+@lru_cache(maxsize=None)
+def _coupling_rel(d2: int, q_odd: bool, left: bool, right: bool, gamma: float) -> float:
+    """The integral of coupling for a basis function at twice-distance d2 = q2 - p2 from the
+    collocation point: it depends only on d2, the basis type and whether the basis function is
+    cut at x = 0 (left) or x = 1 (right)."""
+    c = d2 / 2.0  # centre of the basis function relative to the collocation point (units of h)
+    if q_odd:  # midpoint: 4 u (1 - u) on [c - 1/2, c + 1/2], u = y - (c - 1/2)
+        pieces = [(c - 0.5, c + 0.5, (0.0, 4.0, -4.0))]
+    else:      # node: 2u^2 - u on [c - 1, c] and (1 - u)(1 - 2u) on [c, c + 1], u = y - lower end
+        pieces = []
+        if not left:
+            pieces.append((c - 1, c, (0.0, -1.0, 2.0)))
+        if not right:
+            pieces.append((c, c + 1, (1.0, -3.0, 2.0)))
+    return sum(_element_integral(a, y0, y1, gamma) for y0, y1, a in pieces)
 
 
 def coupling(p2: int, q2: int, N: int, gamma: float) -> float:
     """(3-gamma)(2-gamma)(1-gamma) int phi_q(y) |x_p - y|^{-gamma} dy / h^{1-gamma}, i.e.
     eta_{h,gamma} times the integral, at twice-coordinates p2 (collocation point) and q2."""
-    xp = p2 / 2.0
-    tot = 0.0
-    for y0, y1, a in _basis_pieces(q2, N):
-        tot += _element_integral(a, y0 - xp, y1 - xp, gamma)
+    tot = _coupling_rel(q2 - p2, q2 % 2 == 1, q2 == 0, q2 == 2 * N, float(gamma))
     return (3 - gamma) * (2 - gamma) * (1 - gamma) * tot
 
 

@@ -1,7 +1,8 @@
 """Oracle of the fractional kernel with a horizon (a reading of this build; the paper defines
 only the constant kernel): pinned to the printed matrix at a = -1/2, to exactness on
-quadratics, and (a >= 1/2) to Hadamard's definition of the finite part evaluated by adaptive
-quadrature. Parity of the fractional entries is otherwise unpinned by the paper."""
+quadratics, entry by entry (a < 1/2) to the convergent integral of its definition and
+(a >= 1/2) to Hadamard's definition of the finite part, both evaluated by adaptive quadrature
+on the basis functions. Parity of the fractional entries is otherwise unpinned by the paper."""
 import numpy as np
 import pytest
 import sympy as sp
@@ -57,14 +58,20 @@ def _lagrange_basis(node_type, c):
     """Quadratic Lagrange basis function centred at c (units of h): a vertex of the elements
     [c-1, c] and [c, c+1], or the midpoint of [c-1/2, c+1/2]."""
     def phi(y):
+        # evaluated in the element's own coordinate v (measured from its left end, which is a
+        # half-integer and so subtracted exactly), so that values next to an element end keep
+        # their relative accuracy
         if node_type:
             if c <= y <= c + 1:
-                return 2 * (y - c - 0.5) * (y - c - 1)
+                v = y - c
+                return 2 * (v - 0.5) * (v - 1)
             if c - 1 <= y < c:
-                return 2 * (y - c + 0.5) * (y - c + 1)
+                v = y - (c - 1)
+                return 2 * (v - 0.5) * v
             return 0.0
         if c - 0.5 <= y <= c + 0.5:
-            return -4 * (y - c + 0.5) * (y - c - 0.5)
+            v = y - (c - 0.5)
+            return -4 * v * (v - 1)
         return 0.0
     return phi
 
@@ -107,3 +114,43 @@ def test_finite_parts_follow_hadamards_definition(variant, a, r):
         for d2, wo in zip(d2s, w):
             ref = _hadamard_entry(variant, row_is_node, d2, r, float(a))
             assert abs(ref - wo) <= 1e-10 * scale, (row_is_node, d2)
+
+
+def _convergent_entry(variant, row_is_node, dist2, r, a):
+    """6 int_{-r}^{r} |s|^{-g} [phi_q(0) - phi_q(s)] ds, g = 1 + 2a < 2: an ordinary integral (the
+    bracket vanishes linearly at s = 0), by adaptive quadrature on each piece between the basis
+    function's breakpoints (half steps), no finite-part term. On the piece next to s = 0 the
+    substitution t = u^k, k = 1 / (2 - g), makes the integrand smooth."""
+    g = 1 + 2 * a
+    col_is_node = (dist2 % 2 == 0) == row_is_node
+    node_type = (not col_is_node) if (variant == SPD and not row_is_node) else col_is_node
+    phi = _lagrange_basis(node_type, -dist2 / 2)
+    pts = [k / 2 for k in range(1, 2 * r)] + [float(r)]
+    k = 1.0 / (2.0 - g)
+    total = 0.0
+    for sgn in (1.0, -1.0):
+        def f(t):
+            return phi(0.0) - phi(sgn * t)
+        # on [0, 1/2] the bracket is the quadratic f1 t + f2 t^2 (no breakpoint inside; its
+        # coefficients from two samples, where they carry no cancellation), and with t = u^k the
+        # integrand k (f1 + f2 u^k) is smooth
+        f1 = 8.0 * f(0.25) - 2.0 * f(0.5)
+        f2 = 8.0 * f(0.5) - 16.0 * f(0.25)
+        total += quad(lambda u: k * (f1 + f2 * u ** k), 0.0, 0.5 ** (2 - g), epsrel=1e-13)[0]
+        for lo, hi in zip(pts[:-1], pts[1:]):
+            total += quad(lambda t: f(t) * t ** (-g), lo, hi, epsrel=1e-13, limit=400)[0]
+    return 6 * total
+
+
+@pytest.mark.parametrize("variant", [SPD, NONSYM])
+@pytest.mark.parametrize("a", [sp.Rational(-1, 4), sp.Integer(0), sp.Rational(1, 4),
+                               sp.Rational(2, 5)])
+@pytest.mark.parametrize("r", [1, 3])
+def test_entries_follow_the_convergent_integral(variant, a, r):
+    """a < 1/2: every entry of both row types equals its defining integral (which converges)."""
+    for row_is_node in (True, False):
+        d2s, w = fractional.stencil(variant, row_is_node, r, a)
+        scale = max(abs(x) for x in w)
+        for d2, wo in zip(d2s, w):
+            ref = _convergent_entry(variant, row_is_node, d2, r, float(a))
+            assert abs(ref - wo) <= 1e-10 * scale, (row_is_node, d2, ref, wo)
