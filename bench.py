@@ -76,8 +76,11 @@ def solve_bytes(K, kc, vcycles, outer, mixed, nonsym=False):
 # the kernel sources it was taken with (SHA-256 of the two device headers below, first 16 hex
 # digits) and for the level it was taken at; any other build reports traffic as null.
 KERNEL_SOURCES = ("paper_2202_11288_gb300/csrc/tpc_kernels.cuh",
-                  "paper_2202_11288_gb300/csrc/tpc_fft.cuh")
-TRAFFIC = {"digest": None, "K": 22, "f32": None, "f64_mid": None}
+                  "paper_2202_11288_gb300/csrc/tpc_fft.cuh",
+                  "paper_2202_11288_gb300/csrc/tpc_f32.cuh")
+# per launch, forward pass / contiguous-block kernel / inverse pass (k32_fwd<11, 0>,
+# k32_mid<12, 0>, k32_inv<11, 1> at m = 2^23, cold cache)
+TRAFFIC = {"digest": "f3c22b6c2c57f0d7", "K": 22, "f32": (53.5e6, 155.4e6, 116.2e6), "f64_mid": None}
 
 
 def kernel_digest():
@@ -130,6 +133,8 @@ def parse():
                     help="profiling case: mixed-precision setup, then 3 FP32 finest-level products")
     ap.add_argument("--profile-solve", choices=["fp64", "mixed"], default=None,
                     help="profiling case: set up, then one solve, nothing timed")
+    ap.add_argument("--profile-twod", action="store_true",
+                    help="profiling case: 2-D mixed set-up (n = 4095^2), then one solve")
     return ap.parse_args()
 
 
@@ -766,8 +771,25 @@ def run_profile_solve(args):
                       "relres": rel}))
 
 
+def run_profile_twod(args):
+    """A fixed launch sequence for profilers: the 2-D mixed solver at n = 4095^2, one solve."""
+    import torch
+
+    import paper_2202_11288_gb300 as tpc
+    S = tpc.Solver2D(0.1, 2.0 ** -11, precision=tpc.TPC_MIXED)
+    b = torch.tensor(uniform_pm1(S.nn, 3030), device="cuda")
+    x = torch.zeros_like(b)
+    rc, it, rel = S.solve(b, x, tol=args.tol)
+    torch.cuda.synchronize()
+    S.close()
+    print(json.dumps({"profile_twod": "n=4095^2", "rc": rc, "iters": it, "relres": rel}))
+
+
 def main():
     args = parse()
+    if args.profile_twod:
+        run_profile_twod(args)
+        return
     if args.profile:
         run_profile_case(args)
         return
