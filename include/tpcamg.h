@@ -46,7 +46,8 @@ enum {
   TPC_ECUDA = -3,     /* a CUDA call failed; message in tpc_last_error */
   TPC_ESINGULAR = -4, /* the coarsest matrix has a zero pivot */
   TPC_ENOTSUP = -5,   /* a parameter combination this build does not implement */
-  TPC_EDIVERGED = -6  /* the residual became non-finite */
+  TPC_EDIVERGED = -6, /* the residual became non-finite */
+  TPC_ESYNC = -7      /* a device-side wait of a stage-batched launch gave up (tpc_batch_solve) */
 };
 
 /* eq. (2.10) / eq. (2.9) of the peridynamic model (section 2.2), and the weakly
@@ -155,6 +156,40 @@ int tpc_bdf4_step(tpc_handle* H, const double* u1, const double* u2, const doubl
 int tpc_solve_batch(tpc_handle* const* hs, int count, const double* const* b_dev,
                     double* const* x_dev, double tol, int* iters_out, double* relres_out,
                     int* status_out);
+
+/* Stage-batched solves (the batched configuration, not in the paper). tpc_batch_create groups the
+ * handles whose level structure is identical -- mixed precision, V(1,1), the single-block bottom
+ * of the FP32 V-cycles, the prefix-sum residual (box_residual with the constant kernel), the
+ * same finest and coarsest levels, system and inner_cycles, levels up to m = 2^18 -- and
+ * prepares, per group, every stage's arguments for all its instances. tpc_batch_solve then runs
+ * each outer iteration of a group as ONE launch per stage of Algorithm 2 over all the group's
+ * instances (a three-pass
+ * product is one persistent cooperative launch whose passes are separated by grid-wide barriers
+ * on a device counter), captured once per inner-cycle count as a CUDA graph; the groups run
+ * concurrently on their own streams, and handles outside every group are solved as by
+ * tpc_solve_batch beside them. Each instance computes exactly what tpc_solve computes on its
+ * handle (bitwise). A barrier's wait gives up after a bounded number of polls (about a second):
+ * the launch then returns early and tpc_batch_solve returns TPC_ESYNC (results undefined, the
+ * context stays usable). The handles must be distinct and outlive the batch; the batch holds
+ * device memory of a few KB per instance. */
+typedef struct tpc_batch tpc_batch;
+int tpc_batch_create(tpc_handle* const* hs, int count, tpc_batch** out);
+
+/* As tpc_solve_batch, on the batch's handles in their creation order. */
+int tpc_batch_solve(tpc_batch* B, const double* const* b_dev, double* const* x_dev, double tol,
+                    int* iters_out, double* relres_out, int* status_out);
+
+/* Number of stage-batched groups, and of the instances they hold (-1 for NULL). */
+int tpc_batch_groups(const tpc_batch* B);
+int tpc_batch_grouped_instances(const tpc_batch* B);
+
+/* Frees the batch (not the handles); NULL-safe. */
+void tpc_batch_destroy(tpc_batch* B);
+
+/* Check of the bounded device-side wait: a cooperative launch of 4 blocks waits at a grid barrier
+ * whose target nothing reaches, with max_polls polls. On return *gave_up is 1 when the wait gave
+ * up and flagged it, and *passed counts the blocks that (wrongly) passed the barrier. */
+int tpc_grid_wait_selftest(unsigned max_polls, int* gave_up, int* passed);
 
 /* Same as tpc_solve with host buffers b_host / x_host (n_K doubles each): the call copies
  * b to the device, solves and copies x back before returning. */

@@ -20,11 +20,14 @@ LIB_PATH = os.path.join(_HERE, "libtpcamg.so")
 
 TPC_OK, TPC_ENOTCONV = 0, 1
 TPC_EINVAL, TPC_ENOMEM, TPC_ECUDA, TPC_ESINGULAR, TPC_ENOTSUP, TPC_EDIVERGED = -1, -2, -3, -4, -5, -6
+TPC_ESYNC = -7
 TPC_SPD, TPC_NONSYM, TPC_WEAKLY = 0, 1, 2
 TPC_FP64, TPC_MIXED = 0, 1
 TPC_TRANSFER_PAPER, TPC_TRANSFER_GEOMETRIC = 0, 1
 
 EXPORTED = ["tpc_default_params", "tpc_setup", "tpc_solve", "tpc_solve_batch", "tpc_solve_host",
+            "tpc_batch_create", "tpc_batch_solve", "tpc_batch_groups",
+            "tpc_batch_grouped_instances", "tpc_batch_destroy", "tpc_grid_wait_selftest",
             "tpc_apply",
             "tpc_apply_f32",
             "tpc_vcycle", "tpc_level_size", "tpc_finest_level", "tpc_coarsest_level",
@@ -98,6 +101,18 @@ def lib() -> ctypes.CDLL:
     L.tpc_solve.restype = I
     L.tpc_solve_batch.argtypes = [P, I, P, P, D, P, P, P]
     L.tpc_solve_batch.restype = I
+    L.tpc_batch_create.argtypes = [P, I, ctypes.POINTER(P)]
+    L.tpc_batch_create.restype = I
+    L.tpc_batch_solve.argtypes = [P, P, P, D, P, P, P]
+    L.tpc_batch_solve.restype = I
+    L.tpc_batch_groups.argtypes = [P]
+    L.tpc_batch_groups.restype = I
+    L.tpc_batch_grouped_instances.argtypes = [P]
+    L.tpc_batch_grouped_instances.restype = I
+    L.tpc_batch_destroy.argtypes = [P]
+    L.tpc_batch_destroy.restype = None
+    L.tpc_grid_wait_selftest.argtypes = [ctypes.c_uint, ctypes.POINTER(I), ctypes.POINTER(I)]
+    L.tpc_grid_wait_selftest.restype = I
     L.tpc_solve_host.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]
     L.tpc_solve_host.restype = I
     L.tpc_apply.argtypes = [P, I, P, P]
@@ -321,6 +336,54 @@ def tpc_solve_batch(handles, bs, xs, tol: float = 1e-10):
     if rc < 0 and rc not in (TPC_EDIVERGED,):
         raise TpcError(rc, tpc_last_error(None))
     return rc, list(it), list(rel), list(stt)
+
+
+class Batch:
+    """Stage-batched solves over a fixed list of handles (tpc_batch_*): ``Batch(handles)`` then
+    ``solve(bs, xs)``; groups instances of identical level structure into one launch per stage."""
+
+    def __init__(self, handles):
+        n = len(handles)
+        self._n = n
+        HA = (ctypes.c_void_p * n)(*[h.value if hasattr(h, "value") else h for h in handles])
+        self.handle = ctypes.c_void_p()
+        _check(lib().tpc_batch_create(HA, n, ctypes.byref(self.handle)))
+
+    def solve(self, bs, xs, tol: float = 1e-10):
+        n = self._n
+        BA = (ctypes.c_void_p * n)(*[_ptr(b) for b in bs])
+        XA = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+        it = (ctypes.c_int * n)()
+        rel = (ctypes.c_double * n)()
+        stt = (ctypes.c_int * n)()
+        rc = lib().tpc_batch_solve(self.handle, BA, XA, tol, it, rel, stt)
+        if rc < 0 and rc not in (TPC_EDIVERGED,):
+            raise TpcError(rc, tpc_last_error(None))
+        return rc, list(it), list(rel), list(stt)
+
+    def groups(self) -> int:
+        return int(lib().tpc_batch_groups(self.handle))
+
+    def grouped_instances(self) -> int:
+        return int(lib().tpc_batch_grouped_instances(self.handle))
+
+    def close(self) -> None:
+        if self.handle:
+            lib().tpc_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tpc_grid_wait_selftest(max_polls: int):
+    """(gave_up, passed) of a grid barrier nothing can reach, waited with max_polls polls."""
+    g, p = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().tpc_grid_wait_selftest(int(max_polls), ctypes.byref(g), ctypes.byref(p)))
+    return g.value, p.value
 
 
 def tpc_solve_host(H, b: np.ndarray, x: np.ndarray, tol: float = 1e-10, use_x0: bool = False):

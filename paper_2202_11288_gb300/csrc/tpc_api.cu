@@ -269,10 +269,10 @@ template <typename T> struct Prologue {
   const T* ec = nullptr;
 };
 
-// y = epilogue(A_k u) for one level on the handle's stream, u = x or formed by the prologue.
-template <typename T, bool NS>
-void launch_matvec(tpc_handle* H, const Hier<T>& G, const DevLevel<T>& L, const T* x,
-                   const T* f, T* y, int epi, bool post, const Prologue<T>& pro) {
+// The arguments of one product y = epilogue(A_k u) (u = x or formed by the prologue).
+template <typename T>
+LevelArgs<T> stage_args(const Hier<T>& G, const DevLevel<T>& L, const T* x, const T* f, T* y,
+                        int epi, bool post, const Prologue<T>& pro) {
   LevelArgs<T> a = level_args<T>(G, L);
   a.x = x;
   a.f = f;
@@ -290,6 +290,14 @@ void launch_matvec(tpc_handle* H, const Hier<T>& G, const DevLevel<T>& L, const 
   a.fout = pro.fout;
   a.rfine = pro.rfine;
   a.ec = pro.ec;
+  return a;
+}
+
+// y = epilogue(A_k u) for one level on the handle's stream, u = x or formed by the prologue.
+template <typename T, bool NS>
+void launch_matvec(tpc_handle* H, const Hier<T>& G, const DevLevel<T>& L, const T* x,
+                   const T* f, T* y, int epi, bool post, const Prologue<T>& pro) {
+  const LevelArgs<T> a = stage_args<T>(G, L, x, f, y, epi, post, pro);
   cudaStream_t s = H->stream;
   if (L.logR1 == 0) {
     k_mid_whole<T, NS><<<1, fft_threads<T>(), L.smem_mid, s>>>(a);
@@ -1507,3 +1515,6 @@ const char* tpc_last_error(const tpc_handle* H) {
 
 // The 2-D system (tensor-product reading of section 2.2), built on the 1-D hierarchy above.
 #include "tpc_2d.cuh"
+
+// Stage-batched solves of many instances, built on the handles above.
+#include "tpc_batch.cuh"

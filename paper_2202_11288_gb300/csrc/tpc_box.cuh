@@ -56,11 +56,11 @@ struct BoxArgs {
 
 // Local prefix of each 2048-entry block of v (blocks 0..nblk-1) and of w_bar (nblk..2 nblk-1),
 // the block totals and the block's share of the Cross dot.
-__global__ void __launch_bounds__(NT) k_box_local(BoxArgs a) {
+__device__ __forceinline__ void box_local_body(const BoxArgs& a, int blk) {
   __shared__ double wsum[NT / 32];
   __shared__ double wdot[NT / 32];
-  const int s = blockIdx.x >= a.nblk;
-  const int qb = blockIdx.x - s * a.nblk;
+  const int s = blk >= a.nblk;
+  const int qb = blk - s * a.nblk;
   const int N = a.N;
   const double* xs = a.x + (s ? N + 1 : 0);
   const double* cr = s ? a.zeta : a.q;
@@ -109,10 +109,11 @@ __global__ void __launch_bounds__(NT) k_box_local(BoxArgs a) {
       tot += wsum[w];
       dt += wdot[w];
     }
-    a.bsum[blockIdx.x] = tot;
-    a.part[blockIdx.x] = dt;
+    a.bsum[blk] = tot;
+    a.part[blk] = dt;
   }
 }
+__global__ void __launch_bounds__(NT) k_box_local(BoxArgs a) { box_local_body(a, (int)blockIdx.x); }
 
 // Double-double addition (Knuth's two-sum on the high parts, then the low parts).
 __device__ __forceinline__ double2 dd_add(double2 x, double2 y) {
@@ -126,7 +127,7 @@ __device__ __forceinline__ double2 dd_add(double2 x, double2 y) {
 
 // Exclusive double-double prefix of the block totals of both segments, and the Cross dot (a
 // fixed-order tree sum of the block shares). One block of 1024 threads.
-__global__ void __launch_bounds__(1024) k_box_offsets(BoxArgs a) {
+__device__ __forceinline__ void box_offsets_body(const BoxArgs& a) {
   __shared__ double2 sc[1024];
   __shared__ double red[1024];
   const int t = threadIdx.x;
@@ -167,6 +168,7 @@ __global__ void __launch_bounds__(1024) k_box_offsets(BoxArgs a) {
   }
   if (t == 0) a.dot[0] = red[0];
 }
+__global__ void __launch_bounds__(1024) k_box_offsets(BoxArgs a) { box_offsets_body(a); }
 
 // P(a) - P(b) of segment s (a, b already clamped to [0, N]).
 __device__ __forceinline__ double box_sum(const BoxArgs& a, int s, int ka, int kb) {
@@ -198,24 +200,27 @@ __device__ __forceinline__ double toeplitz_runs(const BoxArgs& a, const Run* run
 
 // r = b - A u for the node rows (blockIdx.y = 0: A v + B_bar w_bar + p w_o) and the midpoint
 // rows (1: C_bar v + D_bar w_bar + xi w_o); block (0, 0) also forms the middle row.
-__global__ void __launch_bounds__(NT) k_box_resid(BoxArgs a) {
+// Block bx of gx (grid-stride over the rows), half 0 / 1 (node / midpoint rows).
+__device__ __forceinline__ void box_resid_body(const BoxArgs& a, int bx, int gx, int half) {
   __shared__ int nr[4];
   __shared__ Run sr[4][MAXR];
   if (threadIdx.x < 4) nr[threadIdx.x] = a.nrun[threadIdx.x];
   if (threadIdx.x < 4 * MAXR) sr[threadIdx.x / MAXR][threadIdx.x % MAXR] =
       a.run[threadIdx.x / MAXR][threadIdx.x % MAXR];
   __syncthreads();
-  const int half = blockIdx.y;
   const int N = a.N;
   const double w_o = a.x[N];
   const int g1 = half ? 2 : 0, g2 = half ? 3 : 1;
-  for (int i = blockIdx.x * NT + threadIdx.x; i < N; i += gridDim.x * NT) {
+  for (int i = bx * NT + threadIdx.x; i < N; i += gx * NT) {
     double y = toeplitz_runs(a, sr[g1], nr[g1], 0, i) + toeplitz_runs(a, sr[g2], nr[g2], 1, i);
     if (i < a.np) y = fma(half ? a.xi[i] : a.p[i], w_o, y);
     const int row = half ? N + 1 + i : i;
     a.r[row] = a.b[row] - y;
   }
-  if (blockIdx.x == 0 && half == 0 && threadIdx.x == 0) a.r[N] = a.b[N] - fma(a.o, w_o, a.dot[0]);
+  if (bx == 0 && half == 0 && threadIdx.x == 0) a.r[N] = a.b[N] - fma(a.o, w_o, a.dot[0]);
+}
+__global__ void __launch_bounds__(NT) k_box_resid(BoxArgs a) {
+  box_resid_body(a, (int)blockIdx.x, (int)gridDim.x, (int)blockIdx.y);
 }
 
 }  // namespace box

@@ -460,8 +460,9 @@ __device__ __forceinline__ void block0_pair(int q, int& p, int& pp) {
 // columns (stride L), each followed by the twiddle W_m^{c k}. One CTA: 2^logC columns.
 // ------------------------------------------------------------------------------------
 // PRO: the prologue, fixed at compile time (the launch selects the instance from a.pro).
-template <typename T, int IN, int PRO, int MINB = fft_min_blocks<T>()>
-__global__ void __launch_bounds__(fft_threads<T>(), MINB) k_fwd_strided(LevelArgs<T> a) {
+// Body of the pass for column block blk (the kernel's block index, or a batched kernel's tile).
+template <typename T, int IN, int PRO>
+__device__ __forceinline__ void fwd_strided_body(const LevelArgs<T>& a, int blk) {
   constexpr int pro = PRO;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2<T>* tab = reinterpret_cast<c2<T>*>(smem_raw);
@@ -471,7 +472,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_fwd_strided(LevelArg
   const c2<T>* tw = step_table_issue<T>(tab, a.twL);  // in flight with the tile's copies
   const int C = 1 << logC;
   const int tile = 1 << (logR1 + logC);
-  const int c0 = (int)blockIdx.x << logC;
+  const int c0 = blk << logC;
   const int half = 1 << (logR1 - 1);
   T dot = 0;
   // FP32 (bound by memory latency): the raw operand values and the Cross rows q, zeta arrive by
@@ -618,10 +619,15 @@ __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_fwd_strided(LevelArg
   if (IN == IN_PACK) {
     const T tot = block_sum<T>(dot, red);
     if (threadIdx.x == 0) {
-      a.partials[blockIdx.x] = tot;
-      if (blockIdx.x == 0 && pro != PRO_NONE) (void)operand<T>(a, a.N, a.pO, pro);  // middle w_o
+      a.partials[blk] = tot;
+      if (blk == 0 && pro != PRO_NONE) (void)operand<T>(a, a.N, a.pO, pro);  // middle w_o
     }
   }
+}
+
+template <typename T, int IN, int PRO, int MINB = fft_min_blocks<T>()>
+__global__ void __launch_bounds__(fft_threads<T>(), MINB) k_fwd_strided(LevelArgs<T> a) {
+  fwd_strided_body<T, IN, PRO>(a, (int)blockIdx.x);
 }
 
 // ------------------------------------------------------------------------------------
@@ -770,7 +776,7 @@ __device__ __forceinline__ void mid_core(const LevelArgs<T>& a, const c2<T>* tw,
 }
 
 template <typename T, int MODE, bool NS, int LOGL_CT = 0>
-__device__ __forceinline__ void mid_body(const LevelArgs<T>& a) {
+__device__ __forceinline__ void mid_body(const LevelArgs<T>& a, int blk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2<T>* tab = reinterpret_cast<c2<T>*>(smem_raw);
   c2<T>* s = tab + tw_slots<T>();
@@ -778,9 +784,9 @@ __device__ __forceinline__ void mid_body(const LevelArgs<T>& a) {
   const c2<T>* tw = step_table_issue<T>(tab, a.twL);  // in flight with the tile's copies
   int b, b2;
   if (MODE == MID_FWD || MODE == MID_FWD_REAL || MODE == MID_WHOLE) {
-    b = b2 = blockIdx.x;
+    b = b2 = blk;
   } else {
-    const int cta = blockIdx.x;
+    const int cta = blk;
     if (cta < 2) {
       b = b2 = cta;
     } else {
@@ -802,27 +808,27 @@ __device__ __forceinline__ void mid_body(const LevelArgs<T>& a) {
 // LOGL_CT: 0 for any L, or log2 L fixed at compile time (the launch picks the instance).
 template <typename T, bool NS, int LOGL_CT = 0>
 __global__ void __launch_bounds__(fft_threads<T>(), mid_min_blocks<T>()) k_mid_pair(LevelArgs<T> a) {
-  mid_body<T, MID_PAIR, NS, LOGL_CT>(a);
+  mid_body<T, MID_PAIR, NS, LOGL_CT>(a, (int)blockIdx.x);
 }
 template <typename T, bool NS>
 __global__ void __launch_bounds__(fft_threads<T>(), mid_min_blocks<T>()) k_mid_whole(LevelArgs<T> a) {
-  mid_body<T, MID_WHOLE, NS>(a);
+  mid_body<T, MID_WHOLE, NS>(a, (int)blockIdx.x);
 }
 template <typename T>
 __global__ void __launch_bounds__(fft_threads<T>(), mid_min_blocks<T>()) k_mid_fwd(LevelArgs<T> a) {
-  mid_body<T, MID_FWD, false>(a);
+  mid_body<T, MID_FWD, false>(a, (int)blockIdx.x);
 }
 template <typename T>
 __global__ void __launch_bounds__(fft_threads<T>(), mid_min_blocks<T>()) k_mid_fwd_real(LevelArgs<T> a) {
-  mid_body<T, MID_FWD_REAL, false>(a);
+  mid_body<T, MID_FWD_REAL, false>(a, (int)blockIdx.x);
 }
 
 // ------------------------------------------------------------------------------------
 // Inverse strided pass: twiddle conj(W_m^{c k}), R1-point DIT per column, epilogue.
 // ------------------------------------------------------------------------------------
 // EPI: the epilogue, fixed at compile time (the launch selects the instance from a.epi).
-template <typename T, int EPI, int MINB = fft_min_blocks<T>()>
-__global__ void __launch_bounds__(fft_threads<T>(), MINB) k_inv_strided(LevelArgs<T> a) {
+template <typename T, int EPI>
+__device__ __forceinline__ void inv_strided_body(const LevelArgs<T>& a, int blk) {
   constexpr int epi = EPI;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2<T>* tab = reinterpret_cast<c2<T>*>(smem_raw);
@@ -830,7 +836,7 @@ __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_inv_strided(LevelArg
   const int logR1 = a.logR1, logC = a.logC, logL = a.logL;
   const int C = 1 << logC;
   const int tile = 1 << (logR1 + logC);
-  const int c0 = (int)blockIdx.x << logC;
+  const int c0 = blk << logC;
   const bool fact = sizeof(T) == 4 && tile >= 2 * (int)blockDim.x &&
                     (long long)tile * C <= (long long)TW_TAB * blockDim.x;
   const TabRegs<T> tr = step_table_load<T>(a.twL);  // in flight with the tile's copies
@@ -939,12 +945,17 @@ __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_inv_strided(LevelArg
       }
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x < 32) {
+  if (blk == 0 && threadIdx.x < 32) {
     T acc = 0;
     for (int i = threadIdx.x; i < a.nparts; i += 32) acc += a.partials[i];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if (threadIdx.x == 0) epi_middle<T>(a, acc, w_o, epi);
   }
+}
+
+template <typename T, int EPI, int MINB = fft_min_blocks<T>()>
+__global__ void __launch_bounds__(fft_threads<T>(), MINB) k_inv_strided(LevelArgs<T> a) {
+  inv_strided_body<T, EPI>(a, (int)blockIdx.x);
 }
 
 // ------------------------------------------------------------------------------------
@@ -979,7 +990,7 @@ __device__ __forceinline__ void copy_args(LevelArgs<T>* dst, const LevelArgs<T>*
 }
 
 template <typename T, bool NS>
-__global__ void __launch_bounds__(fft_threads<T>(), 1) k_vcycle_bottom(const BottomPlan<T>* bp) {
+__device__ __forceinline__ void vcycle_bottom_body(const BottomPlan<T>* bp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2<T>* tab = reinterpret_cast<c2<T>*>(smem_raw);
   c2<T>* s = tab + tw_slots<T>();
@@ -1012,6 +1023,11 @@ __global__ void __launch_bounds__(fft_threads<T>(), 1) k_vcycle_bottom(const Bot
     mid_core<T, MID_WHOLE, NS, 0, 0, PRO_PROLONG, EPI_JACOBI, 2>(la, tw, s, red, 0, 0);
     __syncthreads();
   }
+}
+
+template <typename T, bool NS>
+__global__ void __launch_bounds__(fft_threads<T>(), 1) k_vcycle_bottom(const BottomPlan<T>* bp) {
+  vcycle_bottom_body<T, NS>(bp);
 }
 
 // ------------------------------------------------------------------------------------
