@@ -358,14 +358,32 @@ def time_batch(tpc, torch, args, rank):
         assert rc == tpc.TPC_OK and max(rels) < args.tol
     torch.cuda.synchronize()
     sec = (time.perf_counter() - t0) / steps
+    # the same instances, stage-batched: one cooperative launch per V-cycle stage and group of
+    # instances with equal level structure (tpc_batch_*)
+    B = tpc.Batch(handles)
+    for _ in range(2):
+        rc, its2, rels2, sts2 = B.solve(bs, xs, tol=args.tol)
+        assert rc == tpc.TPC_OK, rc
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        rc, its2, rels2, sts2 = B.solve(bs, xs, tol=args.tol)
+        assert rc == tpc.TPC_OK and max(rels2) < args.tol
+    torch.cuda.synchronize()
+    sec2 = (time.perf_counter() - t0) / steps
+    staged = {"solves_per_s": len(specs) / sec2, "ms_per_batch": 1000.0 * sec2,
+              "groups": B.groups(), "grouped_instances": B.grouped_instances(),
+              "max_outer_iters": max(its2)}
+    B.close()
     dof = sum(S.n for S in solvers)
     for S in solvers:
         S.close()
     return {"instances": len(specs), "solves_per_s": len(specs) / sec, "dof_per_s": dof / sec,
-            "ms_per_batch": 1000.0 * sec, "unknowns_total": dof,
+            "ms_per_batch": 1000.0 * sec, "unknowns_total": dof, "stage_batched": staged,
             "workload": "N=2^K, K uniform in 9..17, delta uniform in [0.02,0.25], SPD/nonsym, "
-                        "constant kernel, mixed precision, tol 1e-10, one tpc_solve_batch per "
-                        "step (host clock)"}
+                        "constant kernel, mixed precision, tol 1e-10; per step one "
+                        "tpc_solve_batch (instance graphs on concurrent streams), and "
+                        "stage_batched: one tpc_batch_solve (host clock)"}
 
 
 def time_fractional(tpc, torch, args, stream):

@@ -163,9 +163,9 @@ int tpc_solve_batch(tpc_handle* const* hs, int count, const double* const* b_dev
  * same finest and coarsest levels, system and inner_cycles, levels up to m = 2^18 -- and
  * prepares, per group, every stage's arguments for all its instances. tpc_batch_solve then runs
  * each outer iteration of a group as ONE launch per stage of Algorithm 2 over all the group's
- * instances (a three-pass
- * product is one persistent cooperative launch whose passes are separated by grid-wide barriers
- * on a device counter), captured once per inner-cycle count as a CUDA graph; the groups run
+ * instances (a three-pass product is either one persistent cooperative launch whose passes are
+ * separated by grid-wide barriers on a device counter, or one launch per pass: see
+ * tpc_batch_set_product_mode), captured once per inner-cycle count as a CUDA graph; the groups run
  * concurrently on their own streams, and handles outside every group are solved as by
  * tpc_solve_batch beside them. Each instance computes exactly what tpc_solve computes on its
  * handle (bitwise). A barrier's wait gives up after a bounded number of polls (about a second):
@@ -178,6 +178,18 @@ int tpc_batch_create(tpc_handle* const* hs, int count, tpc_batch** out);
 /* As tpc_solve_batch, on the batch's handles in their creation order. */
 int tpc_batch_solve(tpc_batch* B, const double* const* b_dev, double* const* x_dev, double tol,
                     int* iters_out, double* relres_out, int* status_out);
+
+/* How a group launches the three-pass products of its levels (a batch starts in TPC_BATCH_AUTO):
+ * TPC_BATCH_COOPERATIVE, one persistent cooperative launch per product as described above;
+ * TPC_BATCH_THREE_PASS, three launches per product (forward strided pass, contiguous blocks,
+ * inverse strided pass), each over the tiles of all live instances; TPC_BATCH_AUTO, the choice
+ * per level that measured faster (three launches on every level of the current kernels: the
+ * barriers' idle blocks and the persistent kernel's two resident blocks per SM cost more than
+ * the two launches they save).
+ * Results are bitwise the same in every mode. Waits for the groups' work in flight and drops
+ * their captured graphs. Returns TPC_EINVAL for NULL or an unknown mode. */
+enum { TPC_BATCH_AUTO = 0, TPC_BATCH_COOPERATIVE = 1, TPC_BATCH_THREE_PASS = 2 };
+int tpc_batch_set_product_mode(tpc_batch* B, int mode);
 
 /* Number of stage-batched groups, and of the instances they hold (-1 for NULL). */
 int tpc_batch_groups(const tpc_batch* B);

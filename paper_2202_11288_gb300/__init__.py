@@ -21,12 +21,13 @@ LIB_PATH = os.path.join(_HERE, "libtpcamg.so")
 TPC_OK, TPC_ENOTCONV = 0, 1
 TPC_EINVAL, TPC_ENOMEM, TPC_ECUDA, TPC_ESINGULAR, TPC_ENOTSUP, TPC_EDIVERGED = -1, -2, -3, -4, -5, -6
 TPC_ESYNC = -7
+TPC_BATCH_AUTO, TPC_BATCH_COOPERATIVE, TPC_BATCH_THREE_PASS = 0, 1, 2
 TPC_SPD, TPC_NONSYM, TPC_WEAKLY = 0, 1, 2
 TPC_FP64, TPC_MIXED = 0, 1
 TPC_TRANSFER_PAPER, TPC_TRANSFER_GEOMETRIC = 0, 1
 
 EXPORTED = ["tpc_default_params", "tpc_setup", "tpc_solve", "tpc_solve_batch", "tpc_solve_host",
-            "tpc_batch_create", "tpc_batch_solve", "tpc_batch_groups",
+            "tpc_batch_create", "tpc_batch_solve", "tpc_batch_groups", "tpc_batch_set_product_mode",
             "tpc_batch_grouped_instances", "tpc_batch_destroy", "tpc_grid_wait_selftest",
             "tpc_apply",
             "tpc_apply_f32",
@@ -105,6 +106,8 @@ def lib() -> ctypes.CDLL:
     L.tpc_batch_create.restype = I
     L.tpc_batch_solve.argtypes = [P, P, P, D, P, P, P]
     L.tpc_batch_solve.restype = I
+    L.tpc_batch_set_product_mode.argtypes = [P, I]
+    L.tpc_batch_set_product_mode.restype = I
     L.tpc_batch_groups.argtypes = [P]
     L.tpc_batch_groups.restype = I
     L.tpc_batch_grouped_instances.argtypes = [P]
@@ -360,6 +363,9 @@ class Batch:
         if rc < 0 and rc not in (TPC_EDIVERGED,):
             raise TpcError(rc, tpc_last_error(None))
         return rc, list(it), list(rel), list(stt)
+
+    def set_product_mode(self, mode: int) -> None:
+        _check(lib().tpc_batch_set_product_mode(self.handle, int(mode)))
 
     def groups(self) -> int:
         return int(lib().tpc_batch_groups(self.handle))

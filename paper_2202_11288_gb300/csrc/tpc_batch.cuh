@@ -7,10 +7,11 @@
 // FP64 refinement, the prefix-sum residual and the norm -- is ONE launch over all instances of
 // the group: a grid dimension runs over the instances, each block reading its instance's
 // arguments from a device array. A three-pass product (forward strided pass, contiguous blocks,
-// inverse strided pass) is one persistent cooperative launch whose blocks take the tiles of all
-// instances pass by pass, separated by grid-wide barriers on a device counter; a barrier's wait
-// gives up after a bounded number of polls, raises an error flag the host reads, and the kernel
-// returns (no hang). Every instance runs exactly the kernels' bodies, arguments and tile
+// inverse strided pass) is either one persistent cooperative launch whose blocks take the tiles
+// of all instances pass by pass, separated by grid-wide barriers on a device counter -- a
+// barrier's wait gives up after a bounded number of polls, raises an error flag the host reads,
+// and the kernel returns (no hang) -- or three launches, one per pass, over the tiles of all
+// instances (the default: measured faster on every level of these kernels). Every instance runs exactly the kernels' bodies, arguments and tile
 // decomposition of its lone solve, so its iterates are bitwise those of tpc_solve; instances
 // that have converged, or that take fewer inner cycles in an iteration, are masked per stage.
 // One iteration of a group is captured once per inner-cycle count as a CUDA graph.
@@ -91,6 +92,37 @@ __global__ void __launch_bounds__(fft_threads<T>(), 2)
     inv_strided_body<T, EPI>(la, w - inst * fwd_blocks);
     __syncthreads();
   }
+}
+
+// The same product as three launches over all live instances, grid (tiles, instances): the
+// lone kernels' bodies and resident-block counts, no grid barrier (the launch boundaries order
+// the passes).
+template <typename T, int PRO, int MINB>
+__global__ void __launch_bounds__(fft_threads<T>(), MINB)
+    k_batch_fwd(const LevelArgs<T>* __restrict__ args, const int* __restrict__ live) {
+  __shared__ __align__(16) LevelArgs<T> la;
+  const int inst = blockIdx.y;
+  if (!live[inst]) return;
+  copy_args<T>(&la, &args[inst]);
+  fwd_strided_body<T, IN_PACK, PRO>(la, (int)blockIdx.x);
+}
+template <typename T, bool NS>
+__global__ void __launch_bounds__(fft_threads<T>(), mid_min_blocks<T>())
+    k_batch_mid(const LevelArgs<T>* __restrict__ args, const int* __restrict__ live) {
+  __shared__ __align__(16) LevelArgs<T> la;
+  const int inst = blockIdx.y;
+  if (!live[inst]) return;
+  copy_args<T>(&la, &args[inst]);
+  mid_pair_dispatch<T, NS>(la, (int)blockIdx.x);
+}
+template <typename T, int EPI, int MINB>
+__global__ void __launch_bounds__(fft_threads<T>(), MINB)
+    k_batch_inv(const LevelArgs<T>* __restrict__ args, const int* __restrict__ live) {
+  __shared__ __align__(16) LevelArgs<T> la;
+  const int inst = blockIdx.y;
+  if (!live[inst]) return;
+  copy_args<T>(&la, &args[inst]);
+  inv_strided_body<T, EPI>(la, (int)blockIdx.x);
 }
 
 // Single-block products (levels with m <= 4096), one block per instance.
@@ -260,6 +292,7 @@ struct tpc_batch {
   std::vector<tpc_handle*> hs;
   std::vector<Group> groups;
   std::vector<int> solo;                 // instances solved with their own iteration graphs
+  int product_mode = TPC_BATCH_AUTO;     // how the three-pass products are launched
   std::vector<void*> dev, pinned;
   std::string err;
 };
@@ -362,6 +395,49 @@ int coop_product(tpc_batch* B, tpc_batch::Group& g, int li, const LevelArgs<floa
   return TPC_OK;
 }
 
+template <int PRO, int EPI, int MB, bool NS>
+int three_pass_mb(tpc_batch* B, tpc_batch::Group& g, const DevLevel<float>& L,
+                  const LevelArgs<float>* args, const int* live) {
+  const int nt = fft_threads<float>();
+  const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  auto kf = k_batch_fwd<float, PRO, MB>;
+  auto km = k_batch_mid<float, NS>;
+  auto ki = k_batch_inv<float, EPI, MB>;
+  TPCB_CUDA(B, cudaFuncSetAttribute(kf, A, (int)L.smem_strided));
+  TPCB_CUDA(B, cudaFuncSetAttribute(km, A, (int)L.smem_mid));
+  TPCB_CUDA(B, cudaFuncSetAttribute(ki, A, (int)L.smem_strided));
+  kf<<<dim3(L.fwd_blocks, g.ninst), nt, L.smem_strided, g.stream>>>(args, live);
+  km<<<dim3(L.mid_blocks, g.ninst), nt, L.smem_mid, g.stream>>>(args, live);
+  ki<<<dim3(L.fwd_blocks, g.ninst), nt, L.smem_strided, g.stream>>>(args, live);
+  TPCB_CUDA(B, cudaGetLastError());
+  return TPC_OK;
+}
+// Resident blocks of the strided passes as the lone launch picks them (launch_fwd_strided).
+template <int PRO, int EPI, bool NS>
+int three_pass(tpc_batch* B, tpc_batch::Group& g, int li, const LevelArgs<float>* args,
+               const int* live) {
+  const DevLevel<float>& L = *g.lev[li];
+  if (L.logm <= LOG_M_HIGH_OCC)
+    return three_pass_mb<PRO, EPI, F32_HIGH_OCC_BLOCKS, NS>(B, g, L, args, live);
+  return three_pass_mb<PRO, EPI, fft_min_blocks<float>(), NS>(B, g, L, args, live);
+}
+
+// Whether level li of the group runs its products as one cooperative launch (else three).
+bool use_coop(const tpc_batch* B, const tpc_batch::Group& g, int li) {
+  if (B->product_mode == TPC_BATCH_COOPERATIVE) return true;
+  if (B->product_mode == TPC_BATCH_THREE_PASS) return false;
+  (void)g;
+  (void)li;
+  return false;
+}
+
+template <int PRO, int EPI, bool NS>
+int product_kind(tpc_batch* B, tpc_batch::Group& g, int li, const LevelArgs<float>* args,
+                 const int* live) {
+  if (use_coop(B, g, li)) return coop_product<NS, PRO, EPI>(B, g, li, args, live);
+  return three_pass<PRO, EPI, NS>(B, g, li, args, live);
+}
+
 // One product stage of level li over the group (prologue / epilogue as in the lone V-cycle).
 int product(tpc_batch* B, tpc_batch::Group& g, int li, const LevelArgs<float>* args, int pro,
             int epi, const int* live) {
@@ -375,17 +451,17 @@ int product(tpc_batch* B, tpc_batch::Group& g, int li, const LevelArgs<float>* a
   const int kind = pro * 4 + epi;
   if (g.ns) {
     switch (kind) {
-      case PRO_SMOOTH * 4 + EPI_RESID: return coop_product<true, PRO_SMOOTH, EPI_RESID>(B, g, li, args, live);
-      case PRO_RESTRICT * 4 + EPI_RESID: return coop_product<true, PRO_RESTRICT, EPI_RESID>(B, g, li, args, live);
-      case PRO_PROLONG * 4 + EPI_JACOBI: return coop_product<true, PRO_PROLONG, EPI_JACOBI>(B, g, li, args, live);
-      default: return coop_product<true, PRO_NONE, EPI_RESID>(B, g, li, args, live);
+      case PRO_SMOOTH * 4 + EPI_RESID: return product_kind<PRO_SMOOTH, EPI_RESID, true>(B, g, li, args, live);
+      case PRO_RESTRICT * 4 + EPI_RESID: return product_kind<PRO_RESTRICT, EPI_RESID, true>(B, g, li, args, live);
+      case PRO_PROLONG * 4 + EPI_JACOBI: return product_kind<PRO_PROLONG, EPI_JACOBI, true>(B, g, li, args, live);
+      default: return product_kind<PRO_NONE, EPI_RESID, true>(B, g, li, args, live);
     }
   }
   switch (kind) {
-    case PRO_SMOOTH * 4 + EPI_RESID: return coop_product<false, PRO_SMOOTH, EPI_RESID>(B, g, li, args, live);
-    case PRO_RESTRICT * 4 + EPI_RESID: return coop_product<false, PRO_RESTRICT, EPI_RESID>(B, g, li, args, live);
-    case PRO_PROLONG * 4 + EPI_JACOBI: return coop_product<false, PRO_PROLONG, EPI_JACOBI>(B, g, li, args, live);
-    default: return coop_product<false, PRO_NONE, EPI_RESID>(B, g, li, args, live);
+    case PRO_SMOOTH * 4 + EPI_RESID: return product_kind<PRO_SMOOTH, EPI_RESID, false>(B, g, li, args, live);
+    case PRO_RESTRICT * 4 + EPI_RESID: return product_kind<PRO_RESTRICT, EPI_RESID, false>(B, g, li, args, live);
+    case PRO_PROLONG * 4 + EPI_JACOBI: return product_kind<PRO_PROLONG, EPI_JACOBI, false>(B, g, li, args, live);
+    default: return product_kind<PRO_NONE, EPI_RESID, false>(B, g, li, args, live);
   }
 }
 
@@ -735,6 +811,24 @@ int tpc_batch_solve(tpc_batch* B, const double* const* b_dev, double* const* x_d
     if (st[i].status < worst || (worst == TPC_OK && st[i].status != TPC_OK)) worst = st[i].status;
   }
   return worst;
+}
+
+int tpc_batch_set_product_mode(tpc_batch* B, int mode) {
+  if (!B || mode < TPC_BATCH_AUTO || mode > TPC_BATCH_THREE_PASS) {
+    set_host_error("bad argument to tpc_batch_set_product_mode");
+    return TPC_EINVAL;
+  }
+  if (mode == B->product_mode) return TPC_OK;
+  for (auto& g : B->groups) {
+    if (g.stream) cudaStreamSynchronize(g.stream);
+    for (cudaGraphExec_t& e : g.exec)
+      if (e) {
+        cudaGraphExecDestroy(e);
+        e = nullptr;
+      }
+  }
+  B->product_mode = mode;
+  return TPC_OK;
 }
 
 int tpc_batch_groups(const tpc_batch* B) { return B ? (int)B->groups.size() : -1; }

@@ -33,7 +33,11 @@ def _solvers(specs):
             for K, d, v, k, a in specs]
 
 
-def test_stage_batched_equals_lone_solves_bitwise():
+MODES = [tpc.TPC_BATCH_AUTO, tpc.TPC_BATCH_COOPERATIVE, tpc.TPC_BATCH_THREE_PASS]
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_stage_batched_equals_lone_solves_bitwise(mode):
     specs = _specs()
     solvers = _solvers(specs)
     try:
@@ -46,6 +50,7 @@ def test_stage_batched_equals_lone_solves_bitwise():
             lone.append((it, x.clone()))
         B = tpc.Batch([S.handle for S in solvers])
         try:
+            B.set_product_mode(mode)
             assert B.groups() == 3 and B.grouped_instances() == 8
             for rep in range(2):                      # twice: graphs are reused
                 xs = [torch.full_like(b, float("nan")) for b in bs]
@@ -62,7 +67,8 @@ def test_stage_batched_equals_lone_solves_bitwise():
             S.close()
 
 
-def test_stage_batched_masks_converged_instances():
+@pytest.mark.parametrize("mode", [tpc.TPC_BATCH_COOPERATIVE, tpc.TPC_BATCH_THREE_PASS])
+def test_stage_batched_masks_converged_instances(mode):
     """Instances that converge in different numbers of outer iterations (a right-hand side that
     is already solved needs none) keep their own results while the group goes on."""
     solvers = _solvers([(12, 0.05, 0, 0, 0.0), (12, 0.09, 0, 0, 0.0)])
@@ -71,6 +77,7 @@ def test_stage_batched_masks_converged_instances():
         b1 = torch.zeros(solvers[1].n, dtype=torch.float64, device="cuda")   # x = 0 at once
         B = tpc.Batch([S.handle for S in solvers])
         try:
+            B.set_product_mode(mode)
             assert B.groups() == 1
             xs = [torch.full_like(b0, 7.0), torch.full_like(b1, 7.0)]
             rc, its, rels, sts = B.solve([b0, b1], xs, tol=1e-10)
@@ -79,6 +86,31 @@ def test_stage_batched_masks_converged_instances():
             x_ref = torch.zeros_like(b0)
             rc, it, rel = solvers[0].solve(b0, x_ref, tol=1e-10)
             assert it == its[0] and torch.equal(xs[0], x_ref)
+        finally:
+            B.close()
+    finally:
+        for S in solvers:
+            S.close()
+
+
+def test_product_mode_switch_keeps_results():
+    """Switching the product mode between solves drops the captured graphs; results stay bitwise."""
+    solvers = _solvers([(13, 0.05, 0, 0, 0.0), (13, 0.12, 0, 0, 0.0)])
+    try:
+        bs = [torch.tensor(uniform_pm1(S.n, 40 + i), device="cuda") for i, S in enumerate(solvers)]
+        B = tpc.Batch([S.handle for S in solvers])
+        try:
+            out = []
+            for mode in (tpc.TPC_BATCH_THREE_PASS, tpc.TPC_BATCH_COOPERATIVE, tpc.TPC_BATCH_AUTO):
+                B.set_product_mode(mode)
+                xs = [torch.zeros_like(b) for b in bs]
+                rc, its, rels, sts = B.solve(bs, xs, tol=1e-10)
+                assert rc == tpc.TPC_OK
+                out.append(xs)
+            for xs in out[1:]:
+                assert all(torch.equal(a, b) for a, b in zip(out[0], xs))
+            with pytest.raises(tpc.TpcError):
+                B.set_product_mode(7)
         finally:
             B.close()
     finally:
