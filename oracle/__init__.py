@@ -29,6 +29,10 @@ Contents
              element integrals of the same collocation, Hadamard finite parts for a >= 1/2.
              PARITY UNPINNED by the paper (pinned only by mathematics: a = -1/2 is the printed
              matrix, exactness on quadratics, Hadamard's definition by quadrature).
+``krylov`` -- an outer iteration that is not the paper's: restarted, right-preconditioned
+             flexible GMRES with one V-cycle as the preconditioner (Saad's FGMRES, classical
+             Gram-Schmidt done twice, Givens rotations), pinned by tests/test_oracle_krylov.py to
+             the minimal-residual property on an explicit Krylov basis and to exact solves.
 ``large``  -- the same finest-level operator for sizes where a dense matrix does not fit:
              selected dense rows, and the product computed with numpy's FFT as the
              convolution step (section 3.2, eq. (3.4)).
