@@ -123,9 +123,9 @@ def parse():
     ap.add_argument("--no-twod", action="store_true", help="skip the 2-D measurement")
     ap.add_argument("--batch", type=int, default=512,
                     help="instances of the batched-uneven measurement (0 = skip it)")
-    ap.add_argument("--serve-rates", default="50,100,200,500,1000,2000",
+    ap.add_argument("--serve-rates", default="50,100,200,300,500",
                     help="Poisson arrival rates (req/s) of the serving measurement ('' = skip)")
-    ap.add_argument("--serve-seconds", type=float, default=2.0,
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="arrival window per rate of the serving measurement")
     ap.add_argument("--profile", action="store_true",
                     help="profiling case: set up, then 3 finest-level products, nothing timed")
@@ -339,51 +339,114 @@ def batch_workload(count, seed=0):
     return specs
 
 
+def batch_mix_workload(count, seed=1):
+    """Uneven 1-D and 2-D instances of 2^10 .. 2^18 unknowns: log2(unknowns) uniform in 10..18;
+    an even exponent 2(K+1) is a 2-D instance with probability 1/2 (n = (2^(K+1) - 1)^2, K in
+    4..8), else a 1-D one (n = 2^(K+1) - 1, K in 9..17). delta uniform in [0.02, 0.25] (redrawn
+    until r >= 1); SPD / nonsymmetric alternating; a 1-D instance takes the fractional kernel
+    with probability 1/2, a uniform in [0.1, 0.4], SPD, geometric transfer (the V-cycle does not
+    converge beyond a ~ 0.43). Entries: (dim, K, delta, variant, kernel, a)."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for i in range(count):
+        e = int(rng.integers(10, 19))
+        dim = 2 if (e % 2 == 0 and rng.random() < 0.5) else 1
+        K = e // 2 - 1 if dim == 2 else e - 1
+        while True:
+            delta = float(rng.uniform(0.02, 0.25))
+            if delta * (1 << K) >= 1.0:
+                break
+        v, kk, a = i % 2, 0, 0.0
+        if dim == 1 and rng.random() < 0.5:
+            v, kk, a = 0, 1, float(rng.uniform(0.1, 0.4))
+        specs.append((dim, K, delta, v, kk, a))
+    return specs
+
+
 def time_batch(tpc, torch, args, rank):
-    """One step = one tpc_solve_batch call over all instances (mixed precision)."""
+    """The batched configuration: one tpc_batch_solve over a mix of 1-D (constant and
+    fractional) and 2-D instances; beside it, the earlier constant-kernel 1-D workload solved
+    both stage-batched and as per-instance graphs on concurrent streams (tpc_solve_batch)."""
+    steps = min(5, max(1, args.steps))  # the batch is a secondary measurement: a few steps
+
+    def timed(f):
+        for _ in range(2):
+            f()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            f()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / steps
+
+    # the mix
+    specs = batch_mix_workload(args.batch)
+    s1 = [s for s in specs if s[0] == 1]
+    s2 = [s for s in specs if s[0] == 2]
+    solvers = [tpc.Solver(d, 2.0 ** -K, variant=v, kernel=kk, kernel_a=a, precision=tpc.TPC_MIXED,
+                          transfer=(tpc.TPC_TRANSFER_GEOMETRIC if kk else tpc.TPC_TRANSFER_PAPER))
+               for _, K, d, v, kk, a in s1]
+    twod = [tpc.Solver2D(d, 2.0 ** -K, variant=v, precision=tpc.TPC_MIXED) for _, K, d, v, _, _ in s2]
+    sizes = [S.n for S in solvers] + [S.nn for S in twod]
+    bs = [torch.tensor(uniform_pm1(n, 7000 + i), device="cuda") for i, n in enumerate(sizes)]
+    xs = [torch.zeros_like(b) for b in bs]
+    B = tpc.Batch([S.handle for S in solvers], [S.handle for S in twod])
+    res = {}
+
+    def mix():
+        rc, its, rels, sts = B.solve(bs, xs, tol=args.tol)
+        assert rc == tpc.TPC_OK and max(rels) < args.tol, (rc, max(rels))
+        res["its"] = its
+
+    sec = timed(mix)
+    dof = sum(sizes)
+    out = {"instances": len(specs), "instances_2d": len(s2),
+           "instances_fractional": sum(1 for s in s1 if s[4]), "solves_per_s": len(specs) / sec,
+           "dof_per_s": dof / sec, "ms_per_batch": 1000.0 * sec, "unknowns_total": dof,
+           "groups": B.groups(), "grouped_instances": B.grouped_instances(),
+           "max_outer_iters": max(res["its"]),
+           "workload": "512 instances of 2^10..2^18 unknowns (log2 uniform in 10..18; even "
+                       "exponents 2-D with probability 1/2), delta uniform in [0.02,0.25], "
+                       "SPD/nonsym, 1-D: constant kernel or (probability 1/2) fractional a "
+                       "uniform in [0.1,0.4] with the geometric transfer, 2-D: constant kernel; "
+                       "mixed precision, tol 1e-10; one tpc_batch_solve per step (host clock)"}
+    B.close()
+    for S in solvers + twod:
+        S.close()
+    # the constant-kernel 1-D workload, stage-batched and on concurrent streams
     specs = batch_workload(args.batch)
     solvers = [tpc.Solver(d, 2.0 ** -K, variant=v, kernel=kk, kernel_a=a,
                           precision=tpc.TPC_MIXED) for K, d, v, kk, a in specs]
     bs = [torch.tensor(uniform_pm1(S.n, 5000 + i), device="cuda") for i, S in enumerate(solvers)]
     xs = [torch.zeros_like(b) for b in bs]
     handles = [S.handle for S in solvers]
-    for _ in range(2):
-        rc, its, rels, sts = tpc.tpc_solve_batch(handles, bs, xs, tol=args.tol)
-        assert rc == tpc.TPC_OK, rc
-    torch.cuda.synchronize()
-    steps = min(5, max(1, args.steps))  # the batch is a secondary measurement: a few steps
-    t0 = time.perf_counter()
-    for _ in range(steps):
+
+    def streams():
         rc, its, rels, sts = tpc.tpc_solve_batch(handles, bs, xs, tol=args.tol)
         assert rc == tpc.TPC_OK and max(rels) < args.tol
-    torch.cuda.synchronize()
-    sec = (time.perf_counter() - t0) / steps
-    # the same instances, stage-batched: one cooperative launch per V-cycle stage and group of
-    # instances with equal level structure (tpc_batch_*)
+
     B = tpc.Batch(handles)
-    for _ in range(2):
-        rc, its2, rels2, sts2 = B.solve(bs, xs, tol=args.tol)
-        assert rc == tpc.TPC_OK, rc
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        rc, its2, rels2, sts2 = B.solve(bs, xs, tol=args.tol)
-        assert rc == tpc.TPC_OK and max(rels2) < args.tol
-    torch.cuda.synchronize()
-    sec2 = (time.perf_counter() - t0) / steps
-    staged = {"solves_per_s": len(specs) / sec2, "ms_per_batch": 1000.0 * sec2,
-              "groups": B.groups(), "grouped_instances": B.grouped_instances(),
-              "max_outer_iters": max(its2)}
-    B.close()
+
+    def staged():
+        rc, its, rels, sts = B.solve(bs, xs, tol=args.tol)
+        assert rc == tpc.TPC_OK and max(rels) < args.tol
+
+    sec_streams = timed(streams)
+    sec_staged = timed(staged)
     dof = sum(S.n for S in solvers)
+    out["constant_1d"] = {
+        "instances": len(specs), "unknowns_total": dof, "groups": B.groups(),
+        "stage_batched": {"solves_per_s": len(specs) / sec_staged, "dof_per_s": dof / sec_staged,
+                          "ms_per_batch": 1000.0 * sec_staged},
+        "streams": {"solves_per_s": len(specs) / sec_streams, "dof_per_s": dof / sec_streams,
+                    "ms_per_batch": 1000.0 * sec_streams},
+        "workload": "N=2^K, K uniform in 9..17, delta uniform in [0.02,0.25], SPD/nonsym, "
+                    "constant kernel, mixed precision, tol 1e-10; stage_batched: tpc_batch_solve, "
+                    "streams: tpc_solve_batch (instance graphs on concurrent streams)"}
+    B.close()
     for S in solvers:
         S.close()
-    return {"instances": len(specs), "solves_per_s": len(specs) / sec, "dof_per_s": dof / sec,
-            "ms_per_batch": 1000.0 * sec, "unknowns_total": dof, "stage_batched": staged,
-            "workload": "N=2^K, K uniform in 9..17, delta uniform in [0.02,0.25], SPD/nonsym, "
-                        "constant kernel, mixed precision, tol 1e-10; per step one "
-                        "tpc_solve_batch (instance graphs on concurrent streams), and "
-                        "stage_batched: one tpc_batch_solve (host clock)"}
+    return out
 
 
 def time_fractional(tpc, torch, args, stream):
@@ -450,78 +513,118 @@ def time_twod(tpc, torch, args, stream, K=11, delta=0.1):
 
 
 def serve_keys():
-    """Problems of the serving measurement: N = 2^K, K in 9..21 (1023 .. 4,194,303 unknowns,
-    log-uniform when K is uniform), delta in {0.05, 0.1, 0.2}, SPD or nonsymmetric, constant
-    kernel: (variant, delta, K, kernel, a)."""
-    return [(v, d, K, 0, 0.0) for K in range(9, 22) for d in (0.05, 0.1, 0.2) for v in (0, 1)]
+    """Problems of the serving measurement, (dim, variant, delta, K, kernel, a, transfer), sizes
+    2^10 .. 2^22 unknowns: 1-D N = 2^K, K in 9..21 (n = 2^(K+1) - 1), delta in {0.05, 0.1, 0.2},
+    SPD or nonsymmetric with the constant kernel, or SPD with the fractional kernel a in {0.1,
+    0.25, 0.4} (geometric transfer); 2-D K in 4..10 (n = (2^(K+1) - 1)^2, the even exponents),
+    delta in {0.1, 0.2}, SPD or nonsymmetric, constant kernel. Requests pick the dimension with
+    probability 1/2 each, then the size uniformly on the log scale, then the rest uniformly."""
+    one = [(1, v, d, K, 0, 0.0, 0) for K in range(9, 22) for d in (0.05, 0.1, 0.2) for v in (0, 1)]
+    one += [(1, 0, d, K, 1, a, 1) for K in range(9, 22) for d in (0.05, 0.2) for a in (0.1, 0.25, 0.4)]
+    two = [(2, v, d, K, 0, 0.0, 0) for K in range(4, 11) for d in (0.1, 0.2) for v in (0, 1)]
+    return one, two
+
+
+def serve_size(key):
+    dim, K = key[0], key[3]
+    n1 = (1 << (K + 1)) - 1
+    return n1 * n1 if dim == 2 else n1
 
 
 def time_serving(tpc, torch, args):
-    """Poisson arrivals into the request server; p50 / p99 latency and throughput per rate."""
+    """Poisson arrivals into the request server; p50 / p99 latency, throughput and the server's
+    occupancy of the GPU (fraction of the window with a solve on it, mean solves on it at once)
+    per rate."""
     rates = [float(r) for r in args.serve_rates.split(",") if r.strip()]
-    keys = serve_keys()
+    one, two = serve_keys()
+    keys = one + two
     rng = np.random.default_rng(17)
-    rhs = {K: torch.tensor(uniform_pm1((1 << (K + 1)) - 1, 900 + K)).pin_memory()
-           for K in range(9, 22)}
-    pool = {K: [] for K in rhs}
+    sizes = sorted(set(serve_size(k) for k in keys))
+    rhs = {n: torch.tensor(uniform_pm1(n, 900 + i)).pin_memory() for i, n in enumerate(sizes)}
+    pool = {n: [] for n in rhs}
 
-    def xbuf(K):
-        return pool[K].pop() if pool[K] else torch.empty(rhs[K].numel(), dtype=torch.float64).pin_memory()
+    def xbuf(n):
+        return pool[n].pop() if pool[n] else torch.empty(n, dtype=torch.float64).pin_memory()
+
+    def pick():
+        # dimension, then the size (log scale), then the rest
+        group = one if rng.random() < 0.5 else two
+        Ks = sorted(set(k[3] for k in group))
+        K = Ks[int(rng.integers(len(Ks)))]
+        cands = [k for k in group if k[3] == K]
+        return cands[int(rng.integers(len(cands)))]
 
     srv = tpc.Server(hbm_budget_bytes=150 << 30, max_inflight=32, precision=tpc.TPC_MIXED)
-    out = {"workload": "Poisson arrivals; N=2^K, K uniform in 9..21 (1023..4,194,303 unknowns), "
-                       "delta in {0.05,0.1,0.2}, SPD/nonsym, constant kernel, mixed precision, "
-                       "tol 1e-10, host buffers (pinned); hierarchies resident (HBM budget "
-                       "150 GB, 32 slots)",
-           "rates": []}
+    out = {"workload": "Poisson arrivals of 1-D and 2-D solves, 2^10..2^22 unknowns (dimension "
+                       "1/2 each, size log-uniform): 1-D N=2^K, K in 9..21, constant kernel "
+                       "(delta in {0.05,0.1,0.2}, SPD/nonsym) or fractional a in {0.1,0.25,0.4} "
+                       "(SPD, geometric transfer, delta in {0.05,0.2}); 2-D K in 4..10, delta in "
+                       "{0.1,0.2}, SPD/nonsym, constant kernel; uniform[-1,1) right-hand sides; "
+                       "mixed precision, tol 1e-10, host buffers (pinned); hierarchies resident "
+                       f"(HBM budget 150 GB, 32 slots); {args.serve_seconds:g} s of arrivals per rate",
+           "keys": len(keys), "rates": []}
     try:
         owner = {}
         t0 = time.perf_counter()
-        for v, d, K, kk, a in keys:                    # prewarm: build every hierarchy once
-            x = xbuf(K)
-            owner[srv.submit(v, d, 2.0 ** -K, rhs[K], x, args.tol, kk, a)] = (K, x)
+        failed_keys = []
+        for key in keys:                    # prewarm: build every hierarchy once
+            dim, v, d, K, kk, a, tr = key
+            n = serve_size(key)
+            x = xbuf(n)
+            owner[srv.submit(v, d, 2.0 ** -K, rhs[n], x, args.tol, kk, a, dim=dim, transfer=tr)] = (n, x, key)
         got = 0
         while got < len(keys):
             for r in srv.poll(256, wait_ms=20):
-                K, x = owner.pop(r["ticket"])
-                pool[K].append(x)
+                n, x, key = owner.pop(r["ticket"])
+                pool[n].append(x)
+                if r["status"] != tpc.TPC_OK:
+                    failed_keys.append(list(key))
                 got += 1
         out["prewarm_s"] = time.perf_counter() - t0
+        out["prewarm_failed_keys"] = failed_keys
+        out["resident_gb"] = srv.stats()["resident_bytes"] / 1e9
         for rate in rates:
             n_req = max(1, int(rate * args.serve_seconds))
             gaps = rng.exponential(1.0 / rate, n_req)
-            picks = rng.integers(len(keys), size=n_req)
             lat, bad = [], 0
+            srv.stats(reset=True)
             start = time.perf_counter()
             t_next = start
             for i in range(n_req):
                 t_next += gaps[i]
                 while True:
                     for r in srv.poll(256, wait_ms=0):
-                        K, x = owner.pop(r["ticket"])
-                        pool[K].append(x)
+                        n, x, _ = owner.pop(r["ticket"])
+                        pool[n].append(x)
                         lat.append(r["latency_s"])
                         bad += r["status"] != tpc.TPC_OK
                     dt = t_next - time.perf_counter()
                     if dt <= 0:
                         break
                     time.sleep(min(dt, 0.0005))
-                v, d, K, kk, a = keys[picks[i]]
-                x = xbuf(K)
-                owner[srv.submit(v, d, 2.0 ** -K, rhs[K], x, args.tol, kk, a)] = (K, x)
+                key = pick()
+                dim, v, d, K, kk, a, tr = key
+                n = serve_size(key)
+                x = xbuf(n)
+                owner[srv.submit(v, d, 2.0 ** -K, rhs[n], x, args.tol, kk, a, dim=dim,
+                                 transfer=tr)] = (n, x, key)
             while owner:
                 for r in srv.poll(256, wait_ms=20):
-                    K, x = owner.pop(r["ticket"])
-                    pool[K].append(x)
+                    n, x, _ = owner.pop(r["ticket"])
+                    pool[n].append(x)
                     lat.append(r["latency_s"])
                     bad += r["status"] != tpc.TPC_OK
             wall = time.perf_counter() - start
+            st = srv.stats()
             lat_ms = np.array(lat) * 1000.0
             out["rates"].append({"rate_req_s": rate, "requests": n_req,
                                  "throughput_req_s": n_req / wall,
                                  "p50_ms": float(np.percentile(lat_ms, 50)),
                                  "p99_ms": float(np.percentile(lat_ms, 99)),
-                                 "failed": int(bad)})
+                                 "failed": int(bad),
+                                 "gpu_busy_frac": st["busy_s"] / max(st["elapsed_s"], 1e-9),
+                                 "mean_inflight_when_busy": st["inflight_s"] / max(st["busy_s"], 1e-9),
+                                 "max_inflight": st["max_inflight_seen"]})
     finally:
         srv.close()
     return out

@@ -100,6 +100,7 @@ typedef struct tpc_params {
 } tpc_params;
 
 typedef struct tpc_handle tpc_handle;
+typedef struct tpc2d_handle tpc2d_handle;  /* the 2-D system: see tpc2d_setup */
 
 /* Fill *p with the defaults: SPD, constant kernel, V(1,1), omega 2/3, kc 3, FP64, 100
  * iterations. */
@@ -174,6 +175,13 @@ int tpc_solve_batch(tpc_handle* const* hs, int count, const double* const* b_dev
  * device memory of a few KB per instance. */
 typedef struct tpc_batch tpc_batch;
 int tpc_batch_create(tpc_handle* const* hs, int count, tpc_batch** out);
+
+/* As tpc_batch_create, with count2 2-D handles (tpc2d_setup) as further instances: each runs its
+ * own iteration graphs on its own stream beside the groups, exactly as tpc2d_solve would. In
+ * tpc_batch_solve the vectors and outputs of the 2-D instances follow the 1-D ones (index
+ * count + i). */
+int tpc_batch_create_2d(tpc_handle* const* hs, int count, tpc2d_handle* const* hs2, int count2,
+                        tpc_batch** out);
 
 /* As tpc_solve_batch, on the batch's handles in their creation order. */
 int tpc_batch_solve(tpc_batch* B, const double* const* b_dev, double* const* x_dev, double tol,
@@ -346,7 +354,6 @@ int tpc_apply_noalloc(long long N, const double* tA, const double* tB, const dou
  * A_k (x) Q_k + Q_k (x) A_k - A_k (x) A_k / (12 r)), damped Jacobi with the diagonal of each level
  * and a dense solve at the coarsest level; products are FFT products (eq. (3.4)) along rows and
  * columns. precision TPC_MIXED runs FP32 V-cycles inside FP64 refinement as tpc_solve does. */
-typedef struct tpc2d_handle tpc2d_handle;
 
 /* Set up on the caller's stream (NULL: a stream of the handle). Needs variant TPC_SPD or
  * TPC_NONSYM, kernel 0, the paper's transfer (else TPC_ENOTSUP), h = 2^-K with K <= 11 and
@@ -383,11 +390,11 @@ void tpc2d_destroy(tpc2d_handle* H);
 
 /* ---- Request server: continuous batching of independent solves (not in the paper) ----
  * A worker thread admits submitted requests while a slot (max_inflight) and device memory
- * (hbm_budget_bytes) are free, keeps level hierarchies resident keyed by (variant, delta, h,
- * precision) and reuses an idle one when a key repeats (evicting idle ones least recently used
- * first), and runs every admitted solve on its own stream exactly as tpc_solve would (the
- * result is bitwise that of solving it alone). Requests that arrive while others are on the
- * GPU start as soon as a slot and memory free up. */
+ * (hbm_budget_bytes) are free, keeps level hierarchies resident keyed by (dimension, variant,
+ * kernel, transfer, delta, h, precision) and reuses an idle one when a key repeats (evicting idle
+ * ones least recently used first), and runs every admitted solve on its own stream exactly as
+ * tpc_solve (1-D) or tpc2d_solve (2-D) would (the result is bitwise that of solving it alone).
+ * Requests that arrive while others are on the GPU start as soon as a slot and memory free up. */
 typedef struct tpc_server tpc_server;
 typedef struct tpc_server_config {
   size_t hbm_budget_bytes; /* device memory the resident hierarchies may hold (default 150 GiB) */
@@ -405,6 +412,9 @@ typedef struct tpc_request {
   double tol;              /* relative residual target                                       */
   int kernel;              /* as tpc_params.kernel (0 constant, 1 fractional)                */
   double kernel_a;         /* as tpc_params.kernel_a                                         */
+  int dim;                 /* 2: the 2-D system of tpc2d_setup (n = (2/h - 1)^2 unknowns);
+                              0 or 1: the 1-D system                                         */
+  int transfer;            /* as tpc_params.transfer (0, the paper's, for zeroed requests)  */
 } tpc_request;
 typedef struct tpc_server_result {
   long long ticket;        /* as returned by tpc_server_submit                               */
@@ -427,6 +437,21 @@ int tpc_server_submit(tpc_server* S, const tpc_request* r, long long* ticket);
 int tpc_server_poll(tpc_server* S, tpc_server_result* out, int cap, int wait_ms);
 /* Requests submitted and not yet finished. */
 long long tpc_server_outstanding(tpc_server* S);
+/* Occupancy of the GPU by the server's solves, accumulated by the worker since the server
+ * started or since the last call with reset != 0. busy_s / elapsed_s is the fraction of the time
+ * with at least one solve on the GPU; inflight_s / busy_s the mean number of solves on the GPU
+ * at once while busy (their streams' work overlaps on the device). */
+typedef struct tpc_server_stats {
+  long long admitted;      /* requests started on the GPU                                   */
+  long long setups;        /* hierarchies built                                             */
+  long long evictions;     /* idle hierarchies freed to make room                           */
+  double elapsed_s;        /* time covered                                                   */
+  double busy_s;           /* of it, time with at least one solve on the GPU                 */
+  double inflight_s;       /* integral over time of the number of solves on the GPU          */
+  int max_inflight_seen;   /* most solves on the GPU at once                                 */
+  size_t resident_bytes;   /* device memory the resident hierarchies hold (at the last update)*/
+} tpc_server_stats;
+int tpc_server_get_stats(tpc_server* S, tpc_server_stats* out, int reset);
 /* Finish every outstanding request, free everything, stop the worker. NULL-safe. */
 void tpc_server_destroy(tpc_server* S);
 

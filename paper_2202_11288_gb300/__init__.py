@@ -27,7 +27,7 @@ TPC_FP64, TPC_MIXED = 0, 1
 TPC_TRANSFER_PAPER, TPC_TRANSFER_GEOMETRIC = 0, 1
 
 EXPORTED = ["tpc_default_params", "tpc_setup", "tpc_solve", "tpc_solve_batch", "tpc_solve_host",
-            "tpc_batch_create", "tpc_batch_solve", "tpc_batch_groups", "tpc_batch_set_product_mode",
+            "tpc_batch_create", "tpc_batch_create_2d", "tpc_batch_solve", "tpc_batch_groups", "tpc_batch_set_product_mode",
             "tpc_batch_grouped_instances", "tpc_batch_destroy", "tpc_grid_wait_selftest",
             "tpc_apply",
             "tpc_apply_f32",
@@ -44,7 +44,8 @@ EXPORTED = ["tpc_default_params", "tpc_setup", "tpc_solve", "tpc_solve_batch", "
             "tpc2d_last_solve_cycles", "tpc2d_kernel_launches", "tpc2d_last_error",
             "tpc2d_destroy",
             "tpc_server_default_config", "tpc_server_create", "tpc_server_submit",
-            "tpc_server_poll", "tpc_server_outstanding", "tpc_server_destroy"]
+            "tpc_server_poll", "tpc_server_outstanding", "tpc_server_get_stats",
+            "tpc_server_destroy"]
 
 
 class TpcParams(ctypes.Structure):
@@ -66,7 +67,15 @@ class TpcServerConfig(ctypes.Structure):
 class TpcRequest(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("delta", ctypes.c_double), ("h", ctypes.c_double),
                 ("n", ctypes.c_longlong), ("b_host", ctypes.c_void_p), ("x_host", ctypes.c_void_p),
-                ("tol", ctypes.c_double), ("kernel", ctypes.c_int), ("kernel_a", ctypes.c_double)]
+                ("tol", ctypes.c_double), ("kernel", ctypes.c_int), ("kernel_a", ctypes.c_double),
+                ("dim", ctypes.c_int), ("transfer", ctypes.c_int)]
+
+
+class TpcServerStats(ctypes.Structure):
+    _fields_ = [("admitted", ctypes.c_longlong), ("setups", ctypes.c_longlong),
+                ("evictions", ctypes.c_longlong), ("elapsed_s", ctypes.c_double),
+                ("busy_s", ctypes.c_double), ("inflight_s", ctypes.c_double),
+                ("max_inflight_seen", ctypes.c_int), ("resident_bytes", ctypes.c_size_t)]
 
 
 class TpcServerResult(ctypes.Structure):
@@ -104,6 +113,8 @@ def lib() -> ctypes.CDLL:
     L.tpc_solve_batch.restype = I
     L.tpc_batch_create.argtypes = [P, I, ctypes.POINTER(P)]
     L.tpc_batch_create.restype = I
+    L.tpc_batch_create_2d.argtypes = [P, I, P, I, ctypes.POINTER(P)]
+    L.tpc_batch_create_2d.restype = I
     L.tpc_batch_solve.argtypes = [P, P, P, D, P, P, P]
     L.tpc_batch_solve.restype = I
     L.tpc_batch_set_product_mode.argtypes = [P, I]
@@ -166,6 +177,8 @@ def lib() -> ctypes.CDLL:
     L.tpc_server_poll.restype = I
     L.tpc_server_outstanding.argtypes = [P]
     L.tpc_server_outstanding.restype = LL
+    L.tpc_server_get_stats.argtypes = [P, ctypes.POINTER(TpcServerStats), I]
+    L.tpc_server_get_stats.restype = I
     L.tpc_server_destroy.argtypes = [P]
     L.tpc_server_destroy.restype = None
     L.tpc_destroy.argtypes = [P]
@@ -343,14 +356,18 @@ def tpc_solve_batch(handles, bs, xs, tol: float = 1e-10):
 
 class Batch:
     """Stage-batched solves over a fixed list of handles (tpc_batch_*): ``Batch(handles)`` then
-    ``solve(bs, xs)``; groups instances of identical level structure into one launch per stage."""
+    ``solve(bs, xs)``; groups instances of identical level structure into one launch per stage.
+    ``handles2d`` (2-D handles) are further instances, solved beside the groups; their vectors
+    follow the 1-D ones in ``bs`` and ``xs``."""
 
-    def __init__(self, handles):
-        n = len(handles)
-        self._n = n
-        HA = (ctypes.c_void_p * n)(*[h.value if hasattr(h, "value") else h for h in handles])
+    def __init__(self, handles, handles2d=()):
+        n, n2 = len(handles), len(handles2d)
+        self._n = n + n2
+        val = lambda h: h.value if hasattr(h, "value") else h
+        HA = (ctypes.c_void_p * max(n, 1))(*[val(h) for h in handles])
+        HB = (ctypes.c_void_p * max(n2, 1))(*[val(h) for h in handles2d])
         self.handle = ctypes.c_void_p()
-        _check(lib().tpc_batch_create(HA, n, ctypes.byref(self.handle)))
+        _check(lib().tpc_batch_create_2d(HA, n, HB, n2, ctypes.byref(self.handle)))
 
     def solve(self, bs, xs, tol: float = 1e-10):
         n = self._n
@@ -607,12 +624,14 @@ class Server:
         self._keep = {}
 
     def submit(self, variant: int, delta: float, h: float, b, x, tol: float = 1e-10,
-               kernel: int = 0, kernel_a: float = 0.0) -> int:
-        """b, x: contiguous float64 host arrays (numpy, or pinned torch CPU tensors)."""
+               kernel: int = 0, kernel_a: float = 0.0, dim: int = 1,
+               transfer: int = TPC_TRANSFER_PAPER) -> int:
+        """b, x: contiguous float64 host arrays (numpy, or pinned torch CPU tensors); dim 2 for
+        the 2-D system ((2/h - 1)^2 unknowns)."""
         n = b.numel() if hasattr(b, "numel") else b.size
         bp = b.data_ptr() if hasattr(b, "data_ptr") else b.ctypes.data
         xp = x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
-        r = TpcRequest(variant, delta, h, n, bp, xp, tol, kernel, kernel_a)
+        r = TpcRequest(variant, delta, h, n, bp, xp, tol, kernel, kernel_a, dim, transfer)
         t = ctypes.c_longlong(0)
         _check(lib().tpc_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)))
         self._keep[t.value] = (b, x)
@@ -631,6 +650,11 @@ class Server:
 
     def outstanding(self) -> int:
         return int(lib().tpc_server_outstanding(self.handle))
+
+    def stats(self, reset: bool = False) -> dict:
+        st = TpcServerStats()
+        _check(lib().tpc_server_get_stats(self.handle, ctypes.byref(st), int(reset)))
+        return {f: getattr(st, f) for f, _ in TpcServerStats._fields_}
 
     def close(self) -> None:
         if self.handle:

@@ -240,9 +240,12 @@ struct tpc2d_handle {
   double* sumsq_host = nullptr;       // pinned
   cudaGraphExec_t iter_exec[33] = {};
   cudaEvent_t ev = nullptr;
+  double* hb = nullptr;               // staging buffers of solves with host buffers (on demand)
+  double* hx = nullptr;
   long long launches = 0;
   int last_cycles = 0;
   std::vector<void*> allocs;
+  size_t dev_bytes = 0;               // device memory of allocs
   std::string err;
 };
 
@@ -272,6 +275,7 @@ int alloc2(tpc2d_handle* H, P** ptr, size_t count) {
     return e == cudaErrorMemoryAllocation ? TPC_ENOMEM : TPC_ECUDA;
   }
   H->allocs.push_back(v);
+  H->dev_bytes += count * sizeof(P) + 16;
   *ptr = reinterpret_cast<P*>(v);
   if (H->prm.poison) TPC2_CUDA(H, cudaMemsetAsync(v, 0xFF, count * sizeof(P) + 16, H->stream));
   return TPC_OK;
@@ -479,6 +483,102 @@ void release2(tpc2d_handle* H) {
   delete H;
 }
 
+// The outer iteration of a 2-D solve as a state machine: solve2_begin enqueues the initial
+// residual norm, each solve2_step (called once the handle's event has completed) reads the
+// latest norm, decides, and enqueues the next iteration's graph and norm read-back, and
+// solve2_finish enqueues the copy of the iterate. tpc2d_solve drives it synchronously, the
+// request server by polling.
+struct Solve2State {
+  tpc2d_handle* H = nullptr;
+  double* x_dev = nullptr;
+  double tol = 0.0, r0 = 0.0, rel = 0.0, rel_prev = 0.0;
+  int it = 0, cycles = 0, status = TPC_OK;
+  bool started = false, done = false;
+};
+
+int solve2_begin(Solve2State& st, const double* b_dev, double* x_dev, double tol, int use_x0) {
+  tpc2d_handle* H = st.H;
+  const long long nn = H->D.lev[0].nn;
+  const size_t bytes = (size_t)nn * sizeof(double);
+  cudaStream_t s = H->stream;
+  st.x_dev = x_dev;
+  st.tol = tol;
+  TPC2_CUDA(H, cudaMemcpyAsync(H->b, b_dev, bytes, cudaMemcpyDeviceToDevice, s));
+  if (use_x0) {
+    TPC2_CUDA(H, cudaMemcpyAsync(H->u, x_dev, bytes, cudaMemcpyDeviceToDevice, s));
+    matvec2<double>(H, 0, H->u, H->b, H->r0, EPI_RESID, nullptr);
+  } else {
+    TPC2_CUDA(H, cudaMemsetAsync(H->u, 0, bytes, s));
+    TPC2_CUDA(H, cudaMemcpyAsync(H->r0, H->b, bytes, cudaMemcpyDeviceToDevice, s));
+  }
+  sumsq2(H, H->r0, nn);
+  TPC2_CUDA(H, cudaMemcpyAsync(H->sumsq_host, H->sumsq, sizeof(double), cudaMemcpyDeviceToHost, s));
+  TPC2_CUDA(H, cudaEventRecord(H->ev, s));
+  H->last_cycles = 0;
+  return TPC_OK;
+}
+
+int solve2_step(Solve2State& st) {
+  tpc2d_handle* H = st.H;
+  const double ss = *H->sumsq_host;
+  if (!st.started) {
+    st.started = true;
+    st.r0 = std::sqrt(ss);
+    st.rel = st.r0 > 0.0 ? 1.0 : 0.0;
+    if (!std::isfinite(st.r0)) {
+      H->err = "right-hand side or initial residual is not finite";
+      st.status = TPC_EINVAL;
+      st.done = true;
+      return TPC_OK;
+    }
+  } else {
+    ++st.it;
+    st.rel = std::sqrt(ss) / st.r0;
+    if (!std::isfinite(st.rel)) {
+      H->err = "residual became non-finite";
+      st.status = TPC_EDIVERGED;
+      st.done = true;
+      return TPC_OK;
+    }
+  }
+  if (!(st.rel >= st.tol && st.r0 > 0.0)) {
+    st.done = true;
+    return TPC_OK;
+  }
+  if (st.it >= H->prm.max_iters) {
+    st.status = TPC_ENOTCONV;
+    st.done = true;
+    return TPC_OK;
+  }
+  // inner cycles: the full count first, then the fewest expected to reach tol / 4 at the rate
+  // per cycle measured by the previous iteration (as the 1-D mixed solve)
+  const int full = H->prm.precision == TPC_MIXED ? H->prm.inner_cycles : 1;
+  int c = full;
+  if (full > 1 && st.it > 0 && st.cycles > 0) {
+    const double red = st.rel / st.rel_prev;
+    const double rho = std::pow(red, 1.0 / st.cycles), need = st.tol / (4.0 * st.rel);
+    if (red > 0.0 && red < 1.0 && rho > 0.0 && rho < 1.0 && need > 0.0 && need < 1.0) {
+      const double cc = std::ceil(std::log(need) / std::log(rho));
+      c = cc < 1.0 ? 1 : (cc > full ? full : (int)cc);
+    }
+  }
+  cudaStream_t s = H->stream;
+  TPC2_CUDA(H, cudaGraphLaunch(H->iter_exec[c], s));
+  TPC2_CUDA(H, cudaMemcpyAsync(H->sumsq_host, H->sumsq, sizeof(double), cudaMemcpyDeviceToHost, s));
+  TPC2_CUDA(H, cudaEventRecord(H->ev, s));
+  H->last_cycles += c;
+  st.rel_prev = st.rel;
+  st.cycles = c;
+  return TPC_OK;
+}
+
+int solve2_finish(Solve2State& st) {
+  tpc2d_handle* H = st.H;
+  const size_t bytes = (size_t)H->D.lev[0].nn * sizeof(double);
+  TPC2_CUDA(H, cudaMemcpyAsync(st.x_dev, H->u, bytes, cudaMemcpyDeviceToDevice, H->stream));
+  return TPC_OK;
+}
+
 int level_index2(const tpc2d_handle* H, int level) {
   if (!H || level < H->kc || level > H->K) return -1;
   return H->K - level;
@@ -583,64 +683,19 @@ int tpc2d_solve(tpc2d_handle* H, const double* b_dev, double* x_dev, double tol,
     if (H) H->err = "bad argument to tpc2d_solve";
     return TPC_EINVAL;
   }
-  const long long nn = H->D.lev[0].nn;
-  const size_t bytes = (size_t)nn * sizeof(double);
-  cudaStream_t s = H->stream;
-  TPC2_CUDA(H, cudaMemcpyAsync(H->b, b_dev, bytes, cudaMemcpyDeviceToDevice, s));
-  if (use_x0) {
-    TPC2_CUDA(H, cudaMemcpyAsync(H->u, x_dev, bytes, cudaMemcpyDeviceToDevice, s));
-    matvec2<double>(H, 0, H->u, H->b, H->r0, EPI_RESID, nullptr);
-  } else {
-    TPC2_CUDA(H, cudaMemsetAsync(H->u, 0, bytes, s));
-    TPC2_CUDA(H, cudaMemcpyAsync(H->r0, H->b, bytes, cudaMemcpyDeviceToDevice, s));
+  Solve2State st;
+  st.H = H;
+  TPC_TRY(solve2_begin(st, b_dev, x_dev, tol, use_x0));
+  while (!st.done) {
+    TPC2_CUDA(H, cudaEventSynchronize(H->ev));
+    TPC_TRY(solve2_step(st));
   }
-  sumsq2(H, H->r0, nn);
-  TPC2_CUDA(H, cudaMemcpyAsync(H->sumsq_host, H->sumsq, sizeof(double), cudaMemcpyDeviceToHost, s));
-  TPC2_CUDA(H, cudaStreamSynchronize(s));
-  const double r0 = std::sqrt(*H->sumsq_host);
-  if (!std::isfinite(r0)) {
-    H->err = "right-hand side or initial residual is not finite";
-    return TPC_EINVAL;
-  }
-  double rel = r0 > 0.0 ? 1.0 : 0.0, rel_prev = 0.0;
-  int it = 0, cycles = 0, status = TPC_OK;
-  const int full = H->prm.precision == TPC_MIXED ? H->prm.inner_cycles : 1;
-  H->last_cycles = 0;
-  while (rel >= tol && r0 > 0.0) {
-    if (it >= H->prm.max_iters) {
-      status = TPC_ENOTCONV;
-      break;
-    }
-    // inner cycles: the full count first, then the fewest expected to reach tol / 4 at the
-    // rate per cycle measured by the previous iteration (as the 1-D mixed solve)
-    int c = full;
-    if (full > 1 && it > 0 && cycles > 0) {
-      const double red = rel / rel_prev;
-      const double rho = std::pow(red, 1.0 / cycles), need = tol / (4.0 * rel);
-      if (red > 0.0 && red < 1.0 && rho > 0.0 && rho < 1.0 && need > 0.0 && need < 1.0) {
-        const double cc = std::ceil(std::log(need) / std::log(rho));
-        c = cc < 1.0 ? 1 : (cc > full ? full : (int)cc);
-      }
-    }
-    TPC2_CUDA(H, cudaGraphLaunch(H->iter_exec[c], s));
-    TPC2_CUDA(H, cudaMemcpyAsync(H->sumsq_host, H->sumsq, sizeof(double), cudaMemcpyDeviceToHost, s));
-    TPC2_CUDA(H, cudaStreamSynchronize(s));
-    H->last_cycles += c;
-    rel_prev = rel;
-    cycles = c;
-    rel = std::sqrt(*H->sumsq_host) / r0;
-    ++it;
-    if (!std::isfinite(rel)) {
-      H->err = "residual became non-finite";
-      status = TPC_EDIVERGED;
-      break;
-    }
-  }
-  TPC2_CUDA(H, cudaMemcpyAsync(x_dev, H->u, bytes, cudaMemcpyDeviceToDevice, s));
-  TPC2_CUDA(H, cudaStreamSynchronize(s));
-  if (iters_out) *iters_out = it;
-  if (relres_out) *relres_out = rel;
-  return status;
+  if (st.status == TPC_EINVAL) return TPC_EINVAL;  // non-finite right-hand side: x untouched
+  TPC_TRY(solve2_finish(st));
+  TPC2_CUDA(H, cudaStreamSynchronize(H->stream));
+  if (iters_out) *iters_out = st.it;
+  if (relres_out) *relres_out = st.rel;
+  return st.status;
 }
 
 int tpc2d_apply(tpc2d_handle* H, int level, const double* x_dev, double* y_dev) {
@@ -697,3 +752,83 @@ const char* tpc2d_last_error(const tpc2d_handle* H) {
 }
 
 }  // extern "C"
+
+// Polled 2-D solve with host buffers (the request server's 2-D requests): as async_begin_host
+// and async_poll of the 1-D solver, on the state machine above.
+namespace tpc {
+struct AsyncSolve2 {
+  twod::Solve2State st;
+  double* x_host = nullptr;
+  bool copying_out = false;
+  bool complete = false;
+};
+
+int async2d_begin_host(tpc2d_handle* H, const double* b_host, double* x_host, double tol,
+                       AsyncSolve2** out) {
+  using namespace twod;
+  const long long nn = H->D.lev[0].nn;
+  if (!H->hb) {
+    TPC_TRY(alloc2(H, &H->hb, (size_t)nn));
+    TPC_TRY(alloc2(H, &H->hx, (size_t)nn));
+  }
+  AsyncSolve2* a = new (std::nothrow) AsyncSolve2();
+  if (!a) return TPC_ENOMEM;
+  a->st.H = H;
+  a->x_host = x_host;
+  cudaError_t e = cudaMemcpyAsync(H->hb, b_host, (size_t)nn * sizeof(double),
+                                  cudaMemcpyHostToDevice, H->stream);
+  if (e != cudaSuccess) {
+    delete a;
+    return fail2(H, e, "cudaMemcpyAsync");
+  }
+  const int rc = solve2_begin(a->st, H->hb, H->hx, tol, 0);
+  if (rc != TPC_OK) {
+    delete a;
+    return rc;
+  }
+  *out = a;
+  return TPC_OK;
+}
+
+int async2d_poll(AsyncSolve2* a, int* done) {
+  using namespace twod;
+  tpc2d_handle* H = a->st.H;
+  *done = 0;
+  if (a->complete) {
+    *done = 1;
+    return TPC_OK;
+  }
+  const cudaError_t q = cudaEventQuery(H->ev);
+  if (q == cudaErrorNotReady) return TPC_OK;
+  if (q != cudaSuccess) return fail2(H, q, "cudaEventQuery");
+  if (a->copying_out) {
+    a->complete = true;
+    *done = 1;
+    return TPC_OK;
+  }
+  TPC_TRY(solve2_step(a->st));
+  if (a->st.done) {
+    if (a->st.status != TPC_EINVAL) {
+      TPC_TRY(solve2_finish(a->st));
+      TPC2_CUDA(H, cudaMemcpyAsync(a->x_host, H->hx, (size_t)H->D.lev[0].nn * sizeof(double),
+                                   cudaMemcpyDeviceToHost, H->stream));
+    }
+    TPC2_CUDA(H, cudaEventRecord(H->ev, H->stream));
+    a->copying_out = true;
+  }
+  return TPC_OK;
+}
+
+void async2d_result(const AsyncSolve2* a, int* status, int* iters, double* relres) {
+  *status = a->st.status;
+  *iters = a->st.it;
+  *relres = a->st.rel;
+}
+
+void async2d_free(AsyncSolve2* a) { delete a; }
+
+size_t handle2d_device_bytes(const tpc2d_handle* H) {
+  return H ? H->dev_bytes + handle_device_bytes(H->h1) : 0;
+}
+
+}  // namespace tpc

@@ -290,6 +290,7 @@ struct tpc_batch {
     bool in_flight = false;
   };
   std::vector<tpc_handle*> hs;
+  std::vector<tpc2d_handle*> hs2;        // 2-D instances, solved beside the groups
   std::vector<Group> groups;
   std::vector<int> solo;                 // instances solved with their own iteration graphs
   int product_mode = TPC_BATCH_AUTO;     // how the three-pass products are launched
@@ -669,12 +670,28 @@ int decide(SolveState& st, double ss) {
 extern "C" {
 
 int tpc_batch_create(tpc_handle* const* hs, int count, tpc_batch** out) {
+  return tpc_batch_create_2d(hs, count, nullptr, 0, out);
+}
+
+int tpc_batch_create_2d(tpc_handle* const* hs, int count, tpc2d_handle* const* hs2, int count2,
+                        tpc_batch** out) {
   using namespace tpc::batch;
-  if (!out || count < 0 || (count > 0 && !hs)) {
+  if (!out || count < 0 || (count > 0 && !hs) || count2 < 0 || (count2 > 0 && !hs2)) {
     set_host_error("bad argument to tpc_batch_create");
     return TPC_EINVAL;
   }
   *out = nullptr;
+  std::vector<tpc2d_handle*> sorted2(hs2, hs2 + count2);
+  for (tpc2d_handle* H : sorted2)
+    if (!H) {
+      set_host_error("tpc_batch_create: NULL 2-D handle");
+      return TPC_EINVAL;
+    }
+  std::sort(sorted2.begin(), sorted2.end());
+  if (std::adjacent_find(sorted2.begin(), sorted2.end()) != sorted2.end()) {
+    set_host_error("tpc_batch_create: a 2-D handle appears twice (each instance needs its own)");
+    return TPC_EINVAL;
+  }
   std::vector<tpc_handle*> sorted(hs, hs + count);
   for (tpc_handle* H : sorted)
     if (!H) {
@@ -689,6 +706,7 @@ int tpc_batch_create(tpc_handle* const* hs, int count, tpc_batch** out) {
   tpc_batch* B = new (std::nothrow) tpc_batch();
   if (!B) return TPC_ENOMEM;
   B->hs.assign(hs, hs + count);
+  B->hs2.assign(hs2, hs2 + count2);
   std::map<std::vector<long long>, std::vector<int>> keyed;
   for (int i = 0; i < count; ++i) {
     if (eligible(B->hs[i])) keyed[group_key(B->hs[i])].push_back(i);
@@ -715,12 +733,13 @@ int tpc_batch_create(tpc_handle* const* hs, int count, tpc_batch** out) {
 int tpc_batch_solve(tpc_batch* B, const double* const* b_dev, double* const* x_dev, double tol,
                     int* iters_out, double* relres_out, int* status_out) {
   using namespace tpc::batch;
-  if (!B || !(tol >= 0.0) || (!B->hs.empty() && (!b_dev || !x_dev))) {
+  const int count = B ? (int)B->hs.size() : 0;
+  const int count2 = B ? (int)B->hs2.size() : 0;
+  if (!B || !(tol >= 0.0) || (count + count2 > 0 && (!b_dev || !x_dev))) {
     set_host_error("bad argument to tpc_batch_solve");
     return TPC_EINVAL;
   }
-  const int count = (int)B->hs.size();
-  for (int i = 0; i < count; ++i)
+  for (int i = 0; i < count + count2; ++i)
     if (!b_dev[i] || !x_dev[i]) {
       set_host_error("tpc_batch_solve: NULL vector");
       return TPC_EINVAL;
@@ -735,6 +754,17 @@ int tpc_batch_solve(tpc_batch* B, const double* const* b_dev, double* const* x_d
       return rc;
     }
   }
+  // the 2-D instances: their own iteration graphs on their own streams, advanced by polling
+  std::vector<tpc::twod::Solve2State> st2(count2);
+  for (int i = 0; i < count2; ++i) {
+    st2[i].H = B->hs2[i];
+    const int rc = tpc::twod::solve2_begin(st2[i], b_dev[count + i], x_dev[count + i], tol, 0);
+    if (rc != TPC_OK) {
+      set_host_error(B->hs2[i]->err);
+      return rc;
+    }
+  }
+  int active2 = count2;
   // the grouped instances' first decisions need their initial norms on the host
   for (auto& g : B->groups)
     for (int j : g.idx) TPCB_CUDA(B, cudaEventSynchronize(B->hs[j]->ev));
@@ -742,49 +772,38 @@ int tpc_batch_solve(tpc_batch* B, const double* const* b_dev, double* const* x_d
   for (auto& g : B->groups)
     for (int j : g.idx) cyc[j] = decide(st[j], *B->hs[j]->sumsq_host);
   int active_solo = (int)B->solo.size();
+  // a group's next iteration, with every member that still iterates (none: the group is done)
+  auto launch = [&](tpc_batch::Group& g) -> int {
+    int cmax = 0;
+    for (int jj = 0; jj < g.ninst; ++jj) cmax = std::max(cmax, cyc[g.idx[jj]]);
+    if (cmax == 0) return TPC_OK;
+    for (int c = 0; c < cmax; ++c)
+      for (int jj = 0; jj < g.ninst; ++jj) {
+        const int ci = cyc[g.idx[jj]];
+        g.live_host[(size_t)c * g.ninst + jj] = (c == 0) ? (ci > 0) : (ci > c);
+      }
+    TPC_TRY(graph(B, g, cmax));
+    TPCB_CUDA(B, cudaMemcpyAsync(g.live, g.live_host, sizeof(int) * (size_t)cmax * g.ninst,
+                                 cudaMemcpyHostToDevice, g.stream));
+    TPCB_CUDA(B, cudaGraphLaunch(g.exec[cmax], g.stream));
+    TPCB_CUDA(B, cudaMemcpyAsync(g.out_host, g.out, sizeof(double) * g.ninst,
+                                 cudaMemcpyDeviceToHost, g.stream));
+    TPCB_CUDA(B, cudaMemcpyAsync(g.err_host, g.err, sizeof(int), cudaMemcpyDeviceToHost, g.stream));
+    TPCB_CUDA(B, cudaEventRecord(g.ev, g.stream));
+    g.in_flight = true;
+    return TPC_OK;
+  };
+  for (auto& g : B->groups) TPC_TRY(launch(g));
+  // every group, lone instance and 2-D instance advances as soon as its own latest read-back
+  // has arrived
   for (;;) {
     bool any = false;
     for (auto& g : B->groups) {
-      int cmax = 0;
-      for (int jj = 0; jj < g.ninst; ++jj) cmax = std::max(cmax, cyc[g.idx[jj]]);
-      if (cmax == 0) continue;
-      any = true;
-      for (int c = 0; c < cmax; ++c)
-        for (int jj = 0; jj < g.ninst; ++jj) {
-          const int ci = cyc[g.idx[jj]];
-          g.live_host[(size_t)c * g.ninst + jj] = (c == 0) ? (ci > 0) : (ci > c);
-        }
-      TPC_TRY(graph(B, g, cmax));
-      TPCB_CUDA(B, cudaMemcpyAsync(g.live, g.live_host, sizeof(int) * (size_t)cmax * g.ninst,
-                                   cudaMemcpyHostToDevice, g.stream));
-      TPCB_CUDA(B, cudaGraphLaunch(g.exec[cmax], g.stream));
-      TPCB_CUDA(B, cudaMemcpyAsync(g.out_host, g.out, sizeof(double) * g.ninst,
-                                   cudaMemcpyDeviceToHost, g.stream));
-      TPCB_CUDA(B, cudaMemcpyAsync(g.err_host, g.err, sizeof(int), cudaMemcpyDeviceToHost, g.stream));
-      TPCB_CUDA(B, cudaEventRecord(g.ev, g.stream));
-      g.in_flight = true;
-    }
-    // instances outside the groups: their own iteration graphs, advanced while groups run
-    if (active_solo > 0) {
-      any = true;
-      for (int i : B->solo) {
-        if (st[i].done) continue;
-        if (cudaEventQuery(B->hs[i]->ev) == cudaErrorNotReady) continue;
-        const int rc = solve_step(st[i]);
-        if (rc != TPC_OK) {
-          set_host_error(B->hs[i]->err);
-          return rc;
-        }
-        if (st[i].done) {
-          TPC_TRY(solve_finish(st[i]));
-          --active_solo;
-        }
-      }
-    }
-    if (!any) break;
-    for (auto& g : B->groups) {
       if (!g.in_flight) continue;
-      TPCB_CUDA(B, cudaEventSynchronize(g.ev));
+      any = true;
+      const cudaError_t q = cudaEventQuery(g.ev);
+      if (q == cudaErrorNotReady) continue;
+      if (q != cudaSuccess) return bfail(B, q, "cudaEventQuery");
       g.in_flight = false;
       if (*g.err_host) {
         B->err = "a device-side wait of a batched product gave up (grid barrier not reached)";
@@ -798,9 +817,57 @@ int tpc_batch_solve(tpc_batch* B, const double* const* b_dev, double* const* x_d
         cyc[j] = decide(st[j], g.out_host[jj]);
         B->hs[j]->launches += 1;
       }
+      TPC_TRY(launch(g));
     }
+    // instances outside the groups: their own iteration graphs
+    if (active_solo > 0) {
+      any = true;
+      for (int i : B->solo) {
+        if (st[i].done) continue;
+        const cudaError_t q = cudaEventQuery(B->hs[i]->ev);
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess) return bfail(B, q, "cudaEventQuery");
+        const int rc = solve_step(st[i]);
+        if (rc != TPC_OK) {
+          set_host_error(B->hs[i]->err);
+          return rc;
+        }
+        if (st[i].done) {
+          TPC_TRY(solve_finish(st[i]));
+          --active_solo;
+        }
+      }
+    }
+    if (active2 > 0) {
+      any = true;
+      for (int i = 0; i < count2; ++i) {
+        if (st2[i].done) continue;
+        tpc2d_handle* H2 = B->hs2[i];
+        const cudaError_t q = cudaEventQuery(H2->ev);
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess) return bfail(B, q, "cudaEventQuery");
+        const int rc = tpc::twod::solve2_step(st2[i]);
+        if (rc != TPC_OK) {
+          set_host_error(H2->err);
+          return rc;
+        }
+        if (st2[i].done) {
+          if (st2[i].status != TPC_EINVAL) TPC_TRY(tpc::twod::solve2_finish(st2[i]));
+          --active2;
+        }
+      }
+    }
+    if (!any) break;
   }
   int worst = TPC_OK;
+  for (int i = 0; i < count2; ++i) {
+    TPCB_CUDA(B, cudaStreamSynchronize(B->hs2[i]->stream));
+    const int j = count + i;
+    if (iters_out) iters_out[j] = st2[i].it;
+    if (relres_out) relres_out[j] = st2[i].rel;
+    if (status_out) status_out[j] = st2[i].status;
+    if (st2[i].status < worst || (worst == TPC_OK && st2[i].status != TPC_OK)) worst = st2[i].status;
+  }
   for (int i = 0; i < count; ++i) {
     tpc_handle* H = B->hs[i];
     if (std::find(B->solo.begin(), B->solo.end(), i) == B->solo.end()) TPC_TRY(solve_finish(st[i]));

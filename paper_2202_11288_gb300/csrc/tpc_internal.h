@@ -56,5 +56,13 @@ int async_poll(AsyncSolve* a, int* done);
 void async_result(const AsyncSolve* a, int* status, int* iters, double* relres);
 void async_free(AsyncSolve* a);
 size_t handle_device_bytes(const tpc_handle* H);
+// The same for 2-D handles (tpc_2d.cuh).
+struct AsyncSolve2;
+int async2d_begin_host(tpc2d_handle* H, const double* b_host, double* x_host, double tol,
+                       AsyncSolve2** out);
+int async2d_poll(AsyncSolve2* a, int* done);
+void async2d_result(const AsyncSolve2* a, int* status, int* iters, double* relres);
+void async2d_free(AsyncSolve2* a);
+size_t handle2d_device_bytes(const tpc2d_handle* H);
 
 }  // namespace tpc

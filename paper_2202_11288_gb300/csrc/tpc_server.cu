@@ -2,8 +2,9 @@
 //
 // A worker thread owns every handle. Requests (problem description + host buffers) are queued
 // by tpc_server_submit; the worker admits them while a slot (max_inflight) and device memory
-// (the HBM budget) are free, keeps level hierarchies resident keyed by the problem (variant,
-// kernel, horizon, mesh size, precision) and reuses an idle one when the key repeats (a request whose
+// (the HBM budget) are free, keeps level hierarchies resident keyed by the problem (dimension,
+// variant, kernel, transfer, horizon, mesh size, precision) and reuses an idle one when the key
+// repeats (a request whose
 // key's hierarchies are all busy waits for one, unless the key may have another; later
 // requests of other keys go ahead), evicting idle hierarchies least-recently-used first when
 // the budget requires. Every admitted solve runs on
@@ -40,9 +41,10 @@ struct Request {
 };
 
 struct Entry {
-  int variant = 0, precision = 0, kernel = 0;
+  int dim = 1, variant = 0, precision = 0, kernel = 0, transfer = 0;
   double delta = 0.0, h = 0.0, kernel_a = 0.0;
-  tpc_handle* H = nullptr;
+  tpc_handle* H = nullptr;        // 1-D requests
+  tpc2d_handle* H2 = nullptr;     // 2-D requests
   size_t bytes = 0;
   bool busy = false;
   unsigned long long last_use = 0;
@@ -52,6 +54,7 @@ struct Active {
   Entry* entry = nullptr;
   Request req;
   tpc::AsyncSolve* a = nullptr;
+  tpc::AsyncSolve2* a2 = nullptr;
   Clock::time_point t_start;
 };
 
@@ -75,24 +78,46 @@ struct tpc_server {
   size_t used_bytes = 0;
   unsigned long long tick = 0;
   std::string worker_err;
+  tpc_server_stats stats{};              // guarded by mu
+  Clock::time_point t_stats, t_last;     // start of the statistics, last worker update
 };
 
 namespace {
 
+int req_dim(const tpc_request& r) { return r.dim == 2 ? 2 : 1; }
+
 bool same_key(const Entry& e, const tpc_request& r, int precision) {
-  return e.variant == r.variant && e.precision == precision && e.delta == r.delta && e.h == r.h &&
-         e.kernel == r.kernel && e.kernel_a == r.kernel_a;
+  return e.dim == req_dim(r) && e.variant == r.variant && e.precision == precision &&
+         e.delta == r.delta && e.h == r.h && e.kernel == r.kernel && e.kernel_a == r.kernel_a &&
+         e.transfer == r.transfer;
 }
 
-// Device bytes a hierarchy of this key needs: the size of a resident one with the same mesh
-// size, variant and precision if there is one, else an estimate from the level sizes (spectra,
-// twiddles, vectors over all levels: about 220 bytes per unknown in FP64, 320 with the FP32
-// copy, plus the fixed tables).
+void destroy_entry(Entry* e) {
+  if (e->H) tpc_destroy(e->H);
+  if (e->H2) tpc2d_destroy(e->H2);
+  delete e;
+}
+
+size_t entry_bytes(const Entry* e) {
+  return e->H2 ? tpc::handle2d_device_bytes(e->H2) : tpc::handle_device_bytes(e->H);
+}
+
+// Device bytes a hierarchy of this key needs: the size of a resident one with the same
+// dimension, mesh size, variant and precision if there is one, else an estimate from the level
+// sizes (1-D: spectra, twiddles, vectors over all levels, about 220 bytes per unknown in FP64,
+// 320 with the FP32 copy; 2-D: the level vectors, about 160 and 240 bytes per unknown), plus
+// the fixed tables.
 size_t estimate_bytes(const tpc_server* S, const tpc_request& r) {
+  const int dim = req_dim(r);
   for (const Entry* e : S->cache)
-    if (e->h == r.h && e->precision == S->cfg.precision && e->variant == r.variant) return e->bytes;
-  const double n = 2.0 / r.h;
-  return (size_t)(n * (S->cfg.precision == TPC_MIXED ? 320.0 : 220.0)) + (size_t(256) << 10);
+    if (e->dim == dim && e->h == r.h && e->precision == S->cfg.precision &&
+        e->variant == r.variant)
+      return e->bytes;
+  const double n1 = 2.0 / r.h;
+  const bool mixed = S->cfg.precision == TPC_MIXED;
+  if (dim == 2)
+    return (size_t)(n1 * n1 * (mixed ? 240.0 : 160.0) + n1 * 320.0) + (size_t(1) << 20);
+  return (size_t)(n1 * (mixed ? 320.0 : 220.0)) + (size_t(256) << 10);
 }
 
 void finish_request(tpc_server* S, Active& act, int status, int iters, double relres) {
@@ -141,9 +166,12 @@ bool admit(tpc_server* S, Request& req) {
           lru = (int)i;
       if (lru < 0) break;
       S->used_bytes -= S->cache[lru]->bytes;
-      tpc_destroy(S->cache[lru]->H);
-      delete S->cache[lru];
+      destroy_entry(S->cache[lru]);
       S->cache.erase(S->cache.begin() + lru);
+      {
+        std::lock_guard<std::mutex> lk(S->mu);
+        ++S->stats.evictions;
+      }
     }
     if (S->used_bytes + need > S->cfg.hbm_budget_bytes) {
       if (!S->active.empty()) return false;  // wait for memory to free up
@@ -154,40 +182,58 @@ bool admit(tpc_server* S, Request& req) {
     p.variant = req.r.variant;
     p.kernel = req.r.kernel;
     p.kernel_a = req.r.kernel_a;
+    p.transfer = req.r.transfer;
     tpc_handle* H = nullptr;
-    const int rc = tpc_setup(&p, req.r.delta, req.r.h, 0, nullptr, &H);
+    tpc2d_handle* H2 = nullptr;
+    const int rc = req_dim(req.r) == 2 ? tpc2d_setup(&p, req.r.delta, req.r.h, nullptr, &H2)
+                                       : tpc_setup(&p, req.r.delta, req.r.h, 0, nullptr, &H);
     if (rc != TPC_OK) {
       finish_request(S, act, rc, 0, 0.0);
       return true;
     }
     ent = new Entry();
+    ent->dim = req_dim(req.r);
     ent->variant = req.r.variant;
     ent->precision = prec;
     ent->delta = req.r.delta;
     ent->h = req.r.h;
     ent->kernel = req.r.kernel;
     ent->kernel_a = req.r.kernel_a;
+    ent->transfer = req.r.transfer;
     ent->H = H;
-    ent->bytes = tpc::handle_device_bytes(H);
+    ent->H2 = H2;
+    ent->bytes = entry_bytes(ent);
     S->used_bytes += ent->bytes;
     S->cache.push_back(ent);
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      ++S->stats.setups;
+    }
   }
   act.entry = ent;
-  const long long n = tpc_level_size(ent->H, tpc_finest_level(ent->H));
+  const long long n = ent->H2 ? tpc2d_level_size(ent->H2, tpc2d_finest_level(ent->H2))
+                              : tpc_level_size(ent->H, tpc_finest_level(ent->H));
   if (req.r.n != n) {
     finish_request(S, act, TPC_EINVAL, 0, 0.0);
     return true;
   }
-  const int rc = tpc::async_begin_host(ent->H, req.r.b_host, req.r.x_host, req.r.tol, &act.a);
+  const int rc = ent->H2
+                     ? tpc::async2d_begin_host(ent->H2, req.r.b_host, req.r.x_host, req.r.tol, &act.a2)
+                     : tpc::async_begin_host(ent->H, req.r.b_host, req.r.x_host, req.r.tol, &act.a);
   if (rc != TPC_OK) {
     finish_request(S, act, rc, 0, 0.0);
     return true;
   }
   // the staging buffers of the first host solve are allocated then: count them
-  S->used_bytes += tpc::handle_device_bytes(ent->H) - ent->bytes;
-  ent->bytes = tpc::handle_device_bytes(ent->H);
+  const size_t now_bytes = entry_bytes(ent);
+  S->used_bytes += now_bytes - ent->bytes;
+  ent->bytes = now_bytes;
   ent->busy = true;
   S->active.push_back(act);
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    ++S->stats.admitted;
+  }
   return true;
 }
 
@@ -197,6 +243,16 @@ void worker_main(tpc_server* S) {
   for (;;) {
     {
       std::unique_lock<std::mutex> lk(S->mu);
+      // occupancy statistics: the time since the last update counted with the solves that
+      // were on the GPU during it
+      const Clock::time_point now = Clock::now();
+      const double dt = std::chrono::duration<double>(now - S->t_last).count();
+      S->t_last = now;
+      const int na = (int)S->active.size();
+      if (na > 0) S->stats.busy_s += dt;
+      S->stats.inflight_s += dt * na;
+      S->stats.max_inflight_seen = std::max(S->stats.max_inflight_seen, na);
+      S->stats.resident_bytes = S->used_bytes;
       if (queue.empty() && S->active.empty() && S->pending.empty() && !S->stop)
         S->cv.wait_for(lk, std::chrono::milliseconds(1));
       if (S->stop && S->pending.empty() && queue.empty() && S->active.empty()) break;
@@ -218,12 +274,16 @@ void worker_main(tpc_server* S) {
     for (size_t i = 0; i < S->active.size();) {
       Active& act = S->active[i];
       int fin = 0;
-      const int rc = tpc::async_poll(act.a, &fin);
+      const int rc = act.a2 ? tpc::async2d_poll(act.a2, &fin) : tpc::async_poll(act.a, &fin);
       if (rc != TPC_OK || fin) {
         int status = rc, iters = 0;
         double rel = 0.0;
-        if (rc == TPC_OK) tpc::async_result(act.a, &status, &iters, &rel);
-        tpc::async_free(act.a);
+        if (rc == TPC_OK) {
+          if (act.a2) tpc::async2d_result(act.a2, &status, &iters, &rel);
+          else tpc::async_result(act.a, &status, &iters, &rel);
+        }
+        if (act.a2) tpc::async2d_free(act.a2);
+        else tpc::async_free(act.a);
         act.entry->busy = false;
         act.entry->last_use = ++S->tick;
         finish_request(S, act, status, iters, rel);
@@ -235,10 +295,7 @@ void worker_main(tpc_server* S) {
     }
     if (!progressed && !S->active.empty()) std::this_thread::yield();
   }
-  for (Entry* e : S->cache) {
-    tpc_destroy(e->H);
-    delete e;
-  }
+  for (Entry* e : S->cache) destroy_entry(e);
   S->cache.clear();
 }
 
@@ -271,6 +328,7 @@ int tpc_server_create(const tpc_server_config* cfg, const tpc_params* p, tpc_ser
   else
     tpc_default_params(&S->prm);
   S->prm.precision = cfg->precision;
+  S->t_stats = S->t_last = Clock::now();
   if (cudaGetDevice(&S->device) != cudaSuccess) {
     (void)cudaGetLastError();
     delete S;
@@ -313,6 +371,21 @@ int tpc_server_poll(tpc_server* S, tpc_server_result* out, int cap, int wait_ms)
 }
 
 long long tpc_server_outstanding(tpc_server* S) { return S ? S->outstanding.load() : 0; }
+
+int tpc_server_get_stats(tpc_server* S, tpc_server_stats* out, int reset) {
+  if (!S || !out) return TPC_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  const Clock::time_point now = Clock::now();
+  *out = S->stats;
+  out->elapsed_s = std::chrono::duration<double>(now - S->t_stats).count();
+  if (reset) {
+    const size_t resident = S->stats.resident_bytes;
+    S->stats = tpc_server_stats{};
+    S->stats.resident_bytes = resident;
+    S->t_stats = S->t_last = now;
+  }
+  return TPC_OK;
+}
 
 void tpc_server_destroy(tpc_server* S) {
   if (!S) return;

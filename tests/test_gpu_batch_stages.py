@@ -125,3 +125,35 @@ def test_grid_wait_gives_up_and_reports():
     assert gave_up == 1 and passed == 0
     x = torch.ones(1000, dtype=torch.float64, device="cuda")
     assert float((x * 2).sum()) == 2000.0
+
+
+def test_batch_with_2d_instances_equals_lone_solves():
+    """2-D instances beside the groups and the lone 1-D instances: every result is bitwise the
+    lone tpc2d_solve / tpc_solve result."""
+    specs = [(12, 0.05, 0, 0, 0.0), (12, 0.2, 0, 0, 0.0), (11, 0.1, 0, 1, 0.3)]
+    solvers = _solvers(specs)
+    twod = [tpc.Solver2D(d, 2.0 ** -K, variant=v, precision=tpc.TPC_MIXED)
+            for K, d, v in [(6, 0.1, tpc.TPC_SPD), (5, 0.2, tpc.TPC_NONSYM), (7, 0.15, tpc.TPC_SPD)]]
+    try:
+        bs = [torch.tensor(uniform_pm1(S.n, 60 + i), device="cuda") for i, S in enumerate(solvers)]
+        bs += [torch.tensor(uniform_pm1(S.nn, 70 + i), device="cuda") for i, S in enumerate(twod)]
+        lone = []
+        for S, b in zip(solvers + twod, bs):
+            x = torch.zeros_like(b)
+            rc, it, rel = S.solve(b, x, tol=1e-10)
+            assert rc == tpc.TPC_OK and rel < 1e-10
+            lone.append((it, rel, x))
+        B = tpc.Batch([S.handle for S in solvers], [S.handle for S in twod])
+        try:
+            assert B.groups() == 1 and B.grouped_instances() == 2
+            xs = [torch.full_like(b, float("nan")) for b in bs]
+            rc, its, rels, sts = B.solve(bs, xs, tol=1e-10)
+            assert rc == tpc.TPC_OK, (rc, sts)
+            for i, (it, rel, x) in enumerate(lone):
+                assert its[i] == it and rels[i] == rel, (i, its[i], it)
+                assert torch.equal(xs[i], x), i
+        finally:
+            B.close()
+    finally:
+        for S in solvers + twod:
+            S.close()

@@ -76,3 +76,53 @@ def test_server_rejects_a_problem_larger_than_its_budget():
         assert len(res) == 1 and res[0]["status"] == tpc.TPC_ENOMEM
     finally:
         srv.close()
+
+
+def test_server_mix_of_2d_fractional_and_transfers_equals_alone():
+    """2-D requests, a fractional kernel under the geometric transfer and two requests that differ
+    only in their transfer: each result equals its lone solve bit for bit, and the occupancy
+    statistics are consistent."""
+    # (dim, variant, delta, K, kernel, a, transfer)
+    keys = [(2, tpc.TPC_SPD, 0.1, 6, 0, 0.0, tpc.TPC_TRANSFER_PAPER),
+            (2, tpc.TPC_NONSYM, 0.2, 5, 0, 0.0, tpc.TPC_TRANSFER_PAPER),
+            (1, tpc.TPC_SPD, 0.1, 11, 1, 0.3, tpc.TPC_TRANSFER_GEOMETRIC),
+            (1, tpc.TPC_SPD, 0.08, 10, 0, 0.0, tpc.TPC_TRANSFER_PAPER),
+            (1, tpc.TPC_SPD, 0.08, 10, 0, 0.0, tpc.TPC_TRANSFER_GEOMETRIC)]
+    reqs = []
+    for i in range(15):
+        dim, v, d, K, kk, a, tr = keys[i % len(keys)]
+        n1 = (1 << (K + 1)) - 1
+        n = n1 * n1 if dim == 2 else n1
+        b = torch.tensor(uniform_pm1(n, 900 + i)).pin_memory()
+        x = torch.zeros(n, dtype=torch.float64).pin_memory()
+        reqs.append((keys[i % len(keys)], b, x))
+    srv = tpc.Server(max_inflight=6, precision=tpc.TPC_MIXED)
+    try:
+        srv.stats(reset=True)
+        tickets = {srv.submit(v, d, 2.0 ** -K, b, x, 1e-10, kk, a, dim=dim, transfer=tr): i
+                   for i, ((dim, v, d, K, kk, a, tr), b, x) in enumerate(reqs)}
+        res = _wait_all(srv, len(reqs))
+        assert len(res) == len(reqs)
+        st = srv.stats()
+    finally:
+        srv.close()
+    assert st["admitted"] == len(reqs) and st["setups"] == len(keys) and st["evictions"] == 0
+    assert 0.0 < st["busy_s"] <= st["elapsed_s"]
+    assert st["inflight_s"] >= st["busy_s"] and 1 <= st["max_inflight_seen"] <= 6
+    for r in res:
+        i = tickets[r["ticket"]]
+        (dim, v, d, K, kk, a, tr), b, x = reqs[i]
+        assert r["status"] == tpc.TPC_OK and r["relres"] < 1e-10, (i, r)
+        bd = b.cuda()
+        xd = torch.zeros_like(bd)
+        if dim == 2:
+            S = tpc.Solver2D(d, 2.0 ** -K, variant=v, precision=tpc.TPC_MIXED)
+        else:
+            S = tpc.Solver(d, 2.0 ** -K, variant=v, kernel=kk, kernel_a=a, transfer=tr,
+                           precision=tpc.TPC_MIXED)
+        try:
+            rc, it, rel = S.solve(bd, xd, tol=1e-10)
+        finally:
+            S.close()
+        assert it == r["iters"] and rel == r["relres"], (i, it, r)
+        assert torch.equal(xd.cpu(), x), i
