@@ -97,7 +97,19 @@ typedef struct tpc_params {
                          the outer FP64 residual b - A u is formed from prefix sums of u, one
                          term per run of equal generator values, instead of two FFTs; 0: the
                          FFT product always. The V-cycles are not affected                 */
+  int outer;          /* TPC_OUTER_VCYCLE (default): the outer iteration of section 5,
+                         u <- u + B (b - A u) with B the V-cycle (TPC_MIXED: inner_cycles FP32
+                         V-cycles of it per FP64 residual). TPC_OUTER_FGMRES (not in the
+                         paper): each outer iteration is one restart cycle of right-
+                         preconditioned flexible GMRES of at most inner_cycles steps, one
+                         V-cycle per step as the preconditioner (FP32 vectors, V-cycles and
+                         products in TPC_MIXED, FP64 dot products and least squares; all FP64
+                         in TPC_FP64); the FP64 residual is formed anew after each cycle.
+                         It converges where the stationary iteration is slow or diverges
+                         (fractional kernels) and needs fewer V-cycles on the constant kernel */
 } tpc_params;
+
+enum { TPC_OUTER_VCYCLE = 0, TPC_OUTER_FGMRES = 1 };
 
 typedef struct tpc_handle tpc_handle;
 typedef struct tpc2d_handle tpc2d_handle;  /* the 2-D system: see tpc2d_setup */

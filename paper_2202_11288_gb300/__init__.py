@@ -25,6 +25,7 @@ TPC_BATCH_AUTO, TPC_BATCH_COOPERATIVE, TPC_BATCH_THREE_PASS = 0, 1, 2
 TPC_SPD, TPC_NONSYM, TPC_WEAKLY = 0, 1, 2
 TPC_FP64, TPC_MIXED = 0, 1
 TPC_TRANSFER_PAPER, TPC_TRANSFER_GEOMETRIC = 0, 1
+TPC_OUTER_VCYCLE, TPC_OUTER_FGMRES = 0, 1
 
 EXPORTED = ["tpc_default_params", "tpc_setup", "tpc_solve", "tpc_solve_batch", "tpc_solve_host",
             "tpc_batch_create", "tpc_batch_create_2d", "tpc_batch_solve", "tpc_batch_groups", "tpc_batch_set_product_mode",
@@ -56,7 +57,8 @@ class TpcParams(ctypes.Structure):
                 ("coarsest_level", ctypes.c_int), ("precision", ctypes.c_int),
                 ("max_iters", ctypes.c_int), ("inner_cycles", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("poison", ctypes.c_int),
-                ("transfer", ctypes.c_int), ("box_residual", ctypes.c_int)]
+                ("transfer", ctypes.c_int), ("box_residual", ctypes.c_int),
+                ("outer", ctypes.c_int)]
 
 
 class TpcServerConfig(ctypes.Structure):

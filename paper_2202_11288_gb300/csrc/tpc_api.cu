@@ -19,6 +19,7 @@
 #include "tpc_kernels.cuh"
 #include "tpc_f32.cuh"
 #include "tpc_box.cuh"
+#include "tpc_krylov.cuh"
 
 namespace tpc {
 void set_host_error(const std::string& s);
@@ -117,6 +118,15 @@ struct tpc_handle {
   // the arguments with the work arrays filled in (operand, right-hand side, result per call)
   bool box_on = false;
   box::BoxArgs box_args{};
+  // TPC_OUTER_FGMRES: basis vectors v_0..v_S and z_0..z_{S-1} (S = inner_cycles; FP32 in
+  // TPC_MIXED, FP64 else; kld apart), the cycle's scalars and the dot products' partial sums
+  float* kv32 = nullptr;
+  float* kz32 = nullptr;
+  double* kv64 = nullptr;
+  double* kz64 = nullptr;
+  long long kld = 0;
+  krylov::KState* ks = nullptr;
+  double* kpart = nullptr;
   std::string err;
   std::vector<void*> dev_allocs;
   size_t dev_bytes = 0;               // device memory held by the handle
@@ -469,14 +479,51 @@ void enqueue_sumsq(tpc_handle* H, const double* r, long long n) {
   k_sumsq_final<<<1, 32, 0, H->stream>>>(H->sumsq_part, NORM_BLOCKS, H->sumsq);
 }
 
+// One restart cycle of flexible GMRES with `steps` steps (tpc_krylov.cuh) on the FP64
+// residual H->r0 (norm in H->sumsq), in the precision of G; u += Z y.
+template <typename T>
+void enqueue_fgmres_cycle(tpc_handle* H, Hier<T>& G, T* V, T* Z, int steps) {
+  using namespace krylov;
+  const long long n = H->d.lev[0].n;
+  const long long ld = H->kld;
+  const int g = grid_for(n);
+  cudaStream_t s = H->stream;
+  k_kry_start<T><<<g, NTHREADS, 0, s>>>(H->r0, V, n, H->sumsq, H->ks);
+  H->launches += 1;
+  for (int j = 0; j < steps; ++j) {
+    T* vj = V + (size_t)j * ld;
+    T* w = V + (size_t)(j + 1) * ld;
+    T* zj = Z + (size_t)j * ld;
+    const T* ec = enqueue_vcycle<T>(H, G, 0, vj, nullptr);
+    k_copy<T><<<g, NTHREADS, 0, s>>>(ec, zj, n);
+    matvec<T>(H, G, 0, zj, nullptr, w, EPI_APPLY, false);
+    for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+      k_kry_dot_partial<T><<<dim3(KNB, j + 1), 256, 0, s>>>(V, ld, w, n, H->kpart);
+      k_kry_dot_final<<<j + 1, 32, 0, s>>>(H->kpart, KNB, H->ks, j, pass);
+      k_kry_axpy<T><<<g, NTHREADS, 0, s>>>(w, V, ld, j + 1, H->ks, n);
+    }
+    k_kry_sumsq_partial<T><<<KNB, 256, 0, s>>>(w, n, H->kpart);
+    k_kry_rotate<<<1, 32, 0, s>>>(H->kpart, KNB, H->ks, j);
+    k_kry_scale<T><<<g, NTHREADS, 0, s>>>(w, n, H->ks);
+    H->launches += 11;
+  }
+  k_kry_solve<<<1, 32, 0, s>>>(H->ks, steps);
+  k_kry_update<T><<<g, NTHREADS, 0, s>>>(H->u, Z, ld, steps, H->ks, n);
+  H->launches += 2;
+}
+
 // One outer iteration.
+//   FGMRES: one restart cycle of `cycles` steps (above); r = b - A u; ||r||^2.
 //   FP64:  u += B_K r; r = b - A u; ||r||^2.
 //   mixed: f = s r in FP32 (s = sqrt(n) / ||r||); `cycles` FP32 iterations
 //          e <- e + B_K (f - A e) from e = 0; u += e / s; then the FP64 residual and norm.
 void enqueue_iteration(tpc_handle* H, int cycles) {
   const long long n = H->d.lev[0].n;
   const int g = grid_for(n);
-  if (H->prm.precision == TPC_MIXED) {
+  if (H->prm.outer == TPC_OUTER_FGMRES) {
+    if (H->prm.precision == TPC_MIXED) enqueue_fgmres_cycle<float>(H, H->s, H->kv32, H->kz32, cycles);
+    else enqueue_fgmres_cycle<double>(H, H->d, H->kv64, H->kz64, cycles);
+  } else if (H->prm.precision == TPC_MIXED) {
     Hier<float>& S = H->s;
     k_to_f32_scaled<<<g, NTHREADS, 0, H->stream>>>(H->r0, S.f[0], n, H->sumsq);
     H->launches += 1;
@@ -501,7 +548,8 @@ void enqueue_iteration(tpc_handle* H, int cycles) {
 }
 
 int full_cycles(const tpc_handle* H) {
-  return H->prm.precision == TPC_MIXED ? H->prm.inner_cycles : 1;
+  return (H->prm.precision == TPC_MIXED || H->prm.outer == TPC_OUTER_FGMRES) ? H->prm.inner_cycles
+                                                                               : 1;
 }
 
 // Captures and instantiates the iteration graph with `cycles` inner cycles unless it exists.
@@ -918,6 +966,19 @@ int setup_device(tpc_handle* H) {
     TPC_TRY(dalloc(H, &H->res32, nK));
     TPC_TRY(dalloc(H, &H->acc32, nK));
   }
+  if (H->prm.outer == TPC_OUTER_FGMRES) {
+    const int S = H->prm.inner_cycles;
+    H->kld = (nK + 63) / 64 * 64;
+    if (mixed) {
+      TPC_TRY(dalloc(H, &H->kv32, (size_t)(S + 1) * H->kld));
+      TPC_TRY(dalloc(H, &H->kz32, (size_t)S * H->kld));
+    } else {
+      TPC_TRY(dalloc(H, &H->kv64, (size_t)(S + 1) * H->kld));
+      TPC_TRY(dalloc(H, &H->kz64, (size_t)S * H->kld));
+    }
+    TPC_TRY(dalloc(H, &H->ks, 1));
+    TPC_TRY(dalloc(H, &H->kpart, (size_t)(krylov::MAXS + 1) * krylov::KNB));
+  }
   TPC_TRY(dalloc(H, &H->sumsq_part, NORM_BLOCKS));
   TPC_TRY(dalloc(H, &H->sumsq, 1));
   TPC_CUDA(H, cudaMallocHost(&H->sumsq_host, sizeof(double)));
@@ -969,10 +1030,11 @@ struct SolveState {
 // fewest that reach tol / 4 if the residual keeps falling at the rate per cycle observed in
 // the previous iteration (the FP64 residuals measure it; a rate slowed by FP32 rounding only
 // asks for more cycles). Fewer cycles in the last iteration save whole V-cycles; a miss costs
-// one more iteration. FP64 solves run one V-cycle per iteration.
+// one more iteration. FP64 solves of the stationary iteration run one V-cycle per iteration;
+// FGMRES restart cycles (either precision) take their step counts by the same rule.
 int next_cycles(const SolveState& st) {
   const int full = full_cycles(st.H);
-  if (st.H->prm.precision != TPC_MIXED || st.it == 0 || st.cycles < 1) return full;
+  if (full <= 1 || st.it == 0 || st.cycles < 1) return full;
   const double red = st.rel / st.rel_prev;
   if (!(red > 0.0 && red < 1.0)) return full;
   const double rho = std::pow(red, 1.0 / st.cycles);
@@ -1270,7 +1332,8 @@ int tpc_setup(const tpc_params* p, double delta, double h, int levels, void* cud
     set_host_error("precision must be TPC_FP64 or TPC_MIXED");
     return TPC_EINVAL;
   }
-  if (p->precision == TPC_MIXED && (p->inner_cycles < 1 || p->inner_cycles > 32)) {
+  if ((p->precision == TPC_MIXED || p->outer == TPC_OUTER_FGMRES) &&
+      (p->inner_cycles < 1 || p->inner_cycles > 32)) {
     set_host_error("inner_cycles must be in 1..32");
     return TPC_EINVAL;
   }

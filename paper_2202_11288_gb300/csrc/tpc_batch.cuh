@@ -340,7 +340,9 @@ int upload_vec(tpc_batch* B, P* dst, const std::vector<P>& src, cudaStream_t s) 
 // Whether an instance can run stage-batched (mixed precision, V(1,1), single-block bottom,
 // prefix-sum residual, levels of the general FP32 kernels), and its group key.
 bool eligible(const tpc_handle* H) {
-  if (H->prm.precision != TPC_MIXED || H->prm.m1 != 1 || H->prm.m2 != 1 || !H->box_on) return false;
+  if (H->prm.precision != TPC_MIXED || H->prm.outer != TPC_OUTER_VCYCLE || H->prm.m1 != 1 ||
+      H->prm.m2 != 1 || !H->box_on)
+    return false;
   const Hier<float>& S = H->s;
   if (!S.bottom || S.bottom_li < 1) return false;
   for (int li = 0; li < S.bottom_li; ++li) {

@@ -657,6 +657,10 @@ int build_host_hierarchy(const tpc_params& p, double delta, double h, int levels
     err = "box_residual must be 0 or 1";
     return TPC_EINVAL;
   }
+  if (p.outer != TPC_OUTER_VCYCLE && p.outer != TPC_OUTER_FGMRES) {
+    err = "outer must be TPC_OUTER_VCYCLE or TPC_OUTER_FGMRES";
+    return TPC_EINVAL;
+  }
   if (!std::isfinite(p.shift)) {
     err = "shift must be finite";
     return TPC_EINVAL;
@@ -799,6 +803,7 @@ void tpc_default_params(tpc_params* p) {
   p->poison = 0;
   p->transfer = TPC_TRANSFER_PAPER;
   p->box_residual = 1;
+  p->outer = TPC_OUTER_VCYCLE;
 }
 
 int tpc_host_hierarchy(const tpc_params* p, double delta, double h, int levels,
