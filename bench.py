@@ -79,8 +79,9 @@ KERNEL_SOURCES = ("paper_2202_11288_gb300/csrc/tpc_kernels.cuh",
                   "paper_2202_11288_gb300/csrc/tpc_fft.cuh",
                   "paper_2202_11288_gb300/csrc/tpc_f32.cuh")
 # per launch, forward pass / contiguous-block kernel / inverse pass (k32_fwd<11, 0>,
-# k32_mid<12, 0>, k32_inv<11, 1> at m = 2^23, cold cache)
-TRAFFIC = {"digest": "f3c22b6c2c57f0d7", "K": 22, "f32": (53.5e6, 155.4e6, 116.2e6), "f64_mid": None}
+# k32_mid<12, 0>, k32_inv<11, 1> at m = 2^23, cold cache), and the FP64 contiguous-block kernel
+# k_mid_pair<double, 0, 0> of the same level
+TRAFFIC = {"digest": "e7c75b60beaa7384", "K": 22, "f32": (50.29e6, 152.64e6, 112.89e6), "f64_mid": 353.50e6}
 
 
 def kernel_digest():
@@ -131,7 +132,7 @@ def parse():
                     help="profiling case: set up, then 3 finest-level products, nothing timed")
     ap.add_argument("--profile-f32", action="store_true",
                     help="profiling case: mixed-precision setup, then 3 FP32 finest-level products")
-    ap.add_argument("--profile-solve", choices=["fp64", "mixed"], default=None,
+    ap.add_argument("--profile-solve", choices=["fp64", "mixed", "fgmres"], default=None,
                     help="profiling case: set up, then one solve, nothing timed")
     ap.add_argument("--profile-twod", action="store_true",
                     help="profiling case: 2-D mixed set-up (n = 4095^2), then one solve")
@@ -480,6 +481,40 @@ def time_fractional(tpc, torch, args, stream):
     return out
 
 
+def time_fgmres(tpc, torch, args, stream, steps=4):
+    """Secondary: the headline problem (and the fractional one of time_fractional) with the
+    flexible GMRES outer iteration (an option, not the paper's: one restart cycle of at most
+    `steps` V-cycle-preconditioned steps per FP64 residual). Mixed and FP64, 3 timed solves each
+    after one warm-up, CUDA events on the solver's stream; cycles = V-cycles per solve."""
+    out = {"workload": f"as the headline; outer iteration = FGMRES({steps}) with one V-cycle per "
+                       f"step as preconditioner; 3 solves after 1 warm-up"}
+    n = 2 ** (args.K + 1) - 1
+    with torch.cuda.stream(stream):
+        b = torch.tensor(uniform_pm1(n, 2024), device="cuda")
+        x = torch.zeros_like(b)
+    cases = (("mixed", tpc.TPC_MIXED, {}), ("fp64", tpc.TPC_FP64, {}),
+             ("fractional_a025_mixed", tpc.TPC_MIXED,
+              dict(kernel=1, kernel_a=0.25, transfer=tpc.TPC_TRANSFER_GEOMETRIC)))
+    for name, prec, kw in cases:
+        S = tpc.Solver(args.delta, 2.0 ** -args.K, stream=stream, precision=prec,
+                       outer=tpc.TPC_OUTER_FGMRES, inner_cycles=steps, **kw)
+        rc, it, rel = S.solve(b, x, tol=args.tol)
+        assert rc == tpc.TPC_OK and rel < args.tol, (rc, rel)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(3):
+            rc, it, rel = S.solve(b, x, tol=args.tol)
+            assert rc == tpc.TPC_OK and rel < args.tol, (rc, rel)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / 3
+        out[name] = {"value": 1000.0 / ms, "unit": UNIT, "ms_per_solve": ms, "outer_iters": it,
+                     "vcycles": tpc.tpc_last_solve_cycles(S.handle), "relres": rel}
+        S.close()
+    return out
+
+
 def time_twod(tpc, torch, args, stream, K=11, delta=0.1):
     """The 2-D configuration: the tensor-product reading of the constant kernel on the unit square
     with a square horizon, n x n unknowns with n = 2^(K+1) - 1 (K = 11: 4095^2 = 16.8 M), delta
@@ -743,7 +778,9 @@ def run_ours(args, rank, world, local_rank):
     digest = kernel_digest()
     # headline path: one FP32 product of the finest level = forward strided pass +
     # contiguous-block kernel + inverse strided pass (residual epilogue), each timed alone
-    names = ("k_fwd_strided<float>", "k_mid_pair<float>", "k_inv_strided<float>")
+    reg = 20 <= args.K + 1 <= 23   # m = 2^(K+1): the register-resident FP32 kernels
+    names = (("k32_fwd", "k32_mid", "k32_inv") if reg else
+             ("k_fwd_strided<float>", "k_mid_pair<float>", "k_inv_strided<float>"))
     t_prod = sum(ms3_32) * 1e-3
     b_prod = product_bytes(NK, 4)
     split = product_bytes_split(NK, 4)
@@ -752,8 +789,8 @@ def run_ours(args, rank, world, local_rank):
     roofline = {"bound": "hbm", "achieved": ach32, "peak": hbm["gbs"], "unit": "GB/s",
                 "frac": ach32 / hbm["gbs"],
                 "traffic": (sum(tr32) if tr32 else None),
-                "kernel": "FP32 finest-level product (k_fwd_strided + k_mid_pair + "
-                          "k_inv_strided, residual epilogue), N_K = 2^%d - 1" % args.K,
+                "kernel": "FP32 finest-level product (%s, residual epilogue), N_K = 2^%d - 1"
+                          % (" + ".join(names), args.K),
                 "algorithmic_bytes_per_launch": b_prod,
                 "algorithmic_bytes_rule": "40 n B per FP32 SPD product, n = N_K (read u 8n, "
                                           "spectra 16n, write y 8n, right-hand side 8n)",
@@ -801,6 +838,7 @@ def run_ours(args, rank, world, local_rank):
                       "at relative residual < %g" % args.tol}
     # the fractional-kernel, batched and served measurements run on one GPU (a single-rank job)
     frac = time_fractional(tpc, torch, args, stream) if world == 1 else None
+    fgmres = time_fgmres(tpc, torch, args, stream) if world == 1 else None
     twod = time_twod(tpc, torch, args, stream) if (world == 1 and not args.no_twod) else None
     batch = time_batch(tpc, torch, args, rank) if (args.batch > 0 and world == 1) else None
     serving = (time_serving(tpc, torch, args)
@@ -823,6 +861,8 @@ def run_ours(args, rank, world, local_rank):
         line["speedup_mixed_vs_fp64"] = line["value"] / line["fp64"]["value"]
         if frac:
             line["fractional_a025"] = frac
+        if fgmres:
+            line["fgmres"] = fgmres
         if twod:
             line["twod"] = twod
         if batch:
@@ -880,9 +920,13 @@ def run_profile_solve(args):
 
     import paper_2202_11288_gb300 as tpc
     n = 2 ** (args.K + 1) - 1
-    prec = tpc.TPC_MIXED if args.profile_solve == "mixed" else tpc.TPC_FP64
-    S = tpc.Solver(args.delta, 2.0 ** -args.K, precision=prec, inner_cycles=args.inner,
-                   autotune=0)
+    prec = tpc.TPC_FP64 if args.profile_solve == "fp64" else tpc.TPC_MIXED
+    if args.profile_solve == "fgmres":   # mixed precision, FGMRES(4) outer iteration
+        S = tpc.Solver(args.delta, 2.0 ** -args.K, precision=prec, inner_cycles=4, autotune=0,
+                       outer=tpc.TPC_OUTER_FGMRES)
+    else:
+        S = tpc.Solver(args.delta, 2.0 ** -args.K, precision=prec, inner_cycles=args.inner,
+                       autotune=0)
     b = torch.tensor(uniform_pm1(n, 0), device="cuda")
     x = torch.zeros_like(b)
     rc, it, rel = S.solve(b, x, tol=args.tol)

@@ -426,8 +426,11 @@ typedef struct tpc_request {
   double kernel_a;         /* as tpc_params.kernel_a                                         */
   int dim;                 /* 2: the 2-D system of tpc2d_setup (n = (2/h - 1)^2 unknowns);
                               0 or 1: the 1-D system                                         */
-  int transfer;            /* as tpc_params.transfer (0, the paper's, for zeroed requests)  */
+  int transfer;            /* TPC_REQUEST_TRANSFER_DEFAULT (0): the server's tpc_params.transfer;
+                              TPC_REQUEST_TRANSFER_PAPER / _GEOMETRIC: that transfer         */
 } tpc_request;
+enum { TPC_REQUEST_TRANSFER_DEFAULT = 0, TPC_REQUEST_TRANSFER_PAPER = 1,
+       TPC_REQUEST_TRANSFER_GEOMETRIC = 2 };
 typedef struct tpc_server_result {
   long long ticket;        /* as returned by tpc_server_submit                               */
   int status;              /* TPC_OK, TPC_ENOTCONV or a negative error                       */

@@ -627,13 +627,15 @@ class Server:
 
     def submit(self, variant: int, delta: float, h: float, b, x, tol: float = 1e-10,
                kernel: int = 0, kernel_a: float = 0.0, dim: int = 1,
-               transfer: int = TPC_TRANSFER_PAPER) -> int:
+               transfer: int | None = None) -> int:
         """b, x: contiguous float64 host arrays (numpy, or pinned torch CPU tensors); dim 2 for
-        the 2-D system ((2/h - 1)^2 unknowns)."""
+        the 2-D system ((2/h - 1)^2 unknowns); transfer: TPC_TRANSFER_PAPER or
+        TPC_TRANSFER_GEOMETRIC, None for the server's parameters' transfer."""
         n = b.numel() if hasattr(b, "numel") else b.size
         bp = b.data_ptr() if hasattr(b, "data_ptr") else b.ctypes.data
         xp = x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
-        r = TpcRequest(variant, delta, h, n, bp, xp, tol, kernel, kernel_a, dim, transfer)
+        rt = 0 if transfer is None else 1 + int(transfer)   # TPC_REQUEST_TRANSFER_*
+        r = TpcRequest(variant, delta, h, n, bp, xp, tol, kernel, kernel_a, dim, rt)
         t = ctypes.c_longlong(0)
         _check(lib().tpc_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)))
         self._keep[t.value] = (b, x)

@@ -86,10 +86,17 @@ namespace {
 
 int req_dim(const tpc_request& r) { return r.dim == 2 ? 2 : 1; }
 
-bool same_key(const Entry& e, const tpc_request& r, int precision) {
+// The transfer a request asks for (the server's parameters' unless the request names one).
+int req_transfer(const tpc_server* S, const tpc_request& r) {
+  if (r.transfer == TPC_REQUEST_TRANSFER_PAPER) return TPC_TRANSFER_PAPER;
+  if (r.transfer == TPC_REQUEST_TRANSFER_GEOMETRIC) return TPC_TRANSFER_GEOMETRIC;
+  return S->prm.transfer;
+}
+
+bool same_key(const tpc_server* S, const Entry& e, const tpc_request& r, int precision) {
   return e.dim == req_dim(r) && e.variant == r.variant && e.precision == precision &&
          e.delta == r.delta && e.h == r.h && e.kernel == r.kernel && e.kernel_a == r.kernel_a &&
-         e.transfer == r.transfer;
+         e.transfer == req_transfer(S, r);
 }
 
 void destroy_entry(Entry* e) {
@@ -144,7 +151,7 @@ bool admit(tpc_server* S, Request& req) {
   Entry* ent = nullptr;
   int same = 0;
   for (Entry* e : S->cache) {
-    if (!same_key(*e, req.r, prec)) continue;
+    if (!same_key(S, *e, req.r, prec)) continue;
     ++same;
     if (!e->busy) {
       ent = e;
@@ -182,7 +189,7 @@ bool admit(tpc_server* S, Request& req) {
     p.variant = req.r.variant;
     p.kernel = req.r.kernel;
     p.kernel_a = req.r.kernel_a;
-    p.transfer = req.r.transfer;
+    p.transfer = req_transfer(S, req.r);
     tpc_handle* H = nullptr;
     tpc2d_handle* H2 = nullptr;
     const int rc = req_dim(req.r) == 2 ? tpc2d_setup(&p, req.r.delta, req.r.h, nullptr, &H2)
@@ -199,7 +206,7 @@ bool admit(tpc_server* S, Request& req) {
     ent->h = req.r.h;
     ent->kernel = req.r.kernel;
     ent->kernel_a = req.r.kernel_a;
-    ent->transfer = req.r.transfer;
+    ent->transfer = p.transfer;
     ent->H = H;
     ent->H2 = H2;
     ent->bytes = entry_bytes(ent);
@@ -341,7 +348,9 @@ int tpc_server_create(const tpc_server_config* cfg, const tpc_params* p, tpc_ser
 }
 
 int tpc_server_submit(tpc_server* S, const tpc_request* r, long long* ticket) {
-  if (!S || !r || !r->b_host || !r->x_host || !(r->tol >= 0.0) || r->n <= 0) {
+  if (!S || !r || !r->b_host || !r->x_host || !(r->tol >= 0.0) || r->n <= 0 || r->dim < 0 ||
+      r->dim > 2 || r->transfer < TPC_REQUEST_TRANSFER_DEFAULT ||
+      r->transfer > TPC_REQUEST_TRANSFER_GEOMETRIC) {
     tpc::set_host_error("bad argument to tpc_server_submit");
     return TPC_EINVAL;
   }
