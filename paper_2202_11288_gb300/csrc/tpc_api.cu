@@ -310,7 +310,7 @@ void launch_matvec(tpc_handle* H, const Hier<T>& G, const DevLevel<T>& L, const 
   const LevelArgs<T> a = stage_args<T>(G, L, x, f, y, epi, post, pro);
   cudaStream_t s = H->stream;
   if (L.logR1 == 0) {
-    k_mid_whole<T, NS><<<1, fft_threads<T>(), L.smem_mid, s>>>(a);
+    launch_k(k_mid_whole<T, NS>, 1, fft_threads<T>(), L.smem_mid, s, a);
     H->launches += 1;
     return;
   }
@@ -355,19 +355,19 @@ T* enqueue_vcycle(tpc_handle* H, Hier<T>& G, int li, const T* f_top, const T* rf
   if constexpr (sizeof(T) == 4) {  // the single-block bottom exists in FP32 only
     if (G.bottom && li == G.bottom_li && rfine) {
       if (H->prm.variant != TPC_SPD)
-        k_vcycle_bottom<T, true><<<1, fft_threads<T>(), G.bottom_smem, s>>>(G.bottom);
+        launch_k(k_vcycle_bottom<T, true>, 1, fft_threads<T>(), G.bottom_smem, s, G.bottom);
       else
-        k_vcycle_bottom<T, false><<<1, fft_threads<T>(), G.bottom_smem, s>>>(G.bottom);
+        launch_k(k_vcycle_bottom<T, false>, 1, fft_threads<T>(), G.bottom_smem, s, G.bottom);
       H->launches += 1;
       return t;  // the last post-smoothing product of level li writes G.t[li]
     }
   }
   if (L.k == H->kc) {
     if (rfine) {
-      k_coarse_solve<T><<<1, 256, 0, s>>>(G.coarse_inv, G.f[li], rfine, e, (int)L.n, G.geo);
+      launch_k(k_coarse_solve<T>, 1, 256, 0, s, G.coarse_inv, G.f[li], rfine, e, (int)L.n, G.geo);
     } else {
-      k_coarse_solve<T><<<1, 256, 0, s>>>(G.coarse_inv, const_cast<T*>(f_top), nullptr, e,
-                                         (int)L.n, G.geo);
+      launch_k(k_coarse_solve<T>, 1, 256, 0, s, G.coarse_inv, const_cast<T*>(f_top), nullptr, e,
+               (int)L.n, G.geo);
     }
     H->launches += 1;
     return e;
@@ -385,7 +385,7 @@ T* enqueue_vcycle(tpc_handle* H, Hier<T>& G, int li, const T* f_top, const T* rf
   matvec<T>(H, G, li, e, f, t, EPI_RESID, false, first);
   const T* ec = enqueue_vcycle<T>(H, G, li + 1, nullptr, t);
   if (H->prm.m2 == 0) {
-    k_prolong_add<T><<<grid_for(L.n), NTHREADS, 0, s>>>(e, ec, L.n, G.geo);
+    launch_k(k_prolong_add<T>, grid_for(L.n), NTHREADS, 0, s, e, ec, L.n, G.geo);
     H->launches += 1;
     return e;
   }
@@ -413,10 +413,10 @@ void enqueue_finest_residual(tpc_handle* H, const double* x, const double* b, do
   a.b = b;
   a.r = r;
   cudaStream_t s = H->stream;
-  box::k_box_local<<<2 * a.nblk, box::NT, 0, s>>>(a);
-  box::k_box_offsets<<<1, 1024, 0, s>>>(a);
+  launch_k(box::k_box_local, 2 * a.nblk, box::NT, 0, s, a);
+  launch_k(box::k_box_offsets, 1, 1024, 0, s, a);
   const int gx = (int)std::min<long long>((a.N + box::NT - 1) / box::NT, 4 * 152);
-  box::k_box_resid<<<dim3(gx, 2), box::NT, 0, s>>>(a);
+  launch_k(box::k_box_resid, dim3(gx, 2), box::NT, 0, s, a);
   H->launches += 3;
 }
 
@@ -475,8 +475,8 @@ int setup_box(tpc_handle* H) {
 
 void enqueue_sumsq(tpc_handle* H, const double* r, long long n) {
   H->launches += 2;
-  k_sumsq_partial<double><<<NORM_BLOCKS, NTHREADS, 0, H->stream>>>(r, n, H->sumsq_part);
-  k_sumsq_final<<<1, 32, 0, H->stream>>>(H->sumsq_part, NORM_BLOCKS, H->sumsq);
+  launch_k(k_sumsq_partial<double>, NORM_BLOCKS, NTHREADS, 0, H->stream, r, n, H->sumsq_part);
+  launch_k(k_sumsq_final, 1, 32, 0, H->stream, H->sumsq_part, NORM_BLOCKS, H->sumsq);
 }
 
 // One restart cycle of flexible GMRES with `steps` steps (tpc_krylov.cuh) on the FP64
@@ -488,27 +488,27 @@ void enqueue_fgmres_cycle(tpc_handle* H, Hier<T>& G, T* V, T* Z, int steps) {
   const long long ld = H->kld;
   const int g = grid_for(n);
   cudaStream_t s = H->stream;
-  k_kry_start<T><<<g, NTHREADS, 0, s>>>(H->r0, V, n, H->sumsq, H->ks);
+  launch_k(k_kry_start<T>, g, NTHREADS, 0, s, H->r0, V, n, H->sumsq, H->ks);
   H->launches += 1;
   for (int j = 0; j < steps; ++j) {
     T* vj = V + (size_t)j * ld;
     T* w = V + (size_t)(j + 1) * ld;
     T* zj = Z + (size_t)j * ld;
     const T* ec = enqueue_vcycle<T>(H, G, 0, vj, nullptr);
-    k_copy<T><<<g, NTHREADS, 0, s>>>(ec, zj, n);
+    launch_k(k_copy<T>, g, NTHREADS, 0, s, ec, zj, n);
     matvec<T>(H, G, 0, zj, nullptr, w, EPI_APPLY, false);
     for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
-      k_kry_dot_partial<T><<<dim3(KNB, j + 1), 256, 0, s>>>(V, ld, w, n, H->kpart);
-      k_kry_dot_final<<<j + 1, 32, 0, s>>>(H->kpart, KNB, H->ks, j, pass);
-      k_kry_axpy<T><<<g, NTHREADS, 0, s>>>(w, V, ld, j + 1, H->ks, n);
+      launch_k(k_kry_dot_partial<T>, dim3(KNB, j + 1), 256, 0, s, V, ld, w, n, H->kpart);
+      launch_k(k_kry_dot_final, j + 1, 32, 0, s, H->kpart, KNB, H->ks, j, pass);
+      launch_k(k_kry_axpy<T>, g, NTHREADS, 0, s, w, V, ld, j + 1, H->ks, n);
     }
-    k_kry_sumsq_partial<T><<<KNB, 256, 0, s>>>(w, n, H->kpart);
-    k_kry_rotate<<<1, 32, 0, s>>>(H->kpart, KNB, H->ks, j);
-    k_kry_scale<T><<<g, NTHREADS, 0, s>>>(w, n, H->ks);
+    launch_k(k_kry_sumsq_partial<T>, KNB, 256, 0, s, w, n, H->kpart);
+    launch_k(k_kry_rotate, 1, 32, 0, s, H->kpart, KNB, H->ks, j);
+    launch_k(k_kry_scale<T>, g, NTHREADS, 0, s, w, n, H->ks);
     H->launches += 11;
   }
-  k_kry_solve<<<1, 32, 0, s>>>(H->ks, steps);
-  k_kry_update<T><<<g, NTHREADS, 0, s>>>(H->u, Z, ld, steps, H->ks, n);
+  launch_k(k_kry_solve, 1, 32, 0, s, H->ks, steps);
+  launch_k(k_kry_update<T>, g, NTHREADS, 0, s, H->u, Z, ld, steps, H->ks, n);
   H->launches += 2;
 }
 
@@ -525,22 +525,22 @@ void enqueue_iteration(tpc_handle* H, int cycles) {
     else enqueue_fgmres_cycle<double>(H, H->d, H->kv64, H->kz64, cycles);
   } else if (H->prm.precision == TPC_MIXED) {
     Hier<float>& S = H->s;
-    k_to_f32_scaled<<<g, NTHREADS, 0, H->stream>>>(H->r0, S.f[0], n, H->sumsq);
+    launch_k(k_to_f32_scaled, g, NTHREADS, 0, H->stream, H->r0, S.f[0], n, H->sumsq);
     H->launches += 1;
     const float* ec = enqueue_vcycle<float>(H, S, 0, S.f[0], nullptr);
-    k_copy<float><<<g, NTHREADS, 0, H->stream>>>(ec, H->acc32, n);
+    launch_k(k_copy<float>, g, NTHREADS, 0, H->stream, ec, H->acc32, n);
     H->launches += 1;
     for (int c = 1; c < cycles; ++c) {
       matvec<float>(H, S, 0, H->acc32, S.f[0], H->res32, EPI_RESID, false);
       ec = enqueue_vcycle<float>(H, S, 0, H->res32, nullptr);
-      k_axpy<float><<<g, NTHREADS, 0, H->stream>>>(H->acc32, ec, n);
+      launch_k(k_axpy<float>, g, NTHREADS, 0, H->stream, H->acc32, ec, n);
       H->launches += 1;
     }
-    k_axpy_f32_scaled<<<g, NTHREADS, 0, H->stream>>>(H->u, H->acc32, n, H->sumsq);
+    launch_k(k_axpy_f32_scaled, g, NTHREADS, 0, H->stream, H->u, H->acc32, n, H->sumsq);
     H->launches += 1;
   } else {
     double* e = enqueue_vcycle<double>(H, H->d, 0, H->r0, nullptr);
-    k_axpy<double><<<g, NTHREADS, 0, H->stream>>>(H->u, e, n);
+    launch_k(k_axpy<double>, g, NTHREADS, 0, H->stream, H->u, e, n);
     H->launches += 1;
   }
   enqueue_finest_residual(H, H->u, H->b, H->r0);

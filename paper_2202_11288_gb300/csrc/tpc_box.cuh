@@ -113,7 +113,10 @@ __device__ __forceinline__ void box_local_body(const BoxArgs& a, int blk) {
     a.part[blk] = dt;
   }
 }
-__global__ void __launch_bounds__(NT) k_box_local(BoxArgs a) { box_local_body(a, (int)blockIdx.x); }
+__global__ void __launch_bounds__(NT) k_box_local(BoxArgs a) {
+  pdl_wait();
+  box_local_body(a, (int)blockIdx.x);
+}
 
 // Double-double addition (Knuth's two-sum on the high parts, then the low parts).
 __device__ __forceinline__ double2 dd_add(double2 x, double2 y) {
@@ -168,7 +171,10 @@ __device__ __forceinline__ void box_offsets_body(const BoxArgs& a) {
   }
   if (t == 0) a.dot[0] = red[0];
 }
-__global__ void __launch_bounds__(1024) k_box_offsets(BoxArgs a) { box_offsets_body(a); }
+__global__ void __launch_bounds__(1024) k_box_offsets(BoxArgs a) {
+  pdl_wait();
+  box_offsets_body(a);
+}
 
 // P(a) - P(b) of segment s (a, b already clamped to [0, N]).
 __device__ __forceinline__ double box_sum(const BoxArgs& a, int s, int ka, int kb) {
@@ -220,6 +226,7 @@ __device__ __forceinline__ void box_resid_body(const BoxArgs& a, int bx, int gx,
   if (bx == 0 && half == 0 && threadIdx.x == 0) a.r[N] = a.b[N] - fma(a.o, w_o, a.dot[0]);
 }
 __global__ void __launch_bounds__(NT) k_box_resid(BoxArgs a) {
+  pdl_wait();
   box_resid_body(a, (int)blockIdx.x, (int)gridDim.x, (int)blockIdx.y);
 }
 

@@ -164,6 +164,7 @@ __device__ __forceinline__ void mac_reg(float sa, float sd, float2 sb, float2 sc
 // ------------------------------------------------------------------------------------------
 template <int LR1, int PRO>
 __global__ void __launch_bounds__(NT_STRIDED, TPC_F32_STRIDED_MINB) k32_fwd(LevelArgs<float> a) {
+  pdl_wait();
   constexpr int R1 = 1 << LR1;
   constexpr int RS = R1 >> 8;                   // radix of the last step (4 or 8)
   constexpr int LRS = LR1 - 8;
@@ -292,6 +293,7 @@ __global__ void __launch_bounds__(NT_STRIDED, TPC_F32_STRIDED_MINB) k32_fwd(Leve
 // ------------------------------------------------------------------------------------------
 template <int LL, bool NS>
 __global__ void __launch_bounds__(1 << (LL - 4), 1 << (13 - LL)) k32_mid(LevelArgs<float> a) {
+  pdl_wait();
   constexpr int L = 1 << LL;
   constexpr int NT = L / 16;
   constexpr int RS = L >> 8;       // radix of the last step: 4, 8, 16
@@ -508,6 +510,7 @@ __global__ void __launch_bounds__(1 << (LL - 4), 1 << (13 - LL)) k32_mid(LevelAr
 // ------------------------------------------------------------------------------------------
 template <int LR1, int EPI>
 __global__ void __launch_bounds__(NT_STRIDED, TPC_F32_STRIDED_MINB) k32_inv(LevelArgs<float> a) {
+  pdl_wait();
   constexpr int R1 = 1 << LR1;
   constexpr int RS = R1 >> 8;
   constexpr int LRS = LR1 - 8;
@@ -652,19 +655,19 @@ template <int LR1>
 inline void launch_fwd_lr(const LevelArgs<float>& a, int blocks, cudaStream_t st) {
   const size_t sm = strided_smem(LR1);
   switch (a.pro) {
-    case PRO_SMOOTH: k32_fwd<LR1, PRO_SMOOTH><<<blocks, NT_STRIDED, sm, st>>>(a); break;
-    case PRO_RESTRICT: k32_fwd<LR1, PRO_RESTRICT><<<blocks, NT_STRIDED, sm, st>>>(a); break;
-    case PRO_PROLONG: k32_fwd<LR1, PRO_PROLONG><<<blocks, NT_STRIDED, sm, st>>>(a); break;
-    default: k32_fwd<LR1, PRO_NONE><<<blocks, NT_STRIDED, sm, st>>>(a); break;
+    case PRO_SMOOTH: launch_k(k32_fwd<LR1, PRO_SMOOTH>, blocks, NT_STRIDED, sm, st, a); break;
+    case PRO_RESTRICT: launch_k(k32_fwd<LR1, PRO_RESTRICT>, blocks, NT_STRIDED, sm, st, a); break;
+    case PRO_PROLONG: launch_k(k32_fwd<LR1, PRO_PROLONG>, blocks, NT_STRIDED, sm, st, a); break;
+    default: launch_k(k32_fwd<LR1, PRO_NONE>, blocks, NT_STRIDED, sm, st, a); break;
   }
 }
 template <int LR1>
 inline void launch_inv_lr(const LevelArgs<float>& a, int blocks, cudaStream_t st) {
   const size_t sm = strided_smem(LR1);
   switch (a.epi) {
-    case EPI_RESID: k32_inv<LR1, EPI_RESID><<<blocks, NT_STRIDED, sm, st>>>(a); break;
-    case EPI_JACOBI: k32_inv<LR1, EPI_JACOBI><<<blocks, NT_STRIDED, sm, st>>>(a); break;
-    default: k32_inv<LR1, EPI_APPLY><<<blocks, NT_STRIDED, sm, st>>>(a); break;
+    case EPI_RESID: launch_k(k32_inv<LR1, EPI_RESID>, blocks, NT_STRIDED, sm, st, a); break;
+    case EPI_JACOBI: launch_k(k32_inv<LR1, EPI_JACOBI>, blocks, NT_STRIDED, sm, st, a); break;
+    default: launch_k(k32_inv<LR1, EPI_APPLY>, blocks, NT_STRIDED, sm, st, a); break;
   }
 }
 inline void launch_fwd(const LevelArgs<float>& a, int blocks, cudaStream_t st) {
@@ -678,9 +681,9 @@ inline void launch_inv(const LevelArgs<float>& a, int blocks, cudaStream_t st) {
 template <bool NS>
 inline void launch_mid(const LevelArgs<float>& a, int blocks, cudaStream_t st) {
   const size_t sm = mid_smem(a.logL);
-  if (a.logL == 12) k32_mid<12, NS><<<blocks, 256, sm, st>>>(a);
-  else if (a.logL == 11) k32_mid<11, NS><<<blocks, 128, sm, st>>>(a);
-  else k32_mid<10, NS><<<blocks, 64, sm, st>>>(a);
+  if (a.logL == 12) launch_k(k32_mid<12, NS>, blocks, 256, sm, st, a);
+  else if (a.logL == 11) launch_k(k32_mid<11, NS>, blocks, 128, sm, st, a);
+  else launch_k(k32_mid<10, NS>, blocks, 64, sm, st, a);
 }
 
 template <int LR1>

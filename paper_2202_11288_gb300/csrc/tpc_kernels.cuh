@@ -24,9 +24,45 @@
 // blocks 0 and 1 pair with themselves.
 #pragma once
 
+#include <cstdlib>
+#include <cstring>
+
 #include "tpc_fft.cuh"
 
 namespace tpc {
+
+// Programmatic dependent launch. The kernels of a solve run back to back on one stream, most
+// of them short (the coarse levels). Launched with the programmatic-serialisation attribute
+// (launch_k), a kernel may be scheduled before its predecessor has finished; it calls
+// pdl_wait() before it touches global memory, which returns once the predecessor has
+// completed and its memory is visible, so the results are those of ordinary stream order and
+// only the launch latency overlaps. The kernels do not signal their successors early: that
+// lets a successor's blocks be scheduled while the predecessor's last blocks run, which
+// measured faster for batches of small solves but slower for the largest single solve.
+// Without the attribute pdl_wait() is a no-op. TPC_PDL=0 in the environment launches without it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+inline bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("TPC_PDL");
+    return !(e && std::strcmp(e, "0") == 0);
+  }();
+  return on;
+}
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                            cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
 
 constexpr int LOG_LMAX = 12;        // longest in-shared-memory sub-transform (4096 points)
 constexpr int NTHREADS = 256;       // elementwise kernels
@@ -627,6 +663,7 @@ __device__ __forceinline__ void fwd_strided_body(const LevelArgs<T>& a, int blk)
 
 template <typename T, int IN, int PRO, int MINB = fft_min_blocks<T>()>
 __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_fwd_strided(LevelArgs<T> a) {
+  pdl_wait();
   fwd_strided_body<T, IN, PRO>(a, (int)blockIdx.x);
 }
 
@@ -808,10 +845,12 @@ __device__ __forceinline__ void mid_body(const LevelArgs<T>& a, int blk) {
 // LOGL_CT: 0 for any L, or log2 L fixed at compile time (the launch picks the instance).
 template <typename T, bool NS, int LOGL_CT = 0>
 __global__ void __launch_bounds__(fft_threads<T>(), mid_min_blocks<T>()) k_mid_pair(LevelArgs<T> a) {
+  pdl_wait();
   mid_body<T, MID_PAIR, NS, LOGL_CT>(a, (int)blockIdx.x);
 }
 template <typename T, bool NS>
 __global__ void __launch_bounds__(fft_threads<T>(), mid_min_blocks<T>()) k_mid_whole(LevelArgs<T> a) {
+  pdl_wait();
   mid_body<T, MID_WHOLE, NS>(a, (int)blockIdx.x);
 }
 template <typename T>
@@ -955,6 +994,7 @@ __device__ __forceinline__ void inv_strided_body(const LevelArgs<T>& a, int blk)
 
 template <typename T, int EPI, int MINB = fft_min_blocks<T>()>
 __global__ void __launch_bounds__(fft_threads<T>(), MINB) k_inv_strided(LevelArgs<T> a) {
+  pdl_wait();
   inv_strided_body<T, EPI>(a, (int)blockIdx.x);
 }
 
@@ -1027,6 +1067,7 @@ __device__ __forceinline__ void vcycle_bottom_body(const BottomPlan<T>* bp) {
 
 template <typename T, bool NS>
 __global__ void __launch_bounds__(fft_threads<T>(), 1) k_vcycle_bottom(const BottomPlan<T>* bp) {
+  pdl_wait();
   vcycle_bottom_body<T, NS>(bp);
 }
 
@@ -1050,6 +1091,7 @@ __global__ void k_extract_cplx(const c2<T>* z, c2<T>* out, long long m, T scale)
 // Correction with P = 2 (I_k^{k-1})^T: e[2I+1] += ec[I], e[2I], e[2I+2] += ec[I] / 2.
 template <typename T>
 __global__ void k_prolong_add(T* e, const T* ec, long long nf, int geo) {
+  pdl_wait();
   const long long nc = (nf - 1) / 2;
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nf;
        j += (long long)gridDim.x * blockDim.x) {
@@ -1082,6 +1124,7 @@ __global__ void k_prolong_add(T* e, const T* ec, long long nf, int geo) {
 template <typename T>
 __global__ void k_coarse_solve(const T* inv, T* f, const T* rfine, T* e, int n, int geo) {
   __shared__ T fs[256];
+  pdl_wait();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     if (rfine) {
       fs[i] = restrict_at<T>(rfine, i, (n - 1) / 2, geo);
@@ -1100,6 +1143,7 @@ __global__ void k_coarse_solve(const T* inv, T* f, const T* rfine, T* e, int n, 
 
 template <typename T>
 __global__ void k_axpy(T* u, const T* e, long long n) {
+  pdl_wait();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     u[i] += e[i];
@@ -1118,6 +1162,7 @@ static __global__ void k_bdf4_rhs(double* b, const double* u1, const double* u2,
 
 template <typename T>
 __global__ void k_copy(const T* src, T* dst, long long n) {
+  pdl_wait();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     dst[i] = src[i];
@@ -1126,6 +1171,7 @@ __global__ void k_copy(const T* src, T* dst, long long n) {
 // Mixed precision: the FP64 residual r enters the FP32 V-cycles scaled to unit RMS,
 // f = r * sqrt(n / ||r||^2), and the FP32 correction e comes back as u += e / that scale.
 static __global__ void k_to_f32_scaled(const double* r, float* f, long long n, const double* sumsq) {
+  pdl_wait();
   const double ss = sumsq[0];
   const double s = (ss > 0.0) ? sqrt((double)n / ss) : 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -1133,6 +1179,7 @@ static __global__ void k_to_f32_scaled(const double* r, float* f, long long n, c
     f[i] = (float)(r[i] * s);
 }
 static __global__ void k_axpy_f32_scaled(double* u, const float* e, long long n, const double* sumsq) {
+  pdl_wait();
   const double inv = sqrt(sumsq[0] / (double)n);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -1148,6 +1195,7 @@ template <typename T>
 __global__ void __launch_bounds__(NTHREADS) k_sumsq_partial(const T* r, long long n,
                                                             double* part) {
   __shared__ double red[NTHREADS / 32];
+  pdl_wait();
   double acc = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -1158,6 +1206,7 @@ __global__ void __launch_bounds__(NTHREADS) k_sumsq_partial(const T* r, long lon
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 static __global__ void k_sumsq_final(const double* part, int np, double* out) {
+  pdl_wait();
   double acc = 0;
   for (int i = threadIdx.x; i < np; i += 32) acc += part[i];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -1170,10 +1219,10 @@ template <typename T, int MB>
 inline void launch_fwd_strided_mb(const LevelArgs<T>& a, int blocks, size_t smem, cudaStream_t s) {
   const int nt = fft_threads<T>();
   switch (a.pro) {
-    case PRO_SMOOTH: k_fwd_strided<T, IN_PACK, PRO_SMOOTH, MB><<<blocks, nt, smem, s>>>(a); break;
-    case PRO_RESTRICT: k_fwd_strided<T, IN_PACK, PRO_RESTRICT, MB><<<blocks, nt, smem, s>>>(a); break;
-    case PRO_PROLONG: k_fwd_strided<T, IN_PACK, PRO_PROLONG, MB><<<blocks, nt, smem, s>>>(a); break;
-    default: k_fwd_strided<T, IN_PACK, PRO_NONE, MB><<<blocks, nt, smem, s>>>(a); break;
+    case PRO_SMOOTH: launch_k(k_fwd_strided<T, IN_PACK, PRO_SMOOTH, MB>, blocks, nt, smem, s, a); break;
+    case PRO_RESTRICT: launch_k(k_fwd_strided<T, IN_PACK, PRO_RESTRICT, MB>, blocks, nt, smem, s, a); break;
+    case PRO_PROLONG: launch_k(k_fwd_strided<T, IN_PACK, PRO_PROLONG, MB>, blocks, nt, smem, s, a); break;
+    default: launch_k(k_fwd_strided<T, IN_PACK, PRO_NONE, MB>, blocks, nt, smem, s, a); break;
   }
 }
 template <typename T>
@@ -1190,9 +1239,9 @@ template <typename T, int MB>
 inline void launch_inv_strided_mb(const LevelArgs<T>& a, int blocks, size_t smem, cudaStream_t s) {
   const int nt = fft_threads<T>();
   switch (a.epi) {
-    case EPI_RESID: k_inv_strided<T, EPI_RESID, MB><<<blocks, nt, smem, s>>>(a); break;
-    case EPI_JACOBI: k_inv_strided<T, EPI_JACOBI, MB><<<blocks, nt, smem, s>>>(a); break;
-    default: k_inv_strided<T, EPI_APPLY, MB><<<blocks, nt, smem, s>>>(a); break;
+    case EPI_RESID: launch_k(k_inv_strided<T, EPI_RESID, MB>, blocks, nt, smem, s, a); break;
+    case EPI_JACOBI: launch_k(k_inv_strided<T, EPI_JACOBI, MB>, blocks, nt, smem, s, a); break;
+    default: launch_k(k_inv_strided<T, EPI_APPLY, MB>, blocks, nt, smem, s, a); break;
   }
 }
 template <typename T>
@@ -1210,10 +1259,10 @@ inline void launch_inv_strided(const LevelArgs<T>& a, int blocks, size_t smem, c
 template <typename T, bool NS>
 inline void launch_mid_pair(const LevelArgs<T>& a, int blocks, size_t smem, cudaStream_t s) {
   const int nt = fft_threads<T>();
-  if (sizeof(T) == 4 && a.logL == 12) k_mid_pair<T, NS, 12><<<blocks, nt, smem, s>>>(a);
-  else if (sizeof(T) == 4 && a.logL == 11) k_mid_pair<T, NS, 11><<<blocks, nt, smem, s>>>(a);
-  else if (sizeof(T) == 4 && a.logL == 10) k_mid_pair<T, NS, 10><<<blocks, nt, smem, s>>>(a);
-  else k_mid_pair<T, NS><<<blocks, nt, smem, s>>>(a);
+  if (sizeof(T) == 4 && a.logL == 12) launch_k(k_mid_pair<T, NS, 12>, blocks, nt, smem, s, a);
+  else if (sizeof(T) == 4 && a.logL == 11) launch_k(k_mid_pair<T, NS, 11>, blocks, nt, smem, s, a);
+  else if (sizeof(T) == 4 && a.logL == 10) launch_k(k_mid_pair<T, NS, 10>, blocks, nt, smem, s, a);
+  else launch_k(k_mid_pair<T, NS>, blocks, nt, smem, s, a);
 }
 template <typename T, bool NS>
 inline cudaError_t mid_pair_smem_attrs(int bytes) {

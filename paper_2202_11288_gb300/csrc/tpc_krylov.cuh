@@ -40,6 +40,7 @@ struct KState {
 template <typename T>
 __global__ void k_kry_start(const double* __restrict__ r, T* __restrict__ v0, long long n,
                             const double* __restrict__ sumsq, KState* ks) {
+  pdl_wait();
   const double beta = sqrt(sumsq[0]);
   const double s = beta > 0.0 ? 1.0 / beta : 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -54,6 +55,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_kry_dot_partial(const T* __restrict__ V, long long ld,
                                                          const T* __restrict__ w, long long n,
                                                          double* __restrict__ part) {
+  pdl_wait();
   __shared__ double red[8];
   const T* v = V + (size_t)blockIdx.y * ld;
   T acc = 0;
@@ -68,6 +70,7 @@ __global__ void __launch_bounds__(256) k_kry_dot_partial(const T* __restrict__ V
 // Hessenberg matrix gets h (first pass) or h added (second pass).
 __global__ void k_kry_dot_final(const double* __restrict__ part, int np, KState* ks, int j,
                                 int accumulate) {
+  pdl_wait();
   const int i = blockIdx.x;
   double acc = 0.0;
   for (int k = threadIdx.x; k < np; k += 32) acc += part[(size_t)i * np + k];
@@ -83,6 +86,7 @@ __global__ void k_kry_dot_final(const double* __restrict__ part, int np, KState*
 template <typename T>
 __global__ void k_kry_axpy(T* __restrict__ w, const T* __restrict__ V, long long ld, int nv,
                            const KState* __restrict__ ks, long long n) {
+  pdl_wait();
   __shared__ T hs[MAXS + 1];
   if (threadIdx.x < nv) hs[threadIdx.x] = (T)ks->h[threadIdx.x];
   __syncthreads();
@@ -98,6 +102,7 @@ __global__ void k_kry_axpy(T* __restrict__ w, const T* __restrict__ V, long long
 template <typename T>
 __global__ void __launch_bounds__(256) k_kry_sumsq_partial(const T* __restrict__ w, long long n,
                                                            double* __restrict__ part) {
+  pdl_wait();
   __shared__ double red[8];
   T acc = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -111,6 +116,7 @@ __global__ void __launch_bounds__(256) k_kry_sumsq_partial(const T* __restrict__
 // earlier ones, and a new one that zeroes h_{j+1,j} (cs = 1, sn = 0 when both entries are 0);
 // g follows the new rotation.
 __global__ void k_kry_rotate(const double* __restrict__ part, int np, KState* ks, int j) {
+  pdl_wait();
   double acc = 0.0;
   for (int k = threadIdx.x; k < np; k += 32) acc += part[k];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -142,6 +148,7 @@ __global__ void k_kry_rotate(const double* __restrict__ part, int np, KState* ks
 // v_{j+1} = w / h_{j+1,j} (0 at a breakdown).
 template <typename T>
 __global__ void k_kry_scale(T* __restrict__ w, long long n, const KState* __restrict__ ks) {
+  pdl_wait();
   const T s = (T)ks->inv;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -150,6 +157,7 @@ __global__ void k_kry_scale(T* __restrict__ w, long long n, const KState* __rest
 
 // y = R^{-1} g by back substitution (a zero pivot gives y_i = 0).
 __global__ void k_kry_solve(KState* ks, int steps) {
+  pdl_wait();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   for (int i = steps - 1; i >= 0; --i) {
     double s = ks->g[i];
@@ -163,6 +171,7 @@ __global__ void k_kry_solve(KState* ks, int steps) {
 template <typename T>
 __global__ void k_kry_update(double* __restrict__ u, const T* __restrict__ Z, long long ld,
                              int steps, const KState* __restrict__ ks, long long n) {
+  pdl_wait();
   __shared__ T ys[MAXS];
   if (threadIdx.x < steps) ys[threadIdx.x] = (T)ks->y[threadIdx.x];
   __syncthreads();
