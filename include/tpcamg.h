@@ -79,9 +79,10 @@ typedef struct tpc_params {
   int max_iters;      /* outer iterations of tpc_solve (default 100)                       */
   int inner_cycles;   /* TPC_MIXED: at most this many FP32 V-cycles per FP64 residual
                          (default 6; see tpc_solve)                                        */
-  int autotune;       /* 1 (default): tpc_setup times the tile widths of the strided FFT
-                         passes of every level and keeps the fastest (results are the same
-                         for every width); 0: the fixed rule                                */
+  int autotune;       /* 1 (default): tpc_setup times, for every three-pass level, the
+                         factorisation of its transform (m = R1 x L, log2 L the rule's value or
+                         one off it) and the tile widths of the strided passes, and keeps the
+                         fastest (see tpc_tune_get; results agree to rounding); 0: the rule */
   int poison;         /* checking aid, 0 (default) or 1: every device buffer of the handle
                          is filled with all-ones bytes (NaN in FP32 and FP64) when it is
                          allocated, so that a value read before it is written shows up as
@@ -173,7 +174,8 @@ int tpc_solve_batch(tpc_handle* const* hs, int count, const double* const* b_dev
 /* Stage-batched solves (the batched configuration, not in the paper). tpc_batch_create groups the
  * handles whose level structure is identical -- mixed precision, V(1,1), the single-block bottom
  * of the FP32 V-cycles, the prefix-sum residual (box_residual with the constant kernel), the
- * same finest and coarsest levels, system and inner_cycles, levels up to m = 2^18 -- and
+ * same finest and coarsest levels, system and inner_cycles, the stationary outer iteration,
+ * every three-pass level on the general FP32 kernels (m <= 2^19), the same FFT plans -- and
  * prepares, per group, every stage's arguments for all its instances. tpc_batch_solve then runs
  * each outer iteration of a group as ONE launch per stage of Algorithm 2 over all the group's
  * instances (a three-pass product is either one persistent cooperative launch whose passes are
@@ -296,6 +298,23 @@ int tpc_bdf4_coefficients(const tpc_params* p, double delta, double h, double ta
  * boundary basis functions (u(0) = g_left[0], u(1) = g_right[0]; other entries unused). */
 int tpc_collocation_rhs(const tpc_params* p, double delta, double h, const double* f_colloc,
                         const double* g_left, const double* g_right, double* rhs_out);
+
+/* Process-wide tuning table of the FFT plans (tpc_params.autotune; not in the paper). For the
+ * levels of size m = 2^logm of one precision (word = 4: FP32, 8: FP64) an entry holds the
+ * factorisation m = R1 x L of the three-pass product (logL = log2 L), the tile width 2^logC of
+ * the strided passes and whether the register-resident FP32 kernels run it (reg). The set-up
+ * autotuner writes the entries it measures (the factorisation with log2 L the rule's value or
+ * one off it, and every tile width); a later set-up with autotune = 1 uses an existing entry
+ * instead of timing, so every handle of the process computes the same products.
+ * tpc_tune_get returns 1 and fills the outputs if there is an entry, 0 if not, TPC_EINVAL for a
+ * bad word or NULL. tpc_tune_set writes an entry (TPC_EINVAL unless 13 <= logm <= 23,
+ * 2^7 <= L <= 2^12, 2^6 <= R1 <= 2^11, R1 x 2^logC <= 8192, 0 <= logC <= 4, and reg = 1 only
+ * with word = 4 and a factorisation the register-resident kernels take: R1 = 2^10 or 2^11,
+ * L = 2^10 .. 2^12); levels with the band of TPC_WEAKLY take the general kernels. Results of
+ * every entry are the method's to rounding. tpc_tune_reset empties the table. */
+int tpc_tune_get(int word, int logm, int* logL, int* logC, int* reg);
+int tpc_tune_set(int word, int logm, int logL, int logC, int reg);
+void tpc_tune_reset(void);
 
 /* Timing of the kernels of one level's product y = f - A_level x on the handle's stream:
  * each kernel of the pipeline is launched reps times (reps >= 1) between two CUDA events,

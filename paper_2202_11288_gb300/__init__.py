@@ -28,7 +28,8 @@ TPC_TRANSFER_PAPER, TPC_TRANSFER_GEOMETRIC = 0, 1
 TPC_OUTER_VCYCLE, TPC_OUTER_FGMRES = 0, 1
 
 EXPORTED = ["tpc_default_params", "tpc_setup", "tpc_solve", "tpc_solve_batch", "tpc_solve_host",
-            "tpc_batch_create", "tpc_batch_create_2d", "tpc_batch_solve", "tpc_batch_groups", "tpc_batch_set_product_mode",
+            "tpc_batch_create", "tpc_batch_create_2d", "tpc_batch_solve",
+            "tpc_tune_get", "tpc_tune_set", "tpc_tune_reset", "tpc_batch_groups", "tpc_batch_set_product_mode",
             "tpc_batch_grouped_instances", "tpc_batch_destroy", "tpc_grid_wait_selftest",
             "tpc_apply",
             "tpc_apply_f32",
@@ -113,6 +114,12 @@ def lib() -> ctypes.CDLL:
     L.tpc_solve.restype = I
     L.tpc_solve_batch.argtypes = [P, I, P, P, D, P, P, P]
     L.tpc_solve_batch.restype = I
+    L.tpc_tune_get.argtypes = [I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
+    L.tpc_tune_get.restype = I
+    L.tpc_tune_set.argtypes = [I, I, I, I, I]
+    L.tpc_tune_set.restype = I
+    L.tpc_tune_reset.argtypes = []
+    L.tpc_tune_reset.restype = None
     L.tpc_batch_create.argtypes = [P, I, ctypes.POINTER(P)]
     L.tpc_batch_create.restype = I
     L.tpc_batch_create_2d.argtypes = [P, I, P, I, ctypes.POINTER(P)]
@@ -402,6 +409,24 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def tpc_tune_get(word: int, logm: int):
+    """(logL, logC, reg) of the process-wide FFT plan table for levels of size 2^logm in FP32
+    (word 4) or FP64 (word 8), or None when there is no entry."""
+    a, c, r = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    rc = lib().tpc_tune_get(word, logm, ctypes.byref(a), ctypes.byref(c), ctypes.byref(r))
+    if rc < 0:
+        raise TpcError(rc, tpc_last_error(None))
+    return (a.value, c.value, r.value) if rc == 1 else None
+
+
+def tpc_tune_set(word: int, logm: int, logL: int, logC: int, reg: int = 0) -> None:
+    _check(lib().tpc_tune_set(word, logm, logL, logC, reg))
+
+
+def tpc_tune_reset() -> None:
+    lib().tpc_tune_reset()
 
 
 def tpc_grid_wait_selftest(max_polls: int):

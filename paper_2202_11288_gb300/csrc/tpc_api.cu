@@ -236,6 +236,35 @@ void plan_level(DevLevel<T>& L) {
       sizeof(c2<T>) * (size_t)(tw_slots<T>() + padded_size(1 << (L.logL + (L.logR1 ? 1 : 0))));
 }
 
+// The plan of a three-pass level for the factorisation m = R1 x L with L = 2^logL: the
+// register-resident FP32 kernels where they apply (reg), else the general kernels with tile
+// width 2^logC (logC < 0: the rule of plan_level).
+template <typename T>
+void apply_split(DevLevel<T>& L, int logL, int logC, bool reg) {
+  L.logL = logL;
+  L.logR1 = L.logm - logL;
+  L.mid_blocks = (1 << (L.logm - logL - 1)) + 1;
+  L.f32reg = reg;
+  if (reg) {
+    L.logC = f32p::LOG_CT;
+    L.fwd_blocks = 1 << (logL - f32p::LOG_CT);
+    L.smem_strided = f32p::strided_smem(L.logR1);
+    L.smem_mid = f32p::mid_smem(logL);
+    return;
+  }
+  if (logC < 0) {
+    logC = 4;
+    if (logC > LOG_TILE_MAX - L.logR1) logC = LOG_TILE_MAX - L.logR1;
+    const int want = logL - 9 > 0 ? logL - 9 : 0;  // >= 512 column blocks on large levels
+    if (logC > want) logC = want;
+    if (logC < 0) logC = 0;
+  }
+  L.logC = logC;
+  L.fwd_blocks = 1 << (logL - logC);
+  L.smem_strided = sizeof(c2<T>) * (size_t)(tw_slots<T>() + padded_size(1 << (L.logR1 + logC)));
+  L.smem_mid = sizeof(c2<T>) * (size_t)(tw_slots<T>() + padded_size(1 << (logL + 1)));
+}
+
 template <typename T>
 LevelArgs<T> level_args(const Hier<T>& G, const DevLevel<T>& L) {
   LevelArgs<T> a{};
@@ -823,8 +852,63 @@ int build_bottom(tpc_handle* H, Hier<T>& G) {
 // bit for bit the same products (a solve alone and in a batch or the server agree exactly), the
 // choice is made once per (precision, level size) and kept for the process.
 std::mutex g_tune_mu;
-std::map<std::pair<int, int>, int> g_tuned_logC;  // (sizeof(T), log2 m) -> logC
+// (sizeof(T), log2 m) -> the chosen factorisation and tile width, shared by every handle of
+// the process so that a solve alone, in a batch and in the server computes the same
+struct TunedLevel {
+  int logL, logC;
+  bool reg;
+};
+std::map<std::pair<int, int>, TunedLevel> g_tuned;
 
+// Mean time of `reps` launches of the level's product (after one warm-up), or of its two
+// strided passes only (passes_only), on zeroed level buffers; < 0 on a CUDA error.
+template <typename T>
+float time_product(tpc_handle* H, Hier<T>& G, int li, bool passes_only, cudaEvent_t* ev) {
+  const DevLevel<T>& L = G.lev[li];
+  cudaStream_t s = H->stream;
+  LevelArgs<T> a = level_args<T>(G, L);
+  a.x = G.e[li];
+  a.f = G.f[li];
+  a.y = G.t[li];
+  a.pro = PRO_NONE;
+  a.epi = EPI_RESID;
+  const bool ns = H->prm.variant != TPC_SPD;
+  const int reps = 3;
+  for (int rep = 0; rep <= reps; ++rep) {
+    if (rep == 1) cudaEventRecord(ev[0], s);
+    if constexpr (sizeof(T) == 4) {
+      if (L.f32reg) {
+        f32p::launch_fwd(a, L.fwd_blocks, s);
+        if (!passes_only) {
+          if (ns) f32p::launch_mid<true>(a, L.mid_blocks, s);
+          else f32p::launch_mid<false>(a, L.mid_blocks, s);
+        }
+        f32p::launch_inv(a, L.fwd_blocks, s);
+        continue;
+      }
+    }
+    launch_fwd_strided<T>(a, L.fwd_blocks, L.smem_strided, s);
+    if (!passes_only) {
+      if (ns) launch_mid_pair<T, true>(a, L.mid_blocks, L.smem_mid, s);
+      else launch_mid_pair<T, false>(a, L.mid_blocks, L.smem_mid, s);
+    }
+    launch_inv_strided<T>(a, L.fwd_blocks, L.smem_strided, s);
+  }
+  cudaEventRecord(ev[1], s);
+  float t = -1.0f;
+  if (cudaEventSynchronize(ev[1]) != cudaSuccess || cudaGetLastError() != cudaSuccess ||
+      cudaEventElapsedTime(&t, ev[0], ev[1]) != cudaSuccess)
+    return -1.0f;
+  H->launches += 3 * (reps + 1);
+  return t / reps;
+}
+
+// Set-up autotuner of the three-pass levels (tpc_params.autotune). Candidates: the
+// factorisations m = R1 x L with log2 L the rule's value or one off it (2^7 <= L <= 2^12,
+// 2^6 <= R1 <= 2^11) and, for the general kernels, every tile width of the strided passes
+// (1 to 16 columns, tile <= 8192 entries); an FP32 factorisation the register-resident
+// kernels take uses them. The width is chosen on the two strided passes, the factorisation on
+// the whole product; the rule's choice stays unless another is more than 3 % faster.
 template <typename T>
 int autotune_levels(tpc_handle* H, Hier<T>& G, bool only_finest) {
   cudaStream_t s = H->stream;
@@ -836,54 +920,63 @@ int autotune_levels(tpc_handle* H, Hier<T>& G, bool only_finest) {
   for (size_t li = 0; li < G.lev.size() && rc == TPC_OK; ++li) {
     if (only_finest && li > 0) break;
     DevLevel<T>& L = G.lev[li];
-    if (L.logR1 == 0 || !L.sA || L.f32reg) continue;
+    if (L.logR1 == 0 || !L.sA) continue;
+    const bool band = L.bd != nullptr;
     const std::pair<int, int> key((int)sizeof(T), L.logm);
-    const auto hit = g_tuned_logC.find(key);
-    if (hit != g_tuned_logC.end()) {
-      L.logC = hit->second;
-      L.fwd_blocks = 1 << (L.logL - L.logC);
-      L.smem_strided =
-          sizeof(c2<T>) * (size_t)(tw_slots<T>() + padded_size(1 << (L.logR1 + L.logC)));
+    const auto hit = g_tuned.find(key);
+    if (hit != g_tuned.end()) {
+      const TunedLevel& t = hit->second;
+      if (t.reg && (band || sizeof(T) != 4)) apply_split<T>(L, t.logL, -1, false);
+      else apply_split<T>(L, t.logL, t.logC, t.reg);
       continue;
     }
     for (T* v : {G.e[li], G.f[li], G.t[li]})
       if (cudaMemsetAsync(v, 0, (size_t)L.n * sizeof(T), s) != cudaSuccess) rc = TPC_ECUDA;
-    const int keep = L.logC;
-    float t[5] = {-1.0f, -1.0f, -1.0f, -1.0f, -1.0f};
-    for (int c = 0; c <= 4 && L.logR1 + c <= LOG_TILE_MAX && c <= L.logL && rc == TPC_OK; ++c) {
-      L.logC = c;
-      L.fwd_blocks = 1 << (L.logL - c);
-      L.smem_strided =
-          sizeof(c2<T>) * (size_t)(tw_slots<T>() + padded_size(1 << (L.logR1 + L.logC)));
-      LevelArgs<T> a = level_args<T>(G, L);
-      a.x = G.e[li];
-      a.f = G.f[li];
-      a.y = G.t[li];
-      a.pro = PRO_NONE;
-      a.epi = EPI_RESID;
-      for (int rep = 0; rep < 4; ++rep) {  // one warm-up, three timed
-        if (rep == 1) cudaEventRecord(ev[0], s);
-        launch_fwd_strided<T>(a, L.fwd_blocks, L.smem_strided, s);
-        launch_inv_strided<T>(a, L.fwd_blocks, L.smem_strided, s);
+    const int rule_logL = L.logL;
+    TunedLevel best{L.logL, L.logC, L.f32reg}, rule = best;
+    float best_t = -1.0f, rule_t = -1.0f;
+    for (int d : {0, 1, -1}) {
+      const int logL = rule_logL + d, logR1 = L.logm - logL;
+      if (rc != TPC_OK) break;
+      if (d != 0 && (logL < 7 || logL > LOG_LMAX || logR1 < 6 || logR1 > LOG_R1_MAX)) continue;
+      const bool reg = sizeof(T) == 4 && f32p::eligible(L.logm, logR1, logL, band);
+      int logC = f32p::LOG_CT;
+      if (!reg) {
+        // the tile width on the strided passes: the rule's unless another is 3 % faster
+        apply_split<T>(L, logL, -1, false);
+        const int keep = L.logC;
+        float tw[5] = {-1.0f, -1.0f, -1.0f, -1.0f, -1.0f};
+        for (int c = 0; c <= 4 && logR1 + c <= LOG_TILE_MAX && c <= logL; ++c) {
+          apply_split<T>(L, logL, c, false);
+          tw[c] = time_product<T>(H, G, li, true, ev);
+          if (tw[c] < 0.0f) rc = TPC_ECUDA;
+        }
+        logC = keep;
+        for (int c = 0; c < 5; ++c)
+          if (tw[c] >= 0.0f && (tw[logC] < 0.0f || tw[c] < tw[logC])) logC = c;
+        if (tw[keep] >= 0.0f && tw[keep] <= 1.03f * tw[logC]) logC = keep;
       }
-      cudaEventRecord(ev[1], s);
-      if (cudaEventSynchronize(ev[1]) != cudaSuccess || cudaGetLastError() != cudaSuccess ||
-          cudaEventElapsedTime(&t[c], ev[0], ev[1]) != cudaSuccess) {
+      apply_split<T>(L, logL, logC, reg);
+      const float t = time_product<T>(H, G, li, false, ev);
+      if (t < 0.0f) {
         rc = TPC_ECUDA;
         break;
       }
-      H->launches += 8;
+      if (d == 0) {
+        rule_t = t;
+        rule = TunedLevel{logL, logC, reg};
+      }
+      if (best_t < 0.0f || t < best_t) {
+        best_t = t;
+        best = TunedLevel{logL, logC, reg};
+      }
     }
-    // the fastest width, unless the rule's own width is within 3 % of it (timing noise)
-    int best = keep;
-    for (int c = 0; c < 5; ++c)
-      if (t[c] >= 0.0f && (t[best] < 0.0f || t[c] < t[best])) best = c;
-    if (t[keep] >= 0.0f && t[keep] <= 1.03f * t[best]) best = keep;
-    if (rc == TPC_OK) g_tuned_logC[key] = best;
-    L.logC = best;
-    L.fwd_blocks = 1 << (L.logL - best);
-    L.smem_strided =
-        sizeof(c2<T>) * (size_t)(tw_slots<T>() + padded_size(1 << (L.logR1 + L.logC)));
+    // the rule's factorisation (with its tuned width) unless another is more than 3 % faster
+    if (rule_t >= 0.0f && best.logL != rule_logL && best_t > rule_t / 1.03f) best = rule;
+    if (rc == TPC_OK) {
+      apply_split<T>(L, best.logL, best.logC, best.reg);
+      g_tuned[key] = TunedLevel{L.logL, L.logC, L.f32reg};
+    }
   }
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
@@ -1535,6 +1628,44 @@ int tpc_export_level(const tpc_handle* H, int level, double* host_buf, size_t ca
   if (cap < *need) return TPC_EINVAL;
   export_level(F, host_buf);
   return TPC_OK;
+}
+
+int tpc_tune_get(int word, int logm, int* logL, int* logC, int* reg) {
+  if ((word != 4 && word != 8) || !logL || !logC || !reg) return TPC_EINVAL;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  const auto hit = g_tuned.find(std::make_pair(word, logm));
+  if (hit == g_tuned.end()) return 0;
+  *logL = hit->second.logL;
+  *logC = hit->second.logC;
+  *reg = hit->second.reg ? 1 : 0;
+  return 1;
+}
+
+int tpc_tune_set(int word, int logm, int logL, int logC, int reg) {
+  const int logR1 = logm - logL;
+  if ((word != 4 && word != 8) || logm < 13 || logm > 23 || logL < 7 || logL > LOG_LMAX ||
+      logR1 < 6 || logR1 > LOG_R1_MAX || (reg != 0 && reg != 1)) {
+    set_host_error("tpc_tune_set: factorisation out of range");
+    return TPC_EINVAL;
+  }
+  if (reg) {
+    if (word != 4 || !f32p::eligible(logm, logR1, logL, false)) {
+      set_host_error("tpc_tune_set: the register-resident kernels do not take this factorisation");
+      return TPC_EINVAL;
+    }
+    logC = f32p::LOG_CT;
+  } else if (logC < 0 || logC > 4 || logR1 + logC > LOG_TILE_MAX || logC > logL) {
+    set_host_error("tpc_tune_set: tile width out of range");
+    return TPC_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[std::make_pair(word, logm)] = TunedLevel{logL, logC, reg != 0};
+  return TPC_OK;
+}
+
+void tpc_tune_reset(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned.clear();
 }
 
 int tpc_time_level_kernels(tpc_handle* H, int level, int reps, const double* x_dev,

@@ -56,8 +56,9 @@ __device__ __forceinline__ bool grid_sync(unsigned* count, unsigned target, int*
   return ok != 0;
 }
 
-// The contiguous-block body as the lone launch runs it for the levels taken here (log2 L <= 9:
-// the general instance; launch_mid_pair picks compile-time L only for log2 L = 10..12).
+// The contiguous-block body of the persistent kernel: the general instance, which the lone
+// launch (launch_mid_pair) also runs for log2 L <= 9; levels with larger L (compile-time
+// instances) take the three-launch form (use_coop).
 template <typename T, bool NS>
 __device__ __forceinline__ void mid_pair_dispatch(const LevelArgs<T>& a, int blk) {
   mid_body<T, MID_PAIR, NS>(a, blk);
@@ -106,14 +107,15 @@ __global__ void __launch_bounds__(fft_threads<T>(), MINB)
   copy_args<T>(&la, &args[inst]);
   fwd_strided_body<T, IN_PACK, PRO>(la, (int)blockIdx.x);
 }
-template <typename T, bool NS>
+// LOGL_CT as launch_mid_pair picks it (the FP32 instances with log2 L = 10..12, else 0).
+template <typename T, bool NS, int LOGL_CT>
 __global__ void __launch_bounds__(fft_threads<T>(), mid_min_blocks<T>())
     k_batch_mid(const LevelArgs<T>* __restrict__ args, const int* __restrict__ live) {
   __shared__ __align__(16) LevelArgs<T> la;
   const int inst = blockIdx.y;
   if (!live[inst]) return;
   copy_args<T>(&la, &args[inst]);
-  mid_pair_dispatch<T, NS>(la, (int)blockIdx.x);
+  mid_body<T, MID_PAIR, NS, LOGL_CT>(la, (int)blockIdx.x);
 }
 template <typename T, int EPI, int MINB>
 __global__ void __launch_bounds__(fft_threads<T>(), MINB)
@@ -347,7 +349,7 @@ bool eligible(const tpc_handle* H) {
   if (!S.bottom || S.bottom_li < 1) return false;
   for (int li = 0; li < S.bottom_li; ++li) {
     const DevLevel<float>& L = S.lev[li];
-    if (L.f32reg || L.bd || !L.sA || (L.logR1 > 0 && L.logL > 9)) return false;
+    if (L.f32reg || L.bd || !L.sA) return false;
   }
   return true;
 }
@@ -404,7 +406,9 @@ int three_pass_mb(tpc_batch* B, tpc_batch::Group& g, const DevLevel<float>& L,
   const int nt = fft_threads<float>();
   const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
   auto kf = k_batch_fwd<float, PRO, MB>;
-  auto km = k_batch_mid<float, NS>;
+  auto km = L.logL == 12 ? k_batch_mid<float, NS, 12>
+            : L.logL == 11 ? k_batch_mid<float, NS, 11>
+            : L.logL == 10 ? k_batch_mid<float, NS, 10> : k_batch_mid<float, NS, 0>;
   auto ki = k_batch_inv<float, EPI, MB>;
   TPCB_CUDA(B, cudaFuncSetAttribute(kf, A, (int)L.smem_strided));
   TPCB_CUDA(B, cudaFuncSetAttribute(km, A, (int)L.smem_mid));
@@ -427,10 +431,9 @@ int three_pass(tpc_batch* B, tpc_batch::Group& g, int li, const LevelArgs<float>
 
 // Whether level li of the group runs its products as one cooperative launch (else three).
 bool use_coop(const tpc_batch* B, const tpc_batch::Group& g, int li) {
+  // the persistent kernel holds the general contiguous-block body only (log2 L <= 9)
+  if (g.lev[li]->logL > 9) return false;
   if (B->product_mode == TPC_BATCH_COOPERATIVE) return true;
-  if (B->product_mode == TPC_BATCH_THREE_PASS) return false;
-  (void)g;
-  (void)li;
   return false;
 }
 

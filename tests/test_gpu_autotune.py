@@ -1,9 +1,10 @@
-"""The setup-time tile-width autotuner of the strided FFT passes. The width decides which block
-transforms which column (every column's transform is the same); only the order of the
-per-block partial sums of the Cross dot follows the block count. So a solve with the tuned
-widths agrees with the fixed rule's to rounding (FP64), or within the solver tolerance
-(mixed precision), and two handles of one process with the same level sizes use the same
-widths and agree bitwise."""
+"""The set-up autotuner of the three-pass FFT products: the factorisation m = R1 x L of every
+level's transform and the tile width of its strided passes. The factorisation changes the
+order of the radix steps (every choice is the same transform, to rounding) and the width which
+block transforms which column; so a solve with the tuned plans agrees with the fixed rule's to
+rounding (FP64), or within the solver tolerance (mixed precision), and two handles of one
+process with the same level sizes use the same plans (the process-wide table) and agree
+bitwise. Every candidate plan is checked against the oracle in tests/test_gpu_fft_plans.py."""
 import numpy as np
 import pytest
 
