@@ -831,26 +831,33 @@ int build_bottom(tpc_handle* H, Hier<T>& G) {
   }
   bp.cinv = G.coarse_inv;
   bp.geo = G.geo;
-  bp.rc = G.t[ic - 1];
-  bp.fc = G.f[ic];
-  bp.ec = G.e[ic];
   bp.nc = (int)G.lev[ic].n;
+  // shared-memory layout of the bottom's vectors (16-byte aligned each)
+  bp.tr_elems = padded_size(1 << G.lev[li0].logm);
+  long long off = 0;
+  auto take = [&off](long long n) {
+    const long long o = off;
+    off += (n + 3) / 4 * 4;
+    return (int)o;
+  };
+  for (int j = 0; j < np; ++j) {
+    const long long n = G.lev[li0 + j].n;
+    bp.off_e[j] = take(n);
+    bp.off_f[j] = take(n);
+    bp.off_t[j] = take(n);
+  }
+  bp.off_fc = take(bp.nc);
+  bp.off_ec = take(bp.nc);
+  const size_t smem = sizeof(c2<T>) * (size_t)(tw_slots<T>() + bp.tr_elems) + sizeof(T) * (size_t)off;
+  if (smem > 150 * 1024) return TPC_OK;  // beyond the kernels' shared-memory limit: no bottom
   TPC_TRY(dalloc(H, &G.bottom, 1));
   TPC_CUDA(H, cudaMemcpyAsync(G.bottom, &bp, sizeof(bp), cudaMemcpyHostToDevice, H->stream));
   TPC_CUDA(H, cudaStreamSynchronize(H->stream));
   G.bottom_li = li0;
-  G.bottom_smem = sizeof(c2<T>) * (size_t)(tw_slots<T>() + padded_size(1 << G.lev[li0].logm));
+  G.bottom_smem = smem;
   return TPC_OK;
 }
 
-// Column-group autotuner for the strided passes of one hierarchy: for every level it times the
-// forward and inverse strided passes (no prologue, residual epilogue, on the level's own work
-// vectors, zeroed) for each tile width 2^logC that fits (tile <= 2^LOG_TILE_MAX entries) and
-// keeps the fastest. The width changes which block transforms which column, not the
-// transforms; only the order in which the per-block partial sums of the Cross dot q.v +
-// zeta.w_bar are added follows the number of blocks. So that every handle of a process computes
-// bit for bit the same products (a solve alone and in a batch or the server agree exactly), the
-// choice is made once per (precision, level size) and kept for the process.
 std::mutex g_tune_mu;
 // (sizeof(T), log2 m) -> the chosen factorisation and tile width, shared by every handle of
 // the process so that a solve alone, in a batch and in the server computes the same

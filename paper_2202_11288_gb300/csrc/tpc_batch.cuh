@@ -541,6 +541,10 @@ int build_group(tpc_batch* B, tpc_batch::Group& g) {
   g.ns = H0->prm.variant != TPC_SPD;
   g.nl = S0.bottom_li;
   g.bottom_smem = S0.bottom_smem;
+  TPCB_CUDA(B, cudaFuncSetAttribute(k_batch_bottom<float, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 150 * 1024));
+  TPCB_CUDA(B, cudaFuncSetAttribute(k_batch_bottom<float, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 150 * 1024));
   g.n = H0->d.lev[0].n;
   g.box_nblk = H0->box_args.nblk;
   g.box_gx = (int)std::min<long long>((H0->box_args.N + box::NT - 1) / box::NT, 4 * 152);

@@ -1015,10 +1015,13 @@ template <typename T> struct BottomPlan {
   LevelArgs<T> post[BOTTOM_MAX_LEVELS];
   const T* cinv;                         // coarsest inverse (nc x nc)
   int geo;                               // transfer (see LevelArgs)
-  const T* rc;                           // residual of the level above the coarsest
-  T* fc;                                 // coarsest right-hand side
-  T* ec;                                 // coarsest solution
-  int nc;
+  int nc;                                // coarsest unknowns
+  // The bottom levels' vectors e, f, t and the coarsest f, e live in shared memory (element
+  // offsets past the transform area of tr_elems complex values); only the input (the residual
+  // of the level above, pre[0].rfine) and the output (post[0].y) are global.
+  int tr_elems;
+  int off_e[BOTTOM_MAX_LEVELS], off_f[BOTTOM_MAX_LEVELS], off_t[BOTTOM_MAX_LEVELS];
+  int off_fc, off_ec;
 };
 
 template <typename T>
@@ -1037,29 +1040,49 @@ __device__ __forceinline__ void vcycle_bottom_body(const BottomPlan<T>* bp) {
   __shared__ T red[FFT_THREADS / 32];
   __shared__ __align__(16) LevelArgs<T> la;
   const int nlev = bp->nlev;
+  T* vec = reinterpret_cast<T*>(s + bp->tr_elems);
   const c2<T>* tw = step_table<T>(tab, bp->pre[0].twL);
   for (int i = 0; i < nlev; ++i) {
     copy_args<T>(&la, &bp->pre[i]);
+    if (threadIdx.x == 0) {
+      T* e = vec + bp->off_e[i];
+      T* f = vec + bp->off_f[i];
+      if (i > 0) la.rfine = vec + bp->off_t[i - 1];
+      la.fout = f;
+      la.xout = e;
+      la.x = e;
+      la.f = f;
+      la.y = vec + bp->off_t[i];
+    }
+    __syncthreads();
     mid_core<T, MID_WHOLE, NS, 0, 0, PRO_RESTRICT, EPI_RESID, 2>(la, tw, s, red, 0, 0);
     __syncthreads();
   }
   {
-    T* fs = reinterpret_cast<T*>(s);
+    T* fs = vec + bp->off_fc;
+    T* es = vec + bp->off_ec;
+    const T* rc = vec + bp->off_t[nlev - 1];
     const int nc = bp->nc;
-    for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-      fs[i] = restrict_at<T>(bp->rc, i, (nc - 1) / 2, bp->geo);
-      bp->fc[i] = fs[i];
-    }
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) fs[i] = restrict_at<T>(rc, i, (nc - 1) / 2, bp->geo);
     __syncthreads();
     for (int i = threadIdx.x; i < nc; i += blockDim.x) {
       T acc = 0;
       for (int j = 0; j < nc; ++j) acc = fma(bp->cinv[(long long)i * nc + j], fs[j], acc);
-      bp->ec[i] = acc;
+      es[i] = acc;
     }
     __syncthreads();
   }
   for (int i = nlev - 1; i >= 0; --i) {
     copy_args<T>(&la, &bp->post[i]);
+    if (threadIdx.x == 0) {
+      T* e = vec + bp->off_e[i];
+      la.x = e;
+      la.xout = e;
+      la.f = vec + bp->off_f[i];
+      la.ec = (i + 1 == nlev) ? vec + bp->off_ec : vec + bp->off_t[i + 1];
+      if (i > 0) la.y = vec + bp->off_t[i];  // post[0].y: the global t of the top bottom level
+    }
+    __syncthreads();
     mid_core<T, MID_WHOLE, NS, 0, 0, PRO_PROLONG, EPI_JACOBI, 2>(la, tw, s, red, 0, 0);
     __syncthreads();
   }
