@@ -124,7 +124,7 @@ def parse():
     ap.add_argument("--no-twod", action="store_true", help="skip the 2-D measurement")
     ap.add_argument("--batch", type=int, default=512,
                     help="instances of the batched-uneven measurement (0 = skip it)")
-    ap.add_argument("--serve-rates", default="50,100,200,300,500",
+    ap.add_argument("--serve-rates", default="50,100,200,500,1000,2000",
                     help="Poisson arrival rates (req/s) of the serving measurement ('' = skip)")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="arrival window per rate of the serving measurement")
@@ -560,6 +560,11 @@ def serve_keys():
     return one, two
 
 
+# Requests a client keeps outstanding at most (their host buffers are pinned); arrivals beyond
+# it are turned away and counted as rejected.
+MAX_OUTSTANDING = 2048
+
+
 def serve_size(key):
     dim, K = key[0], key[3]
     n1 = (1 << (K + 1)) - 1
@@ -596,7 +601,8 @@ def time_serving(tpc, torch, args):
                        "(SPD, geometric transfer, delta in {0.05,0.2}); 2-D K in 4..10, delta in "
                        "{0.1,0.2}, SPD/nonsym, constant kernel; uniform[-1,1) right-hand sides; "
                        "mixed precision, tol 1e-10, host buffers (pinned); hierarchies resident "
-                       f"(HBM budget 150 GB, 32 slots); {args.serve_seconds:g} s of arrivals per rate",
+                       f"(HBM budget 150 GB, 32 slots); {args.serve_seconds:g} s of arrivals per rate; "
+                       f"at most {MAX_OUTSTANDING} requests outstanding (later arrivals rejected)",
            "keys": len(keys), "rates": []}
     try:
         owner = {}
@@ -621,7 +627,7 @@ def time_serving(tpc, torch, args):
         for rate in rates:
             n_req = max(1, int(rate * args.serve_seconds))
             gaps = rng.exponential(1.0 / rate, n_req)
-            lat, bad = [], 0
+            lat, bad, rejected = [], 0, 0
             srv.stats(reset=True)
             start = time.perf_counter()
             t_next = start
@@ -638,6 +644,9 @@ def time_serving(tpc, torch, args):
                         break
                     time.sleep(min(dt, 0.0005))
                 key = pick()
+                if len(owner) >= MAX_OUTSTANDING:   # the client's queue is full: turned away
+                    rejected += 1
+                    continue
                 dim, v, d, K, kk, a, tr = key
                 n = serve_size(key)
                 x = xbuf(n)
@@ -652,8 +661,9 @@ def time_serving(tpc, torch, args):
             wall = time.perf_counter() - start
             st = srv.stats()
             lat_ms = np.array(lat) * 1000.0
-            out["rates"].append({"rate_req_s": rate, "requests": n_req,
-                                 "throughput_req_s": n_req / wall,
+            done = n_req - rejected
+            out["rates"].append({"rate_req_s": rate, "requests": n_req, "rejected": rejected,
+                                 "throughput_req_s": done / wall,
                                  "p50_ms": float(np.percentile(lat_ms, 50)),
                                  "p99_ms": float(np.percentile(lat_ms, 99)),
                                  "failed": int(bad),
