@@ -387,7 +387,10 @@ def time_batch(tpc, torch, args, rank):
     solvers = [tpc.Solver(d, 2.0 ** -K, variant=v, kernel=kk, kernel_a=a, precision=tpc.TPC_MIXED,
                           transfer=(tpc.TPC_TRANSFER_GEOMETRIC if kk else tpc.TPC_TRANSFER_PAPER))
                for _, K, d, v, kk, a in s1]
-    twod = [tpc.Solver2D(d, 2.0 ** -K, variant=v, precision=tpc.TPC_MIXED) for _, K, d, v, _, _ in s2]
+    # the 2-D instances take the FGMRES outer iteration (6 steps a cycle): those with r = 1 or 2
+    # need 30 to 110 V-cycles of the stationary one
+    twod = [tpc.Solver2D(d, 2.0 ** -K, variant=v, precision=tpc.TPC_MIXED,
+                         outer=tpc.TPC_OUTER_FGMRES, inner_cycles=6) for _, K, d, v, _, _ in s2]
     sizes = [S.n for S in solvers] + [S.nn for S in twod]
     bs = [torch.tensor(uniform_pm1(n, 7000 + i), device="cuda") for i, n in enumerate(sizes)]
     xs = [torch.zeros_like(b) for b in bs]
@@ -409,8 +412,9 @@ def time_batch(tpc, torch, args, rank):
            "workload": "512 instances of 2^10..2^18 unknowns (log2 uniform in 10..18; even "
                        "exponents 2-D with probability 1/2), delta uniform in [0.02,0.25], "
                        "SPD/nonsym, 1-D: constant kernel or (probability 1/2) fractional a "
-                       "uniform in [0.1,0.4] with the geometric transfer, 2-D: constant kernel; "
-                       "mixed precision, tol 1e-10; one tpc_batch_solve per step (host clock)"}
+                       "uniform in [0.1,0.4] with the geometric transfer, 2-D: constant kernel "
+                       "with the FGMRES(6) outer iteration; mixed precision, tol 1e-10; one "
+                       "tpc_batch_solve per step (host clock)"}
     B.close()
     for S in solvers + twod:
         S.close()

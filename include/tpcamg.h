@@ -384,7 +384,8 @@ int tpc_apply_noalloc(long long N, const double* tA, const double* tB, const dou
  * section 3.1 transfers on each axis (R (x) R, P (x) P), Galerkin levels (eq. (3.2), of the form
  * A_k (x) Q_k + Q_k (x) A_k - A_k (x) A_k / (12 r)), damped Jacobi with the diagonal of each level
  * and a dense solve at the coarsest level; products are FFT products (eq. (3.4)) along rows and
- * columns. precision TPC_MIXED runs FP32 V-cycles inside FP64 refinement as tpc_solve does. */
+ * columns. precision TPC_MIXED runs FP32 V-cycles inside FP64 refinement as tpc_solve does;
+ * outer = TPC_OUTER_FGMRES runs the flexible GMRES outer iteration of tpc_params.outer. */
 
 /* Set up on the caller's stream (NULL: a stream of the handle). Needs variant TPC_SPD or
  * TPC_NONSYM, kernel 0, the paper's transfer (else TPC_ENOTSUP), h = 2^-K with K <= 11 and

@@ -242,6 +242,14 @@ struct tpc2d_handle {
   cudaEvent_t ev = nullptr;
   double* hb = nullptr;               // staging buffers of solves with host buffers (on demand)
   double* hx = nullptr;
+  // TPC_OUTER_FGMRES: the Krylov basis (FP32 in TPC_MIXED, else FP64), scalars, partial sums
+  float* kv32 = nullptr;
+  float* kz32 = nullptr;
+  double* kv64 = nullptr;
+  double* kz64 = nullptr;
+  long long kld = 0;
+  tpc::krylov::KState* ks = nullptr;
+  double* kpart = nullptr;
   long long launches = 0;
   int last_cycles = 0;
   std::vector<void*> allocs;
@@ -379,7 +387,20 @@ void iteration2(tpc2d_handle* H, int cycles) {
   const long long nn = H->D.lev[0].nn;
   const int g = grid2(nn);
   cudaStream_t s = H->stream;
-  if (H->prm.precision == TPC_MIXED) {
+  if (H->prm.outer == TPC_OUTER_FGMRES) {
+    // one restart cycle of flexible GMRES, V-cycles as the preconditioner (as the 1-D solver)
+    if (H->prm.precision == TPC_MIXED) {
+      H->launches += fgmres_cycle<float>(
+          s, nn, H->kld, H->r0, H->sumsq, H->u, H->kv32, H->kz32, H->ks, H->kpart, cycles,
+          [&](const float* v) -> const float* { return vcycle2<float>(H, 0, v, nullptr); },
+          [&](const float* x, float* y) { matvec2<float>(H, 0, x, nullptr, y, EPI_APPLY, nullptr); });
+    } else {
+      H->launches += fgmres_cycle<double>(
+          s, nn, H->kld, H->r0, H->sumsq, H->u, H->kv64, H->kz64, H->ks, H->kpart, cycles,
+          [&](const double* v) -> const double* { return vcycle2<double>(H, 0, v, nullptr); },
+          [&](const double* x, double* y) { matvec2<double>(H, 0, x, nullptr, y, EPI_APPLY, nullptr); });
+    }
+  } else if (H->prm.precision == TPC_MIXED) {
     float* f32 = H->S.lev[0].f;
     k_to_f32_scaled<<<g, NTHREADS, 0, s>>>(H->r0, f32, nn, H->sumsq);
     const float* ec = vcycle2<float>(H, 0, f32, nullptr);
@@ -552,7 +573,9 @@ int solve2_step(Solve2State& st) {
   }
   // inner cycles: the full count first, then the fewest expected to reach tol / 4 at the rate
   // per cycle measured by the previous iteration (as the 1-D mixed solve)
-  const int full = H->prm.precision == TPC_MIXED ? H->prm.inner_cycles : 1;
+  const int full = (H->prm.precision == TPC_MIXED || H->prm.outer == TPC_OUTER_FGMRES)
+                       ? H->prm.inner_cycles
+                       : 1;
   int c = full;
   if (full > 1 && st.it > 0 && st.cycles > 0) {
     const double red = st.rel / st.rel_prev;
@@ -619,6 +642,13 @@ int tpc2d_setup(const tpc_params* p, double delta, double h, void* cuda_stream,
   tpc_params p1 = *p;
   p1.autotune = 0;
   p1.box_residual = 0;
+  p1.outer = TPC_OUTER_VCYCLE;  // the internal 1-D handle only holds the 1-D levels
+  if ((p->outer != TPC_OUTER_VCYCLE && p->outer != TPC_OUTER_FGMRES) ||
+      (p->outer == TPC_OUTER_FGMRES && (p->inner_cycles < 1 || p->inner_cycles > 32))) {
+    set_host_error("outer must be TPC_OUTER_VCYCLE or TPC_OUTER_FGMRES (inner_cycles 1..32)");
+    delete H;
+    return TPC_EINVAL;
+  }
   int rc = tpc_setup(&p1, delta, h, 0, cuda_stream, &H->h1);
   if (rc != TPC_OK) {
     delete H;
@@ -658,12 +688,26 @@ int tpc2d_setup(const tpc_params* p, double delta, double h, void* cuda_stream,
       TPC_TRY(alloc2(H, &H->res32, (size_t)nn));
       TPC_TRY(alloc2(H, &H->acc32, (size_t)nn));
     }
+    if (H->prm.outer == TPC_OUTER_FGMRES) {
+      const int S = H->prm.inner_cycles;
+      H->kld = (nn + 63) / 64 * 64;
+      if (mixed) {
+        TPC_TRY(alloc2(H, &H->kv32, (size_t)(S + 1) * H->kld));
+        TPC_TRY(alloc2(H, &H->kz32, (size_t)S * H->kld));
+      } else {
+        TPC_TRY(alloc2(H, &H->kv64, (size_t)(S + 1) * H->kld));
+        TPC_TRY(alloc2(H, &H->kz64, (size_t)S * H->kld));
+      }
+      TPC_TRY(alloc2(H, &H->ks, 1));
+      TPC_TRY(alloc2(H, &H->kpart, (size_t)(tpc::krylov::MAXS + 1) * tpc::krylov::KNB));
+    }
     TPC_TRY(alloc2(H, &H->sumsq_part, NORM_BLOCKS));
     TPC_TRY(alloc2(H, &H->sumsq, 1));
     TPC2_CUDA(H, cudaMallocHost(&H->sumsq_host, sizeof(double)));
     TPC2_CUDA(H, cudaEventCreateWithFlags(&H->ev, cudaEventDisableTiming));
     TPC2_CUDA(H, cudaStreamSynchronize(H->stream));
-    for (int c = 1; c <= (mixed ? H->prm.inner_cycles : 1); ++c) TPC_TRY(graph2(H, c));
+    const bool many = mixed || H->prm.outer == TPC_OUTER_FGMRES;
+    for (int c = 1; c <= (many ? H->prm.inner_cycles : 1); ++c) TPC_TRY(graph2(H, c));
     return TPC_OK;
   };
   rc = setup();

@@ -508,37 +508,49 @@ void enqueue_sumsq(tpc_handle* H, const double* r, long long n) {
   launch_k(k_sumsq_final, 1, 32, 0, H->stream, H->sumsq_part, NORM_BLOCKS, H->sumsq);
 }
 
-// One restart cycle of flexible GMRES with `steps` steps (tpc_krylov.cuh) on the FP64
-// residual H->r0 (norm in H->sumsq), in the precision of G; u += Z y.
-template <typename T>
-void enqueue_fgmres_cycle(tpc_handle* H, Hier<T>& G, T* V, T* Z, int steps) {
+// One restart cycle of flexible GMRES with `steps` steps (tpc_krylov.cuh) on the FP64 residual
+// r0 of n unknowns (its squared norm in sumsq): basis vectors V (steps + 1) and Z (steps), ld
+// apart, of the V-cycles' precision T; vcycle(v) enqueues one V-cycle on right-hand side v and
+// returns where its result is, matvec(x, y) enqueues y = A x; u += Z y. Shared by the 1-D and
+// 2-D solvers.
+template <typename T, typename VC, typename MV>
+long long fgmres_cycle(cudaStream_t s, long long n, long long ld, const double* r0,
+                       const double* sumsq, double* u, T* V, T* Z, krylov::KState* ks,
+                       double* kpart, int steps, VC vcycle, MV matvec) {
   using namespace krylov;
-  const long long n = H->d.lev[0].n;
-  const long long ld = H->kld;
   const int g = grid_for(n);
-  cudaStream_t s = H->stream;
-  launch_k(k_kry_start<T>, g, NTHREADS, 0, s, H->r0, V, n, H->sumsq, H->ks);
-  H->launches += 1;
+  long long launches = 0;
+  launch_k(k_kry_start<T>, g, NTHREADS, 0, s, r0, V, n, sumsq, ks);
+  ++launches;
   for (int j = 0; j < steps; ++j) {
     T* vj = V + (size_t)j * ld;
     T* w = V + (size_t)(j + 1) * ld;
     T* zj = Z + (size_t)j * ld;
-    const T* ec = enqueue_vcycle<T>(H, G, 0, vj, nullptr);
+    const T* ec = vcycle(vj);
     launch_k(k_copy<T>, g, NTHREADS, 0, s, ec, zj, n);
-    matvec<T>(H, G, 0, zj, nullptr, w, EPI_APPLY, false);
+    matvec(zj, w);
     for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
-      launch_k(k_kry_dot_partial<T>, dim3(KNB, j + 1), 256, 0, s, V, ld, w, n, H->kpart);
-      launch_k(k_kry_dot_final, j + 1, 32, 0, s, H->kpart, KNB, H->ks, j, pass);
-      launch_k(k_kry_axpy<T>, g, NTHREADS, 0, s, w, V, ld, j + 1, H->ks, n);
+      launch_k(k_kry_dot_partial<T>, dim3(KNB, j + 1), 256, 0, s, V, ld, w, n, kpart);
+      launch_k(k_kry_dot_final, j + 1, 32, 0, s, kpart, KNB, ks, j, pass);
+      launch_k(k_kry_axpy<T>, g, NTHREADS, 0, s, w, V, ld, j + 1, ks, n);
     }
-    launch_k(k_kry_sumsq_partial<T>, KNB, 256, 0, s, w, n, H->kpart);
-    launch_k(k_kry_rotate, 1, 32, 0, s, H->kpart, KNB, H->ks, j);
-    launch_k(k_kry_scale<T>, g, NTHREADS, 0, s, w, n, H->ks);
-    H->launches += 11;
+    launch_k(k_kry_sumsq_partial<T>, KNB, 256, 0, s, w, n, kpart);
+    launch_k(k_kry_rotate, 1, 32, 0, s, kpart, KNB, ks, j);
+    launch_k(k_kry_scale<T>, g, NTHREADS, 0, s, w, n, ks);
+    launches += 11;
   }
-  launch_k(k_kry_solve, 1, 32, 0, s, H->ks, steps);
-  launch_k(k_kry_update<T>, g, NTHREADS, 0, s, H->u, Z, ld, steps, H->ks, n);
-  H->launches += 2;
+  launch_k(k_kry_solve, 1, 32, 0, s, ks, steps);
+  launch_k(k_kry_update<T>, g, NTHREADS, 0, s, u, Z, ld, steps, ks, n);
+  return launches + 2;
+}
+
+template <typename T>
+void enqueue_fgmres_cycle(tpc_handle* H, Hier<T>& G, T* V, T* Z, int steps) {
+  const long long n = H->d.lev[0].n;
+  H->launches += fgmres_cycle<T>(
+      H->stream, n, H->kld, H->r0, H->sumsq, H->u, V, Z, H->ks, H->kpart, steps,
+      [&](const T* v) -> const T* { return enqueue_vcycle<T>(H, G, 0, v, nullptr); },
+      [&](const T* x, T* y) { matvec<T>(H, G, 0, x, nullptr, y, EPI_APPLY, false); });
 }
 
 // One outer iteration.

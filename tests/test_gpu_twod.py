@@ -173,3 +173,60 @@ def test_setup_rejects_what_it_does_not_build():
     with pytest.raises(tpc.TpcError) as ei:
         tpc.Solver2D(0.1, 2.0 ** -8, variant=tpc.TPC_WEAKLY, kernel_a=0.5)
     assert ei.value.code == tpc.TPC_EINVAL
+
+
+@pytest.mark.parametrize("variant", [SPD, NONSYM])
+def test_fgmres_restart_cycle_matches_oracle(oracle5, variant):
+    """The flexible GMRES outer iteration of the 2-D solver (FP64): the iterate after one restart
+    cycle of 4 steps equals the oracle's (oracle/krylov.py with the 2-D oracle V-cycle), and the
+    solve reaches 1e-10 in no more V-cycles than the stationary iteration."""
+    from oracle import krylov
+    K, delta = 5, 0.125
+    H = oracle5[variant]
+    A = H.A[K]
+    b = uniform_pm1(A.shape[0], 19)
+    u1, _, _ = krylov.restart_cycle(A, b, np.zeros_like(b), lambda v: twod.vcycle(H, K, v), 4)
+    S = tpc.Solver2D(delta, 2.0 ** -K, variant=variant, outer=tpc.TPC_OUTER_FGMRES,
+                     inner_cycles=4, max_iters=1)
+    try:
+        xd = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+        rc, it, rel = S.solve(_dev(b), xd, tol=1e-14)
+        assert it == 1
+        assert np.linalg.norm(_host(xd) - u1) <= 1e-9 * np.linalg.norm(u1)
+    finally:
+        S.close()
+    cycles = {}
+    for outer in (tpc.TPC_OUTER_VCYCLE, tpc.TPC_OUTER_FGMRES):
+        S = tpc.Solver2D(delta, 2.0 ** -K, variant=variant, outer=outer, inner_cycles=6)
+        try:
+            xd = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+            rc, it, rel = S.solve(_dev(b), xd, tol=1e-10)
+            assert rc == tpc.TPC_OK and rel < 1e-10
+            assert np.linalg.norm(b - A @ _host(xd)) <= 1.01e-10 * np.linalg.norm(b)
+            cycles[outer] = S.last_cycles()
+        finally:
+            S.close()
+    assert cycles[tpc.TPC_OUTER_FGMRES] <= cycles[tpc.TPC_OUTER_VCYCLE]
+
+
+def test_fgmres_mixed_on_a_slowly_converging_horizon():
+    """r = 1 (delta = h): the stationary 2-D V-cycle iteration needs about a hundred V-cycles;
+    the mixed FGMRES solve reaches 1e-10 in far fewer, checked with the oracle's product."""
+    K, delta = 6, 2.0 ** -6
+    N = 1 << K
+    res = {}
+    for outer in (tpc.TPC_OUTER_VCYCLE, tpc.TPC_OUTER_FGMRES):
+        S = tpc.Solver2D(delta, 2.0 ** -K, variant=NONSYM, precision=tpc.TPC_MIXED, outer=outer,
+                         inner_cycles=8, max_iters=200)
+        try:
+            b = uniform_pm1(S.nn, 23)
+            xd = torch.zeros(S.nn, dtype=torch.float64, device="cuda")
+            rc, it, rel = S.solve(_dev(b), xd, tol=1e-10)
+            assert rc == tpc.TPC_OK and rel < 1e-10
+            x = _host(xd)
+            r = b - twod.matvec_large(NONSYM, N, 1, x)
+            assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(b)
+            res[outer] = S.last_cycles()
+        finally:
+            S.close()
+    assert 2 * res[tpc.TPC_OUTER_FGMRES] <= res[tpc.TPC_OUTER_VCYCLE], res
