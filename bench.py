@@ -584,7 +584,9 @@ def time_serving(tpc, torch, args):
     keys = one + two
     rng = np.random.default_rng(17)
     sizes = sorted(set(serve_size(k) for k in keys))
-    rhs = {n: torch.tensor(uniform_pm1(n, 900 + i)).pin_memory() for i, n in enumerate(sizes)}
+    # three seeded right-hand sides per size, one drawn per request
+    rhs = {n: [torch.tensor(uniform_pm1(n, 900 + 8 * i + j)).pin_memory() for j in range(3)]
+           for i, n in enumerate(sizes)}
     pool = {n: [] for n in rhs}
 
     def xbuf(n):
@@ -603,7 +605,8 @@ def time_serving(tpc, torch, args):
                        "1/2 each, size log-uniform): 1-D N=2^K, K in 9..21, constant kernel "
                        "(delta in {0.05,0.1,0.2}, SPD/nonsym) or fractional a in {0.1,0.25,0.4} "
                        "(SPD, geometric transfer, delta in {0.05,0.2}); 2-D K in 4..10, delta in "
-                       "{0.1,0.2}, SPD/nonsym, constant kernel; uniform[-1,1) right-hand sides; "
+                       "{0.1,0.2}, SPD/nonsym, constant kernel; uniform[-1,1) right-hand sides (one of "
+                       "three seeded ones per size, drawn per request); "
                        "mixed precision, tol 1e-10, host buffers (pinned); hierarchies resident "
                        f"(HBM budget 150 GB, 32 slots); {args.serve_seconds:g} s of arrivals per rate; "
                        f"at most {MAX_OUTSTANDING} requests outstanding (later arrivals rejected)",
@@ -616,7 +619,8 @@ def time_serving(tpc, torch, args):
             dim, v, d, K, kk, a, tr = key
             n = serve_size(key)
             x = xbuf(n)
-            owner[srv.submit(v, d, 2.0 ** -K, rhs[n], x, args.tol, kk, a, dim=dim, transfer=tr)] = (n, x, key)
+            owner[srv.submit(v, d, 2.0 ** -K, rhs[n][0], x, args.tol, kk, a, dim=dim,
+                             transfer=tr)] = (n, x, key)
         got = 0
         while got < len(keys):
             for r in srv.poll(256, wait_ms=20):
@@ -654,8 +658,8 @@ def time_serving(tpc, torch, args):
                 dim, v, d, K, kk, a, tr = key
                 n = serve_size(key)
                 x = xbuf(n)
-                owner[srv.submit(v, d, 2.0 ** -K, rhs[n], x, args.tol, kk, a, dim=dim,
-                                 transfer=tr)] = (n, x, key)
+                owner[srv.submit(v, d, 2.0 ** -K, rhs[n][int(rng.integers(3))], x, args.tol, kk,
+                                 a, dim=dim, transfer=tr)] = (n, x, key)
             while owner:
                 for r in srv.poll(256, wait_ms=20):
                     n, x, _ = owner.pop(r["ticket"])
