@@ -134,6 +134,9 @@ def parse():
                     help="profiling case: mixed-precision setup, then 3 FP32 finest-level products")
     ap.add_argument("--profile-solve", choices=["fp64", "mixed", "fgmres"], default=None,
                     help="profiling case: set up, then one solve, nothing timed")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="profiling case: the 512-instance stage-batched solve, one solve "
+                         "between cudaProfilerStart / Stop")
     ap.add_argument("--profile-twod", action="store_true",
                     help="profiling case: 2-D mixed set-up (n = 4095^2), then one solve")
     return ap.parse_args()
@@ -968,8 +971,38 @@ def run_profile_twod(args):
     print(json.dumps({"profile_twod": "n=4095^2", "rc": rc, "iters": it, "relres": rel}))
 
 
+def run_profile_batch(args):
+    """A fixed launch sequence for profilers: set up the constant-kernel batch of 512 uneven 1-D
+    instances stage-batched (tpc_batch_*), solve it twice, then once more between
+    cudaProfilerStart and cudaProfilerStop (capture with --profile-from-start off)."""
+    import torch
+
+    import paper_2202_11288_gb300 as tpc
+    specs = batch_workload(512)
+    solvers = [tpc.Solver(d, 2.0 ** -K, variant=v, kernel=kk, kernel_a=a, precision=tpc.TPC_MIXED,
+                          autotune=0) for K, d, v, kk, a in specs]
+    bs = [torch.tensor(uniform_pm1(S.n, 5000 + i), device="cuda") for i, S in enumerate(solvers)]
+    xs = [torch.zeros_like(b) for b in bs]
+    B = tpc.Batch([S.handle for S in solvers])
+    for _ in range(2):
+        rc, its, rels, sts = B.solve(bs, xs, tol=args.tol)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    rc, its, rels, sts = B.solve(bs, xs, tol=args.tol)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    B.close()
+    for S in solvers:
+        S.close()
+    print(json.dumps({"profile_batch": 512, "groups": len(set((K, v) for K, _, v, _, _ in specs)),
+                      "rc": rc, "max_iters": max(its), "max_relres": max(rels)}))
+
+
 def main():
     args = parse()
+    if args.profile_batch:
+        run_profile_batch(args)
+        return
     if args.profile_twod:
         run_profile_twod(args)
         return

@@ -404,15 +404,18 @@ template <int PRO, int EPI, int MB, bool NS>
 int three_pass_mb(tpc_batch* B, tpc_batch::Group& g, const DevLevel<float>& L,
                   const LevelArgs<float>* args, const int* live) {
   const int nt = fft_threads<float>();
+  // the limit of each kernel is raised once to the largest any level asks (never lowered: a
+  // graph captured for another group may launch the same kernel with more)
   const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  const int lim = 150 * 1024;
   auto kf = k_batch_fwd<float, PRO, MB>;
   auto km = L.logL == 12 ? k_batch_mid<float, NS, 12>
             : L.logL == 11 ? k_batch_mid<float, NS, 11>
             : L.logL == 10 ? k_batch_mid<float, NS, 10> : k_batch_mid<float, NS, 0>;
   auto ki = k_batch_inv<float, EPI, MB>;
-  TPCB_CUDA(B, cudaFuncSetAttribute(kf, A, (int)L.smem_strided));
-  TPCB_CUDA(B, cudaFuncSetAttribute(km, A, (int)L.smem_mid));
-  TPCB_CUDA(B, cudaFuncSetAttribute(ki, A, (int)L.smem_strided));
+  TPCB_CUDA(B, cudaFuncSetAttribute(kf, A, lim));
+  TPCB_CUDA(B, cudaFuncSetAttribute(km, A, lim));
+  TPCB_CUDA(B, cudaFuncSetAttribute(ki, A, lim));
   kf<<<dim3(L.fwd_blocks, g.ninst), nt, L.smem_strided, g.stream>>>(args, live);
   km<<<dim3(L.mid_blocks, g.ninst), nt, L.smem_mid, g.stream>>>(args, live);
   ki<<<dim3(L.fwd_blocks, g.ninst), nt, L.smem_strided, g.stream>>>(args, live);
