@@ -21,3 +21,27 @@ def test_uniform_range_and_determinism():
     assert a.min() >= -1.0 and a.max() < 1.0
     assert abs(a.mean()) < 0.01 and abs(a.var() - 1.0 / 3.0) < 0.01
     assert uniform_pm1(0, 1).size == 0
+
+
+def test_batched_and_served_workloads_follow_their_recipes():
+    """The batched mix and the served problems of the bench (no GPU): sizes 2^10..2^18 (batch)
+    and 2^10..2^22 (serving) unknowns, r = floor(delta 2^K) >= 1, the kernel and transfer rules."""
+    import bench
+    specs = bench.batch_mix_workload(512)
+    assert len(specs) == 512 and specs == bench.batch_mix_workload(512)   # seeded
+    n2 = 0
+    for dim, K, delta, v, kk, a in specs:
+        n = ((1 << (K + 1)) - 1) ** dim
+        assert 2 ** 9 < n < 2 ** 18 + 1 and 0.02 <= delta <= 0.25 and delta * (1 << K) >= 1.0
+        if dim == 2:
+            n2 += 1
+            assert kk == 0 and 4 <= K <= 8
+        elif kk:
+            assert v == 0 and 0.1 <= a <= 0.4 and 9 <= K <= 17
+    assert 0 < n2 < 512
+    one, two = bench.serve_keys()
+    for dim, v, d, K, kk, a, tr in one + two:
+        n = ((1 << (K + 1)) - 1) ** dim
+        assert 2 ** 9 < n < 2 ** 22 + 1 and d * (1 << K) >= 1.0
+        assert (kk == 1) == (tr == 1) and (kk == 0 or (v == 0 and a <= 0.4))
+    assert {k[0] for k in two} == {2} and {k[0] for k in one} == {1}
