@@ -567,6 +567,12 @@ def serve_keys():
     return one, two
 
 
+def serve_outer(key):
+    """Outer iteration of a served problem: FGMRES for the 2-D ones (their stationary iteration
+    is slow at small r), the stationary one of section 5 otherwise."""
+    return 1 if key[0] == 2 else 0
+
+
 # Requests a client keeps outstanding at most (their host buffers are pinned); arrivals beyond
 # it are turned away and counted as rejected.
 MAX_OUTSTANDING = 2048
@@ -608,7 +614,8 @@ def time_serving(tpc, torch, args):
                        "1/2 each, size log-uniform): 1-D N=2^K, K in 9..21, constant kernel "
                        "(delta in {0.05,0.1,0.2}, SPD/nonsym) or fractional a in {0.1,0.25,0.4} "
                        "(SPD, geometric transfer, delta in {0.05,0.2}); 2-D K in 4..10, delta in "
-                       "{0.1,0.2}, SPD/nonsym, constant kernel; uniform[-1,1) right-hand sides (one of "
+                       "{0.1,0.2}, SPD/nonsym, constant kernel, FGMRES outer iteration; uniform[-1,1) "
+                       "right-hand sides (one of "
                        "three seeded ones per size, drawn per request); "
                        "mixed precision, tol 1e-10, host buffers (pinned); hierarchies resident "
                        f"(HBM budget 150 GB, 32 slots); {args.serve_seconds:g} s of arrivals per rate; "
@@ -623,7 +630,7 @@ def time_serving(tpc, torch, args):
             n = serve_size(key)
             x = xbuf(n)
             owner[srv.submit(v, d, 2.0 ** -K, rhs[n][0], x, args.tol, kk, a, dim=dim,
-                             transfer=tr)] = (n, x, key)
+                             transfer=tr, outer=serve_outer(key))] = (n, x, key)
         got = 0
         while got < len(keys):
             for r in srv.poll(256, wait_ms=20):
@@ -662,7 +669,7 @@ def time_serving(tpc, torch, args):
                 n = serve_size(key)
                 x = xbuf(n)
                 owner[srv.submit(v, d, 2.0 ** -K, rhs[n][int(rng.integers(3))], x, args.tol, kk,
-                                 a, dim=dim, transfer=tr)] = (n, x, key)
+                                 a, dim=dim, transfer=tr, outer=serve_outer(key))] = (n, x, key)
             while owner:
                 for r in srv.poll(256, wait_ms=20):
                     n, x, _ = owner.pop(r["ticket"])

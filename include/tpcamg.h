@@ -423,7 +423,7 @@ void tpc2d_destroy(tpc2d_handle* H);
 /* ---- Request server: continuous batching of independent solves (not in the paper) ----
  * A worker thread admits submitted requests while a slot (max_inflight) and device memory
  * (hbm_budget_bytes) are free, keeps level hierarchies resident keyed by (dimension, variant,
- * kernel, transfer, delta, h, precision) and reuses an idle one when a key repeats (evicting idle
+ * kernel, transfer, outer iteration, delta, h, precision) and reuses an idle one when a key repeats (evicting idle
  * ones least recently used first), and runs every admitted solve on its own stream exactly as
  * tpc_solve (1-D) or tpc2d_solve (2-D) would (the result is bitwise that of solving it alone).
  * Requests that arrive while others are on the GPU start as soon as a slot and memory free up. */
@@ -448,9 +448,12 @@ typedef struct tpc_request {
                               0 or 1: the 1-D system                                         */
   int transfer;            /* TPC_REQUEST_TRANSFER_DEFAULT (0): the server's tpc_params.transfer;
                               TPC_REQUEST_TRANSFER_PAPER / _GEOMETRIC: that transfer         */
+  int outer;               /* TPC_REQUEST_OUTER_DEFAULT (0): the server's tpc_params.outer;
+                              TPC_REQUEST_OUTER_VCYCLE / _FGMRES: that outer iteration        */
 } tpc_request;
 enum { TPC_REQUEST_TRANSFER_DEFAULT = 0, TPC_REQUEST_TRANSFER_PAPER = 1,
        TPC_REQUEST_TRANSFER_GEOMETRIC = 2 };
+enum { TPC_REQUEST_OUTER_DEFAULT = 0, TPC_REQUEST_OUTER_VCYCLE = 1, TPC_REQUEST_OUTER_FGMRES = 2 };
 typedef struct tpc_server_result {
   long long ticket;        /* as returned by tpc_server_submit                               */
   int status;              /* TPC_OK, TPC_ENOTCONV or a negative error                       */

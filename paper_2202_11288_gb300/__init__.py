@@ -71,7 +71,7 @@ class TpcRequest(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("delta", ctypes.c_double), ("h", ctypes.c_double),
                 ("n", ctypes.c_longlong), ("b_host", ctypes.c_void_p), ("x_host", ctypes.c_void_p),
                 ("tol", ctypes.c_double), ("kernel", ctypes.c_int), ("kernel_a", ctypes.c_double),
-                ("dim", ctypes.c_int), ("transfer", ctypes.c_int)]
+                ("dim", ctypes.c_int), ("transfer", ctypes.c_int), ("outer", ctypes.c_int)]
 
 
 class TpcServerStats(ctypes.Structure):
@@ -652,15 +652,17 @@ class Server:
 
     def submit(self, variant: int, delta: float, h: float, b, x, tol: float = 1e-10,
                kernel: int = 0, kernel_a: float = 0.0, dim: int = 1,
-               transfer: int | None = None) -> int:
+               transfer: int | None = None, outer: int | None = None) -> int:
         """b, x: contiguous float64 host arrays (numpy, or pinned torch CPU tensors); dim 2 for
         the 2-D system ((2/h - 1)^2 unknowns); transfer: TPC_TRANSFER_PAPER or
-        TPC_TRANSFER_GEOMETRIC, None for the server's parameters' transfer."""
+        TPC_TRANSFER_GEOMETRIC, outer: TPC_OUTER_VCYCLE or TPC_OUTER_FGMRES, None for the
+        server's parameters' choice."""
         n = b.numel() if hasattr(b, "numel") else b.size
         bp = b.data_ptr() if hasattr(b, "data_ptr") else b.ctypes.data
         xp = x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
         rt = 0 if transfer is None else 1 + int(transfer)   # TPC_REQUEST_TRANSFER_*
-        r = TpcRequest(variant, delta, h, n, bp, xp, tol, kernel, kernel_a, dim, rt)
+        ro = 0 if outer is None else 1 + int(outer)         # TPC_REQUEST_OUTER_*
+        r = TpcRequest(variant, delta, h, n, bp, xp, tol, kernel, kernel_a, dim, rt, ro)
         t = ctypes.c_longlong(0)
         _check(lib().tpc_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)))
         self._keep[t.value] = (b, x)

@@ -3,7 +3,7 @@
 // A worker thread owns every handle. Requests (problem description + host buffers) are queued
 // by tpc_server_submit; the worker admits them while a slot (max_inflight) and device memory
 // (the HBM budget) are free, keeps level hierarchies resident keyed by the problem (dimension,
-// variant, kernel, transfer, horizon, mesh size, precision) and reuses an idle one when the key
+// variant, kernel, transfer, outer iteration, horizon, mesh size, precision) and reuses an idle one when the key
 // repeats (a request whose
 // key's hierarchies are all busy waits for one, unless the key may have another; later
 // requests of other keys go ahead), evicting idle hierarchies least-recently-used first when
@@ -41,7 +41,7 @@ struct Request {
 };
 
 struct Entry {
-  int dim = 1, variant = 0, precision = 0, kernel = 0, transfer = 0;
+  int dim = 1, variant = 0, precision = 0, kernel = 0, transfer = 0, outer = 0;
   double delta = 0.0, h = 0.0, kernel_a = 0.0;
   tpc_handle* H = nullptr;        // 1-D requests
   tpc2d_handle* H2 = nullptr;     // 2-D requests
@@ -93,10 +93,17 @@ int req_transfer(const tpc_server* S, const tpc_request& r) {
   return S->prm.transfer;
 }
 
+// The outer iteration a request asks for (the server's parameters' unless it names one).
+int req_outer(const tpc_server* S, const tpc_request& r) {
+  if (r.outer == TPC_REQUEST_OUTER_VCYCLE) return TPC_OUTER_VCYCLE;
+  if (r.outer == TPC_REQUEST_OUTER_FGMRES) return TPC_OUTER_FGMRES;
+  return S->prm.outer;
+}
+
 bool same_key(const tpc_server* S, const Entry& e, const tpc_request& r, int precision) {
   return e.dim == req_dim(r) && e.variant == r.variant && e.precision == precision &&
          e.delta == r.delta && e.h == r.h && e.kernel == r.kernel && e.kernel_a == r.kernel_a &&
-         e.transfer == req_transfer(S, r);
+         e.transfer == req_transfer(S, r) && e.outer == req_outer(S, r);
 }
 
 void destroy_entry(Entry* e) {
@@ -190,6 +197,7 @@ bool admit(tpc_server* S, Request& req) {
     p.kernel = req.r.kernel;
     p.kernel_a = req.r.kernel_a;
     p.transfer = req_transfer(S, req.r);
+    p.outer = req_outer(S, req.r);
     tpc_handle* H = nullptr;
     tpc2d_handle* H2 = nullptr;
     const int rc = req_dim(req.r) == 2 ? tpc2d_setup(&p, req.r.delta, req.r.h, nullptr, &H2)
@@ -207,6 +215,7 @@ bool admit(tpc_server* S, Request& req) {
     ent->kernel = req.r.kernel;
     ent->kernel_a = req.r.kernel_a;
     ent->transfer = p.transfer;
+    ent->outer = p.outer;
     ent->H = H;
     ent->H2 = H2;
     ent->bytes = entry_bytes(ent);
@@ -350,7 +359,8 @@ int tpc_server_create(const tpc_server_config* cfg, const tpc_params* p, tpc_ser
 int tpc_server_submit(tpc_server* S, const tpc_request* r, long long* ticket) {
   if (!S || !r || !r->b_host || !r->x_host || !(r->tol >= 0.0) || r->n <= 0 || r->dim < 0 ||
       r->dim > 2 || r->transfer < TPC_REQUEST_TRANSFER_DEFAULT ||
-      r->transfer > TPC_REQUEST_TRANSFER_GEOMETRIC) {
+      r->transfer > TPC_REQUEST_TRANSFER_GEOMETRIC || r->outer < TPC_REQUEST_OUTER_DEFAULT ||
+      r->outer > TPC_REQUEST_OUTER_FGMRES) {
     tpc::set_host_error("bad argument to tpc_server_submit");
     return TPC_EINVAL;
   }

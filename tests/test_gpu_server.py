@@ -79,18 +79,22 @@ def test_server_rejects_a_problem_larger_than_its_budget():
 
 
 def test_server_mix_of_2d_fractional_and_transfers_equals_alone():
-    """2-D requests, a fractional kernel under the geometric transfer and two requests that differ
-    only in their transfer: each result equals its lone solve bit for bit, and the occupancy
-    statistics are consistent."""
-    # (dim, variant, delta, K, kernel, a, transfer)
-    keys = [(2, tpc.TPC_SPD, 0.1, 6, 0, 0.0, tpc.TPC_TRANSFER_PAPER),
-            (2, tpc.TPC_NONSYM, 0.2, 5, 0, 0.0, tpc.TPC_TRANSFER_PAPER),
-            (1, tpc.TPC_SPD, 0.1, 11, 1, 0.3, tpc.TPC_TRANSFER_GEOMETRIC),
-            (1, tpc.TPC_SPD, 0.08, 10, 0, 0.0, tpc.TPC_TRANSFER_PAPER),
-            (1, tpc.TPC_SPD, 0.08, 10, 0, 0.0, tpc.TPC_TRANSFER_GEOMETRIC)]
+    """2-D requests, a fractional kernel under the geometric transfer, requests that differ only
+    in their transfer or their outer iteration: each result equals its lone solve bit for bit,
+    and the occupancy statistics are consistent."""
+    # (dim, variant, delta, K, kernel, a, transfer, outer); the last two keys repeat earlier ones
+    # but for the outer iteration, so hierarchies must not be shared across it
+    VC, FG = tpc.TPC_OUTER_VCYCLE, tpc.TPC_OUTER_FGMRES
+    keys = [(2, tpc.TPC_SPD, 0.1, 6, 0, 0.0, tpc.TPC_TRANSFER_PAPER, VC),
+            (2, tpc.TPC_NONSYM, 0.2, 5, 0, 0.0, tpc.TPC_TRANSFER_PAPER, VC),
+            (1, tpc.TPC_SPD, 0.1, 11, 1, 0.3, tpc.TPC_TRANSFER_GEOMETRIC, VC),
+            (1, tpc.TPC_SPD, 0.08, 10, 0, 0.0, tpc.TPC_TRANSFER_PAPER, VC),
+            (1, tpc.TPC_SPD, 0.08, 10, 0, 0.0, tpc.TPC_TRANSFER_GEOMETRIC, VC),
+            (2, tpc.TPC_NONSYM, 0.2, 5, 0, 0.0, tpc.TPC_TRANSFER_PAPER, FG),
+            (1, tpc.TPC_SPD, 0.08, 10, 0, 0.0, tpc.TPC_TRANSFER_PAPER, FG)]
     reqs = []
-    for i in range(15):
-        dim, v, d, K, kk, a, tr = keys[i % len(keys)]
+    for i in range(21):
+        dim, v, d, K, kk, a, tr, oi = keys[i % len(keys)]
         n1 = (1 << (K + 1)) - 1
         n = n1 * n1 if dim == 2 else n1
         b = torch.tensor(uniform_pm1(n, 900 + i)).pin_memory()
@@ -99,8 +103,9 @@ def test_server_mix_of_2d_fractional_and_transfers_equals_alone():
     srv = tpc.Server(max_inflight=6, precision=tpc.TPC_MIXED)
     try:
         srv.stats(reset=True)
-        tickets = {srv.submit(v, d, 2.0 ** -K, b, x, 1e-10, kk, a, dim=dim, transfer=tr): i
-                   for i, ((dim, v, d, K, kk, a, tr), b, x) in enumerate(reqs)}
+        tickets = {srv.submit(v, d, 2.0 ** -K, b, x, 1e-10, kk, a, dim=dim, transfer=tr,
+                              outer=oi): i
+                   for i, ((dim, v, d, K, kk, a, tr, oi), b, x) in enumerate(reqs)}
         res = _wait_all(srv, len(reqs))
         assert len(res) == len(reqs)
         st = srv.stats()
@@ -111,15 +116,15 @@ def test_server_mix_of_2d_fractional_and_transfers_equals_alone():
     assert st["inflight_s"] >= st["busy_s"] and 1 <= st["max_inflight_seen"] <= 6
     for r in res:
         i = tickets[r["ticket"]]
-        (dim, v, d, K, kk, a, tr), b, x = reqs[i]
+        (dim, v, d, K, kk, a, tr, oi), b, x = reqs[i]
         assert r["status"] == tpc.TPC_OK and r["relres"] < 1e-10, (i, r)
         bd = b.cuda()
         xd = torch.zeros_like(bd)
         if dim == 2:
-            S = tpc.Solver2D(d, 2.0 ** -K, variant=v, precision=tpc.TPC_MIXED)
+            S = tpc.Solver2D(d, 2.0 ** -K, variant=v, precision=tpc.TPC_MIXED, outer=oi)
         else:
             S = tpc.Solver(d, 2.0 ** -K, variant=v, kernel=kk, kernel_a=a, transfer=tr,
-                           precision=tpc.TPC_MIXED)
+                           precision=tpc.TPC_MIXED, outer=oi)
         try:
             rc, it, rel = S.solve(bd, xd, tol=1e-10)
         finally:
